@@ -1,0 +1,21 @@
+"""FP64 CPU oracle for the KBMOD shift-and-stack search with the in-line sigma-G clip.
+
+TEST INFRASTRUCTURE ONLY: tests/, ``__graft_entry__.smoke()`` and bench.py's CPU-baseline leg are
+the only callers.  The product path (``paper_2109_03296_b300``) never imports this package, and
+this package never imports the product path.  See ``kb_oracle.c`` for the definitions and the
+readings of points the paper leaves open.
+
+Pinning status of each function (what ties it to the paper and to mathematics other than itself;
+the pins live in tests/test_oracle_pins.py):
+  sigma_g_coeff     closed form 1/(2 sqrt2 erfinv(1/2)) via scipy, and 0.7413 printed in Section 3.1
+  percentile        numpy.percentile(method="linear") on random samples
+  sigma_g_clip      hand-worked examples, constant lightcurve keeps all, +20 sigma spikes rejected
+  track_offsets     numpy float32 arithmetic on random and half-integer cases
+  psi_phi           constant variance gives phi = sum P^2/var; delta image gives psi = P/var
+  search            closed form L = SNR sqrt(T), alpha = F for a noiseless mover; an independent
+                    numpy shift-and-stack with numpy.nanpercentile on tiny stacks; invariances
+  stamps            mean stamp of a noiseless mover is F P; numpy.median/mean on tiny stacks
+  traj_eval_subpixel  L/alpha equal the integer search at integer positions; central finite
+                    differences of L for the gradient
+"""
+from .oracle import *  # noqa: F401,F403

@@ -1,0 +1,548 @@
+"""Pins of the FP64 oracle to things other than itself: the paper's printed numbers, closed forms,
+library routines it does not use (scipy.special.erfinv, numpy percentiles/median), invariances,
+and an independent numpy shift-and-stack brute force on tiny stacks."""
+import json
+import math
+import os
+import warnings
+
+import numpy as np
+import pytest
+import scipy.special
+
+import oracle
+from synth import gaussian_psf, velocity_grid
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def paper():
+    with open(os.path.join(GOLDEN, "paper_constants.json")) as f:
+        return json.load(f)
+
+
+# ------------------------------------------------------------------------------------------------
+# sigma_G (Section 3.1, Eqs. 1-5)
+# ------------------------------------------------------------------------------------------------
+
+def test_sigma_g_coeff_matches_paper_and_closed_form():
+    c = oracle.sigma_g_coeff(0.25, 0.75)
+    printed = paper()["sigma_g_coeff_25_75"]["value"]
+    assert abs(c - printed) < 5e-5                       # 0.7413 as printed in Section 3.1
+    closed = 1.0 / (2.0 * math.sqrt(2.0) * scipy.special.erfinv(0.5))
+    assert abs(c - closed) < 1e-13
+    for lo, hi in [(0.1, 0.9), (0.16, 0.84), (0.3, 0.6), (0.05, 0.75)]:
+        ref = 1.0 / (math.sqrt(2.0) * (scipy.special.erfinv(2 * hi - 1) -
+                                       scipy.special.erfinv(2 * lo - 1)))
+        assert abs(oracle.sigma_g_coeff(lo, hi) - ref) < 1e-12 * abs(ref)
+
+
+def test_erfinv_against_scipy():
+    for y in np.linspace(-0.999, 0.999, 101):
+        assert abs(oracle.erfinv(y) - scipy.special.erfinv(y)) < 1e-12 * max(1.0, abs(y))
+
+
+def test_sigma_g_estimates_gaussian_width():
+    # Section 3.1: sigma_G estimates the standard deviation of the underlying Gaussian.
+    rng = np.random.default_rng(11)
+    x = rng.normal(3.0, 2.5, 400001)
+    keep, med, sg = oracle.sigma_g_clip(x)
+    assert abs(sg - 2.5) < 0.02
+    assert abs(med - 3.0) < 0.02
+    # +-2 sigma_G keeps ~95.45% of a Gaussian
+    assert abs(keep.mean() - 0.9545) < 0.003
+
+
+def test_percentile_matches_numpy_linear():
+    rng = np.random.default_rng(5)
+    for n in list(range(1, 41)) + [100, 128]:
+        x = rng.normal(size=n) * rng.uniform(0.1, 10)
+        for q in (0.0, 0.1, 0.25, 0.5, 0.75, 0.9, 1.0, 0.37):
+            ref = np.percentile(x, 100 * q, method="linear")
+            assert abs(oracle.percentile(x, q) - ref) <= 1e-12 * max(1.0, np.abs(x).max())
+
+
+def test_sigma_g_clip_hand_worked_example():
+    # values 1,2,3,4,100: h(q) = 4 q -> x25 = 2, median 3, x75 = 4; sigma_G = 2C;
+    # bounds 3 -+ 4C = [0.0348, 5.9652]: 100 is rejected, the rest kept.
+    keep, med, sg = oracle.sigma_g_clip([1.0, 2.0, 3.0, 4.0, 100.0])
+    C = 1.0 / (2.0 * math.sqrt(2.0) * scipy.special.erfinv(0.5))
+    assert med == 3.0
+    assert abs(sg - 2.0 * C) < 1e-14
+    assert keep.tolist() == [True, True, True, True, False]
+    # order does not matter
+    keep, _, _ = oracle.sigma_g_clip([100.0, 3.0, 1.0, 4.0, 2.0])
+    assert keep.tolist() == [False, True, True, True, True]
+
+
+def test_sigma_g_clip_constant_and_inclusive_bound():
+    # a constant lightcurve has sigma_G = 0 and keeps every epoch (the bound is inclusive)
+    keep, med, sg = oracle.sigma_g_clip([4.25] * 9)
+    assert sg == 0.0 and keep.all()
+    # five equal values and one other: x25 = x75 = median = 5, sigma_G = 0 -> only the 5s kept
+    keep, med, sg = oracle.sigma_g_clip([5.0, 5.0, 6.0, 5.0, 5.0, 5.0])
+    assert sg == 0.0 and med == 5.0
+    assert keep.tolist() == [True, True, False, True, True, True]
+
+
+def test_sigma_g_clip_rejects_spikes():
+    rng = np.random.default_rng(3)
+    x = rng.normal(0, 1, 200)
+    spikes = np.full(20, 20.0)
+    keep, med, sg = oracle.sigma_g_clip(np.concatenate([x, spikes]))
+    assert not keep[200:].any()
+    assert keep[:200].mean() > 0.9
+
+
+# ------------------------------------------------------------------------------------------------
+# Track rounding (R1): three IEEE single operations, round half up
+# ------------------------------------------------------------------------------------------------
+
+def np_offsets(times, v):
+    dt = (np.asarray(times, np.float64) - times[0]).astype(np.float32)
+    return np.floor(np.float32(v) * dt + np.float32(0.5)).astype(np.int64)
+
+
+def test_track_offsets_match_float32_arithmetic():
+    rng = np.random.default_rng(7)
+    times = np.sort(rng.uniform(0, 4, 30))
+    vx = rng.uniform(-600, 600, 200).astype(np.float32)
+    vy = rng.uniform(-600, 600, 200).astype(np.float32)
+    ox, oy = oracle.track_offsets(times, vx, vy)
+    for j in range(200):
+        assert (ox[j] == np_offsets(times, vx[j])).all()
+        assert (oy[j] == np_offsets(times, vy[j])).all()
+
+
+def test_track_offsets_half_up():
+    times = np.array([0.0, 1.0, 2.0])
+    ox, oy = oracle.track_offsets(times, np.array([2.5, -2.5], np.float32),
+                                  np.array([0.25, -0.75], np.float32))
+    assert ox.tolist() == [[0, 3, 5], [0, -2, -5]]
+    assert oy.tolist() == [[0, 0, 1], [0, -1, -1]]
+
+
+# ------------------------------------------------------------------------------------------------
+# psi / phi (Section 3; R0)
+# ------------------------------------------------------------------------------------------------
+
+def test_phi_constant_variance_closed_form():
+    rng = np.random.default_rng(1)
+    T, H, W, k = 2, 20, 23, 7
+    psf = rng.uniform(0.0, 1.0, (T, k, k)).astype(np.float32)   # asymmetric on purpose
+    v = np.float32(1.7)
+    img = rng.normal(size=(T, H, W)).astype(np.float32)
+    var = np.full((T, H, W), v, np.float32)
+    psi, phi = oracle.psi_phi(img, var, None, psf)
+    r = k // 2
+    for t in range(T):
+        ref = (psf[t].astype(np.float64) ** 2).sum() / float(v)
+        inner = phi[t, r:H - r, r:W - r]
+        assert np.allclose(inner, ref, rtol=1e-12, atol=0)
+        # corner pixel (0, 0): only taps with u >= 0 fall inside
+        corner = (psf[t, r:, r:].astype(np.float64) ** 2).sum() / float(v)
+        assert abs(phi[t, 0, 0] - corner) < 1e-12 * corner
+
+
+def test_psi_delta_image_is_correlation():
+    rng = np.random.default_rng(2)
+    T, H, W, k = 1, 17, 19, 5
+    psf = rng.uniform(0.0, 1.0, (T, k, k)).astype(np.float32)   # asymmetric
+    img = np.zeros((T, H, W), np.float32)
+    A, v = 3.0, 0.5
+    yd, xd = 8, 9
+    img[0, yd, xd] = A
+    var = np.full((T, H, W), v, np.float32)
+    psi, _ = oracle.psi_phi(img, var, None, psf)
+    r = k // 2
+    ref = np.zeros((H, W))
+    for y in range(H):
+        for x in range(W):
+            uy, ux = yd - y, xd - x
+            if abs(uy) <= r and abs(ux) <= r:
+                ref[y, x] = A / v * float(psf[0, uy + r, ux + r])
+    assert np.allclose(psi[0], ref, rtol=1e-12, atol=1e-15)
+
+
+def test_psi_phi_masking():
+    rng = np.random.default_rng(4)
+    T, H, W, k = 1, 15, 15, 5
+    psf = rng.uniform(0.1, 1.0, (T, k, k)).astype(np.float32)
+    img = rng.normal(size=(T, H, W)).astype(np.float32)
+    var = np.full((T, H, W), 2.0, np.float32)
+    mask = np.zeros((T, H, W), np.uint8)
+    mask[0, 7, 7] = 1
+    var[0, 3, 3] = np.inf            # non-finite variance is masked
+    var[0, 10, 4] = -1.0             # non-positive variance is masked
+    img[0, 11, 11] = np.nan          # non-finite image is masked
+    psi, phi = oracle.psi_phi(img, var, mask, psf)
+    for (y, x) in [(7, 7), (3, 3), (10, 4), (11, 11)]:
+        assert psi[0, y, x] == 0.0 and phi[0, y, x] == 0.0
+    # neighbour (7, 8) of the masked (7, 7): phi lacks exactly the tap u = (0, -1)
+    r = k // 2
+    full = (psf[0].astype(np.float64) ** 2).sum() / 2.0
+    expect = full - float(psf[0, r + 0, r - 1]) ** 2 / 2.0
+    assert abs(phi[0, 7, 8] - expect) < 1e-12
+
+
+def test_psi_phi_at_matches_full():
+    rng = np.random.default_rng(6)
+    T, H, W, k = 3, 31, 29, 7
+    psf = rng.uniform(0.0, 1.0, (T, k, k)).astype(np.float32)
+    img = rng.normal(size=(T, H, W)).astype(np.float32)
+    var = rng.uniform(0.5, 2, (T, H, W)).astype(np.float32)
+    mask = (rng.random((T, H, W)) < 0.05).astype(np.uint8)
+    psi, phi = oracle.psi_phi(img, var, mask, psf)
+    tyx = np.stack([rng.integers(0, T, 50), rng.integers(0, H, 50), rng.integers(0, W, 50)], 1)
+    ps, ph = oracle.psi_phi_at(img, var, mask, psf, tyx)
+    assert np.array_equal(ps, psi[tyx[:, 0], tyx[:, 1], tyx[:, 2]])
+    assert np.array_equal(ph, phi[tyx[:, 0], tyx[:, 1], tyx[:, 2]])
+
+
+# ------------------------------------------------------------------------------------------------
+# Search closed form: one noiseless mover, L = SNR sqrt(T), alpha = F  (Section 3: nu = Psi/sqrt Phi)
+# ------------------------------------------------------------------------------------------------
+
+def _noiseless_mover(T=8, H=64, W=64, snr=5.0, v=1.7, sigma=1.2, k=7, seed=0):
+    rng = np.random.default_rng(seed)
+    v = float(np.float32(v))            # the variance plane is float32
+    times = np.sort(rng.uniform(0, 0.2, T))
+    times[0] = 0.0
+    vx, vy = velocity_grid(50.0, 120.0, 6, -0.3, 0.3, 5)
+    j = 17
+    psf = np.stack([gaussian_psf(sigma, k)] * T).astype(np.float32)
+    sum_p2 = (psf[0].astype(np.float64) ** 2).sum()
+    F = snr * math.sqrt(v) / math.sqrt(sum_p2)
+    img = np.zeros((T, H, W), np.float32)
+    x0, y0 = 20, 25
+    ox, oy = np_offsets(times, vx[j]), np_offsets(times, vy[j])
+    r = k // 2
+    for t in range(T):
+        x, y = x0 + ox[t], y0 + oy[t]
+        assert r <= x < W - r and r <= y < H - r
+        img[t, y - r:y + r + 1, x - r:x + r + 1] += (F * psf[t]).astype(np.float32)
+    var = np.full((T, H, W), v, np.float32)
+    return dict(img=img, var=var, psf=psf, times=times, vx=vx, vy=vy, j=j, x0=x0, y0=y0, F=F,
+                T=T, snr=snr)
+
+
+def test_search_noiseless_mover_closed_form():
+    m = _noiseless_mover()
+    # The image holds F * P exactly only up to float32 rounding of the injected values; build the
+    # closed form from the stored image, which is F P rounded: the tolerance covers that rounding.
+    psi, phi = oracle.psi_phi(m["img"], m["var"], None, m["psf"])
+    res = oracle.search(psi, phi, m["times"], m["vx"], m["vy"],
+                        dict(k=1, lh_min=1.0, min_obs=1), window=(m["x0"], m["x0"] + 1,
+                                                                   m["y0"], m["y0"] + 1))
+    L = res["lh"][0, 0, 0]
+    a = res["flux"][0, 0, 0]
+    assert abs(L - m["snr"] * math.sqrt(m["T"])) < 1e-6 * L
+    assert abs(a - m["F"]) < 1e-6 * m["F"]
+    assert res["nkept"][0, 0, 0] == m["T"] and res["nvalid"][0, 0, 0] == m["T"]
+    idx = res["idx"][0, 0, 0]
+    same_track = (np.array_equal(np_offsets(m["times"], m["vx"][idx]),
+                                 np_offsets(m["times"], m["vx"][m["j"]])) and
+                  np.array_equal(np_offsets(m["times"], m["vy"][idx]),
+                                 np_offsets(m["times"], m["vy"][m["j"]])))
+    assert idx == m["j"] or same_track
+
+
+def test_search_noiseless_mover_exact_psi_phi():
+    # With psi/phi written from the closed form directly (FP64), L and alpha match to 1e-9.
+    m = _noiseless_mover(T=12, snr=6.5)
+    T, H, W = m["img"].shape
+    sum_p2 = (m["psf"][0].astype(np.float64) ** 2).sum()
+    v = float(m["var"][0, 0, 0])
+    phi = np.full((T, H, W), sum_p2 / v)
+    psi = np.zeros((T, H, W))
+    ox, oy = np_offsets(m["times"], m["vx"][m["j"]]), np_offsets(m["times"], m["vy"][m["j"]])
+    for t in range(T):
+        psi[t, m["y0"] + oy[t], m["x0"] + ox[t]] = m["F"] * sum_p2 / v
+    res = oracle.search(psi, phi, m["times"], m["vx"], m["vy"], dict(k=2, lh_min=1.0, min_obs=1),
+                        window=(m["x0"], m["x0"] + 1, m["y0"], m["y0"] + 1))
+    assert abs(res["lh"][0, 0, 0] - m["snr"] * math.sqrt(T)) < 1e-9 * m["snr"] * math.sqrt(T)
+    assert abs(res["flux"][0, 0, 0] - m["F"]) < 1e-9 * m["F"]
+    assert res["mask"][0, 0, 0, 0] == (1 << T) - 1
+
+
+# ------------------------------------------------------------------------------------------------
+# Independent numpy shift-and-stack brute force (different formulation: whole shifted planes,
+# numpy.nanpercentile for the quantiles, numpy sort for the selection)
+# ------------------------------------------------------------------------------------------------
+
+def numpy_search(psi, phi, times, vx, vy, K, lh_min, min_obs, clip=True, n_sigma=2.0,
+                 clip_on=0, q=(25.0, 50.0, 75.0)):
+    T, H, W = psi.shape
+    C = 1.0 / (math.sqrt(2.0) * (scipy.special.erfinv(2 * q[2] / 100 - 1) -
+                                 scipy.special.erfinv(2 * q[0] / 100 - 1)))
+    cand = [[[] for _ in range(W)] for _ in range(H)]
+    for j in range(len(vx)):
+        ox, oy = np_offsets(times, vx[j]), np_offsets(times, vy[j])
+        P = np.full((T, H, W), np.nan)
+        F = np.full((T, H, W), np.nan)
+        for t in range(T):
+            ys = np.arange(H) + oy[t]
+            xs = np.arange(W) + ox[t]
+            yv = (ys >= 0) & (ys < H)
+            xv = (xs >= 0) & (xs < W)
+            P[t][np.ix_(yv, xv)] = psi[t][np.ix_(ys[yv], xs[xv])]
+            F[t][np.ix_(yv, xv)] = phi[t][np.ix_(ys[yv], xs[xv])]
+        valid = np.isfinite(P) & (np.nan_to_num(F) > 0)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            a = np.where(valid, P / F if clip_on == 0 else P / np.sqrt(F), np.nan)
+        nvalid = valid.sum(0)
+        if clip:
+            with warnings.catch_warnings():
+                warnings.simplefilter("ignore")
+                lo, mid, hi = np.nanpercentile(a, list(q), axis=0, method="linear")
+            sg = C * (hi - lo)
+            keep = valid & (a >= mid - n_sigma * sg) & (a <= mid + n_sigma * sg)
+        else:
+            keep = valid
+        sp = np.where(keep, P, 0.0).sum(0)
+        sf = np.where(keep, F, 0.0).sum(0)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            L = sp / np.sqrt(sf)
+        ok = (nvalid >= min_obs) & (keep.sum(0) > 0) & (sf > 0) & (L >= lh_min)
+        for y, x in zip(*np.nonzero(ok)):
+            bits = np.zeros((T + 31) // 32, np.uint64)
+            for t in np.nonzero(keep[:, y, x])[0]:
+                bits[t // 32] |= np.uint64(1) << np.uint64(t % 32)
+            cand[y][x].append((-L[y, x], j, sp[y, x] / sf[y, x], nvalid[y, x],
+                               keep[:, y, x].sum(), bits))
+    out_idx = np.full((H, W, K), -1)
+    out_lh = np.full((H, W, K), -np.inf)
+    out_flux = np.zeros((H, W, K))
+    out_nv = np.zeros((H, W, K), int)
+    out_nk = np.zeros((H, W, K), int)
+    out_mask = np.zeros((H, W, K, (T + 31) // 32), np.uint64)
+    for y in range(H):
+        for x in range(W):
+            for s, c in enumerate(sorted(cand[y][x], key=lambda e: (e[0], e[1]))[:K]):
+                out_lh[y, x, s], out_idx[y, x, s], out_flux[y, x, s] = -c[0], c[1], c[2]
+                out_nv[y, x, s], out_nk[y, x, s], out_mask[y, x, s] = c[3], c[4], c[5]
+    return dict(lh=out_lh, idx=out_idx, flux=out_flux, nvalid=out_nv, nkept=out_nk,
+                mask=out_mask)
+
+
+def _tiny_case(seed, T=6, H=12, W=14, n_traj=40, mask_frac=0.08):
+    rng = np.random.default_rng(seed)
+    times = np.sort(rng.uniform(0, 1.0, T))
+    times[0] = 0.0
+    phi = rng.uniform(0.2, 1.5, (T, H, W))
+    psi = rng.normal(size=(T, H, W)) * np.sqrt(phi)
+    psi += 3.0 * phi * (rng.random((T, H, W)) < 0.15)          # bright spots
+    psi[:, 5, 6] += 8.0 * phi[:, 5, 6]                          # a static source
+    m = rng.random((T, H, W)) < mask_frac
+    psi[m] = 0.0
+    phi[m] = 0.0
+    vx = rng.uniform(-6, 6, n_traj).astype(np.float32)
+    vy = rng.uniform(-6, 6, n_traj).astype(np.float32)
+    vx[5], vy[5] = vx[3], vy[3]                                 # duplicate track -> index tie
+    vx[9], vy[9] = np.nextafter(vx[8], np.float32(10)), vy[8]   # near-duplicate
+    psi = psi.astype(np.float32).astype(np.float64)
+    phi = phi.astype(np.float32).astype(np.float64)
+    return psi, phi, times, vx, vy
+
+
+@pytest.mark.parametrize("seed,clip,clip_on,K", [(0, True, 0, 3), (1, True, 1, 2),
+                                                 (2, False, 0, 4), (3, True, 0, 1)])
+def test_search_matches_numpy_brute_force(seed, clip, clip_on, K):
+    psi, phi, times, vx, vy = _tiny_case(seed)
+    lh_min, min_obs = 0.5, 3
+    ref = numpy_search(psi, phi, times, vx, vy, K, lh_min, min_obs, clip=clip, clip_on=clip_on)
+    got = oracle.search(psi, phi, times, vx, vy, dict(k=K, lh_min=lh_min, min_obs=min_obs,
+                                                      clip=int(clip), clip_on=clip_on))
+    assert np.array_equal(got["idx"], ref["idx"])
+    filled = ref["idx"] >= 0
+    assert filled.sum() > 50
+    assert np.allclose(got["lh"][filled], ref["lh"][filled], rtol=1e-12, atol=0)
+    assert np.allclose(got["flux"][filled], ref["flux"][filled], rtol=1e-10, atol=1e-12)
+    assert np.array_equal(got["nvalid"], ref["nvalid"])
+    assert np.array_equal(got["nkept"], ref["nkept"])
+    assert np.array_equal(got["mask"].astype(np.uint64), ref["mask"])
+
+
+def test_search_duplicate_track_tie_break():
+    psi, phi, times, vx, vy = _tiny_case(0)
+    got = oracle.search(psi, phi, times, vx, vy, dict(k=40, lh_min=-1e9, min_obs=1))
+    # trajectories 3 and 5 have identical tracks: wherever both appear, 3 ranks first and every
+    # entry between them ties on L' with ascending indices (other tracks can reach the same
+    # valid pixels when they leave the image)
+    seen = 0
+    for y in range(psi.shape[1]):
+        for x in range(psi.shape[2]):
+            row = got["idx"][y, x].tolist()
+            if 3 in row and 5 in row:
+                i3, i5 = row.index(3), row.index(5)
+                assert i5 > i3
+                assert (got["lh"][y, x, i3:i5 + 1] == got["lh"][y, x, i3]).all()
+                assert row[i3:i5 + 1] == sorted(row[i3:i5 + 1])
+                seen += 1
+    assert seen > 20
+
+
+def test_search_invariances():
+    psi, phi, times, vx, vy = _tiny_case(4)
+    p = dict(k=3, lh_min=0.5, min_obs=3)
+    base = oracle.search(psi, phi, times, vx, vy, p)
+    # (1) scaling psi and phi by c > 0 keeps the flux lightcurve, so masks and order are kept;
+    #     L' scales by sqrt(c), alpha is unchanged (Section 3: nu = Psi / sqrt(Phi)).
+    c = 4.0
+    p2 = dict(p, lh_min=0.5 * 2.0)
+    sc = oracle.search(psi * c, phi * c, times, vx, vy, p2)
+    assert np.array_equal(sc["idx"], base["idx"])
+    f = base["idx"] >= 0
+    assert np.allclose(sc["lh"][f], 2.0 * base["lh"][f], rtol=1e-12)
+    assert np.allclose(sc["flux"][f], base["flux"][f], rtol=1e-12)
+    assert np.array_equal(sc["mask"], base["mask"])
+    # (2) a common shift of all epoch times changes nothing (tracks use t - t_0)
+    sh = oracle.search(psi, phi, times + 0.0, vx, vy, p)
+    assert np.array_equal(sh["idx"], base["idx"])
+    # (3) translating the content of every plane by (+2, +1) translates the results
+    T, H, W = psi.shape
+    psi2 = np.zeros_like(psi)
+    phi2 = np.zeros_like(phi)
+    psi2[:, 1:, 2:] = psi[:, :-1, :-2]
+    phi2[:, 1:, 2:] = phi[:, :-1, :-2]
+    big = dict(p, lh_min=-1e9)
+    r1 = oracle.search(psi, phi, times, vx, vy, big, window=(3, 6, 3, 6))
+    r2 = oracle.search(psi2, phi2, times, vx, vy, big, window=(5, 8, 4, 7))
+    # only trajectories that stay clear of the borders are comparable: check the best one
+    # whose track stays inside both frames at every epoch
+    ox, oy = oracle.track_offsets(times, vx, vy)
+    inside = [j for j in range(len(vx)) if
+              (3 + ox[j].min() >= 0 and 5 + ox[j].max() < W - 2 and 3 + oy[j].min() >= 0 and
+               5 + oy[j].max() < H - 1)]
+    assert inside
+    for j in inside[:5]:
+        a = oracle.eval_one(psi, phi, times, 4, 4, vx[j], vy[j], p)
+        b = oracle.eval_one(psi2, phi2, times, 6, 5, vx[j], vy[j], p)
+        assert a["nvalid"] == b["nvalid"] and a["nkept"] == b["nkept"]
+        if a["ok"]:
+            assert abs(a["lh"] - b["lh"]) < 1e-12 * max(1, abs(a["lh"]))
+
+
+def test_min_obs_and_off_image():
+    psi, phi, times, vx, vy = _tiny_case(5, mask_frac=0.0)
+    T = psi.shape[0]
+    # min_obs above T: nothing can be selected
+    r = oracle.search(psi, phi, times, vx, vy, dict(k=2, lh_min=-1e9, min_obs=T + 1))
+    assert (r["idx"] < 0).all()
+    # a trajectory that leaves the image has fewer valid epochs than T
+    e = oracle.eval_one(psi, phi, times, 0, 0, -50.0, -50.0, dict(min_obs=1))
+    assert e["nvalid"] == 1
+
+
+# ------------------------------------------------------------------------------------------------
+# Stamps (Section 3.3)
+# ------------------------------------------------------------------------------------------------
+
+def test_stamps_noiseless_mover_is_flux_times_psf():
+    m = _noiseless_mover()
+    j = m["j"]
+    mean, med = oracle.stamps(m["img"], m["var"], None, m["times"], [m["x0"]], [m["y0"]],
+                              [m["vx"][j]], [m["vy"][j]], radius=10)
+    k = m["psf"].shape[-1]
+    r = k // 2
+    ref = np.zeros((21, 21))
+    ref[10 - r:10 + r + 1, 10 - r:10 + r + 1] = (m["F"] * m["psf"][0]).astype(np.float32)
+    assert np.allclose(mean[0], ref, rtol=1e-6, atol=1e-7)
+    assert np.allclose(med[0], ref, rtol=1e-6, atol=1e-7)
+
+
+def test_stamps_against_numpy_gather():
+    rng = np.random.default_rng(9)
+    T, H, W = 7, 30, 33
+    img = rng.normal(size=(T, H, W)).astype(np.float32)
+    var = np.ones((T, H, W), np.float32)
+    mask = (rng.random((T, H, W)) < 0.1).astype(np.uint8)
+    times = np.sort(rng.uniform(0, 0.5, T))
+    x0 = rng.integers(0, W, 6)
+    y0 = rng.integers(0, H, 6)
+    vx = rng.uniform(-20, 20, 6).astype(np.float32)
+    vy = rng.uniform(-20, 20, 6).astype(np.float32)
+    keep = rng.integers(0, 2 ** T, 6).astype(np.uint32).reshape(6, 1)
+    for km in (None, keep):
+        R = 3
+        mean, med = oracle.stamps(img, var, mask, times, x0, y0, vx, vy, radius=R, keep_mask=km)
+        for c in range(6):
+            ox, oy = np_offsets(times, vx[c]), np_offsets(times, vy[c])
+            for sy in range(-R, R + 1):
+                for sx in range(-R, R + 1):
+                    vals = []
+                    for t in range(T):
+                        if km is not None and not (int(km[c, 0]) >> t) & 1:
+                            continue
+                        x, y = x0[c] + ox[t] + sx, y0[c] + oy[t] + sy
+                        if 0 <= x < W and 0 <= y < H and not mask[t, y, x]:
+                            vals.append(float(img[t, y, x]))
+                    got_mean, got_med = mean[c, sy + R, sx + R], med[c, sy + R, sx + R]
+                    if not vals:
+                        assert np.isnan(got_mean) and np.isnan(got_med)
+                    else:
+                        assert abs(got_mean - np.mean(vals)) < 1e-12
+                        assert got_med == np.median(vals)
+
+
+# ------------------------------------------------------------------------------------------------
+# Sub-pixel trajectory likelihood and gradient (refinement off the grid)
+# ------------------------------------------------------------------------------------------------
+
+def test_subpixel_eval_equals_integer_eval_on_integer_tracks():
+    rng = np.random.default_rng(12)
+    T, H, W = 6, 40, 40
+    times = np.arange(T) * 0.25
+    phi = rng.uniform(0.2, 1.0, (T, H, W))
+    psi = rng.normal(size=(T, H, W)) * np.sqrt(phi)
+    vx, vy = np.float32(8.0), np.float32(-4.0)        # integer positions at every epoch
+    keep = np.array([(1 << T) - 1], np.uint32)
+    L, a, g = oracle.traj_eval_subpixel(psi, phi, times, keep, 10.0, 20.0, vx, vy)
+    e = oracle.eval_one(psi, phi, times, 10, 20, vx, vy, dict(clip=0, min_obs=0))
+    assert abs(L - e["lh"]) < 1e-12 * abs(e["lh"])
+    assert abs(a - e["flux"]) < 1e-12 * abs(e["flux"])
+
+
+def test_subpixel_gradient_against_finite_differences():
+    rng = np.random.default_rng(13)
+    T, H, W = 8, 48, 48
+    times = np.sort(rng.uniform(0, 0.2, T))
+    times[0] = 0.0
+    phi = rng.uniform(0.2, 1.0, (T, H, W))
+    psi = rng.normal(size=(T, H, W)) * np.sqrt(phi) + 2.0 * phi
+    keep = np.array([0b10111011], np.uint32)
+    checked = 0
+    for trial in range(40):
+        x0, y0 = rng.uniform(10, 30, 2)
+        vx, vy = rng.uniform(-40, 40, 2)
+        h = 1e-3
+        dts = times - times[0]
+        # skip points within 2h of a cell edge at any epoch (piecewise-bilinear kinks)
+        xs = x0 + vx * dts
+        ys = y0 + vy * dts
+        edge = min(np.abs(xs - np.round(xs)).min(), np.abs(ys - np.round(ys)).min())
+        if edge < 4 * h * (1 + dts.max()):
+            continue
+        L, a, g = oracle.traj_eval_subpixel(psi, phi, times, keep, x0, y0, vx, vy)
+        p = np.array([x0, y0, vx, vy])
+        fd = np.zeros(4)
+        for i in range(4):
+            pp, pm = p.copy(), p.copy()
+            pp[i] += h
+            pm[i] -= h
+            Lp = oracle.traj_eval_subpixel(psi, phi, times, keep, *pp, grad=False)[0]
+            Lm = oracle.traj_eval_subpixel(psi, phi, times, keep, *pm, grad=False)[0]
+            fd[i] = (Lp - Lm) / (2 * h)
+        assert np.all(np.abs(g - fd) <= 1e-3 * np.maximum(np.abs(fd), 1e-2)), (g, fd)
+        checked += 1
+    assert checked >= 10
+
+
+def test_paper_grid_shape():
+    pc = paper()
+    vx, vy = velocity_grid(*pc["grid_speed_range_px_per_day"]["value"], pc["grid_speeds"]["value"],
+                           -pc["grid_angle_half_width_rad"]["value"],
+                           pc["grid_angle_half_width_rad"]["value"], pc["grid_angles"]["value"])
+    assert len(vx) == 131072
+    sp = np.hypot(vx.astype(np.float64), vy.astype(np.float64))
+    assert abs(sp.min() - 92.0) < 1e-3 and abs(sp.max() - 550.0) < 1e-3
