@@ -1,0 +1,233 @@
+/*
+ * kb.h -- C ABI of the B300 (sm_103a) KBMOD shift-and-stack library, libkb_b300.so.
+ *
+ * The method is the GPU search of Smotherman et al. 2021 ("Sifting Through the Static: Moving
+ * Object Detection in Difference Images", arXiv 2109.03296): PSF-matched likelihood images
+ * psi/phi are summed along every linear trajectory of a velocity grid from every start pixel
+ * (Section 3: Psi_coadd = sum psi_i, Phi_coadd = sum phi_i, nu = Psi/sqrt(Phi)); the sigma-G
+ * percentile clip of Section 3.1 (Eqs. 1-5) is applied to each trajectory's lightcurve inside
+ * the search (Section 3.2), the clipped likelihood sum LH' is thresholded, and the best K
+ * trajectories of every start pixel are kept on the device (Section 3.2).  Coadded mean and
+ * median postage stamps are cut along surviving trajectories (Section 3.3).
+ *
+ * Conventions for every entry point:
+ *  - Array arguments are DEVICE pointers owned by the caller unless the comment says HOST.
+ *    The library never allocates device memory in these calls; scratch space is the caller's
+ *    workspace, sized by the matching *_workspace_size query.
+ *  - Images are row-major float32 planes stacked epoch-major: element (t, y, x) of a [T][H][W]
+ *    array is at t*H*W + y*W + x; x is the column (fastest), y the row.
+ *  - Work is enqueued asynchronously on `stream` (a cudaStream_t passed as void*; NULL is the
+ *    legacy default stream).  A call returns once its kernels are enqueued.
+ *  - Every call returns a kb_status.  KB_OK (0) means enqueued; any other value means nothing
+ *    was enqueued (argument errors are found on the host before any launch) or, for
+ *    KB_ERR_CUDA, that a CUDA runtime call failed.  kb_last_error() describes the last failure
+ *    of the calling thread.
+ *  - Integer-pixel trajectory positions are x_t = x0 + round(vx * dt_t), y_t = y0 + round(vy * dt_t)
+ *    with dt_t = (float)(t_t - t_0) (difference in float64, then rounded to float32), the
+ *    product taken as one IEEE float32 multiply and round() = floor(d + 0.5f) (round half up).
+ */
+#ifndef KB_B300_H
+#define KB_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define KB_API __attribute__((visibility("default")))
+#else
+#define KB_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define KB_OK 0
+#define KB_ERR_INVALID_ARG 1   /* a null pointer, a bad size or a bad parameter value */
+#define KB_ERR_UNSUPPORTED 2   /* a valid request beyond this build's limits (e.g. T > KB_MAX_T) */
+#define KB_ERR_CUDA 3          /* a CUDA runtime call failed; kb_last_error() names it */
+#define KB_ERR_WORKSPACE 4     /* the workspace is null, misaligned or smaller than required */
+#define KB_ERR_TIMEOUT 5       /* a bounded device-side wait gave up (reported by kb_check) */
+
+#define KB_MAX_T 128           /* epochs per stack */
+#define KB_MAX_K 32            /* results kept per start pixel */
+#define KB_WORKSPACE_ALIGN 256 /* required alignment of a workspace pointer, in bytes */
+
+/* Parameters of the search (Sections 3.1-3.2). */
+typedef struct kb_search_params {
+  int32_t k_per_pixel; /* K: results kept per start pixel, 1..KB_MAX_K (the paper keeps 8) */
+  float lh_min;        /* keep a trajectory only if its clipped sum LH' >= lh_min (paper: 10) */
+  int32_t min_obs;     /* minimum number of valid epochs (paper: 15) */
+  int32_t clip;        /* 1 = apply the sigma-G clip, 0 = keep every valid epoch */
+  float q_lo;          /* lower quantile of sigma_G (paper: 0.25), 0 <= q_lo < q_hi <= 1 */
+  float q_mid;         /* centre quantile, the median (0.5) */
+  float q_hi;          /* upper quantile of sigma_G (paper: 0.75) */
+  float n_sigma;       /* keep points within median +- n_sigma * sigma_G (paper: 2) */
+  int32_t clip_on;     /* lightcurve that is clipped: 0 = flux psi_t/phi_t,
+                          1 = per-epoch likelihood psi_t/sqrt(phi_t) (Section 3.1, "likelihood
+                          and/or flux values") */
+  int32_t x_lo, x_hi;  /* start-pixel window [x_lo, x_hi) x [y_lo, y_hi); the whole image is */
+  int32_t y_lo, y_hi;  /* 0..W, 0..H */
+} kb_search_params;
+
+/* Library version (major*10000 + minor*100 + patch). */
+KB_API int kb_version(void);
+
+/* Message describing the calling thread's last failure ("" if none).  The pointer stays valid
+ * until the next failing call on the same thread. */
+KB_API const char* kb_last_error(void);
+
+/* Fills p with the paper's settings for the whole image: K = 8, LH' >= 10, min_obs = 15,
+ * sigma-G clip on the flux with quantiles 0.25/0.5/0.75 and n_sigma = 2 (Sections 3.1, 3.2,
+ * 4.3).  The window is set to [0, W) x [0, H). */
+KB_API void kb_search_params_default(kb_search_params* p, int H, int W);
+
+/*
+ * kb_make_psi_phi -- PSF-matched likelihood images (Section 3, first paragraph; the formula
+ * itself is KBMOD's: psi_t = (I_t / var_t) (x) PSF_t, phi_t = (1 / var_t) (x) PSF_t^2).
+ *
+ *   psi[t,y,x] = sum_{u,v in [-r,r]} w[t,y+v,x+u] * img[t,y+v,x+u] * psf[t,v+r,u+r]
+ *   phi[t,y,x] = sum_{u,v in [-r,r]} w[t,y+v,x+u] * psf[t,v+r,u+r]^2
+ *
+ * with r = k/2 and w = 1/var, where w = 0 outside the image and at masked pixels (mask != 0,
+ * var not finite or <= 0, img not finite); psi = phi = 0 is written at masked pixels
+ * (Section 3: masked pixels carry no data).  This is a correlation; for the symmetric PSFs of
+ * the paper it equals the convolution.  No renormalisation at the edges.
+ *
+ *   img, var  [T][H][W] float32 (device).       mask  [T][H][W] uint8 (device) or NULL.
+ *   psf       [T][k][k] float32 (device), k odd, 1 <= k <= 31.
+ *   psi, phi  [T][H][W] float32 (device) outputs; must not alias the inputs.
+ * Errors: KB_ERR_INVALID_ARG for null pointers, T/H/W < 1, even k or k > 31.
+ */
+KB_API int kb_make_psi_phi(const float* img, const float* var, const uint8_t* mask, const float* psf,
+                    int T, int H, int W, int k, float* psi, float* phi, void* stream);
+
+/*
+ * kb_search_workspace_size -- bytes of workspace kb_search needs for these sizes (the result
+ * depends on T, H, W, n_traj and the window of p).  Returns KB_ERR_INVALID_ARG / UNSUPPORTED
+ * for the same argument errors kb_search reports.
+ */
+KB_API int kb_search_workspace_size(int T, int H, int W, int n_traj, const kb_search_params* p,
+                             size_t* bytes);
+
+/*
+ * kb_search -- exhaustive integer-pixel shift-and-stack search with the in-line sigma-G clip,
+ * threshold and per-start-pixel top-K (Section 3 pointer arithmetic; Section 3.1 clip and
+ * recomputed sum LH'; Section 3.2 clip before the per-pixel selection).
+ *
+ * For every start pixel (x0, y0) of the window and every trajectory j (vx[j], vy[j]):
+ *   1. epoch t is valid iff (x_t, y_t) is inside the image and phi > 0 there (psi, phi finite);
+ *      a trajectory with fewer than min_obs valid epochs is discarded;
+ *   2. the lightcurve a_t (flux psi/phi, or psi/sqrt(phi) with clip_on = 1) of the valid
+ *      epochs gives the q_lo, q_mid, q_hi percentiles by linear interpolation between order
+ *      statistics (h = (n-1) q); sigma_G = C (x_hi - x_lo), C = 1/(sqrt2 (erfinv(2 q_hi - 1) -
+ *      erfinv(2 q_lo - 1))) (Eq. 3 solved for sigma_G; Eq. 4 as printed drops its sqrt2);
+ *      epoch t is kept iff x_mid - n_sigma sigma_G <= a_t <= x_mid + n_sigma sigma_G;
+ *   3. over the kept epochs LH' = sum psi / sqrt(sum phi) and the flux alpha = sum psi / sum phi;
+ *      discarded if no epoch is kept;
+ *   4. kept in the start pixel's list if LH' >= lh_min; each list holds the K best, ordered by
+ *      LH' descending and, for equal LH', by ascending trajectory index.
+ * The result equals evaluating every pair; pairs are skipped only when an upper bound on LH'
+ * proves they cannot enter the list.
+ *
+ *   psi, phi     [T][H][W] float32 (device).
+ *   times        [T] float64, HOST pointer, finite; read during the call only.
+ *   vx, vy       [n_traj] float32 (device), pixels per unit of `times`.
+ *   p            HOST pointer to the parameters.
+ *   out_*        (device) [npix][K] with npix = (x_hi - x_lo) * (y_hi - y_lo), start pixels in
+ *                row-major order of the window; out_mask is [npix][K][ceil(T/32)] uint32
+ *                (bit t%32 of word t/32 set = epoch t kept).  Empty slots: out_idx = -1,
+ *                out_lh = -inf, out_flux = 0, counts 0, mask 0.
+ *   workspace    device scratch of at least kb_search_workspace_size() bytes, aligned to
+ *                KB_WORKSPACE_ALIGN; its contents on entry do not matter.  It must not be used
+ *                by another call until this one has finished on the stream.
+ * Velocities must be finite; a track offset beyond +-2^24 pixels is clamped there (it is off
+ * the image either way).
+ * Errors: KB_ERR_INVALID_ARG (null pointers, sizes, non-finite times or parameters, bad window,
+ * K outside 1..KB_MAX_K), KB_ERR_UNSUPPORTED (T > KB_MAX_T, n_traj > 2^24, H or W > 2^20, an
+ * image plane beyond 2^31 pixels), KB_ERR_WORKSPACE, KB_ERR_CUDA.
+ */
+KB_API int kb_search(const float* psi, const float* phi, const double* times, int T, int H, int W,
+              const float* vx, const float* vy, int n_traj, const kb_search_params* p,
+              float* out_lh, float* out_flux, int32_t* out_idx, uint16_t* out_nvalid,
+              uint16_t* out_nkept, uint32_t* out_mask, void* workspace, size_t ws_bytes,
+              void* stream);
+
+/*
+ * kb_search_stats -- counters of the last kb_search that used `workspace` (device counters
+ * copied to the HOST array stats[4]; synchronises the stream):
+ *   stats[0] trajectory-epochs covered (start pixels x trajectories x T),
+ *   stats[1] (pixel, trajectory) pairs whose bound required a full clipped evaluation,
+ *   stats[2] pairs inserted into a top-K list,
+ *   stats[3] device-side error flags (0 = none; KB_ERR_TIMEOUT bit 0x1 if a bounded wait gave up).
+ */
+KB_API int kb_search_stats(const void* workspace, unsigned long long* stats, void* stream);
+
+/*
+ * kb_stamps -- coadded postage stamps along trajectories (Section 3.3: per-pixel median over
+ * the epochs of the trajectory; also the mean).  For candidate c and stamp pixel (sy, sx) in
+ * [-radius, radius]^2, the values img[t, y_t + sy, x_t + sx] of every epoch t that is inside the
+ * image, not masked (as in kb_make_psi_phi) and, if keep_mask is given, set in keep_mask[c]
+ * are combined: mean = their average, median = the middle value (mean of the two middle values
+ * for an even count); NaN if no epoch contributes.
+ *
+ *   img, var     [T][H][W] float32 (device); mask [T][H][W] uint8 (device) or NULL.
+ *   times        [T] float64 HOST pointer.
+ *   x0, y0       [n] int32 start pixels; vx, vy [n] float32 (device).
+ *   keep_mask    [n][ceil(T/32)] uint32 (device) or NULL for all valid epochs.
+ *   out_mean, out_median  [n][2r+1][2r+1] float32 (device).
+ * Errors: KB_ERR_INVALID_ARG (null pointers, sizes, radius outside 0..15), KB_ERR_UNSUPPORTED
+ * (T > KB_MAX_T).
+ */
+KB_API int kb_stamps(const float* img, const float* var, const uint8_t* mask, const double* times,
+              int T, int H, int W, const int32_t* x0, const int32_t* y0, const float* vx,
+              const float* vy, const uint32_t* keep_mask, int n, int radius, float* out_mean,
+              float* out_median, void* stream);
+
+/*
+ * kb_collect -- GPU-to-host handoff of the survivors (Section 3.1 reworked handoff; Section 3.2
+ * returns the per-pixel results to the CPU): gathers every filled slot of a kb_search result
+ * and orders them by LH' descending, then start pixel, then slot; the first n_max are written.
+ *
+ *   lh, idx      [npix][K] kb_search outputs (device).
+ *   cand_pix     [n_max] int32 (device): window pixel index (row-major) of each survivor.
+ *   cand_slot    [n_max] int32 (device): its slot in that pixel's list.
+ *   count        [1] int32 (device): total number of filled slots (may exceed n_max).
+ *   workspace    kb_collect_workspace_size(n_max) bytes, aligned to KB_WORKSPACE_ALIGN.
+ * Errors: KB_ERR_INVALID_ARG (null pointers, sizes, K outside 1..KB_MAX_K), KB_ERR_UNSUPPORTED
+ * (npix * K >= 2^32 or n_max > 2^24), KB_ERR_WORKSPACE.
+ */
+KB_API int kb_collect_workspace_size(int n_max, size_t* bytes);
+KB_API int kb_collect(const float* lh, const int32_t* idx, int npix, int K, int n_max,
+               int32_t* cand_pix, int32_t* cand_slot, int32_t* count, void* workspace,
+               size_t ws_bytes, void* stream);
+
+/*
+ * kb_candidate_tracks -- start pixel and velocity of collected survivors, for kb_stamps.
+ * For i < n with cand_pix[i] >= 0: x0[i] = x_lo + cand_pix[i] % wx, y0[i] = y_lo + cand_pix[i] / wx,
+ * traj[i] = idx[cand_pix[i] * K + cand_slot[i]], out_vx/out_vy = vx/vy[traj[i]].  Entries with
+ * cand_pix[i] < 0 get traj = -1 and a start pixel far outside any image (their stamps are NaN).
+ * All arrays are device arrays; idx is the kb_search output of the window (x_lo, y_lo, wx).
+ */
+KB_API int kb_candidate_tracks(const int32_t* cand_pix, const int32_t* cand_slot, int n,
+                               const int32_t* idx, int K, const float* vx, const float* vy,
+                               int x_lo, int y_lo, int wx, int32_t* x0, int32_t* y0,
+                               float* out_vx, float* out_vy, int32_t* traj, void* stream);
+
+/* Number of kernels this library has launched in the process so far (all entry points). */
+KB_API unsigned long long kb_launch_count(void);
+
+/*
+ * kb_profile_events -- when both are non-NULL (cudaEvent_t passed as void*), every following
+ * kb_search on this thread records `start` on its stream immediately before the main search
+ * kernel and `stop` immediately after it, so the caller can time that kernel alone with
+ * cudaEventElapsedTime.  Pass NULL, NULL to stop.  The events are owned by the caller.
+ */
+KB_API void kb_profile_events(void* start, void* stop);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KB_B300_H */

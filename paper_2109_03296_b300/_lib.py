@@ -1,0 +1,89 @@
+"""ctypes loader for libkb_b300.so (the C ABI declared in include/kb.h).
+
+The library is built in-tree by ``paper_2109_03296_b300.build``.  There is no fallback: if the
+library is missing or cannot be loaded, every call raises.
+"""
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libkb_b300.so")
+
+KB_OK = 0
+KB_ERR_INVALID_ARG = 1
+KB_ERR_UNSUPPORTED = 2
+KB_ERR_CUDA = 3
+KB_ERR_WORKSPACE = 4
+KB_ERR_TIMEOUT = 5
+KB_MAX_T = 128
+KB_MAX_K = 32
+KB_WORKSPACE_ALIGN = 256
+
+EXPORTS = ("kb_version", "kb_last_error", "kb_search_params_default", "kb_make_psi_phi",
+           "kb_search_workspace_size", "kb_search", "kb_search_stats", "kb_stamps",
+           "kb_collect_workspace_size", "kb_collect", "kb_candidate_tracks", "kb_launch_count",
+           "kb_profile_events")
+
+
+class KbError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("kb error %d: %s" % (code, msg))
+        self.code = code
+
+
+class SearchParamsC(C.Structure):
+    _fields_ = [("k_per_pixel", C.c_int32), ("lh_min", C.c_float), ("min_obs", C.c_int32),
+                ("clip", C.c_int32), ("q_lo", C.c_float), ("q_mid", C.c_float),
+                ("q_hi", C.c_float), ("n_sigma", C.c_float), ("clip_on", C.c_int32),
+                ("x_lo", C.c_int32), ("x_hi", C.c_int32), ("y_lo", C.c_int32),
+                ("y_hi", C.c_int32)]
+
+
+_LIB = None
+
+
+def lib():
+    """Loads the library (building it first if the sources are newer and nvcc is present)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libkb_b300.so is not built: run paper_2109_03296_b300/build.py "
+                          "(or __graft_entry__.build())")
+    L = C.CDLL(LIB_PATH)
+    p, i, f, sz = C.c_void_p, C.c_int, C.c_float, C.c_size_t
+    L.kb_version.restype = i
+    L.kb_version.argtypes = []
+    L.kb_last_error.restype = C.c_char_p
+    L.kb_last_error.argtypes = []
+    L.kb_search_params_default.restype = None
+    L.kb_search_params_default.argtypes = [C.POINTER(SearchParamsC), i, i]
+    L.kb_make_psi_phi.restype = i
+    L.kb_make_psi_phi.argtypes = [p, p, p, p, i, i, i, i, p, p, p]
+    L.kb_search_workspace_size.restype = i
+    L.kb_search_workspace_size.argtypes = [i, i, i, i, C.POINTER(SearchParamsC), C.POINTER(sz)]
+    L.kb_search.restype = i
+    L.kb_search.argtypes = [p, p, p, i, i, i, p, p, i, C.POINTER(SearchParamsC), p, p, p, p, p,
+                            p, p, sz, p]
+    L.kb_search_stats.restype = i
+    L.kb_search_stats.argtypes = [p, p, p]
+    L.kb_stamps.restype = i
+    L.kb_stamps.argtypes = [p, p, p, p, i, i, i, p, p, p, p, p, i, i, p, p, p]
+    L.kb_collect_workspace_size.restype = i
+    L.kb_collect_workspace_size.argtypes = [i, C.POINTER(sz)]
+    L.kb_collect.restype = i
+    L.kb_collect.argtypes = [p, p, i, i, i, p, p, p, p, sz, p]
+    L.kb_candidate_tracks.restype = i
+    L.kb_candidate_tracks.argtypes = [p, p, i, p, i, p, p, i, i, i, p, p, p, p, p, p]
+    L.kb_launch_count.restype = C.c_ulonglong
+    L.kb_launch_count.argtypes = []
+    L.kb_profile_events.restype = None
+    L.kb_profile_events.argtypes = [p, p]
+    _LIB = L
+    return L
+
+
+def check(rc):
+    if rc != KB_OK:
+        raise KbError(rc, lib().kb_last_error().decode(errors="replace"))
+    return rc
