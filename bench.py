@@ -232,6 +232,9 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
+    for a, b in kev:        # torch creates the CUDA event on first record
+        a.record(stream)
+        b.record(stream)
 
     def step(inp, kernel_events=None):
         if kernel_events is not None:

@@ -128,7 +128,7 @@ __global__ void plan_reset_kernel(Ctrl* ctrl, uint32_t* counts, unsigned long lo
   }
 }
 
-__global__ void plan_minmax_kernel(const float* __restrict__ vx, const float* __restrict__ vy,
+__global__ void __launch_bounds__(1024) plan_minmax_kernel(const float* __restrict__ vx, const float* __restrict__ vy,
                                    int n, float4* vbox) {
   __shared__ float s[4][32];
   float a = INFINITY, b = -INFINITY, c = INFINITY, d = -INFINITY;
@@ -180,17 +180,13 @@ __global__ void plan_hist_kernel(const float* __restrict__ vx, const float* __re
 }
 
 // Exclusive scan of N_CELLS counts by one block of 1024 threads (64 consecutive cells each).
-__global__ void plan_scan_kernel(const uint32_t* __restrict__ counts, uint32_t* cursor) {
+__global__ void __launch_bounds__(1024) plan_scan_kernel(const uint32_t* __restrict__ counts,
+                                                         uint32_t* cursor) {
   __shared__ uint32_t part[1024];
   constexpr int PER = N_CELLS / 1024;
   int t = threadIdx.x;
-  uint32_t local[PER];
   uint32_t s = 0;
-#pragma unroll
-  for (int i = 0; i < PER; ++i) {
-    local[i] = s;
-    s += counts[t * PER + i];
-  }
+  for (int i = 0; i < PER; ++i) s += counts[t * PER + i];
   part[t] = s;
   __syncthreads();
   for (int o = 1; o < 1024; o <<= 1) {
@@ -200,8 +196,10 @@ __global__ void plan_scan_kernel(const uint32_t* __restrict__ counts, uint32_t* 
     __syncthreads();
   }
   uint32_t base = part[t] - s;
-#pragma unroll
-  for (int i = 0; i < PER; ++i) cursor[t * PER + i] = base + local[i];
+  for (int i = 0; i < PER; ++i) {
+    cursor[t * PER + i] = base;
+    base += counts[t * PER + i];
+  }
 }
 
 __global__ void plan_scatter_kernel(const uint32_t* __restrict__ keys, int n, uint32_t* cursor,
