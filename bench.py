@@ -316,10 +316,11 @@ def run_ours(args):
     k_ms = statistics.mean(kernel_ms)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_max = float(peaks.get("sm_max_mhz", 2032.0))
-    # Shared-memory load roofline of the bound pass: one 128-byte wavefront per SM per clock.
+    # Shared-memory load roofline of the bound pass: one 128-byte wavefront per SM per clock;
+    # the bound pass reads one fp16 bound term (2 B) per trajectory-epoch from shared memory.
     smem_peak = sms * 128 * sm_max * 1e6 / 1e9                 # GB/s
     te_per_s_kernel = te_step / (k_ms / 1e3)
-    achieved = te_per_s_kernel * 4 / 1e9                      # 4 B of bound data per TE
+    achieved = te_per_s_kernel * 2 / 1e9
     traffic = None
     tp = os.path.join(ROOT, "profiles", "search_kernel_traffic.json")
     if os.path.exists(tp):
@@ -339,7 +340,7 @@ def run_ours(args):
                      "kernel": "search_kernel", "kernel_ms": k_ms,
                      "peak_source": "derived: %d SMs x 128 B/clk shared-memory loads x %g MHz "
                                     "(sm_max_mhz, %s)" % (sms, sm_max, peaks_src),
-                     "algorithmic_bytes_per_te": 4,
+                     "algorithmic_bytes_per_te": 2,
                      "hbm_gather_equiv": {"bytes_per_te": 8,
                                           "achieved_gbs": te_per_s_kernel * 8 / 1e9,
                                           "hbm_peak_gbs": peaks["hbm_gbs"],

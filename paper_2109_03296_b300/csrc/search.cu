@@ -20,22 +20,26 @@
 //  * Bound pass layout.  nu2 is written once per call into the workspace as [T][H][Wp] float32
 //    (Wp = W rounded up to 32, zero padded) so that a 3-D TMA tensor map can address it.  A
 //    block owns a tile of 32 x 64 start pixels (lane = x, 8 rows per thread) and sweeps the
-//    velocity list in chunks of 16 trajectories that are close in velocity space (the list is
+//    velocity list in chunks of 32 trajectories that are close in velocity space (the list is
 //    reordered by a Morton key of (vx, vy) in the plan kernels).  For each (chunk, epoch) the
-//    union of the tile's 16 shifted footprints is one small rectangle; it is fetched with TMA
+//    union of the tile's 32 shifted footprints is one small rectangle; it is fetched with TMA
 //    into a double-buffered shared-memory stage (zero fill outside the image) while the
-//    previous epoch is being summed.  Each thread then does 8 x 16 shared loads + adds per
+//    previous epoch is being summed.  Each thread then does 4 x 32 shared loads + adds per
 //    epoch with immediate row offsets.  A (chunk, epoch) rectangle too large for a stage falls
 //    back to direct global loads.
 //
-//  * Full evaluation.  After each chunk, the block queues the pairs whose bound passes; one
-//    warp evaluates one pair with lanes over epochs (up to 4 epochs per lane): gather, validity
-//    ballot, warp bitonic sort of the lightcurve for the three percentiles, clip, butterfly sums
-//    (same order for identical inputs, so identical tracks give bit-identical LH').  The owner
-//    thread of the start pixel then inserts the result into the pixel's list in the output
-//    arrays (LH' descending, trajectory index ascending).
+//  * Full evaluation.  After each chunk, the pairs whose bound passes are appended to a queue
+//    in shared memory (with a per-pixel linked list); the queue is evaluated in one batch once
+//    it holds S_FLUSH_MIN pairs (and at the end of a tile), so every thread has work and no
+//    warp idles at a barrier for a lone candidate.  For T <= 32 one thread evaluates one pair:
+//    gather into registers, bitonic sorting network on the lightcurve, percentiles, clip, sums in
+//    epoch order (identical tracks give bit-identical LH').  For T > 32 one warp evaluates one
+//    pair with lanes over epochs.  The owner thread of each start pixel then walks its list and
+//    inserts the results into the pixel's output list (LH' descending, trajectory index
+//    ascending).
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_fp16.h>
 
 #include <climits>
 #include <cmath>
@@ -50,21 +54,31 @@ namespace kb {
 // Compile-time configuration of the search kernel
 // ---------------------------------------------------------------------------------------------
 constexpr int S_TX = 32;                 // tile width (lane = x)
-constexpr int S_ROWS = 8;                // rows per thread
-constexpr int S_WARPS = 8;
-constexpr int S_THREADS = S_WARPS * 32;  // 256
+constexpr int S_ROWS = 4;                // rows per thread (two row pairs)
+constexpr int S_WARPS = 16;
+constexpr int S_THREADS = S_WARPS * 32;  // 512
 constexpr int S_TY = S_WARPS * S_ROWS;   // 64
-constexpr int S_C = 16;                  // trajectories per chunk
-constexpr int S_PITCH = 128;             // staged row pitch in floats (= TMA box width)
-constexpr int S_BOX_Y = 8;               // TMA box height
-constexpr int S_CAP_ROWS = 128;          // staged rows per stage
-constexpr int S_STAGE_FLOATS = S_CAP_ROWS * S_PITCH;
-constexpr int S_QCAP = 1024;             // queued full evaluations per round
+constexpr int S_NPIX = S_TX * S_TY;      // 2048 start pixels per tile
+constexpr int S_C = 32;                  // trajectories per chunk
+constexpr int S_BOX_Y = 8;               // TMA box height (word rows)
+constexpr int S_STAGE_BYTES = 65536;     // one pipeline stage
+constexpr int S_QCAP = 1024;             // queued full evaluations
+constexpr int S_FLUSH_MIN = 512;         // evaluate the queue once it holds this many
 constexpr int S_REC_WORDS = 8;           // L', alpha, nvalid|nkept<<16, mask[4], pad
 constexpr float S_PRUNE_MARGIN = 1.0f - 1e-4f;
+// staging modes of a (chunk, epoch): 0 = direct global loads, 1 = 64-word rows, 2 = 128-word rows
+constexpr int S_PITCH1 = 64, S_PITCH2 = 128;
 
-constexpr int MORTON_BITS = 8;           // per axis: 256 x 256 velocity cells
-constexpr int N_CELLS = 1 << (2 * MORTON_BITS);
+constexpr int HILBERT_BITS = 8;          // 256 x 256 velocity cells
+constexpr int N_CELLS = 1 << (2 * HILBERT_BITS);
+
+// Staging plan of one (chunk, epoch): the rectangle and the 32 per-trajectory byte offsets
+// into it.  Copied into shared memory with the stage it describes.
+struct __align__(16) PlanRec {
+  int4 box;           // x offset, y offset, 8-row boxes, mode (0 direct, 1 pitch 64, 2 pitch 128)
+  int32_t rel[32];    // byte offset of each trajectory's footprint in the stage
+};
+static_assert(sizeof(PlanRec) == 144, "plan record layout");
 
 struct SearchConsts {
   float dt[KB_MAX_T];   // (float)(t_t - t_0)
@@ -73,11 +87,12 @@ struct SearchConsts {
 struct EvalParams {
   int T, H, W, min_obs, clip, clip_on, K, mw;
   float q_lo, q_mid, q_hi, n_sigma, c_sigma, lh_min;
+  float prune_scale, prune_slack;  // fp16 bound sums: see admission_threshold()
 };
 
 // Workspace layout (offsets in bytes from the workspace base).
 struct WsLayout {
-  size_t ctrl, vbox, keys, counts, cursor, sorted, orig, offs, box, rel, bound, total;
+  size_t ctrl, vbox, keys, counts, cursor, sorted, orig, offs, plan, bound, total;
   int n_pad, nchunk, Wp;
 };
 
@@ -100,9 +115,8 @@ static WsLayout ws_layout(int T, int H, int W, int n_traj) {
   L.sorted = take(sizeof(int32_t) * (size_t)n_traj);
   L.orig = take(sizeof(int32_t) * (size_t)L.n_pad);
   L.offs = take(sizeof(int2) * (size_t)L.n_pad * T);
-  L.box = take(sizeof(int4) * (size_t)L.nchunk * T);
-  L.rel = take(sizeof(int32_t) * (size_t)L.nchunk * T * S_C);
-  L.bound = take(sizeof(float) * (size_t)T * H * L.Wp);
+  L.plan = take(sizeof(PlanRec) * (size_t)L.nchunk * T);
+  L.bound = take(sizeof(uint32_t) * (size_t)T * (H + 1) * L.Wp);
   L.total = o;
   return L;
 }
@@ -154,27 +168,39 @@ __global__ void __launch_bounds__(1024) plan_minmax_kernel(const float* __restri
   }
 }
 
-__device__ __forceinline__ uint32_t spread_bits8(uint32_t v) {
-  v &= 0xffu;
-  v = (v | (v << 4)) & 0x0f0fu;
-  v = (v | (v << 2)) & 0x3333u;
-  v = (v | (v << 1)) & 0x5555u;
-  return v;
+// Hilbert index of cell (x, y) on a 2^HILBERT_BITS square: consecutive indices are adjacent
+// cells, so consecutive trajectories of the sorted list are close in velocity space.
+__device__ __forceinline__ uint32_t hilbert_index(uint32_t x, uint32_t y) {
+  const uint32_t n1 = (1u << HILBERT_BITS) - 1u;
+  uint32_t d = 0;
+  for (uint32_t sq = 1u << (HILBERT_BITS - 1); sq > 0; sq >>= 1) {
+    const uint32_t rx = (x & sq) ? 1u : 0u, ry = (y & sq) ? 1u : 0u;
+    d += sq * sq * ((3u * rx) ^ ry);
+    if (ry == 0u) {  // rotate the quadrant (only the lower bits matter from here on)
+      if (rx == 1u) {
+        x ^= n1;
+        y ^= n1;
+      }
+      const uint32_t tmp = x;
+      x = y;
+      y = tmp;
+    }
+  }
+  return d;
 }
 
+// Velocities quantised on square cells (the same cell size along vx and vy).
 __global__ void plan_hist_kernel(const float* __restrict__ vx, const float* __restrict__ vy,
                                  int n, const float4* vbox, uint32_t* keys, uint32_t* counts) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   float4 b = *vbox;
-  const float cells = (float)(1 << MORTON_BITS);
-  float sx = (b.y > b.x) ? cells / (b.y - b.x) : 0.0f;
-  float sy = (b.w > b.z) ? cells / (b.w - b.z) : 0.0f;
-  int qx = min((int)((vx[i] - b.x) * sx), (1 << MORTON_BITS) - 1);
-  int qy = min((int)((vy[i] - b.z) * sy), (1 << MORTON_BITS) - 1);
-  qx = max(qx, 0);
-  qy = max(qy, 0);
-  uint32_t key = spread_bits8((uint32_t)qx) | (spread_bits8((uint32_t)qy) << 1);
+  const int nc = 1 << HILBERT_BITS;
+  const float ext = fmaxf(b.y - b.x, b.w - b.z);
+  const float sc = ext > 0.0f ? (float)nc / ext : 0.0f;
+  int qx = min(max((int)((vx[i] - b.x) * sc), 0), nc - 1);
+  int qy = min(max((int)((vy[i] - b.z) * sc), 0), nc - 1);
+  uint32_t key = hilbert_index((uint32_t)qx, (uint32_t)qy);
   keys[i] = key;
   atomicAdd(&counts[key], 1u);
 }
@@ -254,10 +280,10 @@ __global__ void plan_offsets_kernel(const float* __restrict__ vx, const float* _
 
 // One thread per (chunk, epoch): staging rectangle and per-trajectory byte offsets into it.
 // box = {x offset of the rectangle from the tile origin (x_lo + dxmin - xshift is a multiple
-// of 4 so that the TMA x coordinate is 16-byte aligned), y offset, number of 8-row boxes,
-// fits-in-a-stage flag}.
+// of 4 so that the TMA x coordinate is 16-byte aligned), y offset, number of 8-row boxes, mode}
+// with mode 1 = 64-word rows, 2 = 128-word rows, 0 = too large for a stage (direct loads).
 __global__ void plan_boxes_kernel(const int2* __restrict__ offs, int nchunk, int T, int x_lo,
-                                  int4* box, int32_t* rel) {
+                                  PlanRec* plan) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nchunk * T) return;
   int c = i / T, t = i - c * T;
@@ -267,36 +293,62 @@ __global__ void plan_boxes_kernel(const int2* __restrict__ offs, int nchunk, int
     dxmin = min(dxmin, o.x); dxmax = max(dxmax, o.x);
     dymin = min(dymin, o.y); dymax = max(dymax, o.y);
   }
-  int xshift = ((x_lo + dxmin) % 4 + 4) % 4;
-  int rw = S_TX + (dxmax - dxmin) + xshift;
-  int rh = S_TY + (dymax - dymin);
-  int nb = (rh + S_BOX_Y - 1) / S_BOX_Y;
-  // overflow-safe check: spans are compared before being added
-  bool fits = (dxmax - dxmin) <= S_PITCH && (dymax - dymin) <= S_CAP_ROWS && rw <= S_PITCH &&
-              nb * S_BOX_Y <= S_CAP_ROWS;
-  box[i] = make_int4(dxmin - xshift, dymin, nb, fits ? 1 : 0);
+  // offsets are clamped to +-2^24, so these spans cannot overflow
+  const int xshift = ((x_lo + dxmin) % 4 + 4) % 4;
+  const int rw = S_TX + (dxmax - dxmin) + xshift;
+  const int rh = S_TY + (dymax - dymin);
+  const int nb = (rh + S_BOX_Y - 1) / S_BOX_Y;
+  int mode = 0, pitch = 0;
+  if (rw <= S_PITCH1 && nb * S_BOX_Y * S_PITCH1 * 4 <= S_STAGE_BYTES) {
+    mode = 1;
+    pitch = S_PITCH1;
+  } else if (rw <= S_PITCH2 && nb * S_BOX_Y * S_PITCH2 * 4 <= S_STAGE_BYTES) {
+    mode = 2;
+    pitch = S_PITCH2;
+  }
+  PlanRec& pr = plan[i];
+  pr.box = make_int4(dxmin - xshift, dymin, nb, mode);
   for (int v = 0; v < S_C; ++v) {
     int2 o = offs[(size_t)(c * S_C + v) * T + t];
-    rel[(size_t)i * S_C + v] =
-        fits ? ((o.y - dymin) * S_PITCH + (o.x - dxmin + xshift)) * (int)sizeof(float) : 0;
+    pr.rel[v] = mode ? ((o.y - dymin) * pitch + (o.x - dxmin + xshift)) * 4 : 0;
   }
 }
 
-// nu2 = psi^2/phi for valid epochs with psi > 0, else 0; [T][H][Wp] with zero padding.
+// nu2 = psi^2/phi at a valid pixel with psi > 0, else 0 (also outside the image).
+__device__ __forceinline__ float nu2_at(const float* __restrict__ psi,
+                                        const float* __restrict__ phi, int H, int W, size_t plane,
+                                        int y, int x) {
+  if (y < 0 || y >= H || x >= W) return 0.0f;
+  const size_t s = plane + (size_t)y * W + x;
+  const float p = __ldg(psi + s), f = __ldg(phi + s);
+  if (f > 0.0f && p > 0.0f && isfinite(p) && isfinite(f)) return __fdiv_rn(__fmul_rn(p, p), f);
+  return 0.0f;
+}
+
+// The smallest fp16 value >= v (v >= 0); values above the fp16 range become +inf.
+__device__ __forceinline__ unsigned short half_round_up(float v) {
+  __half h = __float2half_rn(v);
+  unsigned short u = __half_as_ushort(h);
+  if (__half2float(h) < v) ++u;  // v >= 0: the next encoding is the next larger value (or inf)
+  return u;
+}
+
+// Bound planes as fp16 row pairs, [T][H+1][Wp] 32-bit words: word (t, r, x) holds nu2 of image
+// rows r-1 (low half) and r (high half) at column x, each rounded up to fp16, zero outside the
+// image and in the padding.  A thread summing start-pixel rows y and y+1 at row offset dy reads
+// the single word at r = y + dy + 1.
 __global__ void bound_prep_kernel(const float* __restrict__ psi, const float* __restrict__ phi,
-                                  int T, int H, int W, int Wp, float* __restrict__ bound) {
-  size_t total = (size_t)T * H * Wp;
+                                  int T, int H, int W, int Wp, uint32_t* __restrict__ bound) {
+  const size_t total = (size_t)T * (H + 1) * Wp;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (size_t)gridDim.x * blockDim.x) {
-    int x = (int)(i % Wp);
-    size_t row = i / Wp;  // t*H + y
-    float v = 0.0f;
-    if (x < W) {
-      size_t s = row * W + x;
-      float p = __ldg(psi + s), f = __ldg(phi + s);
-      if (f > 0.0f && p > 0.0f && isfinite(p) && isfinite(f)) v = __fdiv_rn(__fmul_rn(p, p), f);
-    }
-    bound[i] = v;
+    const int x = (int)(i % Wp);
+    const size_t row = i / Wp;  // t*(H+1) + r
+    const int t = (int)(row / (H + 1)), r = (int)(row % (H + 1));
+    const size_t plane = (size_t)t * H * W;
+    const unsigned short lo = half_round_up(nu2_at(psi, phi, H, W, plane, r - 1, x));
+    const unsigned short hi = half_round_up(nu2_at(psi, phi, H, W, plane, r, x));
+    bound[i] = (uint32_t)lo | ((uint32_t)hi << 16);
   }
 }
 
@@ -449,16 +501,125 @@ __device__ void eval_pair_warp(const float* __restrict__ psi, const float* __res
 }
 
 // ---------------------------------------------------------------------------------------------
+// Thread-level full evaluation (T <= NT <= 32): one thread, one (start pixel, trajectory) pair
+// ---------------------------------------------------------------------------------------------
+template <int NT>
+__device__ __forceinline__ void thread_bitonic_sort(float (&v)[NT]) {
+#pragma unroll
+  for (int k = 2; k <= NT; k <<= 1)
+#pragma unroll
+    for (int d = k >> 1; d > 0; d >>= 1)
+#pragma unroll
+      for (int i = 0; i < NT; ++i) {
+        const int p = i ^ d;
+        if (p > i) {
+          const bool up = (i & k) == 0;
+          const float a = v[i], b = v[p];
+          v[i] = up ? fminf(a, b) : fmaxf(a, b);
+          v[p] = up ? fmaxf(a, b) : fminf(a, b);
+        }
+      }
+}
+
+// Percentile of the n smallest of the ascending values in loc[] (linear interpolation, h = (n-1) q).
+template <int NT>
+__device__ __forceinline__ float sorted_percentile(const float (&loc)[NT], int n, float q) {
+  const float h = (float)(n - 1) * q;
+  int lo = (int)floorf(h);
+  lo = max(0, min(lo, n - 1));
+  const int hi = min(lo + 1, n - 1);
+  const float f = h - (float)lo;
+  const float a = loc[lo], b = loc[hi];
+  return a + f * (b - a);
+}
+
+__device__ __forceinline__ bool gather_pair(const float* __restrict__ psi,
+                                            const float* __restrict__ phi, const EvalParams& ep,
+                                            size_t plane, int t, int x, int y, float& p,
+                                            float& f) {
+  if (x < 0 || x >= ep.W || y < 0 || y >= ep.H) return false;
+  const size_t i = (size_t)t * plane + (size_t)y * ep.W + x;
+  p = __ldg(psi + i);
+  f = __ldg(phi + i);
+  return f > 0.0f && isfinite(p) && isfinite(f);
+}
+
+template <int NT>
+__device__ void eval_pair_thread(const float* __restrict__ psi, const float* __restrict__ phi,
+                                 const EvalParams& ep, int x0, int y0,
+                                 const int2* __restrict__ off, uint32_t* rec) {
+  float a[NT];
+  uint32_t vm = 0u;
+  const size_t plane = (size_t)ep.H * ep.W;
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    a[t] = INFINITY;
+    if (t < ep.T) {
+      const int2 o = __ldg(off + t);
+      float p, f;
+      if (gather_pair(psi, phi, ep, plane, t, x0 + o.x, y0 + o.y, p, f)) {
+        vm |= 1u << t;
+        a[t] = ep.clip_on ? __fdiv_rn(p, __fsqrt_rn(f)) : __fdiv_rn(p, f);
+      }
+    }
+  }
+  const int nvalid = __popc(vm);
+  if (nvalid < ep.min_obs || nvalid == 0) {
+    rec[0] = __float_as_uint(NAN);
+    rec[2] = (uint32_t)nvalid;
+    return;
+  }
+  uint32_t km = vm;
+  if (ep.clip) {
+    float loc[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) loc[t] = a[t];
+    thread_bitonic_sort<NT>(loc);
+    const float x_lo = sorted_percentile<NT>(loc, nvalid, ep.q_lo);
+    const float x_mid = sorted_percentile<NT>(loc, nvalid, ep.q_mid);
+    const float x_hi = sorted_percentile<NT>(loc, nvalid, ep.q_hi);
+    const float sg = ep.c_sigma * (x_hi - x_lo);
+    const float lo_b = x_mid - ep.n_sigma * sg, hi_b = x_mid + ep.n_sigma * sg;
+    km = 0u;
+#pragma unroll
+    for (int t = 0; t < NT; ++t)
+      if (((vm >> t) & 1u) && a[t] >= lo_b && a[t] <= hi_b) km |= 1u << t;
+  }
+  // sums over the kept epochs, in epoch order (second gather: the lines are in L1)
+  float sp = 0.0f, sf = 0.0f;
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    if ((km >> t) & 1u) {
+      const int2 o = __ldg(off + t);
+      float p = 0.0f, f = 0.0f;
+      gather_pair(psi, phi, ep, plane, t, x0 + o.x, y0 + o.y, p, f);
+      sp += p;
+      sf += f;
+    }
+  }
+  const int nkept = __popc(km);
+  float L = NAN, alpha = 0.0f;
+  if (nkept > 0 && sf > 0.0f) {
+    L = __fdiv_rn(sp, __fsqrt_rn(sf));
+    alpha = __fdiv_rn(sp, sf);
+  }
+  rec[0] = __float_as_uint(L);
+  rec[1] = __float_as_uint(alpha);
+  rec[2] = (uint32_t)nvalid | ((uint32_t)nkept << 16);
+  rec[3] = km;
+  rec[4] = rec[5] = rec[6] = 0u;
+}
+
+// ---------------------------------------------------------------------------------------------
 // The search kernel
 // ---------------------------------------------------------------------------------------------
 struct SearchArgs {
   const float* psi;
   const float* phi;
-  const float* bound;
+  const uint32_t* bound;
   const int32_t* orig;
   const int2* offs;
-  const int4* box;
-  const int32_t* rel;
+  const PlanRec* plan;
   float* out_lh;
   float* out_flux;
   int32_t* out_idx;
@@ -473,15 +634,33 @@ struct SearchArgs {
 
 struct SmemLayout {
   static constexpr size_t stage = 0;  // 2 stages
-  static constexpr size_t rec = stage + 2 * S_STAGE_FLOATS * sizeof(float);
-  static constexpr size_t queue = rec + S_QCAP * S_REC_WORDS * sizeof(uint32_t);
-  static constexpr size_t filled = queue + S_QCAP * sizeof(uint16_t);
-  static constexpr size_t misc = filled + S_TX * S_TY;
+  static constexpr size_t rec = stage + 2 * (size_t)S_STAGE_BYTES;
+  static constexpr size_t qtraj = rec + S_QCAP * S_REC_WORDS * sizeof(uint32_t);
+  static constexpr size_t qpix = qtraj + S_QCAP * sizeof(int32_t);
+  static constexpr size_t qnext = qpix + S_QCAP * sizeof(uint16_t);
+  static constexpr size_t head = qnext + S_QCAP * sizeof(int16_t);
+  static constexpr size_t filled = head + S_NPIX * sizeof(int32_t);
+  static constexpr size_t planslot = filled + S_NPIX;           // 2 x PlanRec (16-B aligned)
+  static constexpr size_t misc = planslot + 2 * sizeof(PlanRec);
   static constexpr size_t total = misc + 64;
 };
+static_assert(SmemLayout::planslot % 16 == 0, "plan slots must be 16-byte aligned");
 
-__device__ __forceinline__ void issue_stage(const CUtensorMap* tmap, const SearchArgs& A,
-                                            float* stage, uint64_t* bar, long long it) {
+// Admission threshold of a pixel for the fp16 bound sums.  With every stored term rounded up,
+// an RN fp16 sum of T non-negative terms satisfies  exact <= sum (1 + 2^-11)^T + T 2^-25  (the
+// second term covers subnormal rounding), and the fp32 nu2 itself is within (1 + 2^-23) of the
+// exact value.  A pair is dropped only if  sum < (thr^2 (1 - 1e-4) - slack) * scale, which
+// implies  sqrt(exact bound) < thr.
+__device__ __forceinline__ float admission_threshold(float thr, const EvalParams& ep) {
+  if (!(thr > 0.0f)) return -1.0f;
+  return (thr * thr * S_PRUNE_MARGIN - ep.prune_slack) * ep.prune_scale;
+}
+
+// Issues the copies of iteration `it` (tile, chunk, epoch) of this block into one stage: the plan
+// record (always) and, in modes 1/2, the rectangle of fp16 pair words.
+__device__ __forceinline__ void issue_stage(const CUtensorMap* tmap64, const CUtensorMap* tmap128,
+                                            const SearchArgs& A, unsigned char* stage,
+                                            PlanRec* slot, uint64_t* bar, long long it) {
   const int T = A.ep.T;
   const long long per_tile = (long long)A.nchunk * T;
   const int k = (int)(it / per_tile);
@@ -490,13 +669,39 @@ __device__ __forceinline__ void issue_stage(const CUtensorMap* tmap, const Searc
   const int tile = blockIdx.x + k * gridDim.x;
   const int tx0 = A.x_lo + (tile % A.ntx) * S_TX;
   const int ty0 = A.y_lo + (tile / A.ntx) * S_TY;
-  const int4 b = __ldg(A.box + (size_t)c * T + t);
+  const PlanRec* pr = A.plan + (size_t)c * T + t;
+  const int4 b = __ldg(&pr->box);
+  const int pitch = b.w == 1 ? S_PITCH1 : S_PITCH2;
+  const int box_bytes = S_BOX_Y * pitch * 4;
+  mbar_arrive_expect_tx(bar, (uint32_t)(sizeof(PlanRec) + (b.w ? b.z * box_bytes : 0)));
+  bulk_copy_g2s(slot, pr, (uint32_t)sizeof(PlanRec), bar);
   if (b.w) {
-    mbar_arrive_expect_tx(bar, (uint32_t)(b.z * S_BOX_Y * S_PITCH * sizeof(float)));
+    const CUtensorMap* tm = b.w == 1 ? tmap64 : tmap128;
+    // word row r = image row + 1 (the pair planes carry one leading row)
     for (int i = 0; i < b.z; ++i)
-      tma_load_3d(stage + i * S_BOX_Y * S_PITCH, tmap, bar, tx0 + b.x, ty0 + b.y + i * S_BOX_Y, t);
-  } else {
-    mbar_arrive(bar);
+      tma_load_3d(stage + i * box_bytes, tm, bar, tx0 + b.x, ty0 + b.y + 1 + i * S_BOX_Y, t);
+  }
+}
+
+// Sums one staged (chunk, epoch) into the fp16 row-pair accumulators.
+template <int PITCH>
+__device__ __forceinline__ void accumulate_stage(__half2 (&acc)[2][S_C], const unsigned char* st,
+                                                 const PlanRec* slot, int warp, int lane) {
+  const unsigned char* base = st + (size_t)(warp * S_ROWS * PITCH + lane) * 4;
+  const int4* relv = reinterpret_cast<const int4*>(slot->rel);
+#pragma unroll
+  for (int vq = 0; vq < S_C / 4; ++vq) {
+    const int4 r4 = relv[vq];
+    const int rr[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const uint32_t* q = reinterpret_cast<const uint32_t*>(base + rr[u]);
+#pragma unroll
+      for (int pp = 0; pp < 2; ++pp) {
+        const uint32_t w = q[2 * pp * PITCH];
+        acc[pp][vq * 4 + u] = __hadd2(acc[pp][vq * 4 + u], *reinterpret_cast<const __half2*>(&w));
+      }
+    }
   }
 }
 
@@ -528,18 +733,29 @@ __device__ __noinline__ bool insert_sorted(const SearchArgs& A, size_t wp, int K
   return true;
 }
 
-template <int J>
+// NT > 0: thread-per-pair evaluation with an NT-wide sorting network (T <= NT <= 32);
+// NT == 0: warp-per-pair evaluation with J epochs per lane (32 < T <= 32 J).
+template <int NT, int J>
 __global__ void __launch_bounds__(S_THREADS, 1)
-search_kernel(const __grid_constant__ CUtensorMap tmap, const SearchArgs A) {
+search_kernel(const __grid_constant__ CUtensorMap tmap64, const __grid_constant__ CUtensorMap tmap128,
+              const SearchArgs A) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  float* stages = reinterpret_cast<float*>(smem + SmemLayout::stage);
+  unsigned char* stages = smem + SmemLayout::stage;
   uint32_t* recs = reinterpret_cast<uint32_t*>(smem + SmemLayout::rec);
-  uint16_t* queue = reinterpret_cast<uint16_t*>(smem + SmemLayout::queue);
+  int32_t* q_traj = reinterpret_cast<int32_t*>(smem + SmemLayout::qtraj);
+  uint16_t* q_pix = reinterpret_cast<uint16_t*>(smem + SmemLayout::qpix);
+  int16_t* q_next = reinterpret_cast<int16_t*>(smem + SmemLayout::qnext);
+  int32_t* head = reinterpret_cast<int32_t*>(smem + SmemLayout::head);
+  uint8_t* s_filled = reinterpret_cast<uint8_t*>(smem + SmemLayout::filled);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + SmemLayout::misc);
   unsigned int* s_qcount = reinterpret_cast<unsigned int*>(smem + SmemLayout::misc + 16);
-  unsigned int* s_evals = s_qcount + 1;
-  unsigned int* s_ins = s_qcount + 2;
-  uint8_t* s_filled = reinterpret_cast<uint8_t*>(smem + SmemLayout::filled);
+  unsigned int* s_new = s_qcount + 1;
+  unsigned int* s_evals = s_qcount + 2;
+  unsigned int* s_ins = s_qcount + 3;
+  unsigned int* s_done = s_qcount + 4;   // [2]: warps finished with each stage
+  unsigned int* s_abort = s_qcount + 6;  // a bounded wait gave up: stop using the stages
+  long long* s_last = reinterpret_cast<long long*>(smem + SmemLayout::misc + 48);  // [2]
+  PlanRec* slots = reinterpret_cast<PlanRec*>(smem + SmemLayout::planslot);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int T = A.ep.T, K = A.ep.K, mw = A.ep.mw;
@@ -547,40 +763,48 @@ search_kernel(const __grid_constant__ CUtensorMap tmap, const SearchArgs A) {
   const long long per_tile = (long long)A.nchunk * T;
   const long long total_it = (long long)my_tiles * per_tile;
 
+  for (int i = tid; i < S_NPIX; i += S_THREADS) head[i] = -1;
   if (tid == 0) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
+    *s_qcount = 0u;
+    *s_new = 0u;
     *s_evals = 0u;
     *s_ins = 0u;
+    s_done[0] = s_done[1] = 0u;
+    *s_abort = 0u;
+    s_last[0] = 0;
+    s_last[1] = 1;
     fence_mbar_init();
-    prefetch_tmap(&tmap);
+    prefetch_tmap(&tmap64);
+    prefetch_tmap(&tmap128);
   }
   __syncthreads();
   if (tid == 0) {
-    if (total_it > 0) issue_stage(&tmap, A, stages, &bars[0], 0);
-    if (total_it > 1) issue_stage(&tmap, A, stages + S_STAGE_FLOATS, &bars[1], 1);
+    if (total_it > 0) issue_stage(&tmap64, &tmap128, A, stages, &slots[0], &bars[0], 0);
+    if (total_it > 1)
+      issue_stage(&tmap64, &tmap128, A, stages + S_STAGE_BYTES, &slots[1], &bars[1], 1);
   }
 
   const float lh_min = A.ep.lh_min;
   const size_t wx = (size_t)(A.x_hi - A.x_lo);
   long long it = 0;
-  bool aborted = false;
 
-  for (int k = 0; k < my_tiles && !aborted; ++k) {
+  for (int k = 0; k < my_tiles; ++k) {
     const int tile = blockIdx.x + k * gridDim.x;
     const int tx0 = A.x_lo + (tile % A.ntx) * S_TX;
     const int ty0 = A.y_lo + (tile / A.ntx) * S_TY;
     const int px = tx0 + lane;
-    // per-pixel state of the 8 owned pixels: admission threshold for the bound, list fill
     float thr2[S_ROWS];
     uint32_t active = 0u;
 #pragma unroll
     for (int i = 0; i < S_ROWS; ++i) {
-      const int py = ty0 + warp * S_ROWS + i;
+      const int row = warp * S_ROWS + i;
+      const int py = ty0 + row;
       const bool act = px < A.x_hi && py < A.y_hi;
       active |= (act ? 1u : 0u) << i;
-      s_filled[((warp * S_ROWS + i) << 5) | lane] = 0;
-      thr2[i] = lh_min > 0.0f ? lh_min * lh_min * S_PRUNE_MARGIN : -1.0f;
+      s_filled[(row << 5) | lane] = 0;
+      thr2[i] = admission_threshold(lh_min, A.ep);
       if (act) {
         const size_t wp = (size_t)(py - A.y_lo) * wx + (size_t)(px - A.x_lo);
         for (int s = 0; s < K; ++s) {
@@ -594,175 +818,192 @@ search_kernel(const __grid_constant__ CUtensorMap tmap, const SearchArgs A) {
       }
     }
 
-    for (int c = 0; c < A.nchunk && !aborted; ++c) {
-      float acc[S_ROWS][S_C];
+    // Evaluate every queued pair, insert the results, reset the queue.  Called by all threads
+    // right after a barrier.
+    auto flush = [&]() {
+      const int nq = (int)*s_qcount;
+      if (NT > 0) {
+        for (int e = tid; e < nq; e += S_THREADS) {
+          const int pl = q_pix[e];
+          const int s = q_traj[e];
+          eval_pair_thread<(NT > 0 ? NT : 1)>(A.psi, A.phi, A.ep, tx0 + (pl & 31), ty0 + (pl >> 5),
+                                              A.offs + (size_t)s * T, recs + e * S_REC_WORDS);
+        }
+      } else {
+        for (int e = warp; e < nq; e += S_WARPS) {
+          const int pl = q_pix[e];
+          const int s = q_traj[e];
+          eval_pair_warp<J>(A.psi, A.phi, A.ep, tx0 + (pl & 31), ty0 + (pl >> 5),
+                            A.offs + (size_t)s * T, recs + e * S_REC_WORDS, lane);
+        }
+      }
+      __syncthreads();
+#pragma unroll 1
+      for (int i = 0; i < S_ROWS; ++i) {
+        const int row = warp * S_ROWS + i;
+        const int pl = (row << 5) | lane;
+        int e = head[pl];
+        if (e < 0) continue;
+        const size_t wp = (size_t)(ty0 + row - A.y_lo) * wx + (size_t)(px - A.x_lo);
+        int nf = s_filled[pl];
+        while (e >= 0) {
+          const uint32_t* rc = recs + e * S_REC_WORDS;
+          const float L = __uint_as_float(rc[0]);
+          if (L >= lh_min) {  // false for NaN (pair not eligible)
+            if (insert_sorted(A, wp, K, mw, nf, L, A.orig[q_traj[e]], rc)) {
+              nf = min(nf + 1, K);
+              atomicAdd(s_ins, 1u);
+            }
+          }
+          e = q_next[e];
+        }
+        head[pl] = -1;
+        s_filled[pl] = (uint8_t)nf;
+        if (nf == K) {
+          const float t2 = admission_threshold(fmaxf(A.out_lh[wp * K + K - 1], lh_min), A.ep);
 #pragma unroll
-      for (int i = 0; i < S_ROWS; ++i)
-#pragma unroll
-        for (int v = 0; v < S_C; ++v) acc[i][v] = 0.0f;
+          for (int ii = 0; ii < S_ROWS; ++ii)
+            if (ii == i) thr2[ii] = t2;
+        }
+      }
+      if (tid == 0) atomicAdd(s_evals, (unsigned int)nq);
+      __syncthreads();
+      if (tid == 0) *s_qcount = 0u;
+      __syncthreads();
+    };
 
+    for (int c = 0; c < A.nchunk; ++c) {
+      __half2 acc[2][S_C];
+#pragma unroll
+      for (int pp = 0; pp < 2; ++pp)
+#pragma unroll
+        for (int v = 0; v < S_C; ++v) acc[pp][v] = __float2half2_rn(0.0f);
+
+      // Stages are released per warp, without a block barrier: the last warp to finish with a
+      // stage issues the copies of the iteration two ahead into it.
       for (int t = 0; t < T; ++t, ++it) {
         const int st = (int)(it & 1);
-        const bool ok = mbar_wait_parity(&bars[st], (uint32_t)((it >> 1) & 1));
-        const int4 b = __ldg(A.box + (size_t)c * T + t);
+        bool ok = *(volatile unsigned int*)s_abort == 0u &&
+                  mbar_wait_parity(&bars[st], (uint32_t)((it >> 1) & 1));
         if (ok) {
-          if (b.w) {
-            const int4* relv = reinterpret_cast<const int4*>(A.rel + ((size_t)c * T + t) * S_C);
-            const char* base = reinterpret_cast<const char*>(stages + st * S_STAGE_FLOATS) +
-                               (size_t)(warp * S_ROWS * S_PITCH + lane) * sizeof(float);
-#pragma unroll
-            for (int vq = 0; vq < S_C / 4; ++vq) {
-              const int4 r4 = __ldg(relv + vq);
-              const int rr[4] = {r4.x, r4.y, r4.z, r4.w};
-#pragma unroll
-              for (int u = 0; u < 4; ++u) {
-                const float* p = reinterpret_cast<const float*>(base + rr[u]);
-#pragma unroll
-                for (int i = 0; i < S_ROWS; ++i) acc[i][vq * 4 + u] += p[i * S_PITCH];
-              }
-            }
+          const PlanRec* slot = &slots[st];
+          const int mode = slot->box.w;
+          if (mode == 1) {
+            accumulate_stage<S_PITCH1>(acc, stages + st * S_STAGE_BYTES, slot, warp, lane);
+          } else if (mode == 2) {
+            accumulate_stage<S_PITCH2>(acc, stages + st * S_STAGE_BYTES, slot, warp, lane);
           } else {
-            const float* bp = A.bound + (size_t)t * A.ep.H * A.Wp;
+            // direct loads from the pair planes (word row = image row + 1)
+            const uint32_t* bp = A.bound + (size_t)t * (A.ep.H + 1) * A.Wp;
 #pragma unroll
             for (int v = 0; v < S_C; ++v) {
               const int2 o = __ldg(A.offs + (size_t)(c * S_C + v) * T + t);
               const int x = px + o.x;
 #pragma unroll
-              for (int i = 0; i < S_ROWS; ++i) {
-                const int y = ty0 + warp * S_ROWS + i + o.y;
-                if (x >= 0 && x < A.Wp && y >= 0 && y < A.ep.H)
-                  acc[i][v] += __ldg(bp + (size_t)y * A.Wp + x);
+              for (int pp = 0; pp < 2; ++pp) {
+                const int r = ty0 + warp * S_ROWS + 2 * pp + o.y + 1;
+                if (x >= 0 && x < A.Wp && r >= 0 && r <= A.ep.H) {
+                  const uint32_t w = __ldg(bp + (size_t)r * A.Wp + x);
+                  acc[pp][v] = __hadd2(acc[pp][v], *reinterpret_cast<const __half2*>(&w));
+                }
               }
             }
           }
+        } else if (lane == 0 && atomicExch(s_abort, 1u) == 0u) {
+          atomicOr(&A.ctrl->err, kErrTimeout);
         }
-        const int bad = __syncthreads_or(ok ? 0 : 1);
-        if (bad) {
-          aborted = true;
-          break;
+        __syncwarp();
+        if (lane == 0) {
+          __threadfence_block();  // this warp's reads of the stage come before its release
+          const unsigned int prev = atomicAdd(&s_done[st], 1u);
+          if (prev == S_WARPS - 1) {
+            s_done[st] = 0u;
+            __threadfence_block();
+            if (it + 2 < total_it && *(volatile unsigned int*)s_abort == 0u) {
+              fence_proxy_async_smem();
+              issue_stage(&tmap64, &tmap128, A, stages + st * S_STAGE_BYTES, &slots[st], &bars[st],
+                          it + 2);
+              s_last[st] = it + 2;
+            }
+          }
         }
-        if (tid == 0 && it + 2 < total_it) {
-          fence_proxy_async_smem();
-          issue_stage(&tmap, A, stages + st * S_STAGE_FLOATS, &bars[st], it + 2);
-        }
+        __syncwarp();
       }
-      if (aborted) break;
 
-      // ---- candidates of this chunk: pairs whose bound reaches the admission threshold ----
+      // ---- pairs whose bound reaches the admission threshold join the queue ----
       const int nv = min(S_C, A.n_traj - c * S_C);
-      uint32_t cb0 = 0u, cb1 = 0u, cb2 = 0u, cb3 = 0u;  // 16 bits per owned pixel
+      const uint32_t vmask = nv >= 32 ? 0xffffffffu : ((1u << nv) - 1u);
+      uint32_t cb[S_ROWS];
       int ncand = 0;
 #pragma unroll
-      for (int i = 0; i < S_ROWS; ++i) {
-        uint32_t bits = 0u;
+      for (int pp = 0; pp < 2; ++pp) {
+        uint32_t b0 = 0u, b1 = 0u;
 #pragma unroll
-        for (int v = 0; v < S_C; ++v)
-          if (((active >> i) & 1u) && v < nv && acc[i][v] >= thr2[i]) bits |= 1u << v;
-        ncand += __popc(bits);
-        const uint32_t sh = bits << ((i & 1) * 16);
-        if ((i >> 1) == 0) cb0 |= sh;
-        else if ((i >> 1) == 1) cb1 |= sh;
-        else if ((i >> 1) == 2) cb2 |= sh;
-        else cb3 |= sh;
+        for (int v = 0; v < S_C; ++v) {
+          const float2 f = __half22float2(acc[pp][v]);
+          if (f.x >= thr2[2 * pp]) b0 |= 1u << v;
+          if (f.y >= thr2[2 * pp + 1]) b1 |= 1u << v;
+        }
+        cb[2 * pp] = ((active >> (2 * pp)) & 1u) ? (b0 & vmask) : 0u;
+        cb[2 * pp + 1] = ((active >> (2 * pp + 1)) & 1u) ? (b1 & vmask) : 0u;
       }
-      // block-wide exclusive rank of this thread's candidates
+#pragma unroll
+      for (int i = 0; i < S_ROWS; ++i) ncand += __popc(cb[i]);
       int incl = ncand;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const int y = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += y;
       }
-      if (tid == 0) *s_qcount = 0u;
+      if (tid == 0) *s_new = 0u;
       __syncthreads();
       unsigned int wbase = 0;
-      if (lane == 31 && incl > 0) wbase = atomicAdd(s_qcount, (unsigned int)incl);
+      if (lane == 31 && incl > 0) wbase = atomicAdd(s_new, (unsigned int)incl);
       wbase = __shfl_sync(0xffffffffu, wbase, 31);
       const int my_base = (int)wbase + incl - ncand;
       __syncthreads();
-      const int total = (int)*s_qcount;
-
-      for (int r0 = 0; r0 < total; r0 += S_QCAP) {
-        // enqueue this round's candidates (bit order: owned pixel, then trajectory)
+      const int new_total = (int)*s_new;
+      int taken = 0;
+      while (taken < new_total) {
+        const int qc = (int)*s_qcount;
+        const int n_this = min(S_QCAP - qc, new_total - taken);
         if (ncand > 0) {
           int rank = my_base;
 #pragma unroll 1
-          for (int w4 = 0; w4 < 4; ++w4) {
-            uint32_t bits = w4 == 0 ? cb0 : w4 == 1 ? cb1 : w4 == 2 ? cb2 : cb3;
+          for (int i = 0; i < S_ROWS; ++i) {
+            uint32_t bits = i == 0 ? cb[0] : i == 1 ? cb[1] : i == 2 ? cb[2] : cb[3];
             while (bits) {
-              const int b = __ffs(bits) - 1;
+              const int v = __ffs(bits) - 1;
               bits &= bits - 1u;
-              if (rank >= r0 && rank < r0 + S_QCAP) {
-                const int i = 2 * w4 + (b >> 4), v = b & 15;
-                queue[rank - r0] = (uint16_t)((((warp * S_ROWS + i) << 5) | lane) << 4 | v);
+              if (rank >= taken && rank < taken + n_this) {
+                const int e = qc + rank - taken;
+                const int pl = ((warp * S_ROWS + i) << 5) | lane;
+                q_traj[e] = c * S_C + v;
+                q_pix[e] = (uint16_t)pl;
+                q_next[e] = (int16_t)atomicExch(&head[pl], e);
               }
               ++rank;
             }
           }
         }
         __syncthreads();
-        const int nq = min(S_QCAP, total - r0);
-        for (int q = warp; q < nq; q += S_WARPS) {
-          const uint32_t e = queue[q];
-          const int v = (int)(e & 15u), pl = (int)(e >> 4);
-          const int x0 = tx0 + (pl & 31), y0 = ty0 + (pl >> 5);
-          eval_pair_warp<J>(A.psi, A.phi, A.ep, x0, y0, A.offs + (size_t)(c * S_C + v) * T,
-                            recs + q * S_REC_WORDS, lane);
-        }
+        if (tid == 0) *s_qcount = (unsigned int)(qc + n_this);
         __syncthreads();
-        // owners insert their results into the output lists
-        if (ncand > 0) {
-          int rank = my_base;
-#pragma unroll 1
-          for (int w4 = 0; w4 < 4; ++w4) {
-            uint32_t bits = w4 == 0 ? cb0 : w4 == 1 ? cb1 : w4 == 2 ? cb2 : cb3;
-            while (bits) {
-              const int b = __ffs(bits) - 1;
-              bits &= bits - 1u;
-              if (rank >= r0 && rank < r0 + S_QCAP) {
-                const int i = 2 * w4 + (b >> 4), v = b & 15;
-                const uint32_t* rc = recs + (rank - r0) * S_REC_WORDS;
-                const float L = __uint_as_float(rc[0]);
-                if (L >= lh_min) {  // false for NaN (pair not eligible)
-                  const int row = warp * S_ROWS + i;
-                  const int j = A.orig[c * S_C + v];
-                  const size_t wp = (size_t)(ty0 + row - A.y_lo) * wx + (size_t)(px - A.x_lo);
-                  const int nf = s_filled[(row << 5) | lane];
-                  if (insert_sorted(A, wp, K, mw, nf, L, j, rc)) {
-                    s_filled[(row << 5) | lane] = (uint8_t)min(nf + 1, K);
-                    atomicAdd(s_ins, 1u);
-                  }
-                }
-              }
-              ++rank;
-            }
-          }
-        }
-        __syncthreads();
+        taken += n_this;
+        if (qc + n_this == S_QCAP) flush();
       }
-      if (tid == 0 && total > 0) atomicAdd(s_evals, (unsigned int)total);
-      // new admission thresholds: once a list is full, its K-th LH' (with the same margin)
-#pragma unroll
-      for (int i = 0; i < S_ROWS; ++i) {
-        const int row = warp * S_ROWS + i;
-        if (((active >> i) & 1u) && s_filled[(row << 5) | lane] == K) {
-          const size_t wp = (size_t)(ty0 + row - A.y_lo) * wx + (size_t)(px - A.x_lo);
-          const float thr = fmaxf(A.out_lh[wp * K + K - 1], lh_min);
-          thr2[i] = thr > 0.0f ? thr * thr * S_PRUNE_MARGIN : -1.0f;
-        }
-      }
+      if ((int)*s_qcount >= S_FLUSH_MIN) flush();
     }
+    if (*s_qcount > 0u) flush();
   }
 
-  if (aborted) {
-    if (tid == 0) {
-      atomicOr(&A.ctrl->err, kErrTimeout);
-      // wait (bounded) for copies still in flight into either stage before leaving
-      mbar_wait_parity(&bars[it & 1], (uint32_t)((it >> 1) & 1));
-      mbar_wait_parity(&bars[(it + 1) & 1], (uint32_t)(((it + 1) >> 1) & 1));
-    }
-    return;
-  }
   __syncthreads();
+  if (*(volatile unsigned int*)s_abort != 0u && tid == 0) {
+    // a wait gave up: wait (bounded) for the last copies issued into each stage
+    for (int sidx = 0; sidx < 2; ++sidx)
+      if (s_last[sidx] < total_it)
+        mbar_wait_parity(&bars[sidx], (uint32_t)((s_last[sidx] >> 1) & 1));
+  }
   if (tid == 0) {
     atomicAdd(&A.ctrl->evals, (unsigned long long)*s_evals);
     atomicAdd(&A.ctrl->inserts, (unsigned long long)*s_ins);
@@ -884,9 +1125,8 @@ extern "C" int kb_search(const float* psi, const float* phi, const double* times
   int32_t* sorted = reinterpret_cast<int32_t*>(ws + L.sorted);
   int32_t* orig = reinterpret_cast<int32_t*>(ws + L.orig);
   int2* offs = reinterpret_cast<int2*>(ws + L.offs);
-  int4* box = reinterpret_cast<int4*>(ws + L.box);
-  int32_t* rel = reinterpret_cast<int32_t*>(ws + L.rel);
-  float* bound = reinterpret_cast<float*>(ws + L.bound);
+  PlanRec* plan = reinterpret_cast<PlanRec*>(ws + L.plan);
+  uint32_t* bound = reinterpret_cast<uint32_t*>(ws + L.bound);
 
   SearchConsts cs{};
   for (int t = 0; t < T; ++t) cs.dt[t] = (float)(times[t] - times[0]);
@@ -909,25 +1149,26 @@ extern "C" int kb_search(const float* psi, const float* phi, const double* times
   plan_offsets_kernel<<<(L.n_pad + 255) / 256, 256, 0, st>>>(vx, vy, sorted, n_traj, L.n_pad, T,
                                                                cs, orig, offs);
   KB_LAUNCH_CHECK("plan_offsets_kernel");
-  plan_boxes_kernel<<<(L.nchunk * T + 255) / 256, 256, 0, st>>>(offs, L.nchunk, T, p->x_lo, box, rel);
+  plan_boxes_kernel<<<(L.nchunk * T + 255) / 256, 256, 0, st>>>(offs, L.nchunk, T, p->x_lo, plan);
   KB_LAUNCH_CHECK("plan_boxes_kernel");
   {
-    size_t total = (size_t)T * H * L.Wp;
+    size_t total = (size_t)T * (H + 1) * L.Wp;
     int blocks = (int)std::min<size_t>((total + 255) / 256, (size_t)g_num_sms * 16);
     bound_prep_kernel<<<blocks, 256, 0, st>>>(psi, phi, T, H, W, L.Wp, bound);
     KB_LAUNCH_CHECK("bound_prep_kernel");
   }
 
-  CUtensorMap tmap;
-  {
-    cuuint64_t dims[3] = {(cuuint64_t)L.Wp, (cuuint64_t)H, (cuuint64_t)T};
-    cuuint64_t strides[2] = {(cuuint64_t)L.Wp * sizeof(float), (cuuint64_t)L.Wp * H * sizeof(float)};
-    cuuint32_t boxd[3] = {(cuuint32_t)S_PITCH, (cuuint32_t)S_BOX_Y, 1u};
+  CUtensorMap tmap64, tmap128;
+  for (int m = 0; m < 2; ++m) {
+    cuuint64_t dims[3] = {(cuuint64_t)L.Wp, (cuuint64_t)H + 1, (cuuint64_t)T};
+    cuuint64_t strides[2] = {(cuuint64_t)L.Wp * 4, (cuuint64_t)L.Wp * (H + 1) * 4};
+    cuuint32_t boxd[3] = {(cuuint32_t)(m == 0 ? S_PITCH1 : S_PITCH2), (cuuint32_t)S_BOX_Y, 1u};
     cuuint32_t estr[3] = {1u, 1u, 1u};
-    CUresult r = enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, bound, dims, strides, boxd, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+    CUresult r = enc(m == 0 ? &tmap64 : &tmap128, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, bound, dims,
+                     strides, boxd, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return fail(KB_ERR_CUDA, "kb_search: cuTensorMapEncodeTiled failed (%d)", (int)r);
+    if (r != CUDA_SUCCESS)
+      return fail(KB_ERR_CUDA, "kb_search: cuTensorMapEncodeTiled failed (%d)", (int)r);
   }
 
   SearchArgs A{};
@@ -936,8 +1177,7 @@ extern "C" int kb_search(const float* psi, const float* phi, const double* times
   A.bound = bound;
   A.orig = orig;
   A.offs = offs;
-  A.box = box;
-  A.rel = rel;
+  A.plan = plan;
   A.out_lh = out_lh;
   A.out_flux = out_flux;
   A.out_idx = out_idx;
@@ -961,6 +1201,8 @@ extern "C" int kb_search(const float* psi, const float* phi, const double* times
                                                              erfinv_newton(2.0 * p->q_lo - 1.0))))
                          : 0.0f;
   A.ep.lh_min = p->lh_min;
+  A.ep.prune_scale = (float)(1.0 / (std::pow(1.0 + std::ldexp(1.0, -11), T) * (1.0 + 3e-7)));
+  A.ep.prune_slack = (float)(T * std::ldexp(1.0, -25) * 2.0);
   A.n_traj = n_traj;
   A.nchunk = L.nchunk;
   A.Wp = L.Wp;
@@ -973,19 +1215,19 @@ extern "C" int kb_search(const float* psi, const float* phi, const double* times
   A.ntiles = A.ntx * A.nty;
   const int grid = std::min(A.ntiles, g_num_sms);
   const size_t smem = SmemLayout::total;
-  const int J = (T + 31) / 32;
-#define KB_SEARCH_LAUNCH(JJ)                                                                   \
+#define KB_SEARCH_LAUNCH(NT, JJ)                                                               \
   do {                                                                                         \
-    KB_CUDA_TRY(cudaFuncSetAttribute(search_kernel<JJ>,                                        \
+    KB_CUDA_TRY(cudaFuncSetAttribute(search_kernel<NT, JJ>,                                    \
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-    search_kernel<JJ><<<grid, S_THREADS, smem, st>>>(tmap, A);                                 \
+    search_kernel<NT, JJ><<<grid, S_THREADS, smem, st>>>(tmap64, tmap128, A);                             \
   } while (0)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   profile_events(&ev0, &ev1);
   if (ev0 && ev1) KB_CUDA_TRY(cudaEventRecord(ev0, st));
-  if (J == 1) KB_SEARCH_LAUNCH(1);
-  else if (J == 2) KB_SEARCH_LAUNCH(2);
-  else KB_SEARCH_LAUNCH(4);
+  if (T <= 16) KB_SEARCH_LAUNCH(16, 1);
+  else if (T <= 32) KB_SEARCH_LAUNCH(32, 1);
+  else if (T <= 64) KB_SEARCH_LAUNCH(0, 2);
+  else KB_SEARCH_LAUNCH(0, 4);
 #undef KB_SEARCH_LAUNCH
   KB_LAUNCH_CHECK("search_kernel");
   if (ev0 && ev1) KB_CUDA_TRY(cudaEventRecord(ev1, st));
