@@ -43,9 +43,9 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 // Device error flag bits (kb_search_stats()[3]).
 constexpr unsigned int kErrTimeout = 0x1u;
 
-// Bounded spin limit for mbarrier waits: try_wait suspends for a hardware-chosen interval per
-// attempt, so this bounds the wait at well over a second but keeps it finite.
-constexpr uint32_t kMaxWaitTries = 1u << 22;
+// Every device-side wait is bounded in time: after this many nanoseconds of %globaltimer the
+// waiter gives up, records an error flag and stops using the buffer it waited for.
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;
 
 // ---------------------------------------------------------------------------------------------
 // Device helpers
@@ -79,22 +79,34 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
                : "memory");
 }
 
-// Returns true once the phase with the given parity has completed, false if the bounded number
-// of attempts ran out (the caller records kErrTimeout and stops using the buffer).
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return done != 0u;
+}
+
+// Returns true once the phase with the given parity has completed, false after kWaitLimitNs
+// (the caller records the timeout and stops using the buffer).  Each attempt may suspend the
+// thread for up to 20 us, so a waiting warp issues few instructions.
 __device__ __forceinline__ bool mbar_wait_parity(uint64_t* bar, uint32_t parity) {
-  uint32_t addr = smem_u32(bar);
-  for (uint32_t i = 0; i < kMaxWaitTries; ++i) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(addr), "r"(parity)
-        : "memory");
-    if (done) return true;
+  if (mbar_try_wait(bar, parity, 20000u)) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  for (;;) {
+    if (mbar_try_wait(bar, parity, 20000u)) return true;
+    if (globaltimer_ns() - t0 > kWaitLimitNs) return false;
   }
-  return false;
 }
 
 // 3-D tiled TMA load (global -> shared), completion signalled on an mbarrier as tx bytes.

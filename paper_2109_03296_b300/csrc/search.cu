@@ -54,29 +54,39 @@ namespace kb {
 // Compile-time configuration of the search kernel
 // ---------------------------------------------------------------------------------------------
 constexpr int S_TX = 32;                 // tile width (lane = x)
-constexpr int S_ROWS = 4;                // rows per thread (two row pairs)
-constexpr int S_WARPS = 16;
-constexpr int S_THREADS = S_WARPS * 32;  // 512
-constexpr int S_TY = S_WARPS * S_ROWS;   // 64
-constexpr int S_NPIX = S_TX * S_TY;      // 2048 start pixels per tile
+constexpr int S_ROWS = 4;                // rows per consumer thread (two row pairs)
+constexpr int S_CWARPS = 14;             // consumer warps
+constexpr int S_PWARPS = 2;              // producer warps: iteration `it` belongs to it % S_PWARPS
+constexpr int S_CTHREADS = S_CWARPS * 32;
+constexpr int S_THREADS = (S_CWARPS + S_PWARPS) * 32;
+constexpr int S_TY = S_CWARPS * S_ROWS;  // 56
+constexpr int S_NPIX = S_TX * S_TY;      // 1792 start pixels per tile
 constexpr int S_C = 32;                  // trajectories per chunk
-constexpr int S_BOX_Y = 8;               // TMA box height (word rows)
-constexpr int S_STAGE_BYTES = 65536;     // one pipeline stage
-constexpr int S_QCAP = 1024;             // queued full evaluations
-constexpr int S_FLUSH_MIN = 512;         // evaluate the queue once it holds this many
+constexpr int S_D = 8;                   // pipeline slots (iterations in flight), S_D % S_PWARPS == 0
+constexpr int S_ARENA_BYTES = 168 * 1024;  // rings of staged rectangles, one per producer
+constexpr int S_RING_BYTES = S_ARENA_BYTES / S_PWARPS;
+constexpr int S_REGION_MAX = 64 * 1024;  // larger rectangles use direct loads
+constexpr int S_QCAP = 1024;             // block queue of full evaluations
+constexpr int S_FLUSH_MIN = S_CTHREADS;  // evaluate the queue once it holds one pair per thread
 constexpr int S_REC_WORDS = 8;           // L', alpha, nvalid|nkept<<16, mask[4], pad
 constexpr float S_PRUNE_MARGIN = 1.0f - 1e-4f;
-// staging modes of a (chunk, epoch): 0 = direct global loads, 1 = 64-word rows, 2 = 128-word rows
-constexpr int S_PITCH1 = 64, S_PITCH2 = 128;
+static_assert(S_D % S_PWARPS == 0 && S_REGION_MAX <= S_RING_BYTES, "pipeline configuration");
+// A staged rectangle is one TMA box: width class w = 1..4 (rows of 48/64/96/128 words) and
+// height class h = 0..4 (64/80/96/112/128 word rows); mode 0 = direct global loads.
+constexpr int S_NW = 4, S_NH = 5;
+__host__ __device__ constexpr int stage_width(int mode) {
+  return mode == 1 ? 48 : mode == 2 ? 64 : mode == 3 ? 96 : 128;
+}
+__host__ __device__ constexpr int stage_height(int h) { return 64 + 16 * h; }
 
 constexpr int HILBERT_BITS = 8;          // 256 x 256 velocity cells
 constexpr int N_CELLS = 1 << (2 * HILBERT_BITS);
 
 // Staging plan of one (chunk, epoch): the rectangle and the 32 per-trajectory byte offsets
-// into it.  Copied into shared memory with the stage it describes.
+// into it.  Copied into shared memory with the rectangle it describes.
 struct __align__(16) PlanRec {
-  int4 box;           // x offset, y offset, 8-row boxes, mode (0 direct, 1 pitch 64, 2 pitch 128)
-  int32_t rel[32];    // byte offset of each trajectory's footprint in the stage
+  int4 box;           // x offset, y offset, height class, mode (0 direct loads, 1..4 row width)
+  int32_t rel[32];    // byte offset of each trajectory's footprint in the staged rectangle
 };
 static_assert(sizeof(PlanRec) == 144, "plan record layout");
 
@@ -124,7 +134,7 @@ static WsLayout ws_layout(int T, int H, int W, int n_traj) {
 // ctrl block: [0] error flags (u32), [8] stats: te, evals, inserts (u64 each)
 struct Ctrl {
   unsigned int err;
-  unsigned int pad;
+  unsigned int tile_counter;  // dynamic tile scheduling of the search kernel
   unsigned long long te, evals, inserts;
 };
 
@@ -136,6 +146,7 @@ __global__ void plan_reset_kernel(Ctrl* ctrl, uint32_t* counts, unsigned long lo
   if (i < N_CELLS) counts[i] = 0u;
   if (i == 0) {
     ctrl->err = 0u;
+    ctrl->tile_counter = 0u;
     ctrl->te = te;
     ctrl->evals = 0ull;
     ctrl->inserts = 0ull;
@@ -280,8 +291,9 @@ __global__ void plan_offsets_kernel(const float* __restrict__ vx, const float* _
 
 // One thread per (chunk, epoch): staging rectangle and per-trajectory byte offsets into it.
 // box = {x offset of the rectangle from the tile origin (x_lo + dxmin - xshift is a multiple
-// of 4 so that the TMA x coordinate is 16-byte aligned), y offset, number of 8-row boxes, mode}
-// with mode 1 = 64-word rows, 2 = 128-word rows, 0 = too large for a stage (direct loads).
+// of 4 so that the TMA x coordinate is 16-byte aligned), y offset, height class, mode} with
+// mode 1..4 = rows of 48/64/96/128 words: the narrowest, then lowest, TMA box that holds the
+// rectangle; mode 0 = no box within S_REGION_MAX (direct loads).
 __global__ void plan_boxes_kernel(const int2* __restrict__ offs, int nchunk, int T, int x_lo,
                                   PlanRec* plan) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -297,17 +309,18 @@ __global__ void plan_boxes_kernel(const int2* __restrict__ offs, int nchunk, int
   const int xshift = ((x_lo + dxmin) % 4 + 4) % 4;
   const int rw = S_TX + (dxmax - dxmin) + xshift;
   const int rh = S_TY + (dymax - dymin);
-  const int nb = (rh + S_BOX_Y - 1) / S_BOX_Y;
-  int mode = 0, pitch = 0;
-  if (rw <= S_PITCH1 && nb * S_BOX_Y * S_PITCH1 * 4 <= S_STAGE_BYTES) {
-    mode = 1;
-    pitch = S_PITCH1;
-  } else if (rw <= S_PITCH2 && nb * S_BOX_Y * S_PITCH2 * 4 <= S_STAGE_BYTES) {
-    mode = 2;
-    pitch = S_PITCH2;
-  }
+  int mode = 0, pitch = 0, hcls = 0;
+  for (int m = 1; m <= S_NW && !mode; ++m)
+    for (int h = 0; h < S_NH; ++h)
+      if (rw <= stage_width(m) && rh <= stage_height(h) &&
+          stage_width(m) * stage_height(h) * 4 <= S_REGION_MAX) {
+        mode = m;
+        pitch = stage_width(m);
+        hcls = h;
+        break;
+      }
   PlanRec& pr = plan[i];
-  pr.box = make_int4(dxmin - xshift, dymin, nb, mode);
+  pr.box = make_int4(dxmin - xshift, dymin, hcls, mode);
   for (int v = 0; v < S_C; ++v) {
     int2 o = offs[(size_t)(c * S_C + v) * T + t];
     pr.rel[v] = mode ? ((o.y - dymin) * pitch + (o.x - dxmin + xshift)) * 4 : 0;
@@ -632,19 +645,27 @@ struct SearchArgs {
   int x_lo, x_hi, y_lo, y_hi, ntx, nty, ntiles;
 };
 
+struct TmapSet {
+  CUtensorMap m[S_NW * S_NH];  // box (width class w, height class h) at m[(w-1)*S_NH + h]
+};
+
 struct SmemLayout {
-  static constexpr size_t stage = 0;  // 2 stages
-  static constexpr size_t rec = stage + 2 * (size_t)S_STAGE_BYTES;
+  static constexpr size_t arena = 0;
+  static constexpr size_t rec = arena + S_ARENA_BYTES;             // [S_QCAP][S_REC_WORDS]
   static constexpr size_t qtraj = rec + S_QCAP * S_REC_WORDS * sizeof(uint32_t);
   static constexpr size_t qpix = qtraj + S_QCAP * sizeof(int32_t);
   static constexpr size_t qnext = qpix + S_QCAP * sizeof(uint16_t);
-  static constexpr size_t head = qnext + S_QCAP * sizeof(int16_t);
-  static constexpr size_t filled = head + S_NPIX * sizeof(int32_t);
-  static constexpr size_t planslot = filled + S_NPIX;           // 2 x PlanRec (16-B aligned)
-  static constexpr size_t misc = planslot + 2 * sizeof(PlanRec);
+  static constexpr size_t head = qnext + S_QCAP * sizeof(int16_t);  // [pixel] list of queued pairs
+  static constexpr size_t filled = head + S_NPIX * sizeof(int16_t);
+  static constexpr size_t slots = (filled + S_NPIX + 15) / 16 * 16;          // S_D plan records
+  static constexpr size_t sinfo = slots + S_D * sizeof(PlanRec);  // S_D x {offset, tile, bytes}
+  static constexpr size_t full = sinfo + S_D * sizeof(int4);       // S_D mbarriers: data landed
+  static constexpr size_t empty = full + S_D * sizeof(uint64_t);   // S_D mbarriers: slot released
+  static constexpr size_t misc = empty + S_D * sizeof(uint64_t);
   static constexpr size_t total = misc + 64;
 };
-static_assert(SmemLayout::planslot % 16 == 0, "plan slots must be 16-byte aligned");
+static_assert(SmemLayout::total <= 232448, "shared memory budget");
+static_assert(SmemLayout::slots % 16 == 0 && SmemLayout::full % 8 == 0, "alignment");
 
 // Admission threshold of a pixel for the fp16 bound sums.  With every stored term rounded up,
 // an RN fp16 sum of T non-negative terms satisfies  exact <= sum (1 + 2^-11)^T + T 2^-25  (the
@@ -656,31 +677,184 @@ __device__ __forceinline__ float admission_threshold(float thr, const EvalParams
   return (thr * thr * S_PRUNE_MARGIN - ep.prune_slack) * ep.prune_scale;
 }
 
-// Issues the copies of iteration `it` (tile, chunk, epoch) of this block into one stage: the plan
-// record (always) and, in modes 1/2, the rectangle of fp16 pair words.
-__device__ __forceinline__ void issue_stage(const CUtensorMap* tmap64, const CUtensorMap* tmap128,
-                                            const SearchArgs& A, unsigned char* stage,
-                                            PlanRec* slot, uint64_t* bar, long long it) {
-  const int T = A.ep.T;
-  const long long per_tile = (long long)A.nchunk * T;
-  const int k = (int)(it / per_tile);
-  const int rem = (int)(it - (long long)k * per_tile);
-  const int c = rem / T, t = rem - c * T;
-  const int tile = blockIdx.x + k * gridDim.x;
-  const int tx0 = A.x_lo + (tile % A.ntx) * S_TX;
-  const int ty0 = A.y_lo + (tile / A.ntx) * S_TY;
-  const PlanRec* pr = A.plan + (size_t)c * T + t;
-  const int4 b = __ldg(&pr->box);
-  const int pitch = b.w == 1 ? S_PITCH1 : S_PITCH2;
-  const int box_bytes = S_BOX_Y * pitch * 4;
-  mbar_arrive_expect_tx(bar, (uint32_t)(sizeof(PlanRec) + (b.w ? b.z * box_bytes : 0)));
-  bulk_copy_g2s(slot, pr, (uint32_t)sizeof(PlanRec), bar);
-  if (b.w) {
-    const CUtensorMap* tm = b.w == 1 ? tmap64 : tmap128;
-    // word row r = image row + 1 (the pair planes carry one leading row)
-    for (int i = 0; i < b.z; ++i)
-      tma_load_3d(stage + i * box_bytes, tm, bar, tx0 + b.x, ty0 + b.y + 1 + i * S_BOX_Y, t);
+// The largest fp16 value <= x (admission thresholds are compared in fp16; rounding them down
+// keeps every pair the fp32 test would keep).
+__device__ __forceinline__ __half half_round_down(float x) {
+  __half h = __float2half_rn(x);
+  if (__half2float(h) > x) {
+    unsigned short u = __half_as_ushort(h);
+    u = (u & 0x8000u) ? (unsigned short)(u + 1u) : (unsigned short)(u - 1u);
+    h = __ushort_as_half(u);
   }
+  return h;
+}
+
+__device__ __forceinline__ void consumer_sync() {
+  asm volatile("bar.sync 1, %0;" ::"r"(S_CTHREADS) : "memory");
+}
+
+// Barrier of the consumer threads that returns whether any of them passed pred != 0.
+__device__ __forceinline__ bool consumer_sync_or(int pred) {
+  int r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.s32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, 1, %2, p;\n\tselp.s32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"(pred), "r"(S_CTHREADS)
+      : "memory");
+  return r != 0;
+}
+
+// Shared tile sequence of the producers: producer 0 takes tiles from the global counter and
+// publishes them; the others read them in the same order.
+struct TileRing {
+  int tile[4];
+  unsigned int published;
+};
+
+// Producer warp p (all lanes run the same control flow; lane 0 issues) handles the iterations
+// it with it % S_PWARPS == p: for each, it retires its own released iterations (in order,
+// waiting on their 'empty' barriers) until its slot and room in its own arena ring are free,
+// writes the plan record and copies the staged rectangle (one TMA box).  Each producer issuing
+// its own TMA operations keeps the per-thread issue cost of TMA off the critical path.  The plan
+// records of the next 32 iterations are loaded by the 32 lanes at once.  The slot after the last
+// tile carries tile -1.
+__device__ void producer_loop(const TmapSet& maps, const SearchArgs& A, unsigned char* ring,
+                              int ring_base, PlanRec* slots, int4* sinfo, uint64_t* full,
+                              uint64_t* empty, unsigned int* s_abort, TileRing* tr,
+                              long long* issued_out, int pw, int lane) {
+  const int T = A.ep.T;
+  const int n_it_tile = A.nchunk * T;
+  long long it_base = 0;        // global iteration number of the current tile's first iteration
+  long long oldest = pw;        // oldest unretired iteration of this producer
+  long long last_issued = -1;
+  int head = 0, tail = 0, live = 0;  // ring: [tail, head) cyclically, `live` regions
+  for (int k = 0;; ++k) {
+    int tile = 0;
+    if (pw == 0) {
+      if (lane == 0) {
+        tile = (int)atomicAdd(&A.ctrl->tile_counter, 1u);
+        tr->tile[k & 3] = tile;
+        __threadfence_block();
+        *(volatile unsigned int*)&tr->published = (unsigned int)(k + 1);
+      }
+    } else if (lane == 0) {
+      const unsigned long long t0 = globaltimer_ns();
+      while (*(volatile unsigned int*)&tr->published <= (unsigned int)k) {
+        if (*(volatile unsigned int*)s_abort != 0u || globaltimer_ns() - t0 > kWaitLimitNs) {
+          tile = -2;
+          break;
+        }
+        __nanosleep(32);
+      }
+      if (tile != -2) {
+        __threadfence_block();
+        tile = *(volatile int*)&tr->tile[k & 3];
+      }
+    }
+    tile = __shfl_sync(0xffffffffu, tile, 0);
+    if (tile == -2) {
+      if (lane == 0 && atomicExch(s_abort, 1u) == 0u) atomicOr(&A.ctrl->err, kErrTimeout);
+      break;
+    }
+    const bool last = tile >= A.ntiles;
+    const int n_it = last ? 1 : n_it_tile;
+    const int tx0 = last ? 0 : A.x_lo + (tile % A.ntx) * S_TX;
+    const int ty0 = last ? 0 : A.y_lo + (tile / A.ntx) * S_TY;
+    // this producer's iterations of the tile: q = first_q, first_q + S_PWARPS, ...
+    const int first_q = (int)(((pw - it_base) % S_PWARPS + S_PWARPS) % S_PWARPS);
+    for (int qb = first_q; qb < n_it; qb += 32 * S_PWARPS) {
+      int4 rec[sizeof(PlanRec) / 16];
+#pragma unroll
+      for (int i = 0; i < (int)(sizeof(PlanRec) / 16); ++i) rec[i] = make_int4(0, 0, 0, 0);
+      const int my_q = qb + lane * S_PWARPS;
+      if (!last && my_q < n_it) {
+        const int4* src = reinterpret_cast<const int4*>(A.plan + my_q);
+#pragma unroll
+        for (int i = 0; i < (int)(sizeof(PlanRec) / 16); ++i) rec[i] = __ldg(src + i);
+      }
+      const int4 mine = rec[0];
+      for (int kk = 0; kk < 32; ++kk) {
+        const int q = qb + kk * S_PWARPS;
+        if (q >= n_it) break;
+        const long long it = it_base + q;
+        const int t = q % T;
+        const int slot = (int)(it % S_D);
+        int4 b;
+        b.x = __shfl_sync(0xffffffffu, mine.x, kk);
+        b.y = __shfl_sync(0xffffffffu, mine.y, kk);
+        b.z = __shfl_sync(0xffffffffu, mine.z, kk);
+        b.w = __shfl_sync(0xffffffffu, mine.w, kk);
+        const int sz = (!last && b.w) ? stage_width(b.w) * stage_height(b.z) * 4 : 0;
+        int pos = 0;
+        for (;;) {
+          bool room = it - oldest < S_D;
+          if (room && sz > 0) {
+            if (live == 0) {
+              head = tail = 0;
+              pos = 0;
+            } else if (head > tail) {
+              if (head + sz <= S_RING_BYTES) pos = head;
+              else if (sz <= tail) pos = 0;
+              else room = false;
+            } else if (head + sz <= tail) {
+              pos = head;
+            } else {
+              room = false;
+            }
+          }
+          if (room) break;
+          // retire this producer's oldest iteration once every consumer warp has released it
+          const bool ok = *(volatile unsigned int*)s_abort == 0u &&
+                          mbar_wait_parity(&empty[oldest % S_D], (uint32_t)((oldest / S_D) & 1));
+          if (!__all_sync(0xffffffffu, ok)) {
+            if (lane == 0 && atomicExch(s_abort, 1u) == 0u) atomicOr(&A.ctrl->err, kErrTimeout);
+            *issued_out = last_issued;
+            return;
+          }
+          const int4 so = sinfo[oldest % S_D];
+          if (so.z > 0) {
+            --live;
+            for (long long j = oldest + S_PWARPS; j < it; j += S_PWARPS) {
+              const int4 sj = sinfo[j % S_D];
+              if (sj.z > 0) {
+                tail = sj.x - ring_base;
+                break;
+              }
+            }
+          }
+          oldest += S_PWARPS;
+        }
+        if (sz > 0) {
+          if (live == 0) tail = pos;
+          head = pos + sz;
+          ++live;
+        }
+        __syncwarp();  // every lane has read sinfo before this slot is rewritten
+        if (!last && lane == kk) {  // the plan record, from the registers of the lane holding it
+          int4* dst = reinterpret_cast<int4*>(&slots[slot]);
+#pragma unroll
+          for (int i = 0; i < (int)(sizeof(PlanRec) / 16); ++i) dst[i] = rec[i];
+        }
+        __syncwarp();
+        if (lane == 0) {
+          sinfo[slot] = make_int4(ring_base + pos, last ? -1 : tile, sz, 0);
+          if (sz == 0) {
+            mbar_arrive(&full[slot]);
+          } else {  // word row r = image row + 1 (the pair planes carry one leading row)
+            mbar_arrive_expect_tx(&full[slot], (uint32_t)sz);
+            tma_load_3d(ring + pos, &maps.m[(b.w - 1) * S_NH + b.z], &full[slot], tx0 + b.x,
+                        ty0 + b.y + 1, t);
+          }
+        }
+        last_issued = it;
+        __syncwarp();
+      }
+    }
+    it_base += n_it;
+    if (last) break;
+  }
+  *issued_out = last_issued;
 }
 
 // Sums one staged (chunk, epoch) into the fp16 row-pair accumulators.
@@ -737,276 +911,283 @@ __device__ __noinline__ bool insert_sorted(const SearchArgs& A, size_t wp, int K
 // NT == 0: warp-per-pair evaluation with J epochs per lane (32 < T <= 32 J).
 template <int NT, int J>
 __global__ void __launch_bounds__(S_THREADS, 1)
-search_kernel(const __grid_constant__ CUtensorMap tmap64, const __grid_constant__ CUtensorMap tmap128,
-              const SearchArgs A) {
+search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* stages = smem + SmemLayout::stage;
+  unsigned char* arena = smem + SmemLayout::arena;
   uint32_t* recs = reinterpret_cast<uint32_t*>(smem + SmemLayout::rec);
   int32_t* q_traj = reinterpret_cast<int32_t*>(smem + SmemLayout::qtraj);
   uint16_t* q_pix = reinterpret_cast<uint16_t*>(smem + SmemLayout::qpix);
   int16_t* q_next = reinterpret_cast<int16_t*>(smem + SmemLayout::qnext);
-  int32_t* head = reinterpret_cast<int32_t*>(smem + SmemLayout::head);
+  PlanRec* slots = reinterpret_cast<PlanRec*>(smem + SmemLayout::slots);
+  int4* sinfo = reinterpret_cast<int4*>(smem + SmemLayout::sinfo);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + SmemLayout::full);
+  uint64_t* empty = reinterpret_cast<uint64_t*>(smem + SmemLayout::empty);
+  int16_t* head = reinterpret_cast<int16_t*>(smem + SmemLayout::head);
   uint8_t* s_filled = reinterpret_cast<uint8_t*>(smem + SmemLayout::filled);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + SmemLayout::misc);
-  unsigned int* s_qcount = reinterpret_cast<unsigned int*>(smem + SmemLayout::misc + 16);
-  unsigned int* s_new = s_qcount + 1;
-  unsigned int* s_evals = s_qcount + 2;
-  unsigned int* s_ins = s_qcount + 3;
-  unsigned int* s_done = s_qcount + 4;   // [2]: warps finished with each stage
-  unsigned int* s_abort = s_qcount + 6;  // a bounded wait gave up: stop using the stages
-  long long* s_last = reinterpret_cast<long long*>(smem + SmemLayout::misc + 48);  // [2]
-  PlanRec* slots = reinterpret_cast<PlanRec*>(smem + SmemLayout::planslot);
+  unsigned int* s_qcount = reinterpret_cast<unsigned int*>(smem + SmemLayout::misc);
+  unsigned int* s_evals = s_qcount + 1;
+  unsigned int* s_ins = s_qcount + 2;
+  unsigned int* s_abort = s_qcount + 3;
+  int* s_tile = reinterpret_cast<int*>(s_qcount + 4);
+  TileRing* tr = reinterpret_cast<TileRing*>(s_qcount + 5);       // 20 bytes
+  long long* s_issued = reinterpret_cast<long long*>(smem + SmemLayout::misc + 48);  // [2]
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int T = A.ep.T, K = A.ep.K, mw = A.ep.mw;
-  const int my_tiles = (A.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
-  const long long per_tile = (long long)A.nchunk * T;
-  const long long total_it = (long long)my_tiles * per_tile;
 
   for (int i = tid; i < S_NPIX; i += S_THREADS) head[i] = -1;
   if (tid == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
+    for (int i = 0; i < S_D; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], S_CWARPS);
+    }
     *s_qcount = 0u;
-    *s_new = 0u;
     *s_evals = 0u;
     *s_ins = 0u;
-    s_done[0] = s_done[1] = 0u;
     *s_abort = 0u;
-    s_last[0] = 0;
-    s_last[1] = 1;
+    *s_tile = -1;
+    tr->published = 0u;
+    s_issued[0] = s_issued[1] = -1;
     fence_mbar_init();
-    prefetch_tmap(&tmap64);
-    prefetch_tmap(&tmap128);
   }
   __syncthreads();
-  if (tid == 0) {
-    if (total_it > 0) issue_stage(&tmap64, &tmap128, A, stages, &slots[0], &bars[0], 0);
-    if (total_it > 1)
-      issue_stage(&tmap64, &tmap128, A, stages + S_STAGE_BYTES, &slots[1], &bars[1], 1);
-  }
 
-  const float lh_min = A.ep.lh_min;
-  const size_t wx = (size_t)(A.x_hi - A.x_lo);
-  long long it = 0;
-
-  for (int k = 0; k < my_tiles; ++k) {
-    const int tile = blockIdx.x + k * gridDim.x;
-    const int tx0 = A.x_lo + (tile % A.ntx) * S_TX;
-    const int ty0 = A.y_lo + (tile / A.ntx) * S_TY;
-    const int px = tx0 + lane;
-    float thr2[S_ROWS];
-    uint32_t active = 0u;
+  if (warp >= S_CWARPS) {
+    // ------------------------------- producer warps --------------------------------------
+    const int pw = warp - S_CWARPS;
+    if (pw == 0 && lane < S_NW * S_NH) prefetch_tmap(&maps.m[lane]);
+    long long issued = -1;
+    producer_loop(maps, A, arena + pw * S_RING_BYTES, pw * S_RING_BYTES, slots, sinfo, full,
+                  empty, s_abort, tr, &issued, pw, lane);
+    if (lane == 0) s_issued[pw] = issued;
+  } else {
+    // ------------------------------- consumer warps --------------------------------------
+    const float lh_min = A.ep.lh_min;
+    const size_t wx = (size_t)(A.x_hi - A.x_lo);
+    long long it = 0;
+    for (;;) {
+      // the first slot of the next tile names it (-1: none left); decided by one thread
+      consumer_sync();
+      if (tid == 0) {
+        const int slot0 = (int)(it % S_D);
+        const bool ok = *(volatile unsigned int*)s_abort == 0u &&
+                        mbar_wait_parity(&full[slot0], (uint32_t)((it / S_D) & 1));
+        if (!ok && atomicExch(s_abort, 1u) == 0u) atomicOr(&A.ctrl->err, kErrTimeout);
+        *s_tile = ok ? sinfo[slot0].y : -1;
+      }
+      consumer_sync();
+      const int tile = *s_tile;
+      if (tile < 0) break;
+      const int tx0 = A.x_lo + (tile % A.ntx) * S_TX;
+      const int ty0 = A.y_lo + (tile / A.ntx) * S_TY;
+      const int px = tx0 + lane;
+      float thr2[S_ROWS];
+      uint32_t active = 0u;
 #pragma unroll
-    for (int i = 0; i < S_ROWS; ++i) {
-      const int row = warp * S_ROWS + i;
-      const int py = ty0 + row;
-      const bool act = px < A.x_hi && py < A.y_hi;
-      active |= (act ? 1u : 0u) << i;
-      s_filled[(row << 5) | lane] = 0;
-      thr2[i] = admission_threshold(lh_min, A.ep);
-      if (act) {
-        const size_t wp = (size_t)(py - A.y_lo) * wx + (size_t)(px - A.x_lo);
-        for (int s = 0; s < K; ++s) {
-          A.out_lh[wp * K + s] = -INFINITY;
-          A.out_flux[wp * K + s] = 0.0f;
-          A.out_idx[wp * K + s] = -1;
-          A.out_nvalid[wp * K + s] = 0;
-          A.out_nkept[wp * K + s] = 0;
-          for (int m = 0; m < mw; ++m) A.out_mask[(wp * K + s) * mw + m] = 0u;
-        }
-      }
-    }
-
-    // Evaluate every queued pair, insert the results, reset the queue.  Called by all threads
-    // right after a barrier.
-    auto flush = [&]() {
-      const int nq = (int)*s_qcount;
-      if (NT > 0) {
-        for (int e = tid; e < nq; e += S_THREADS) {
-          const int pl = q_pix[e];
-          const int s = q_traj[e];
-          eval_pair_thread<(NT > 0 ? NT : 1)>(A.psi, A.phi, A.ep, tx0 + (pl & 31), ty0 + (pl >> 5),
-                                              A.offs + (size_t)s * T, recs + e * S_REC_WORDS);
-        }
-      } else {
-        for (int e = warp; e < nq; e += S_WARPS) {
-          const int pl = q_pix[e];
-          const int s = q_traj[e];
-          eval_pair_warp<J>(A.psi, A.phi, A.ep, tx0 + (pl & 31), ty0 + (pl >> 5),
-                            A.offs + (size_t)s * T, recs + e * S_REC_WORDS, lane);
-        }
-      }
-      __syncthreads();
-#pragma unroll 1
       for (int i = 0; i < S_ROWS; ++i) {
         const int row = warp * S_ROWS + i;
-        const int pl = (row << 5) | lane;
-        int e = head[pl];
-        if (e < 0) continue;
-        const size_t wp = (size_t)(ty0 + row - A.y_lo) * wx + (size_t)(px - A.x_lo);
-        int nf = s_filled[pl];
-        while (e >= 0) {
-          const uint32_t* rc = recs + e * S_REC_WORDS;
-          const float L = __uint_as_float(rc[0]);
-          if (L >= lh_min) {  // false for NaN (pair not eligible)
-            if (insert_sorted(A, wp, K, mw, nf, L, A.orig[q_traj[e]], rc)) {
-              nf = min(nf + 1, K);
-              atomicAdd(s_ins, 1u);
-            }
+        const int py = ty0 + row;
+        const bool act = px < A.x_hi && py < A.y_hi;
+        active |= (act ? 1u : 0u) << i;
+        s_filled[(row << 5) | lane] = 0;
+        thr2[i] = admission_threshold(lh_min, A.ep);
+        if (act) {
+          const size_t wp = (size_t)(py - A.y_lo) * wx + (size_t)(px - A.x_lo);
+          for (int s = 0; s < K; ++s) {
+            A.out_lh[wp * K + s] = -INFINITY;
+            A.out_flux[wp * K + s] = 0.0f;
+            A.out_idx[wp * K + s] = -1;
+            A.out_nvalid[wp * K + s] = 0;
+            A.out_nkept[wp * K + s] = 0;
+            for (int m = 0; m < mw; ++m) A.out_mask[(wp * K + s) * mw + m] = 0u;
           }
-          e = q_next[e];
-        }
-        head[pl] = -1;
-        s_filled[pl] = (uint8_t)nf;
-        if (nf == K) {
-          const float t2 = admission_threshold(fmaxf(A.out_lh[wp * K + K - 1], lh_min), A.ep);
-#pragma unroll
-          for (int ii = 0; ii < S_ROWS; ++ii)
-            if (ii == i) thr2[ii] = t2;
         }
       }
-      if (tid == 0) atomicAdd(s_evals, (unsigned int)nq);
-      __syncthreads();
-      if (tid == 0) *s_qcount = 0u;
-      __syncthreads();
-    };
 
-    for (int c = 0; c < A.nchunk; ++c) {
-      __half2 acc[2][S_C];
+      // Evaluate every queued pair (all consumer threads), insert the results (owner threads
+      // walk their pixels' lists), empty the queue.  Called by all consumer threads after a
+      // consumer barrier.
+      auto flush = [&]() {
+        const int nq = min((int)*s_qcount, S_QCAP);
+        if (NT > 0) {
+          for (int e = tid; e < nq; e += S_CTHREADS)
+            eval_pair_thread<(NT > 0 ? NT : 1)>(A.psi, A.phi, A.ep, tx0 + (q_pix[e] & 31),
+                                                ty0 + (q_pix[e] >> 5),
+                                                A.offs + (size_t)q_traj[e] * T,
+                                                recs + e * S_REC_WORDS);
+        } else {
+          for (int e = warp; e < nq; e += S_CWARPS)
+            eval_pair_warp<J>(A.psi, A.phi, A.ep, tx0 + (q_pix[e] & 31), ty0 + (q_pix[e] >> 5),
+                              A.offs + (size_t)q_traj[e] * T, recs + e * S_REC_WORDS, lane);
+        }
+        consumer_sync();
+#pragma unroll 1
+        for (int i = 0; i < S_ROWS; ++i) {
+          const int row = warp * S_ROWS + i;
+          const int pl = (row << 5) | lane;
+          int e = head[pl];
+          if (e < 0) continue;
+          const size_t wp = (size_t)(ty0 + row - A.y_lo) * wx + (size_t)(px - A.x_lo);
+          int nf = s_filled[pl];
+          while (e >= 0) {
+            const uint32_t* rc = recs + e * S_REC_WORDS;
+            const float L = __uint_as_float(rc[0]);
+            if (L >= lh_min) {  // false for NaN (pair not eligible)
+              if (insert_sorted(A, wp, K, mw, nf, L, A.orig[q_traj[e]], rc)) {
+                nf = min(nf + 1, K);
+                atomicAdd(s_ins, 1u);
+              }
+            }
+            e = q_next[e];
+          }
+          head[pl] = -1;
+          s_filled[pl] = (uint8_t)nf;
+          if (nf == K) {
+            const float t2 = admission_threshold(fmaxf(A.out_lh[wp * K + K - 1], lh_min), A.ep);
 #pragma unroll
-      for (int pp = 0; pp < 2; ++pp)
-#pragma unroll
-        for (int v = 0; v < S_C; ++v) acc[pp][v] = __float2half2_rn(0.0f);
+            for (int ii = 0; ii < S_ROWS; ++ii)
+              if (ii == i) thr2[ii] = t2;
+          }
+        }
+        if (tid == 0) atomicAdd(s_evals, (unsigned int)nq);
+        consumer_sync();
+        if (tid == 0) *s_qcount = 0u;
+        consumer_sync();
+      };
 
-      // Stages are released per warp, without a block barrier: the last warp to finish with a
-      // stage issues the copies of the iteration two ahead into it.
-      for (int t = 0; t < T; ++t, ++it) {
-        const int st = (int)(it & 1);
-        bool ok = *(volatile unsigned int*)s_abort == 0u &&
-                  mbar_wait_parity(&bars[st], (uint32_t)((it >> 1) & 1));
-        if (ok) {
-          const PlanRec* slot = &slots[st];
-          const int mode = slot->box.w;
-          if (mode == 1) {
-            accumulate_stage<S_PITCH1>(acc, stages + st * S_STAGE_BYTES, slot, warp, lane);
-          } else if (mode == 2) {
-            accumulate_stage<S_PITCH2>(acc, stages + st * S_STAGE_BYTES, slot, warp, lane);
-          } else {
-            // direct loads from the pair planes (word row = image row + 1)
-            const uint32_t* bp = A.bound + (size_t)t * (A.ep.H + 1) * A.Wp;
+      for (int c = 0; c < A.nchunk; ++c) {
+        __half2 acc[2][S_C];
 #pragma unroll
-            for (int v = 0; v < S_C; ++v) {
-              const int2 o = __ldg(A.offs + (size_t)(c * S_C + v) * T + t);
-              const int x = px + o.x;
+        for (int pp = 0; pp < 2; ++pp)
 #pragma unroll
-              for (int pp = 0; pp < 2; ++pp) {
-                const int r = ty0 + warp * S_ROWS + 2 * pp + o.y + 1;
-                if (x >= 0 && x < A.Wp && r >= 0 && r <= A.ep.H) {
-                  const uint32_t w = __ldg(bp + (size_t)r * A.Wp + x);
-                  acc[pp][v] = __hadd2(acc[pp][v], *reinterpret_cast<const __half2*>(&w));
+          for (int v = 0; v < S_C; ++v) acc[pp][v] = __float2half2_rn(0.0f);
+
+        for (int t = 0; t < T; ++t, ++it) {
+          const int slot = (int)(it % S_D);
+          const bool ok = *(volatile unsigned int*)s_abort == 0u &&
+                          mbar_wait_parity(&full[slot], (uint32_t)((it / S_D) & 1));
+          if (ok) {
+            const PlanRec* rec = &slots[slot];
+            const int mode = rec->box.w;
+            const unsigned char* st = arena + sinfo[slot].x;
+            if (mode == 1) {
+              accumulate_stage<stage_width(1)>(acc, st, rec, warp, lane);
+            } else if (mode == 2) {
+              accumulate_stage<stage_width(2)>(acc, st, rec, warp, lane);
+            } else if (mode == 3) {
+              accumulate_stage<stage_width(3)>(acc, st, rec, warp, lane);
+            } else if (mode == 4) {
+              accumulate_stage<stage_width(4)>(acc, st, rec, warp, lane);
+            } else {
+              // direct loads from the pair planes (word row = image row + 1)
+              const uint32_t* bp = A.bound + (size_t)t * (A.ep.H + 1) * A.Wp;
+#pragma unroll
+              for (int v = 0; v < S_C; ++v) {
+                const int2 o = __ldg(A.offs + (size_t)(c * S_C + v) * T + t);
+                const int x = px + o.x;
+#pragma unroll
+                for (int pp = 0; pp < 2; ++pp) {
+                  const int r = ty0 + warp * S_ROWS + 2 * pp + o.y + 1;
+                  if (x >= 0 && x < A.Wp && r >= 0 && r <= A.ep.H) {
+                    const uint32_t w = __ldg(bp + (size_t)r * A.Wp + x);
+                    acc[pp][v] = __hadd2(acc[pp][v], *reinterpret_cast<const __half2*>(&w));
+                  }
                 }
               }
             }
+          } else if (lane == 0 && atomicExch(s_abort, 1u) == 0u) {
+            atomicOr(&A.ctrl->err, kErrTimeout);
           }
-        } else if (lane == 0 && atomicExch(s_abort, 1u) == 0u) {
-          atomicOr(&A.ctrl->err, kErrTimeout);
+          __syncwarp();  // every lane's reads of the slot come before the warp's release
+          if (lane == 0) mbar_arrive(&empty[slot]);
         }
-        __syncwarp();
-        if (lane == 0) {
-          __threadfence_block();  // this warp's reads of the stage come before its release
-          const unsigned int prev = atomicAdd(&s_done[st], 1u);
-          if (prev == S_WARPS - 1) {
-            s_done[st] = 0u;
-            __threadfence_block();
-            if (it + 2 < total_it && *(volatile unsigned int*)s_abort == 0u) {
-              fence_proxy_async_smem();
-              issue_stage(&tmap64, &tmap128, A, stages + st * S_STAGE_BYTES, &slots[st], &bars[st],
-                          it + 2);
-              s_last[st] = it + 2;
-            }
-          }
-        }
-        __syncwarp();
-      }
 
-      // ---- pairs whose bound reaches the admission threshold join the queue ----
-      const int nv = min(S_C, A.n_traj - c * S_C);
-      const uint32_t vmask = nv >= 32 ? 0xffffffffu : ((1u << nv) - 1u);
-      uint32_t cb[S_ROWS];
-      int ncand = 0;
+        // ---- pairs whose bound reaches the admission threshold join the block queue ----
+        const int nv = min(S_C, A.n_traj - c * S_C);
+        const uint32_t vmask = nv >= 32 ? 0xffffffffu : ((1u << nv) - 1u);
+        uint32_t cb[S_ROWS];
 #pragma unroll
-      for (int pp = 0; pp < 2; ++pp) {
-        uint32_t b0 = 0u, b1 = 0u;
+        for (int pp = 0; pp < 2; ++pp) {
+          const __half2 th = __halves2half2(half_round_down(thr2[2 * pp]),
+                                            half_round_down(thr2[2 * pp + 1]));
+          uint32_t b0 = 0u, b1 = 0u;
 #pragma unroll
-        for (int v = 0; v < S_C; ++v) {
-          const float2 f = __half22float2(acc[pp][v]);
-          if (f.x >= thr2[2 * pp]) b0 |= 1u << v;
-          if (f.y >= thr2[2 * pp + 1]) b1 |= 1u << v;
+          for (int v = 0; v < S_C; ++v) {
+            const uint32_t m = __hge2_mask(acc[pp][v], th);
+            b0 |= (m & 1u) << v;
+            b1 |= ((m >> 16) & 1u) << v;
+          }
+          cb[2 * pp] = ((active >> (2 * pp)) & 1u) ? (b0 & vmask) : 0u;
+          cb[2 * pp + 1] = ((active >> (2 * pp + 1)) & 1u) ? (b1 & vmask) : 0u;
         }
-        cb[2 * pp] = ((active >> (2 * pp)) & 1u) ? (b0 & vmask) : 0u;
-        cb[2 * pp + 1] = ((active >> (2 * pp + 1)) & 1u) ? (b1 & vmask) : 0u;
-      }
+        // Append without a barrier: each warp reserves queue positions with one atomic; pairs
+        // beyond the capacity stay in cb and are appended after a flush.
+        for (;;) {
+          int ncand = 0;
 #pragma unroll
-      for (int i = 0; i < S_ROWS; ++i) ncand += __popc(cb[i]);
-      int incl = ncand;
+          for (int i = 0; i < S_ROWS; ++i) ncand += __popc(cb[i]);
+          int incl = ncand;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-      }
-      if (tid == 0) *s_new = 0u;
-      __syncthreads();
-      unsigned int wbase = 0;
-      if (lane == 31 && incl > 0) wbase = atomicAdd(s_new, (unsigned int)incl);
-      wbase = __shfl_sync(0xffffffffu, wbase, 31);
-      const int my_base = (int)wbase + incl - ncand;
-      __syncthreads();
-      const int new_total = (int)*s_new;
-      int taken = 0;
-      while (taken < new_total) {
-        const int qc = (int)*s_qcount;
-        const int n_this = min(S_QCAP - qc, new_total - taken);
-        if (ncand > 0) {
-          int rank = my_base;
+          for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+          }
+          const int wtotal = __shfl_sync(0xffffffffu, incl, 31);
+          unsigned int wbase = 0;
+          if (lane == 31 && wtotal > 0) wbase = atomicAdd(s_qcount, (unsigned int)wtotal);
+          wbase = __shfl_sync(0xffffffffu, wbase, 31);
+          int pos = (int)wbase + incl - ncand;
+          bool deferred = false;
+          if (ncand > 0) {
 #pragma unroll 1
-          for (int i = 0; i < S_ROWS; ++i) {
-            uint32_t bits = i == 0 ? cb[0] : i == 1 ? cb[1] : i == 2 ? cb[2] : cb[3];
-            while (bits) {
-              const int v = __ffs(bits) - 1;
-              bits &= bits - 1u;
-              if (rank >= taken && rank < taken + n_this) {
-                const int e = qc + rank - taken;
-                const int pl = ((warp * S_ROWS + i) << 5) | lane;
-                q_traj[e] = c * S_C + v;
-                q_pix[e] = (uint16_t)pl;
-                q_next[e] = (int16_t)atomicExch(&head[pl], e);
+            for (int i = 0; i < S_ROWS; ++i) {
+              uint32_t bits = i == 0 ? cb[0] : i == 1 ? cb[1] : i == 2 ? cb[2] : cb[3];
+              uint32_t left = 0u;
+              while (bits) {
+                const int v = __ffs(bits) - 1;
+                bits &= bits - 1u;
+                if (pos < S_QCAP) {
+                  const int pl = ((warp * S_ROWS + i) << 5) | lane;
+                  q_traj[pos] = c * S_C + v;
+                  q_pix[pos] = (uint16_t)pl;
+                  q_next[pos] = head[pl];  // this thread owns pixel pl
+                  head[pl] = (int16_t)pos;
+                } else {
+                  left |= 1u << v;
+                  deferred = true;
+                }
+                ++pos;
               }
-              ++rank;
+              if (i == 0) cb[0] = left;
+              else if (i == 1) cb[1] = left;
+              else if (i == 2) cb[2] = left;
+              else cb[3] = left;
             }
           }
+          // one barrier per chunk decides, for all consumer threads alike, whether to flush
+          const bool full_q = consumer_sync_or(deferred);
+          if (full_q || *(volatile unsigned int*)s_qcount >= (unsigned int)S_FLUSH_MIN) {
+            flush();
+            if (full_q) continue;  // append the pairs that did not fit
+          }
+          break;
         }
-        __syncthreads();
-        if (tid == 0) *s_qcount = (unsigned int)(qc + n_this);
-        __syncthreads();
-        taken += n_this;
-        if (qc + n_this == S_QCAP) flush();
       }
-      if ((int)*s_qcount >= S_FLUSH_MIN) flush();
+      consumer_sync();
+      if (*(volatile unsigned int*)s_qcount > 0u) flush();
     }
-    if (*s_qcount > 0u) flush();
   }
 
   __syncthreads();
-  if (*(volatile unsigned int*)s_abort != 0u && tid == 0) {
-    // a wait gave up: wait (bounded) for the last copies issued into each stage
-    for (int sidx = 0; sidx < 2; ++sidx)
-      if (s_last[sidx] < total_it)
-        mbar_wait_parity(&bars[sidx], (uint32_t)((s_last[sidx] >> 1) & 1));
-  }
   if (tid == 0) {
     atomicAdd(&A.ctrl->evals, (unsigned long long)*s_evals);
     atomicAdd(&A.ctrl->inserts, (unsigned long long)*s_ins);
+  }
+  if (warp >= S_CWARPS && lane == 0 && *(volatile unsigned int*)s_abort != 0u) {
+    // a wait gave up: wait (bounded) for this producer's last copies
+    const long long n = s_issued[warp - S_CWARPS];
+    for (long long j = n; j >= 0 && j > n - S_D; j -= S_PWARPS)
+      mbar_wait_parity(&full[j % S_D], (uint32_t)((j / S_D) & 1));
   }
 }
 
@@ -1158,18 +1339,20 @@ extern "C" int kb_search(const float* psi, const float* phi, const double* times
     KB_LAUNCH_CHECK("bound_prep_kernel");
   }
 
-  CUtensorMap tmap64, tmap128;
-  for (int m = 0; m < 2; ++m) {
-    cuuint64_t dims[3] = {(cuuint64_t)L.Wp, (cuuint64_t)H + 1, (cuuint64_t)T};
-    cuuint64_t strides[2] = {(cuuint64_t)L.Wp * 4, (cuuint64_t)L.Wp * (H + 1) * 4};
-    cuuint32_t boxd[3] = {(cuuint32_t)(m == 0 ? S_PITCH1 : S_PITCH2), (cuuint32_t)S_BOX_Y, 1u};
-    cuuint32_t estr[3] = {1u, 1u, 1u};
-    CUresult r = enc(m == 0 ? &tmap64 : &tmap128, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, bound, dims,
-                     strides, boxd, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS)
-      return fail(KB_ERR_CUDA, "kb_search: cuTensorMapEncodeTiled failed (%d)", (int)r);
-  }
+  TmapSet maps;
+  for (int w = 1; w <= S_NW; ++w)
+    for (int h = 0; h < S_NH; ++h) {
+      cuuint64_t dims[3] = {(cuuint64_t)L.Wp, (cuuint64_t)H + 1, (cuuint64_t)T};
+      cuuint64_t strides[2] = {(cuuint64_t)L.Wp * 4, (cuuint64_t)L.Wp * (H + 1) * 4};
+      cuuint32_t boxd[3] = {(cuuint32_t)stage_width(w), (cuuint32_t)stage_height(h), 1u};
+      cuuint32_t estr[3] = {1u, 1u, 1u};
+      CUresult r = enc(&maps.m[(w - 1) * S_NH + h], CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, bound,
+                       dims, strides, boxd, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                       CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS)
+        return fail(KB_ERR_CUDA, "kb_search: cuTensorMapEncodeTiled failed (%d)", (int)r);
+    }
 
   SearchArgs A{};
   A.psi = psi;
@@ -1219,7 +1402,7 @@ extern "C" int kb_search(const float* psi, const float* phi, const double* times
   do {                                                                                         \
     KB_CUDA_TRY(cudaFuncSetAttribute(search_kernel<NT, JJ>,                                    \
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-    search_kernel<NT, JJ><<<grid, S_THREADS, smem, st>>>(tmap64, tmap128, A);                             \
+    search_kernel<NT, JJ><<<grid, S_THREADS, smem, st>>>(maps, A);                             \
   } while (0)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   profile_events(&ev0, &ev1);

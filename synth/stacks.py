@@ -14,7 +14,9 @@ Section 4.1).  The DECam NEO data are not available, so these stand in for them:
             15x15, 1000 movers SNR U[1,8]; grid 512 x 256 (92-550 px/day, +-pi/10).
   refine    the tiny stack with movers at off-grid sub-pixel starts and velocities.
   decam_small  the decam recipe on 1024x1024 with 50 movers (psi+phi 218 MB, above the 126 MB
-            L2): the size used for detailed kernel profiles.
+            L2).
+  decam_half   the decam recipe on 2046x2048 with 100 movers (same mover density; psi+phi
+            0.87 GB): the size used for detailed kernel profiles, with ~15 tiles per SM.
 
 A mover of per-epoch matched-filter SNR s has flux F_t = s sqrt(var_t) / sqrt(sum P_t^2) and is
 drawn as F_t times the PSF centred on its position (integer positions for 'tiny', exact
@@ -59,6 +61,12 @@ CONFIGS = {
                         times=("nights", (7, 7, 6, 6)), integer_tracks=False,
                         movers_on_grid=False, start_margin=0, seed=5, K=8, lh_min=10.0,
                         min_obs=15),
+    "decam_half": dict(T=26, H=2046, W=2048, psf_k=15, psf_sigma=(1.0, 2.0), var=(0.5, 2.0),
+                       mask_frac=0.005, n_movers=100, snr=("loguniform", 1.5, 10.0),
+                       spike_frac=0.1, grid=(90.0, 500.0, 256, -0.3, 0.3, 128),
+                       times=("nights", (7, 7, 6, 6)), integer_tracks=False,
+                       movers_on_grid=False, start_margin=0, seed=6, K=8, lh_min=10.0,
+                       min_obs=15),
     "full": dict(T=100, H=4096, W=4096, psf_k=15, psf_sigma=(1.0, 2.5), var=(0.5, 2.0),
                  mask_frac=0.01, n_movers=1000, snr=("uniform", 1.0, 8.0), spike_frac=0.0,
                  grid=(92.0, 550.0, 512, -math.pi / 10, math.pi / 10, 256),
