@@ -155,6 +155,34 @@ KB_API int kb_search(const float* psi, const float* phi, const double* times, in
               void* stream);
 
 /*
+ * kb_search_no_alloc -- kb_search for callers that must not allocate device memory.  Some
+ * callers cannot call cudaMalloc or hand out a workspace: a plug-in running inside a host program
+ * whose device memory is owned by another allocator (a caching or fixed-size pool it may not grow),
+ * or code that must keep a fixed device footprint after start-up.  This entry point takes the
+ * same arguments as kb_search minus the workspace and uses scratch memory built into the library
+ * instead: one array of KB_STATIC_SCRATCH_BYTES in device global memory, which every GPU that
+ * loads the library holds until the process exits.  The paper has no counterpart; it is a
+ * packaging of kb_search.
+ *
+ *  - Sizes whose kb_search_workspace_size exceeds KB_STATIC_SCRATCH_BYTES are rejected with
+ *    KB_ERR_UNSUPPORTED (use kb_search with a workspace for them).
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ *    that device current; make that first call before any stream capture on the device.
+ *  - All calls share the one array, and it keeps whatever the last call left in it (kb_search
+ *    does not depend on the workspace's previous contents).  Calls whose work overlaps on the
+ *    GPU (different streams, or threads without ordering) race on the array: serialise them.
+ *  - No allocation of any kind (no cudaMalloc, no cudaFree, no allocating library routine).
+ * Errors: as kb_search, plus KB_ERR_UNSUPPORTED for sizes beyond the built-in scratch and
+ * KB_ERR_CUDA if the address lookup fails.
+ */
+#define KB_STATIC_SCRATCH_BYTES (32u << 20)
+KB_API int kb_search_no_alloc(const float* psi, const float* phi, const double* times, int T,
+                              int H, int W, const float* vx, const float* vy, int n_traj,
+                              const kb_search_params* p, float* out_lh, float* out_flux,
+                              int32_t* out_idx, uint16_t* out_nvalid, uint16_t* out_nkept,
+                              uint32_t* out_mask, void* stream);
+
+/*
  * kb_search_stats -- counters of the last kb_search that used `workspace` (device counters
  * copied to the HOST array stats[4]; synchronises the stream):
  *   stats[0] trajectory-epochs covered (start pixels x trajectories x T),

@@ -19,6 +19,7 @@ from ._lib import (KB_MAX_K, KB_MAX_T, KB_WORKSPACE_ALIGN, KbError, SearchParams
 
 __all__ = ["SearchParams", "make_psi_phi", "search", "search_workspace_size", "search_stats",
            "stamps", "collect", "candidate_tracks", "launch_count", "profile_events", "KbError",
+           "search_no_alloc",
            "KB_MAX_T", "KB_MAX_K", "lib", "version", "alloc_workspace"]
 
 
@@ -223,3 +224,35 @@ def profile_events(start=None, stop=None):
     """Time the next searches' main kernel with these torch.cuda.Events (None, None: off)."""
     lib().kb_profile_events(None if start is None else C.c_void_p(start.cuda_event),
                             None if stop is None else C.c_void_p(stop.cuda_event))
+
+
+def search_no_alloc(psi, phi, times, vx, vy, params=None, out=None, stream=None):
+    """kb_search_no_alloc: the search with the library's built-in scratch instead of a workspace,
+    for callers that must not allocate device memory.  Same results as search(); the outputs
+    (`out`, same layout as search() returns) may be passed in so that the call allocates
+    nothing.  Sizes beyond the built-in scratch raise KbError (KB_ERR_UNSUPPORTED)."""
+    params = params or SearchParams()
+    _dev(psi, torch.float32, "psi", 3)
+    _dev(phi, torch.float32, "phi", 3)
+    _dev(vx, torch.float32, "vx", 1)
+    _dev(vy, torch.float32, "vy", 1)
+    T, H, W = psi.shape
+    times = _host_times(times)
+    pc = params.to_c(H, W)
+    K = pc.k_per_pixel
+    wy, wx = pc.y_hi - pc.y_lo, pc.x_hi - pc.x_lo
+    mw = (T + 31) // 32
+    dev = psi.device
+    if out is None:
+        out = dict(lh=torch.empty((wy, wx, K), dtype=torch.float32, device=dev),
+                   flux=torch.empty((wy, wx, K), dtype=torch.float32, device=dev),
+                   idx=torch.empty((wy, wx, K), dtype=torch.int32, device=dev),
+                   nvalid=torch.empty((wy, wx, K), dtype=torch.int16, device=dev),
+                   nkept=torch.empty((wy, wx, K), dtype=torch.int16, device=dev),
+                   mask=torch.empty((wy, wx, K, mw), dtype=torch.int32, device=dev))
+    check(lib().kb_search_no_alloc(_ptr(psi), _ptr(phi), times.ctypes.data_as(C.c_void_p), T, H,
+                                   W, _ptr(vx), _ptr(vy), vx.numel(), C.byref(pc),
+                                   _ptr(out["lh"]), _ptr(out["flux"]), _ptr(out["idx"]),
+                                   _ptr(out["nvalid"]), _ptr(out["nkept"]), _ptr(out["mask"]),
+                                   _stream(stream)))
+    return out

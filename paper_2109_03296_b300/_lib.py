@@ -18,11 +18,12 @@ KB_ERR_TIMEOUT = 5
 KB_MAX_T = 128
 KB_MAX_K = 32
 KB_WORKSPACE_ALIGN = 256
+KB_STATIC_SCRATCH_BYTES = 32 << 20
 
 EXPORTS = ("kb_version", "kb_last_error", "kb_search_params_default", "kb_make_psi_phi",
            "kb_search_workspace_size", "kb_search", "kb_search_stats", "kb_stamps",
            "kb_collect_workspace_size", "kb_collect", "kb_candidate_tracks", "kb_launch_count",
-           "kb_profile_events")
+           "kb_profile_events", "kb_search_no_alloc")
 
 
 class KbError(RuntimeError):
@@ -79,6 +80,9 @@ def lib():
     L.kb_launch_count.argtypes = []
     L.kb_profile_events.restype = None
     L.kb_profile_events.argtypes = [p, p]
+    L.kb_search_no_alloc.restype = i
+    L.kb_search_no_alloc.argtypes = [p, p, p, i, i, i, p, p, i, C.POINTER(SearchParamsC), p, p, p,
+                                     p, p, p, p]
     _LIB = L
     return L
 

@@ -1430,3 +1430,56 @@ extern "C" int kb_search_stats(const void* workspace, unsigned long long* stats,
   stats[3] = c.err;
   return KB_OK;
 }
+
+// ---------------------------------------------------------------------------------------------
+// kb_search_no_alloc: kb_search with scratch memory built into the library
+// ---------------------------------------------------------------------------------------------
+namespace kb {
+
+// The built-in scratch: file-scope device memory, present on every device that loads the
+// library.  Host code must not take its address directly (that is a host-side stand-in); the
+// device address is looked up per device with cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_no_alloc_scratch[KB_STATIC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+static std::mutex g_no_alloc_mu;
+static void* g_no_alloc_ptr[kMaxDevices] = {};
+
+}  // namespace kb
+
+extern "C" int kb_search_no_alloc(const float* psi, const float* phi, const double* times, int T,
+                                  int H, int W, const float* vx, const float* vy, int n_traj,
+                                  const kb_search_params* p, float* out_lh, float* out_flux,
+                                  int32_t* out_idx, uint16_t* out_nvalid, uint16_t* out_nkept,
+                                  uint32_t* out_mask, void* stream) {
+  using namespace kb;
+  int rc = validate(psi, phi, times, T, H, W, vx, vy, n_traj, p);
+  if (rc != KB_OK) return rc;
+  const size_t need = ws_layout(T, H, W, n_traj).total;
+  if (need > (size_t)KB_STATIC_SCRATCH_BYTES)
+    return fail(KB_ERR_UNSUPPORTED,
+                "kb_search_no_alloc: this search needs %zu bytes of scratch, more than the %u "
+                "built into the library; use kb_search with a workspace",
+                need, (unsigned)KB_STATIC_SCRATCH_BYTES);
+  int dev = 0;
+  KB_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices)
+    return fail(KB_ERR_UNSUPPORTED, "kb_search_no_alloc: device ordinal %d beyond %d", dev,
+                kMaxDevices);
+  void* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_no_alloc_mu);
+    if (!g_no_alloc_ptr[dev]) {
+      void* ptr = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&ptr, g_no_alloc_scratch);
+      if (e != cudaSuccess || !ptr)
+        return fail(KB_ERR_CUDA, "kb_search_no_alloc: cudaGetSymbolAddress failed: %s",
+                    cudaGetErrorString(e));
+      g_no_alloc_ptr[dev] = ptr;
+    }
+    scratch = g_no_alloc_ptr[dev];
+  }
+  return kb_search(psi, phi, times, T, H, W, vx, vy, n_traj, p, out_lh, out_flux, out_idx,
+                   out_nvalid, out_nkept, out_mask, scratch, (size_t)KB_STATIC_SCRATCH_BYTES,
+                   stream);
+}
