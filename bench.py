@@ -121,16 +121,27 @@ class ClockSampler:
 # ------------------------------------------------------------------------------------------------
 # the oracle on a bounded window (CPU baseline and the reference arm)
 # ------------------------------------------------------------------------------------------------
+_ORACLE_DATA = {}
+
+
+def _oracle_inputs(workload):
+    """The workload's likelihood planes as FP64 (generated once per process)."""
+    if workload not in _ORACLE_DATA:
+        import numpy as np
+        from synth import make_likelihood_stack
+        psi, phi, times, vx, vy, movers = make_likelihood_stack(workload)
+        _ORACLE_DATA[workload] = (psi.astype(np.float64), phi.astype(np.float64), times, vx, vy)
+    return _ORACLE_DATA[workload]
+
+
 def oracle_rate(target_s, workload):
-    """Oracle search TE/s on a window of the workload's likelihood planes, sized to ~target_s."""
-    import numpy as np
+    """Oracle search TE/s on a square window of start pixels of the workload's likelihood planes
+    (every trajectory, every epoch); the window side doubles until one run takes more than half
+    of target_s (so the timed sample is about target_s/2 to 2 target_s of CPU time)."""
     import oracle
-    from synth import CONFIGS, make_likelihood_stack
+    from synth import CONFIGS
     c = CONFIGS[workload]
-    psi, phi, times, vx, vy, movers = make_likelihood_stack(workload)
-    psi64 = psi.astype(np.float64)
-    phi64 = phi.astype(np.float64)
-    del psi, phi
+    psi64, phi64, times, vx, vy = _oracle_inputs(workload)
     T, H, W = psi64.shape
     params = dict(k=c["K"], lh_min=c["lh_min"], min_obs=c["min_obs"], clip=1)
     cx, cy = W // 2, H // 2
@@ -140,7 +151,7 @@ def oracle_rate(target_s, workload):
         oracle.search(psi64, phi64, times, vx, vy, params, window=(cx, cx + side, cy, cy + side))
         dt = time.perf_counter() - t0
         te = side * side * len(vx) * T
-        if dt * 4 > target_s or side >= 64:
+        if dt * 2 > target_s or side >= 64:
             break
         side *= 2
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
@@ -154,7 +165,7 @@ def run_reference(args):
         return
     r = None
     for _ in range(args.warmup):
-        oracle_rate(args.cpu_seconds / 4, args.workload)
+        oracle_rate(args.cpu_seconds / 8, args.workload)
     vals = []
     t_all = 0.0
     for _ in range(args.steps):
