@@ -17,5 +17,10 @@ the pins live in tests/test_oracle_pins.py):
   stamps            mean stamp of a noiseless mover is F P; numpy.median/mean on tiny stacks
   traj_eval_subpixel  L/alpha equal the integer search at integer positions; central finite
                     differences of L for the gradient
+  traj_vjp          central finite differences of L and alpha in the track parameters and in
+                    single psi/phi pixels; tap support; Euler's theorem for the homogeneity
+                    degrees of L and alpha in psi and phi
+  refine_adam       closed form of Adam's first step; convergence to a noiseless off-grid mover;
+                    stop where Phi vanishes
 """
 from .oracle import *  # noqa: F401,F403

@@ -453,3 +453,84 @@ int kbo_traj_eval_subpixel(const double* psi, const double* phi, const double* t
   }
   return 0;
 }
+
+/* Vector-Jacobian product of the sub-pixel evaluation: given upstream weights gL on L and gA on
+ * alpha = Psi/Phi, adds to grad_params[4] (nullable) the values gL dL/dp + gA dalpha/dp for
+ * p = (x0, y0, vx, vy), and to the dense [T][H][W] arrays grad_psi, grad_phi (nullable) the
+ * weights of every pixel: L and alpha depend on a pixel only through Psi or Phi, each a sum of
+ * bilinear taps (R13), so a tap of weight w on kept epoch t receives cPsi w (psi) or cPhi w (phi)
+ * with cPsi = gL/sqrt(Phi) + gA/Phi and cPhi = -gL Psi/(2 Phi^{3/2}) - gA Psi/Phi^2.
+ * Taps outside the image get nothing.  Returns -1 (nothing added) if Phi <= 0. */
+int kbo_traj_vjp(const double* psi, const double* phi, const double* times, int T, int H, int W,
+                 const uint32_t* keep, double x0, double y0, double vx, double vy, double gL,
+                 double gA, double* grad_params, double* grad_psi, double* grad_phi) {
+  size_t hw = (size_t)H * W;
+  double Ps = 0, Ph = 0;
+  double dPs[4] = {0, 0, 0, 0}, dPh[4] = {0, 0, 0, 0};
+  for (int t = 0; t < T; ++t) {
+    if (!((keep[t >> 5] >> (t & 31)) & 1u)) continue;
+    double dt = times[t] - times[0];
+    double x = x0 + vx * dt, y = y0 + vy * dt;
+    double gpx, gpy, gfx, gfy;
+    Ps += bilinear(psi + (size_t)t * hw, H, W, x, y, &gpx, &gpy);
+    Ph += bilinear(phi + (size_t)t * hw, H, W, x, y, &gfx, &gfy);
+    dPs[0] += gpx; dPs[1] += gpy; dPs[2] += gpx * dt; dPs[3] += gpy * dt;
+    dPh[0] += gfx; dPh[1] += gfy; dPh[2] += gfx * dt; dPh[3] += gfy * dt;
+  }
+  if (!(Ph > 0.0)) return -1;
+  double cPs = gL / sqrt(Ph) + gA / Ph;
+  double cPh = -0.5 * gL * Ps / (Ph * sqrt(Ph)) - gA * Ps / (Ph * Ph);
+  if (grad_params)
+    for (int i = 0; i < 4; ++i) grad_params[i] += cPs * dPs[i] + cPh * dPh[i];
+  if (!grad_psi && !grad_phi) return 0;
+  for (int t = 0; t < T; ++t) {
+    if (!((keep[t >> 5] >> (t & 31)) & 1u)) continue;
+    double dt = times[t] - times[0];
+    double x = x0 + vx * dt, y = y0 + vy * dt;
+    double fx = floor(x), fy = floor(y);
+    int ix = (int)fx, iy = (int)fy;
+    double ax = x - fx, ay = y - fy;
+    for (int k = 0; k < 4; ++k) {
+      int xx = ix + (k & 1), yy = iy + (k >> 1);
+      if (xx < 0 || xx >= W || yy < 0 || yy >= H) continue;
+      double w = ((k & 1) ? ax : 1.0 - ax) * ((k >> 1) ? ay : 1.0 - ay);
+      size_t i = (size_t)t * hw + (size_t)yy * W + xx;
+      if (grad_psi) grad_psi[i] += cPs * w;
+      if (grad_phi) grad_phi[i] += cPh * w;
+    }
+  }
+  return 0;
+}
+
+/* Gradient ascent on the sub-pixel likelihood L(x0, y0, vx, vy) with Adam (Kingma & Ba 2015:
+ * m <- b1 m + (1-b1) g, v <- b2 v + (1-b2) g^2, step lr * mhat / (sqrt(vhat) + eps) with
+ * mhat = m/(1-b1^k), vhat = v/(1-b2^k)), learning rate lr_pos for (x0, y0) and lr_vel for
+ * (vx, vy); the kept mask stays fixed.  params [4] are updated in place.  Each of the n_steps
+ * steps evaluates L and its gradient at the current params and moves them; the final L and alpha
+ * are those at the returned params.  If Phi <= 0 at some evaluation the ascent stops there,
+ * params keep their values, lh and flux are NaN and -1 is returned. */
+int kbo_refine_adam(const double* psi, const double* phi, const double* times, int T, int H,
+                    int W, const uint32_t* keep, double* params, int n_steps, double lr_pos,
+                    double lr_vel, double b1, double b2, double eps, double* lh, double* flux) {
+  double m[4] = {0, 0, 0, 0}, v[4] = {0, 0, 0, 0};
+  double b1k = 1.0, b2k = 1.0;
+  for (int k = 1; k <= n_steps; ++k) {
+    double L, fl, g[4];
+    if (kbo_traj_eval_subpixel(psi, phi, times, T, H, W, keep, params[0], params[1], params[2],
+                               params[3], &L, &fl, g)) {
+      *lh = NAN; *flux = NAN;
+      return -1;
+    }
+    b1k *= b1;
+    b2k *= b2;
+    for (int i = 0; i < 4; ++i) {
+      m[i] = b1 * m[i] + (1.0 - b1) * g[i];
+      v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];
+      double mh = m[i] / (1.0 - b1k), vh = v[i] / (1.0 - b2k);
+      double lr = i < 2 ? lr_pos : lr_vel;
+      params[i] += lr * mh / (sqrt(vh) + eps);  /* ascent */
+    }
+  }
+  return kbo_traj_eval_subpixel(psi, phi, times, T, H, W, keep, params[0], params[1], params[2],
+                                params[3], lh, flux, NULL);
+}

@@ -45,6 +45,10 @@ def lib():
         _LIB.kbo_stamps.argtypes = [p, p, p, p, i, i, i, p, p, p, p, p, i, i, p, p]
         _LIB.kbo_traj_eval_subpixel.restype = i
         _LIB.kbo_traj_eval_subpixel.argtypes = [p, p, p, i, i, i, p, d, d, d, d, p, p, p]
+        _LIB.kbo_traj_vjp.restype = i
+        _LIB.kbo_traj_vjp.argtypes = [p, p, p, i, i, i, p, d, d, d, d, d, d, p, p, p]
+        _LIB.kbo_refine_adam.restype = i
+        _LIB.kbo_refine_adam.argtypes = [p, p, p, i, i, i, p, p, i, d, d, d, d, d, p, p]
     return _LIB
 
 
@@ -214,3 +218,35 @@ def traj_eval_subpixel(psi, phi, times, keep, x0, y0, vx, vy, grad=True):
                                  float(x0), float(y0), float(vx), float(vy), C.byref(lh),
                                  C.byref(fl), _ptr(g) if grad else None)
     return lh.value, fl.value, g
+
+
+def traj_vjp(psi, phi, times, keep, x0, y0, vx, vy, gL=1.0, gA=0.0, images=True):
+    """gL dL/d. + gA dalpha/d. of the sub-pixel evaluation: (grad_params [4], grad_psi, grad_phi)
+    with dense [T][H][W] image gradients (None unless images); None if Phi <= 0."""
+    psi, phi, times = _f64(psi), _f64(phi), _f64(times)
+    T, H, W = psi.shape
+    keep = np.ascontiguousarray(keep, np.uint32)
+    gp = np.zeros(4)
+    gpsi = np.zeros((T, H, W)) if images else None
+    gphi = np.zeros((T, H, W)) if images else None
+    rc = lib().kbo_traj_vjp(_ptr(psi), _ptr(phi), _ptr(times), T, H, W, _ptr(keep), float(x0),
+                            float(y0), float(vx), float(vy), float(gL), float(gA), _ptr(gp),
+                            _ptr(gpsi), _ptr(gphi))
+    if rc != 0:
+        return None
+    return gp, gpsi, gphi
+
+
+def refine_adam(psi, phi, times, keep, params, n_steps, lr_pos, lr_vel, b1=0.9, b2=0.999,
+                eps=1e-8):
+    """Adam ascent of L from params (x0, y0, vx, vy); returns (params, L, alpha), L and alpha NaN
+    if Phi <= 0 was met (params then as they were at that point)."""
+    psi, phi, times = _f64(psi), _f64(phi), _f64(times)
+    T, H, W = psi.shape
+    keep = np.ascontiguousarray(keep, np.uint32)
+    pr = np.array(params, dtype=np.float64)
+    lh, fl = C.c_double(0), C.c_double(0)
+    lib().kbo_refine_adam(_ptr(psi), _ptr(phi), _ptr(times), T, H, W, _ptr(keep), _ptr(pr),
+                          int(n_steps), float(lr_pos), float(lr_vel), float(b1), float(b2),
+                          float(eps), C.byref(lh), C.byref(fl))
+    return pr, lh.value, fl.value

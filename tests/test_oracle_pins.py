@@ -546,3 +546,158 @@ def test_paper_grid_shape():
     assert len(vx) == 131072
     sp = np.hypot(vx.astype(np.float64), vy.astype(np.float64))
     assert abs(sp.min() - 92.0) < 1e-3 and abs(sp.max() - 550.0) < 1e-3
+
+
+def _subpixel_case(seed, T=8, H=40, W=44):
+    rng = np.random.default_rng(seed)
+    times = np.sort(rng.uniform(0, 0.3, T))
+    times[0] = 0.0
+    phi = rng.uniform(0.2, 1.0, (T, H, W))
+    psi = rng.normal(size=(T, H, W)) * np.sqrt(phi) + 2.0 * phi
+    return rng, times, psi, phi
+
+
+def _clear_of_kinks(times, p, h):
+    dts = times - times[0]
+    xs, ys = p[0] + p[2] * dts, p[1] + p[3] * dts
+    edge = min(np.abs(xs - np.round(xs)).min(), np.abs(ys - np.round(ys)).min())
+    return edge > 4 * h * (1 + dts.max())
+
+
+def test_vjp_params_against_finite_differences_of_L_and_alpha():
+    rng, times, psi, phi = _subpixel_case(21)
+    keep = np.array([0b11011101], np.uint32)
+    h = 1e-4
+    checked = 0
+    for trial in range(40):
+        p = np.concatenate([rng.uniform(8, 30, 2), rng.uniform(-30, 30, 2)])
+        if not _clear_of_kinks(times, p, h):
+            continue
+        gL, gA = rng.normal(size=2)
+        g = oracle.traj_vjp(psi, phi, times, keep, *p, gL=gL, gA=gA, images=False)[0]
+        fd = np.zeros(4)
+        for i in range(4):
+            pp, pm = p.copy(), p.copy()
+            pp[i] += h
+            pm[i] -= h
+            Lp, Ap, _ = oracle.traj_eval_subpixel(psi, phi, times, keep, *pp, grad=False)
+            Lm, Am, _ = oracle.traj_eval_subpixel(psi, phi, times, keep, *pm, grad=False)
+            fd[i] = (gL * (Lp - Lm) + gA * (Ap - Am)) / (2 * h)
+        assert np.all(np.abs(g - fd) <= 1e-6 * np.maximum(np.abs(fd), 1.0)), (g, fd)
+        checked += 1
+    assert checked >= 10
+
+
+def test_vjp_images_against_finite_differences_and_support():
+    rng, times, psi, phi = _subpixel_case(22)
+    keep = np.array([0b10111111], np.uint32)
+    T, H, W = psi.shape
+    p = np.array([15.37, 20.71, 23.3, -17.9])
+    gL, gA = 0.7, -1.3
+    _, gpsi, gphi = oracle.traj_vjp(psi, phi, times, keep, *p, gL=gL, gA=gA)
+
+    def obj(ps, ph):
+        L, A, _ = oracle.traj_eval_subpixel(ps, ph, times, keep, *p, grad=False)
+        return gL * L + gA * A
+
+    # every pixel the track's taps touch, plus untouched pixels, which must read zero
+    touched = np.argwhere((gpsi != 0) | (gphi != 0))
+    assert 0 < len(touched) <= 4 * int(bin(int(keep[0])).count("1"))
+    dts = times - times[0]
+    for t in range(T):
+        inside = (keep[0] >> t) & 1
+        n_t = (touched[:, 0] == t).sum()
+        assert n_t == (4 if inside else 0)
+        if inside:   # the four taps of epoch t surround its position
+            x, y = p[0] + p[2] * dts[t], p[1] + p[3] * dts[t]
+            ys, xs = touched[touched[:, 0] == t, 1], touched[touched[:, 0] == t, 2]
+            assert set(xs) == {math.floor(x), math.floor(x) + 1}
+            assert set(ys) == {math.floor(y), math.floor(y) + 1}
+    picks = [tuple(r) for r in touched[rng.choice(len(touched), 12, replace=False)]]
+    picks += [(1, 2, 3), (5, 39, 43)]
+    h = 1e-4
+    for (t, y, x) in picks:
+        for which, grad in (("psi", gpsi), ("phi", gphi)):
+            a, b = psi.copy(), phi.copy()
+            c, d = psi.copy(), phi.copy()
+            if which == "psi":
+                a[t, y, x] += h
+                c[t, y, x] -= h
+            else:
+                b[t, y, x] += h
+                d[t, y, x] -= h
+            fd = (obj(a, b) - obj(c, d)) / (2 * h)
+            assert abs(grad[t, y, x] - fd) <= 1e-6 * max(abs(fd), 1.0), (which, t, y, x)
+
+
+def test_vjp_euler_homogeneity():
+    # L = Psi/sqrt(Phi) is homogeneous of degree 1 in the psi pixels and -1/2 in the phi pixels;
+    # alpha = Psi/Phi of degree 1 and -1.  Euler's theorem fixes the pixel-weighted gradient sums.
+    rng, times, psi, phi = _subpixel_case(23)
+    keep = np.array([0b01111110], np.uint32)
+    for trial in range(5):
+        p = np.concatenate([rng.uniform(8, 30, 2), rng.uniform(-30, 30, 2)])
+        L, A, _ = oracle.traj_eval_subpixel(psi, phi, times, keep, *p, grad=False)
+        _, gpsi, gphi = oracle.traj_vjp(psi, phi, times, keep, *p, gL=1.0, gA=0.0)
+        assert abs((gpsi * psi).sum() - L) <= 1e-12 * max(abs(L), 1)
+        assert abs((gphi * phi).sum() + 0.5 * L) <= 1e-12 * max(abs(L), 1)
+        _, gpsi, gphi = oracle.traj_vjp(psi, phi, times, keep, *p, gL=0.0, gA=1.0)
+        assert abs((gpsi * psi).sum() - A) <= 1e-12 * max(abs(A), 1)
+        assert abs((gphi * phi).sum() + A) <= 1e-12 * max(abs(A), 1)
+
+
+def test_vjp_off_image_and_empty():
+    _, times, psi, phi = _subpixel_case(24)
+    keep = np.array([0xFF], np.uint32)
+    assert oracle.traj_vjp(psi, phi, times, keep, -500.0, -500.0, 0.0, 0.0) is None
+    assert oracle.traj_vjp(psi, phi, times, np.array([0], np.uint32), 10.0, 10.0, 1.0,
+                           1.0) is None
+
+
+def test_adam_first_step_closed_form():
+    # After one step the bias-corrected moments are g and g^2, so the move is lr g/(|g| + eps).
+    rng, times, psi, phi = _subpixel_case(25)
+    keep = np.array([0xFF], np.uint32)
+    p = np.array([17.3, 21.9, 11.0, -7.0])
+    _, _, g = oracle.traj_eval_subpixel(psi, phi, times, keep, *p)
+    lr = np.array([0.1, 0.1, 0.3, 0.3])
+    pr, L, A = oracle.refine_adam(psi, phi, times, keep, p, 1, 0.1, 0.3)
+    assert np.allclose(pr - p, lr * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=0)
+    L1, A1, _ = oracle.traj_eval_subpixel(psi, phi, times, keep, *pr, grad=False)
+    assert L == L1 and A == A1
+
+
+def test_adam_refine_converges_on_a_noiseless_off_grid_mover():
+    # A noiseless point source with a sub-pixel start and off-grid velocity: ascent from an offset
+    # start must raise L to the maximum near the true track (bilinear sampling moves the maximum
+    # by a fraction of a pixel) and bring position and velocity close to the truth.
+    rng = np.random.default_rng(26)
+    T, H, W, k, sig = 12, 64, 96, 9, 1.4
+    times = np.sort(rng.uniform(0, 2.0, T))
+    times[0] = 0.0
+    tru = np.array([20.3, 30.6, 17.37, -4.81])
+    img = np.zeros((T, H, W))
+    psf = np.stack([gaussian_psf(sig, k, 0, 0)] * T)
+    for t in range(T):
+        x, y = tru[0] + tru[2] * times[t], tru[1] + tru[3] * times[t]
+        ix, iy = math.floor(x + 0.5), math.floor(y + 0.5)
+        img[t, iy - 7:iy + 8, ix - 7:ix + 8] += 10.0 * gaussian_psf(sig, 15, x - ix, y - iy)
+    psi, phi = oracle.psi_phi(img, np.ones((T, H, W)), None, psf)
+    keep = np.array([(1 << T) - 1], np.uint32)
+    L_true = oracle.traj_eval_subpixel(psi, phi, times, keep, *tru, grad=False)[0]
+    for off in ((0.8, -0.7, 1.0, -0.8), (-0.5, 0.5, -0.8, 0.6), (0.4, 0.9, 0.7, 0.9)):
+        p0 = tru + np.array(off)
+        L0 = oracle.traj_eval_subpixel(psi, phi, times, keep, *p0, grad=False)[0]
+        pr, L, _ = oracle.refine_adam(psi, phi, times, keep, p0, 100, 0.1, 0.2)
+        assert L0 < 0.8 * L_true
+        assert L >= L_true * (1 - 1e-3)
+        err = np.abs(pr - tru)
+        assert err[:2].max() < 0.3 and err[2:].max() < 0.3, err
+
+
+def test_adam_stops_where_phi_vanishes():
+    _, times, psi, phi = _subpixel_case(27)
+    keep = np.array([0xFF], np.uint32)
+    pr, L, A = oracle.refine_adam(psi, phi, times, keep, [-300.0, -300.0, 0.0, 0.0], 5, 0.1, 0.1)
+    assert np.isnan(L) and np.isnan(A)
+    assert np.array_equal(pr, [-300.0, -300.0, 0.0, 0.0])
