@@ -243,6 +243,92 @@ KB_API int kb_candidate_tracks(const int32_t* cand_pix, const int32_t* cand_slot
                                int x_lo, int y_lo, int wx, int32_t* x0, int32_t* y0,
                                float* out_vx, float* out_vy, int32_t* traj, void* stream);
 
+/*
+ * Sub-pixel evaluation of single trajectories, its backward pass, and refinement off the velocity
+ * grid.  Section 4.1 evaluates single given trajectories along their own tracks, and spaces the
+ * search grid so that neighbouring trajectories stay within about two PSF widths of each other
+ * over the run; the grid spacing thus bounds how closely a found trajectory follows its object.
+ * These calls evaluate a trajectory at a real-valued start and velocity: psi_t and phi_t are read
+ * at (x0 + vx dt_t, y0 + vy dt_t), dt_t = times[t] - times[0], by bilinear interpolation (pixel
+ * centres at integer coordinates; the cell of a position is (floor x, floor y); taps outside the
+ * image read zero), and over a FIXED set of kept epochs (the clip is not re-run)
+ *     Psi = sum_{t kept} psi_t(.),  Phi = sum_{t kept} phi_t(.),
+ *     L = Psi / sqrt(Phi),  alpha = Psi / Phi        (Eq. 1 and 2 on the kept epochs).
+ * L is piecewise bilinear in (x0, y0, vx, vy); its gradient is the one-sided derivative on the
+ * cell containing the position.  Positions are formed in float64 (x0 + vx dt_t with the product
+ * and the sum rounded separately), the bilinear weights and the sums in float32.  A candidate
+ * whose Phi is not > 0 (no kept tap inside the image with phi > 0) gets L = alpha = NaN and a zero
+ * gradient.
+ *
+ * Common arguments:
+ *   psi, phi   [T][H][W] float32 (device), as written by kb_make_psi_phi.
+ *   times      [T] float64 HOST pointer (finite).
+ *   params     [n][4] float32 (device): x0, y0 in pixels, vx, vy in pixels per unit of times.
+ *   keep       [n][ceil(T/32)] uint32 (device): bit t of word t/32 set = epoch t kept (the
+ *              out_mask layout of kb_search); NULL keeps every epoch.
+ * All outputs are caller-owned device arrays.  n = 0 enqueues nothing.
+ * Errors: KB_ERR_INVALID_ARG (null pointers, bad sizes, non-finite times or bad refine
+ * parameters), KB_ERR_UNSUPPORTED (T > KB_MAX_T, sides > 2^20).
+ */
+
+/* kb_traj_eval_fwd -- out_lh, out_flux [n]; out_grad [n][4] (nullable) receives dL/d(params). */
+KB_API int kb_traj_eval_fwd(const float* psi, const float* phi, const double* times, int T, int H,
+                            int W, const float* params, const uint32_t* keep, int n,
+                            float* out_lh, float* out_flux, float* out_grad, void* stream);
+
+/*
+ * kb_traj_eval_bwd -- vector-Jacobian product of kb_traj_eval_fwd.  With upstream weights
+ * gL = grad_lh[c] and gA = grad_flux[c] (either array nullable, read as zeros):
+ *   out_grad_params [n][4] (nullable, overwritten) = gL dL/dparams + gA dalpha/dparams;
+ *   grad_psi, grad_phi [T][H][W] (nullable, ACCUMULATED with atomic adds, in no fixed order):
+ *   each kept in-image tap of weight w on epoch t adds cPsi w to grad_psi and cPhi w to grad_phi,
+ *   cPsi = gL / sqrt(Phi) + gA / Phi,  cPhi = -gL Psi / (2 Phi^1.5) - gA Psi / Phi^2.
+ */
+KB_API int kb_traj_eval_bwd(const float* psi, const float* phi, const double* times, int T, int H,
+                            int W, const float* params, const uint32_t* keep, int n,
+                            const float* grad_lh, const float* grad_flux, float* out_grad_params,
+                            float* grad_psi, float* grad_phi, void* stream);
+
+/* Adam (Kingma & Ba 2015) settings of kb_refine; kb_refine_params_default gives 20 steps,
+ * lr_pos 0.1 px, lr_vel 0.2 px per unit of times, beta1 0.9, beta2 0.999, eps 1e-8. */
+typedef struct kb_refine_params {
+  int n_steps;  /* 0..100000 */
+  float lr_pos; /* step size of x0, y0 (>= 0) */
+  float lr_vel; /* step size of vx, vy (>= 0) */
+  float beta1;  /* [0, 1) */
+  float beta2;  /* [0, 1) */
+  float eps;    /* > 0 */
+} kb_refine_params;
+
+KB_API void kb_refine_params_default(kb_refine_params* rp);
+
+/*
+ * kb_refine -- gradient ascent of L from each candidate's params with Adam, the kept set fixed.
+ * Step k = 1..n_steps evaluates L and g = dL/dparams at the current params and moves them by
+ * lr mhat / (sqrt(vhat) + eps), m = beta1 m + (1 - beta1) g, v = beta2 v + (1 - beta2) g^2,
+ * mhat = m / (1 - beta1^k), vhat = v / (1 - beta2^k); lr is lr_pos for x0, y0 and lr_vel for
+ * vx, vy.  The gradient and the moments are float32; the parameters are carried in float64
+ * between steps and rounded to float32 once at the end.  params are updated in place;
+ * out_lh, out_flux [n] are L and alpha at the returned (rounded) params; out_lh_start [n]
+ * (nullable) is L at the given params.  Where Phi <= 0 is met the ascent of that candidate stops
+ * there (params as they were, rounded; L = alpha = NaN).
+ */
+KB_API int kb_refine(const float* psi, const float* phi, const double* times, int T, int H, int W,
+                     float* params, const uint32_t* keep, int n, const kb_refine_params* rp,
+                     float* out_lh, float* out_flux, float* out_lh_start, void* stream);
+
+/*
+ * kb_candidate_params -- refine inputs of collected survivors: for i < n with cand_pix[i] >= 0,
+ * out_params[i] = (x_lo + cand_pix[i] % wx, y_lo + cand_pix[i] / wx, vx[traj], vy[traj]) with
+ * traj = idx[cand_pix[i] * K + cand_slot[i]], and out_keep[i] (nullable; needs mask) = that
+ * slot's kept-epoch mask from kb_search's out_mask [npix][K][ceil(T/32)].  Other entries get NaN
+ * params (kb_refine then reports NaN) and an all-zero mask.  All arrays are device arrays.
+ */
+KB_API int kb_candidate_params(const int32_t* cand_pix, const int32_t* cand_slot, int n,
+                               const int32_t* idx, const uint32_t* mask, int K, int T,
+                               const float* vx, const float* vy, int x_lo, int y_lo, int wx,
+                               float* out_params, uint32_t* out_keep, void* stream);
+
 /* Number of kernels this library has launched in the process so far (all entry points). */
 KB_API unsigned long long kb_launch_count(void);
 

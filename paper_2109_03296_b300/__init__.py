@@ -8,6 +8,9 @@ Every step of the computation runs in the library's sm_103a kernels; CPU tensors
     res = search(psi, phi, times, vx, vy, SearchParams(...))      # Sections 3, 3.1, 3.2
     pix, slot, count = collect(res, n_max)                        # GPU -> host handoff
     mean, median = stamps(img, var, mask, times, x0, y0, vx, vy)  # Section 3.3
+    params, keep = candidate_params(pix, slot, res, vx, vy)       # off-grid refinement:
+    params, L, alpha, L0 = refine(psi, phi, times, params, keep)  #   Section 4.1, bilinear
+    L, alpha = traj_likelihood(params, psi, phi, times, keep)     # differentiable (autograd)
 """
 import ctypes as C
 from dataclasses import dataclass
@@ -15,11 +18,13 @@ from dataclasses import dataclass
 import numpy as np
 import torch
 
-from ._lib import (KB_MAX_K, KB_MAX_T, KB_WORKSPACE_ALIGN, KbError, SearchParamsC, check, lib)
+from ._lib import (KB_MAX_K, KB_MAX_T, KB_WORKSPACE_ALIGN, KbError, RefineParamsC, SearchParamsC,
+                   check, lib)
 
 __all__ = ["SearchParams", "make_psi_phi", "search", "search_workspace_size", "search_stats",
            "stamps", "collect", "candidate_tracks", "launch_count", "profile_events", "KbError",
-           "search_no_alloc",
+           "search_no_alloc", "RefineParams", "traj_eval", "traj_eval_backward", "TrajEval",
+           "traj_likelihood", "refine", "candidate_params",
            "KB_MAX_T", "KB_MAX_K", "lib", "version", "alloc_workspace"]
 
 
@@ -256,3 +261,139 @@ def search_no_alloc(psi, phi, times, vx, vy, params=None, out=None, stream=None)
                                    _ptr(out["nvalid"]), _ptr(out["nkept"]), _ptr(out["mask"]),
                                    _stream(stream)))
     return out
+
+
+# ------------------------------------------------------------------------------------------------
+# Sub-pixel evaluation, its backward pass and refinement off the velocity grid
+# ------------------------------------------------------------------------------------------------
+
+@dataclass
+class RefineParams:
+    """kb_refine_params (include/kb.h): Adam settings of refine()."""
+    n_steps: int = 20
+    lr_pos: float = 0.1
+    lr_vel: float = 0.2
+    beta1: float = 0.9
+    beta2: float = 0.999
+    eps: float = 1e-8
+
+    def to_c(self):
+        return RefineParamsC(int(self.n_steps), float(self.lr_pos), float(self.lr_vel),
+                             float(self.beta1), float(self.beta2), float(self.eps))
+
+
+def _traj_args(psi, phi, params, keep):
+    _dev(psi, torch.float32, "psi", 3)
+    _dev(phi, torch.float32, "phi", 3)
+    if psi.shape != phi.shape:
+        raise ValueError("psi and phi shapes differ")
+    _dev(params, torch.float32, "params", 2)
+    if params.shape[1] != 4:
+        raise ValueError("params must be [n, 4] (x0, y0, vx, vy)")
+    T = psi.shape[0]
+    if keep is not None:
+        _dev(keep, torch.int32, "keep", 2)
+        if keep.shape != (params.shape[0], (T + 31) // 32):
+            raise ValueError("keep must be [n, ceil(T/32)]")
+    return psi.shape
+
+
+def traj_eval(psi, phi, times, params, keep=None, grad=False, stream=None):
+    """L and alpha [n] of each trajectory by bilinear sampling over its kept epochs; with grad,
+    also dL/dparams [n, 4]."""
+    T, H, W = _traj_args(psi, phi, params, keep)
+    n = params.shape[0]
+    lh = torch.empty(n, dtype=torch.float32, device=psi.device)
+    flux = torch.empty(n, dtype=torch.float32, device=psi.device)
+    g = torch.empty((n, 4), dtype=torch.float32, device=psi.device) if grad else None
+    times = _host_times(times)
+    check(lib().kb_traj_eval_fwd(_ptr(psi), _ptr(phi), times.ctypes.data_as(C.c_void_p), T, H, W,
+                                 _ptr(params), _ptr(keep), n, _ptr(lh), _ptr(flux), _ptr(g),
+                                 _stream(stream)))
+    return (lh, flux, g) if grad else (lh, flux)
+
+
+def traj_eval_backward(psi, phi, times, params, keep, grad_lh=None, grad_flux=None,
+                       want_params=True, want_psi=False, want_phi=False, stream=None):
+    """Vector-Jacobian product of traj_eval: (grad_params [n, 4], grad_psi, grad_phi [T, H, W]),
+    each None unless asked for."""
+    T, H, W = _traj_args(psi, phi, params, keep)
+    n = params.shape[0]
+    dev = psi.device
+    for name, g in (("grad_lh", grad_lh), ("grad_flux", grad_flux)):
+        if g is not None:
+            _dev(g, torch.float32, name, 1)
+    gp = torch.empty((n, 4), dtype=torch.float32, device=dev) if want_params else None
+    gpsi = torch.zeros((T, H, W), dtype=torch.float32, device=dev) if want_psi else None
+    gphi = torch.zeros((T, H, W), dtype=torch.float32, device=dev) if want_phi else None
+    times = _host_times(times)
+    check(lib().kb_traj_eval_bwd(_ptr(psi), _ptr(phi), times.ctypes.data_as(C.c_void_p), T, H, W,
+                                 _ptr(params), _ptr(keep), n, _ptr(grad_lh), _ptr(grad_flux),
+                                 _ptr(gp), _ptr(gpsi), _ptr(gphi), _stream(stream)))
+    return gp, gpsi, gphi
+
+
+class TrajEval(torch.autograd.Function):
+    """(L, alpha) = TrajEval.apply(params, psi, phi, times, keep) with the library's hand-written
+    backward kernel; the kept set is fixed (no gradient flows through the clip)."""
+
+    @staticmethod
+    def forward(ctx, params, psi, phi, times, keep):
+        lh, flux = traj_eval(psi, phi, times, params, keep)
+        ctx.save_for_backward(params, psi, phi, keep)
+        ctx.times = _host_times(times)
+        return lh, flux
+
+    @staticmethod
+    def backward(ctx, grad_lh, grad_flux):
+        params, psi, phi, keep = ctx.saved_tensors
+        need_p, need_psi, need_phi = ctx.needs_input_grad[:3]
+        if grad_lh is not None:
+            grad_lh = grad_lh.contiguous()
+        if grad_flux is not None:
+            grad_flux = grad_flux.contiguous()
+        gp, gpsi, gphi = traj_eval_backward(psi, phi, ctx.times, params, keep, grad_lh, grad_flux,
+                                            need_p, need_psi, need_phi)
+        return gp, gpsi, gphi, None, None
+
+
+def traj_likelihood(params, psi, phi, times, keep=None):
+    """Differentiable (L, alpha) of trajectories params [n, 4]; see TrajEval."""
+    return TrajEval.apply(params, psi, phi, times, keep)
+
+
+def refine(psi, phi, times, params, keep=None, rp=None, inplace=False, stream=None):
+    """Adam ascent of L from params [n, 4] with the kept sets fixed.  Returns (params, L, alpha,
+    L_start); params is updated in place when inplace, else a refined copy."""
+    T, H, W = _traj_args(psi, phi, params, keep)
+    rp = RefineParams() if rp is None else rp
+    n = params.shape[0]
+    if not inplace:
+        params = params.clone()
+    dev = psi.device
+    lh = torch.empty(n, dtype=torch.float32, device=dev)
+    flux = torch.empty(n, dtype=torch.float32, device=dev)
+    lh0 = torch.empty(n, dtype=torch.float32, device=dev)
+    c = rp.to_c()
+    times = _host_times(times)
+    check(lib().kb_refine(_ptr(psi), _ptr(phi), times.ctypes.data_as(C.c_void_p), T, H, W,
+                          _ptr(params), _ptr(keep), n, C.byref(c), _ptr(lh), _ptr(flux), _ptr(lh0),
+                          _stream(stream)))
+    return params, lh, flux, lh0
+
+
+def candidate_params(pix, slot, result, vx, vy, window=None, stream=None):
+    """(params [n, 4], keep [n, ceil(T/32)]) of collected survivors, the inputs of refine()."""
+    idx, mask = result["idx"], result["mask"]
+    wy, wx, K = idx.shape
+    MW = mask.shape[-1]
+    T = 32 * MW     # any T with this word count gives the same gather
+    x_lo, y_lo = (0, 0) if window is None else (window[0], window[2])
+    n = pix.numel()
+    dev = idx.device
+    params = torch.empty((n, 4), dtype=torch.float32, device=dev)
+    keep = torch.empty((n, MW), dtype=torch.int32, device=dev)
+    check(lib().kb_candidate_params(_ptr(pix), _ptr(slot), n, _ptr(idx), _ptr(mask), K, T,
+                                    _ptr(vx), _ptr(vy), int(x_lo), int(y_lo), wx, _ptr(params),
+                                    _ptr(keep), _stream(stream)))
+    return params, keep

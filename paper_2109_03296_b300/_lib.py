@@ -23,7 +23,8 @@ KB_STATIC_SCRATCH_BYTES = 32 << 20
 EXPORTS = ("kb_version", "kb_last_error", "kb_search_params_default", "kb_make_psi_phi",
            "kb_search_workspace_size", "kb_search", "kb_search_stats", "kb_stamps",
            "kb_collect_workspace_size", "kb_collect", "kb_candidate_tracks", "kb_launch_count",
-           "kb_profile_events", "kb_search_no_alloc")
+           "kb_profile_events", "kb_search_no_alloc", "kb_traj_eval_fwd", "kb_traj_eval_bwd",
+           "kb_refine_params_default", "kb_refine", "kb_candidate_params")
 
 
 class KbError(RuntimeError):
@@ -38,6 +39,11 @@ class SearchParamsC(C.Structure):
                 ("q_hi", C.c_float), ("n_sigma", C.c_float), ("clip_on", C.c_int32),
                 ("x_lo", C.c_int32), ("x_hi", C.c_int32), ("y_lo", C.c_int32),
                 ("y_hi", C.c_int32)]
+
+
+class RefineParamsC(C.Structure):
+    _fields_ = [("n_steps", C.c_int32), ("lr_pos", C.c_float), ("lr_vel", C.c_float),
+                ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float)]
 
 
 _LIB = None
@@ -83,6 +89,16 @@ def lib():
     L.kb_search_no_alloc.restype = i
     L.kb_search_no_alloc.argtypes = [p, p, p, i, i, i, p, p, i, C.POINTER(SearchParamsC), p, p, p,
                                      p, p, p, p]
+    L.kb_traj_eval_fwd.restype = i
+    L.kb_traj_eval_fwd.argtypes = [p, p, p, i, i, i, p, p, i, p, p, p, p]
+    L.kb_traj_eval_bwd.restype = i
+    L.kb_traj_eval_bwd.argtypes = [p, p, p, i, i, i, p, p, i, p, p, p, p, p, p]
+    L.kb_refine_params_default.restype = None
+    L.kb_refine_params_default.argtypes = [C.POINTER(RefineParamsC)]
+    L.kb_refine.restype = i
+    L.kb_refine.argtypes = [p, p, p, i, i, i, p, p, i, C.POINTER(RefineParamsC), p, p, p, p]
+    L.kb_candidate_params.restype = i
+    L.kb_candidate_params.argtypes = [p, p, i, p, p, i, i, p, p, i, i, i, p, p, p]
     _LIB = L
     return L
 

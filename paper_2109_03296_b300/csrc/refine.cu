@@ -1,0 +1,464 @@
+// refine.cu -- sub-pixel evaluation of single trajectories, its backward pass, and gradient
+// ascent of the likelihood off the velocity grid (Section 4.1: the grid spacing bounds how
+// closely a found trajectory follows the object; single given trajectories are evaluated along
+// their own tracks).
+//
+// For a candidate with real start (x0, y0) and velocity (vx, vy), epoch t is read at
+// (x0 + vx dt_t, y0 + vy dt_t) by bilinear interpolation of psi_t and phi_t (pixel centres at
+// integer coordinates; taps outside the image read zero), and over the kept epochs
+//   Psi = sum psi_t(.),  Phi = sum phi_t(.),  L = Psi / sqrt(Phi),  alpha = Psi / Phi.
+// The kept set is an input and stays fixed, so L is differentiable almost everywhere in
+// (x0, y0, vx, vy) (piecewise bilinear) and linear / rational in the psi / phi pixels.
+//
+// One warp per candidate, lanes over epochs (lane l takes epochs l, l+32, ...).  Each lane forms
+// its position in float64 (product and sum rounded separately), splits it into cell and
+// fraction, reads the four taps of psi_t and phi_t through the read-only path, and contributes to
+// ten float32 sums: Psi, Phi and the derivatives of both in the four parameters.  A butterfly
+// reduction leaves the same sums, bit for bit, in every lane, so the Adam update of the refine
+// loop runs redundantly in all lanes with no further communication.
+#include <cmath>
+
+#include "kb_internal.cuh"
+
+namespace kb {
+
+constexpr int RF_WARPS = 8;
+constexpr int RF_THREADS = RF_WARPS * 32;
+
+struct EpochDt {
+  double dt[KB_MAX_T];
+};
+
+// The four bilinear taps of one epoch: flat index of the lower-left tap (may point before the
+// image when a tap row or column is outside), fractions, and a validity bit per tap
+// (bit 0: (ix, iy), 1: (ix+1, iy), 2: (ix, iy+1), 3: (ix+1, iy+1)).
+struct Taps {
+  long long base;
+  float ax, ay;
+  unsigned valid;
+};
+
+__device__ __forceinline__ Taps make_taps(double x, double y, int H, int W) {
+  Taps tp;
+  tp.base = 0;
+  tp.ax = 0.f;
+  tp.ay = 0.f;
+  tp.valid = 0u;
+  double fx = floor(x), fy = floor(y);
+  // also false for NaN: such a position has no tap inside the image
+  if (!(fx >= -1.0 && fx <= (double)(W - 1) && fy >= -1.0 && fy <= (double)(H - 1))) return tp;
+  int ix = (int)fx, iy = (int)fy;
+  tp.ax = (float)(x - fx);
+  tp.ay = (float)(y - fy);
+  bool c0 = ix >= 0, c1 = ix + 1 < W, r0 = iy >= 0, r1 = iy + 1 < H;
+  tp.valid = (unsigned)(c0 && r0) | (unsigned)(c1 && r0) << 1 | (unsigned)(c0 && r1) << 2 |
+             (unsigned)(c1 && r1) << 3;
+  tp.base = (long long)iy * W + ix;
+  return tp;
+}
+
+struct Quad {
+  float v00, v01, v10, v11;
+};
+
+__device__ __forceinline__ Quad load_quad(const float* __restrict__ plane, const Taps& tp, int W) {
+  Quad q;
+  q.v00 = (tp.valid & 1u) ? __ldg(plane + tp.base) : 0.f;
+  q.v01 = (tp.valid & 2u) ? __ldg(plane + tp.base + 1) : 0.f;
+  q.v10 = (tp.valid & 4u) ? __ldg(plane + tp.base + W) : 0.f;
+  q.v11 = (tp.valid & 8u) ? __ldg(plane + tp.base + W + 1) : 0.f;
+  return q;
+}
+
+// value and d/dx, d/dy of the bilinear sample
+__device__ __forceinline__ void bilerp(const Quad& q, float ax, float ay, float& v, float& gx,
+                                       float& gy) {
+  float top = fmaf(ax, q.v01 - q.v00, q.v00);
+  float bot = fmaf(ax, q.v11 - q.v10, q.v10);
+  v = fmaf(ay, bot - top, top);
+  gx = fmaf(ay, (q.v11 - q.v10) - (q.v01 - q.v00), q.v01 - q.v00);
+  gy = bot - top;
+}
+
+// s[0] = Psi, s[1] = Phi, s[2..5] = dPsi/d(x0, y0, vx, vy), s[6..9] = dPhi/d(...)
+constexpr int NSUM = 10;
+
+// Track parameters in float64: the inputs are float32, but the refine loop accumulates its steps
+// in float64 so that the side of a bilinear cell edge on which an epoch falls is decided as in
+// exact arithmetic (float32 parameters near x ~ 4000 px carry 2.4e-4 px of rounding, times dt).
+struct Track {
+  double x0, y0, vx, vy;
+};
+
+__device__ __forceinline__ Track to_track(float4 p) {
+  return Track{(double)p.x, (double)p.y, (double)p.z, (double)p.w};
+}
+
+__device__ __forceinline__ double track_pos(double p0, double v, double dt) {
+  return __dadd_rn(p0, __dmul_rn(v, dt));
+}
+
+template <int J>
+__device__ __forceinline__ void lane_sums(const float* __restrict__ psi,
+                                          const float* __restrict__ phi, int T, int H, int W,
+                                          const double (&dt)[J], unsigned kbits, const Track& p,
+                                          float (&s)[NSUM]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < NSUM; ++i) s[i] = 0.f;
+  const size_t hw = (size_t)H * W;
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    int t = lane + 32 * j;
+    if (t >= T || !((kbits >> j) & 1u)) continue;
+    Taps tp = make_taps(track_pos(p.x0, p.vx, dt[j]), track_pos(p.y0, p.vy, dt[j]), H, W);
+    if (!tp.valid) continue;
+    Quad qp = load_quad(psi + (size_t)t * hw, tp, W);
+    Quad qf = load_quad(phi + (size_t)t * hw, tp, W);
+    float vp, gpx, gpy, vf, gfx, gfy;
+    bilerp(qp, tp.ax, tp.ay, vp, gpx, gpy);
+    bilerp(qf, tp.ax, tp.ay, vf, gfx, gfy);
+    float d = (float)dt[j];
+    s[0] += vp;
+    s[1] += vf;
+    s[2] += gpx;
+    s[3] += gpy;
+    s[4] = fmaf(gpx, d, s[4]);
+    s[5] = fmaf(gpy, d, s[5]);
+    s[6] += gfx;
+    s[7] += gfy;
+    s[8] = fmaf(gfx, d, s[8]);
+    s[9] = fmaf(gfy, d, s[9]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int i = 0; i < NSUM; ++i) s[i] += __shfl_xor_sync(0xffffffffu, s[i], o);
+}
+
+// Per-lane state loaded once per candidate: the lane's dt values and its kept bits (bit j for
+// epoch lane + 32 j).
+template <int J>
+__device__ __forceinline__ unsigned lane_setup(const double* s_dt, const uint32_t* __restrict__ keep,
+                                               int MW, long long c, int T, double (&dt)[J]) {
+  const int lane = threadIdx.x & 31;
+  unsigned kbits = 0u;
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    int t = lane + 32 * j;
+    dt[j] = t < T ? s_dt[t] : 0.0;
+    unsigned b = 0u;
+    if (t < T) b = keep ? ((__ldg(keep + c * MW + j) >> lane) & 1u) : 1u;
+    kbits |= b << j;
+  }
+  return kbits;
+}
+
+__device__ __forceinline__ void load_dt(double* s_dt, const EpochDt& e, int T) {
+  for (int t = threadIdx.x; t < T; t += blockDim.x) s_dt[t] = e.dt[t];
+  __syncthreads();
+}
+
+template <int J>
+__global__ void __launch_bounds__(RF_THREADS) traj_fwd_kernel(
+    const float* __restrict__ psi, const float* __restrict__ phi, int T, int H, int W,
+    const float4* __restrict__ params, const uint32_t* __restrict__ keep, int MW, int n,
+    EpochDt e, float* __restrict__ out_lh, float* __restrict__ out_flux,
+    float4* __restrict__ out_grad) {
+  __shared__ double s_dt[KB_MAX_T];
+  load_dt(s_dt, e, T);
+  const long long c = (long long)blockIdx.x * RF_WARPS + (threadIdx.x >> 5);
+  if (c >= n) return;
+  double dt[J];
+  unsigned kbits = lane_setup<J>(s_dt, keep, MW, c, T, dt);
+  const Track p = to_track(__ldg(params + c));
+  float s[NSUM];
+  lane_sums<J>(psi, phi, T, H, W, dt, kbits, p, s);
+  if ((threadIdx.x & 31) != 0) return;
+  if (!(s[1] > 0.f)) {
+    out_lh[c] = __int_as_float(0x7fc00000);
+    out_flux[c] = __int_as_float(0x7fc00000);
+    if (out_grad) out_grad[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
+  float rs = sqrtf(s[1]);
+  out_lh[c] = s[0] / rs;
+  out_flux[c] = s[0] / s[1];
+  if (out_grad) {
+    float a = 1.f / rs, b = -0.5f * s[0] / (s[1] * rs);
+    out_grad[c] = make_float4(fmaf(b, s[6], a * s[2]), fmaf(b, s[7], a * s[3]),
+                              fmaf(b, s[8], a * s[4]), fmaf(b, s[9], a * s[5]));
+  }
+}
+
+template <int J>
+__global__ void __launch_bounds__(RF_THREADS) traj_bwd_kernel(
+    const float* __restrict__ psi, const float* __restrict__ phi, int T, int H, int W,
+    const float4* __restrict__ params, const uint32_t* __restrict__ keep, int MW, int n,
+    EpochDt e, const float* __restrict__ grad_lh, const float* __restrict__ grad_flux,
+    float4* __restrict__ out_grad, float* __restrict__ grad_psi, float* __restrict__ grad_phi) {
+  __shared__ double s_dt[KB_MAX_T];
+  load_dt(s_dt, e, T);
+  const long long c = (long long)blockIdx.x * RF_WARPS + (threadIdx.x >> 5);
+  if (c >= n) return;
+  const int lane = threadIdx.x & 31;
+  double dt[J];
+  unsigned kbits = lane_setup<J>(s_dt, keep, MW, c, T, dt);
+  const Track p = to_track(__ldg(params + c));
+  float s[NSUM];
+  lane_sums<J>(psi, phi, T, H, W, dt, kbits, p, s);
+  if (!(s[1] > 0.f)) {
+    if (lane == 0 && out_grad) out_grad[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
+  float gL = grad_lh ? __ldg(grad_lh + c) : 0.f;
+  float gA = grad_flux ? __ldg(grad_flux + c) : 0.f;
+  float rs = sqrtf(s[1]);
+  // dL/dPsi = 1/sqrt(Phi), dL/dPhi = -Psi/(2 Phi^1.5); dalpha/dPsi = 1/Phi, dalpha/dPhi = -Psi/Phi^2
+  float cps = gL / rs + gA / s[1];
+  float cph = -0.5f * gL * s[0] / (s[1] * rs) - gA * s[0] / (s[1] * s[1]);
+  if (lane == 0 && out_grad)
+    out_grad[c] = make_float4(fmaf(cph, s[6], cps * s[2]), fmaf(cph, s[7], cps * s[3]),
+                              fmaf(cph, s[8], cps * s[4]), fmaf(cph, s[9], cps * s[5]));
+  if (!grad_psi && !grad_phi) return;
+  const size_t hw = (size_t)H * W;
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    int t = lane + 32 * j;
+    if (t >= T || !((kbits >> j) & 1u)) continue;
+    Taps tp = make_taps(track_pos(p.x0, p.vx, dt[j]), track_pos(p.y0, p.vy, dt[j]), H, W);
+    const float w[4] = {(1.f - tp.ax) * (1.f - tp.ay), tp.ax * (1.f - tp.ay),
+                        (1.f - tp.ax) * tp.ay, tp.ax * tp.ay};
+    const long long off[4] = {0, 1, W, (long long)W + 1};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (!((tp.valid >> k) & 1u)) continue;
+      size_t i = (size_t)t * hw + (size_t)(tp.base + off[k]);
+      if (grad_psi) atomicAdd(grad_psi + i, cps * w[k]);
+      if (grad_phi) atomicAdd(grad_phi + i, cph * w[k]);
+    }
+  }
+}
+
+struct AdamConsts {
+  int n_steps;
+  float lr_pos, lr_vel, b1, b2, eps;
+};
+
+template <int J>
+__global__ void __launch_bounds__(RF_THREADS) refine_kernel(
+    const float* __restrict__ psi, const float* __restrict__ phi, int T, int H, int W,
+    float4* __restrict__ params, const uint32_t* __restrict__ keep, int MW, int n, EpochDt e,
+    AdamConsts ac, float* __restrict__ out_lh, float* __restrict__ out_flux,
+    float* __restrict__ out_lh_start) {
+  __shared__ double s_dt[KB_MAX_T];
+  load_dt(s_dt, e, T);
+  const long long c = (long long)blockIdx.x * RF_WARPS + (threadIdx.x >> 5);
+  if (c >= n) return;
+  const int lane = threadIdx.x & 31;
+  double dt[J];
+  unsigned kbits = lane_setup<J>(s_dt, keep, MW, c, T, dt);
+  Track p = to_track(params[c]);
+  float m[4] = {0.f, 0.f, 0.f, 0.f}, v[4] = {0.f, 0.f, 0.f, 0.f};
+  float b1k = 1.f, b2k = 1.f;
+  float s[NSUM];
+  bool ok = true;
+  for (int k = 0; k <= ac.n_steps; ++k) {
+    // the returned params are float32: evaluate the final L and alpha at exactly those
+    if (k == ac.n_steps && k > 0)
+      p = to_track(make_float4((float)p.x0, (float)p.y0, (float)p.vx, (float)p.vy));
+    lane_sums<J>(psi, phi, T, H, W, dt, kbits, p, s);
+    if (!(s[1] > 0.f)) {
+      if (k == 0 && out_lh_start && lane == 0) out_lh_start[c] = __int_as_float(0x7fc00000);
+      ok = false;
+      break;
+    }
+    float rs = sqrtf(s[1]);
+    if (k == 0 && out_lh_start && lane == 0) out_lh_start[c] = s[0] / rs;
+    if (k == ac.n_steps) break;
+    float a = 1.f / rs, b = -0.5f * s[0] / (s[1] * rs);
+    float g[4] = {fmaf(b, s[6], a * s[2]), fmaf(b, s[7], a * s[3]), fmaf(b, s[8], a * s[4]),
+                  fmaf(b, s[9], a * s[5])};
+    b1k *= ac.b1;
+    b2k *= ac.b2;
+    float step[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      m[i] = fmaf(ac.b1, m[i], (1.f - ac.b1) * g[i]);
+      v[i] = fmaf(ac.b2, v[i], (1.f - ac.b2) * g[i] * g[i]);
+      float mh = m[i] / (1.f - b1k), vh = v[i] / (1.f - b2k);
+      step[i] = (i < 2 ? ac.lr_pos : ac.lr_vel) * mh / (sqrtf(vh) + ac.eps);
+    }
+    p.x0 += (double)step[0];
+    p.y0 += (double)step[1];
+    p.vx += (double)step[2];
+    p.vy += (double)step[3];
+  }
+  if (lane != 0) return;
+  params[c] = make_float4((float)p.x0, (float)p.y0, (float)p.vx, (float)p.vy);
+  if (ok) {
+    float rs = sqrtf(s[1]);
+    out_lh[c] = s[0] / rs;
+    out_flux[c] = s[0] / s[1];
+  } else {
+    out_lh[c] = __int_as_float(0x7fc00000);
+    out_flux[c] = __int_as_float(0x7fc00000);
+  }
+}
+
+__global__ void candidate_params_kernel(const int32_t* __restrict__ cand_pix,
+                                        const int32_t* __restrict__ cand_slot, int n,
+                                        const int32_t* __restrict__ idx,
+                                        const uint32_t* __restrict__ mask, int K, int MW,
+                                        const float* __restrict__ vx, const float* __restrict__ vy,
+                                        int x_lo, int y_lo, int wx, float4* __restrict__ out_params,
+                                        uint32_t* __restrict__ out_keep) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int pix = cand_pix[i];
+  int traj = -1;
+  long long slot = -1;
+  if (pix >= 0) {
+    slot = (long long)pix * K + cand_slot[i];
+    traj = idx[slot];
+  }
+  if (traj < 0) {
+    float q = __int_as_float(0x7fc00000);
+    out_params[i] = make_float4(q, q, q, q);
+    if (out_keep)
+      for (int w = 0; w < MW; ++w) out_keep[i * MW + w] = 0u;
+    return;
+  }
+  out_params[i] = make_float4((float)(x_lo + pix % wx), (float)(y_lo + pix / wx), vx[traj],
+                              vy[traj]);
+  if (out_keep)
+    for (int w = 0; w < MW; ++w) out_keep[i * MW + w] = mask[slot * MW + w];
+}
+
+static int check_common(const char* who, const float* psi, const float* phi, const double* times,
+                        int T, int H, int W, const void* params, int n, EpochDt& e) {
+  if (!psi || !phi || !times) return fail(KB_ERR_INVALID_ARG, "%s: null pointer argument", who);
+  if (n < 0 || T < 1 || H < 1 || W < 1) return fail(KB_ERR_INVALID_ARG, "%s: bad sizes", who);
+  if (n > 0 && !params) return fail(KB_ERR_INVALID_ARG, "%s: null params", who);
+  if (T > KB_MAX_T) return fail(KB_ERR_UNSUPPORTED, "%s: T > KB_MAX_T", who);
+  if (H > (1 << 20) || W > (1 << 20))
+    return fail(KB_ERR_UNSUPPORTED, "%s: image sides are limited to 2^20 pixels", who);
+  for (int t = 0; t < T; ++t) {
+    if (!std::isfinite(times[t])) return fail(KB_ERR_INVALID_ARG, "%s: times not finite", who);
+    e.dt[t] = times[t] - times[0];
+  }
+  return KB_OK;
+}
+
+static inline unsigned rf_blocks(int n) { return (unsigned)((n + RF_WARPS - 1) / RF_WARPS); }
+
+}  // namespace kb
+
+extern "C" int kb_traj_eval_fwd(const float* psi, const float* phi, const double* times, int T,
+                                int H, int W, const float* params, const uint32_t* keep, int n,
+                                float* out_lh, float* out_flux, float* out_grad, void* stream) {
+  using namespace kb;
+  EpochDt e{};
+  if (int rc = check_common("kb_traj_eval_fwd", psi, phi, times, T, H, W, params, n, e)) return rc;
+  if (n > 0 && (!out_lh || !out_flux))
+    return fail(KB_ERR_INVALID_ARG, "kb_traj_eval_fwd: null output");
+  if (n == 0) return KB_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int MW = (T + 31) / 32;
+  const float4* p4 = reinterpret_cast<const float4*>(params);
+  float4* g4 = reinterpret_cast<float4*>(out_grad);
+  if (MW == 1)
+    traj_fwd_kernel<1><<<rf_blocks(n), RF_THREADS, 0, st>>>(psi, phi, T, H, W, p4, keep, MW, n, e,
+                                                             out_lh, out_flux, g4);
+  else
+    traj_fwd_kernel<4><<<rf_blocks(n), RF_THREADS, 0, st>>>(psi, phi, T, H, W, p4, keep, MW, n, e,
+                                                             out_lh, out_flux, g4);
+  KB_LAUNCH_CHECK("traj_fwd_kernel");
+  return KB_OK;
+}
+
+extern "C" int kb_traj_eval_bwd(const float* psi, const float* phi, const double* times, int T,
+                                int H, int W, const float* params, const uint32_t* keep, int n,
+                                const float* grad_lh, const float* grad_flux,
+                                float* out_grad_params, float* grad_psi, float* grad_phi,
+                                void* stream) {
+  using namespace kb;
+  EpochDt e{};
+  if (int rc = check_common("kb_traj_eval_bwd", psi, phi, times, T, H, W, params, n, e)) return rc;
+  if (n == 0) return KB_OK;
+  if (!out_grad_params && !grad_psi && !grad_phi) return KB_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int MW = (T + 31) / 32;
+  const float4* p4 = reinterpret_cast<const float4*>(params);
+  float4* g4 = reinterpret_cast<float4*>(out_grad_params);
+  if (MW == 1)
+    traj_bwd_kernel<1><<<rf_blocks(n), RF_THREADS, 0, st>>>(
+        psi, phi, T, H, W, p4, keep, MW, n, e, grad_lh, grad_flux, g4, grad_psi, grad_phi);
+  else
+    traj_bwd_kernel<4><<<rf_blocks(n), RF_THREADS, 0, st>>>(
+        psi, phi, T, H, W, p4, keep, MW, n, e, grad_lh, grad_flux, g4, grad_psi, grad_phi);
+  KB_LAUNCH_CHECK("traj_bwd_kernel");
+  return KB_OK;
+}
+
+extern "C" void kb_refine_params_default(kb_refine_params* rp) {
+  if (!rp) return;
+  rp->n_steps = 20;
+  rp->lr_pos = 0.1f;
+  rp->lr_vel = 0.2f;
+  rp->beta1 = 0.9f;
+  rp->beta2 = 0.999f;
+  rp->eps = 1e-8f;
+}
+
+extern "C" int kb_refine(const float* psi, const float* phi, const double* times, int T, int H,
+                         int W, float* params, const uint32_t* keep, int n,
+                         const kb_refine_params* rp, float* out_lh, float* out_flux,
+                         float* out_lh_start, void* stream) {
+  using namespace kb;
+  EpochDt e{};
+  if (int rc = check_common("kb_refine", psi, phi, times, T, H, W, params, n, e)) return rc;
+  if (!rp) return fail(KB_ERR_INVALID_ARG, "kb_refine: null refine parameters");
+  if (rp->n_steps < 0 || rp->n_steps > 100000)
+    return fail(KB_ERR_INVALID_ARG, "kb_refine: n_steps outside 0..100000");
+  if (!(std::isfinite(rp->lr_pos) && rp->lr_pos >= 0.f && std::isfinite(rp->lr_vel) &&
+        rp->lr_vel >= 0.f))
+    return fail(KB_ERR_INVALID_ARG, "kb_refine: learning rates must be finite and >= 0");
+  if (!(rp->beta1 >= 0.f && rp->beta1 < 1.f && rp->beta2 >= 0.f && rp->beta2 < 1.f))
+    return fail(KB_ERR_INVALID_ARG, "kb_refine: beta1, beta2 must lie in [0, 1)");
+  if (!(rp->eps > 0.f && std::isfinite(rp->eps)))
+    return fail(KB_ERR_INVALID_ARG, "kb_refine: eps must be finite and > 0");
+  if (n > 0 && (!out_lh || !out_flux)) return fail(KB_ERR_INVALID_ARG, "kb_refine: null output");
+  if (n == 0) return KB_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  AdamConsts ac{rp->n_steps, rp->lr_pos, rp->lr_vel, rp->beta1, rp->beta2, rp->eps};
+  const int MW = (T + 31) / 32;
+  float4* p4 = reinterpret_cast<float4*>(params);
+  if (MW == 1)
+    refine_kernel<1><<<rf_blocks(n), RF_THREADS, 0, st>>>(psi, phi, T, H, W, p4, keep, MW, n, e,
+                                                           ac, out_lh, out_flux, out_lh_start);
+  else
+    refine_kernel<4><<<rf_blocks(n), RF_THREADS, 0, st>>>(psi, phi, T, H, W, p4, keep, MW, n, e,
+                                                           ac, out_lh, out_flux, out_lh_start);
+  KB_LAUNCH_CHECK("refine_kernel");
+  return KB_OK;
+}
+
+extern "C" int kb_candidate_params(const int32_t* cand_pix, const int32_t* cand_slot, int n,
+                                   const int32_t* idx, const uint32_t* mask, int K, int T,
+                                   const float* vx, const float* vy, int x_lo, int y_lo, int wx,
+                                   float* out_params, uint32_t* out_keep, void* stream) {
+  using namespace kb;
+  if (n < 0 || K < 1 || K > KB_MAX_K || T < 1 || wx < 1)
+    return fail(KB_ERR_INVALID_ARG, "kb_candidate_params: bad sizes");
+  if (T > KB_MAX_T) return fail(KB_ERR_UNSUPPORTED, "kb_candidate_params: T > KB_MAX_T");
+  if (n == 0) return KB_OK;
+  if (!cand_pix || !cand_slot || !idx || !vx || !vy || !out_params || (out_keep && !mask))
+    return fail(KB_ERR_INVALID_ARG, "kb_candidate_params: null pointer argument");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  candidate_params_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+      cand_pix, cand_slot, n, idx, mask, K, (T + 31) / 32, vx, vy, x_lo, y_lo, wx,
+      reinterpret_cast<float4*>(out_params), out_keep);
+  KB_LAUNCH_CHECK("candidate_params_kernel");
+  return KB_OK;
+}

@@ -13,6 +13,8 @@ Section 4.1).  The DECam NEO data are not available, so these stand in for them:
   full      T=100 over 5 nights, 4096x4096, var_t U[0.5,2], 1% masked, PSF sigma_t U[1,2.5] on
             15x15, 1000 movers SNR U[1,8]; grid 512 x 256 (92-550 px/day, +-pi/10).
   refine    the tiny stack with movers at off-grid sub-pixel starts and velocities.
+  decam_refine  the decam recipe (own seed) with movers at sub-pixel starts and off-grid
+            velocities, uniform between grid points: the workload of the off-grid refinement.
   decam_small  the decam recipe on 1024x1024 with 50 movers (psi+phi 218 MB, above the 126 MB
             L2).
   decam_half   the decam recipe on 2046x2048 with 100 movers (same mover density; psi+phi
@@ -76,7 +78,13 @@ CONFIGS = {
                    mask_frac=0.0, n_movers=3, snr=("const", 5.0), spike_frac=0.0,
                    grid=(50.0, 400.0, 16, -0.2, 0.2, 8), times="uniform0.2",
                    integer_tracks=False, movers_on_grid=False, start_margin=28, seed=3,
-                   K=1, lh_min=7.0, min_obs=5),
+                   K=1, lh_min=7.0, min_obs=5, subpixel_starts=True),
+    "decam_refine": dict(T=26, H=2046, W=4094, psf_k=15, psf_sigma=(1.0, 2.0), var=(0.5, 2.0),
+                         mask_frac=0.005, n_movers=200, snr=("loguniform", 1.5, 10.0),
+                         spike_frac=0.1, grid=(90.0, 500.0, 256, -0.3, 0.3, 128),
+                         times=("nights", (7, 7, 6, 6)), integer_tracks=False,
+                         movers_on_grid=False, start_margin=0, seed=7, K=8, lh_min=10.0,
+                         min_obs=15, subpixel_starts=True),
 }
 
 
@@ -186,7 +194,7 @@ def make_stack(name="tiny", seed=None, H=None, W=None, T=None, n_movers=None, gr
         mvx, mvy = sp * np.cos(an), sp * np.sin(an)
         gidx = np.full(nm, -1)
     mx0f, my0f = mx0.astype(np.float64), my0.astype(np.float64)
-    if name == "refine":
+    if c.get("subpixel_starts"):
         mx0f = mx0f + rng.uniform(-0.5, 0.5, nm)
         my0f = my0f + rng.uniform(-0.5, 0.5, nm)
     snr = _snr(c["snr"], nm, rng)
