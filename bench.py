@@ -8,6 +8,12 @@ trajectory-epoch evaluations per second: start pixels x trajectories x epochs of
 the step's device time.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+  python bench.py --workload decam_refine     # off-grid refinement of the best candidates
+
+The decam_refine line times the refinement stage on its own: the stack is searched once, the
+best --n-refine survivors are gathered, and one step = 20 Adam steps of every candidate
+(bilinear sub-pixel evaluation and its gradient, kept sets fixed) plus one forward and one
+backward pass at the refined tracks that also accumulates dL/dpsi and dL/dphi.
 
 N > 1 runs under torchrun, one rank per GPU; each rank searches its own stack (stacks are
 independent: weak scaling, no collective on the data path).  --impl reference times the FP64 CPU
@@ -31,11 +37,14 @@ WORKLOAD = "decam"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 3; for decam_refine, enough for ~1.5 s)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--n-stamps", type=int, default=10000)
+    ap.add_argument("--n-refine", type=int, default=100000)
+    ap.add_argument("--refine-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -159,10 +168,57 @@ def oracle_rate(target_s, workload):
                 n_traj=len(vx), H=H, W=W)
 
 
+def _refine_oracle_inputs(workload, n_rand=2000):
+    """Likelihood planes of the workload (FP64) and candidate tracks drawn from them without the
+    CUDA path: for each injected mover the grid velocity nearest to the truth at the rounded start
+    (what a grid search reports), plus random grid tracks; every epoch kept."""
+    key = ("refine", workload)
+    if key not in _ORACLE_DATA:
+        import numpy as np
+        from synth import make_likelihood_stack
+        psi, phi, times, vx, vy, mv = make_likelihood_stack(workload)
+        T, H, W = psi.shape
+        rng = np.random.default_rng(12345)
+        P = []
+        for i in range(len(mv["x0"])):
+            g = np.argmin((vx - mv["vx"][i]) ** 2 + (vy - mv["vy"][i]) ** 2)
+            P.append([math.floor(mv["x0"][i] + 0.5), math.floor(mv["y0"][i] + 0.5), vx[g], vy[g]])
+        for _ in range(n_rand):
+            k = rng.integers(len(vx))
+            P.append([rng.integers(0, W), rng.integers(0, H), vx[k], vy[k]])
+        P = np.array(P, np.float32).astype(np.float64)
+        keep = np.array([(1 << T) - 1 if T < 32 else 0xFFFFFFFF] * ((T + 31) // 32), np.uint32)
+        if T % 32:
+            keep[-1] = (1 << (T % 32)) - 1
+        _ORACLE_DATA[key] = (psi.astype(np.float64), phi.astype(np.float64), times, P, keep)
+    return _ORACLE_DATA[key]
+
+
+def oracle_refine_rate(target_s, workload, n_steps):
+    """Oracle refine (FP64 C Adam, one candidate per call, one thread) on the first candidates of
+    _refine_oracle_inputs; the count doubles until a run takes more than half of target_s.
+    Returns TE/s counting (n_steps + 1) evaluations x T epochs per candidate."""
+    import oracle
+    psi, phi, times, P, keep = _refine_oracle_inputs(workload)
+    T = psi.shape[0]
+    m = 16
+    while True:
+        t0 = time.perf_counter()
+        for i in range(m):
+            oracle.refine_adam(psi, phi, times, keep, P[i % len(P)], n_steps, 0.1, 0.2)
+        dt = time.perf_counter() - t0
+        if dt * 2 > target_s or m >= (1 << 20):
+            break
+        m *= 2
+    return dict(value=m * (n_steps + 1) * T / dt, seconds=dt, n=m, T=T, threads=1)
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
+    if args.workload == "decam_refine":
+        return run_reference_refine(args)
     r = None
     for _ in range(args.warmup):
         oracle_rate(args.cpu_seconds / 8, args.workload)
@@ -185,6 +241,38 @@ def run_reference(args):
         "cpu_baseline": {"value": v, "unit": "TE/s", "cores": r["threads"], "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": v, "unit": "TE/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def run_reference_refine(args):
+    for _ in range(args.warmup):
+        oracle_refine_rate(args.cpu_seconds / 8, args.workload, args.refine_steps)
+    vals, t_all, r = [], 0.0, None
+    for _ in range(args.steps):
+        r = oracle_refine_rate(args.cpu_seconds, args.workload, args.refine_steps)
+        vals.append(r["value"])
+        t_all += r["seconds"]
+    v = statistics.median(vals)
+    sample = ("oracle refine (FP64 C Adam, %d steps, one thread) of %d candidate tracks x %d "
+              "epochs of the %s likelihood planes; TE/s" % (args.refine_steps, r["n"], r["T"],
+                                                          args.workload))
+    print(json.dumps({
+        "impl": "reference", "metric": "refine trajectory-epoch evals/sec", "value": v,
+        "unit": "TE/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * t_all / max(1, args.steps), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": refine_config(args),
+        "cpu_baseline": {"value": v, "unit": "TE/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": "TE/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def refine_config(args):
+    cfg = workload_config(args.workload)
+    cfg["workload"] = ("%s; refinement of the best %d survivors: %d Adam steps (lr 0.1 px, "
+                       "0.2 px/day), then forward + backward with dL/dpsi, dL/dphi"
+                       % (cfg["workload"], args.n_refine, args.refine_steps))
+    cfg.update(n_refine=args.n_refine, refine_steps=args.refine_steps)
+    return cfg
 
 
 def workload_config(name):
@@ -375,10 +463,249 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------------------------------------------
+# our arm, refinement stage
+# ------------------------------------------------------------------------------------------------
+def _match_movers(params, lh, movers, times, max_px=2.5):
+    """Highest-L candidate whose track stays within max_px of each mover's true track at the
+    first and last epoch (-1 if none)."""
+    import numpy as np
+    span = times[-1] - times[0]
+    P = params.astype(np.float64)
+    out = []
+    for i in range(len(movers["x0"])):
+        tx0, ty0, tvx, tvy = (movers[k][i] for k in ("x0", "y0", "vx", "vy"))
+        d0 = np.hypot(P[:, 0] - tx0, P[:, 1] - ty0)
+        d1 = np.hypot(P[:, 0] + P[:, 2] * span - (tx0 + tvx * span),
+                      P[:, 1] + P[:, 3] * span - (ty0 + tvy * span))
+        m = (d0 <= max_px) & (d1 <= max_px) & np.isfinite(lh)
+        out.append(int(np.argmax(np.where(m, lh, -np.inf))) if m.any() else -1)
+    return np.array(out)
+
+
+def run_refine(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2109_03296_b300 as kb
+    from synth import CONFIGS, make_stack
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    c = CONFIGS[args.workload]
+    s = make_stack(args.workload, seed=c["seed"] + 100 * rank)
+    T, H, W = s.img.shape
+    sp = kb.SearchParams(k=c["K"], lh_min=c["lh_min"], min_obs=c["min_obs"])
+    rp = kb.RefineParams(n_steps=args.refine_steps)
+    stream = torch.cuda.current_stream()
+
+    # search once (not timed): the candidates and their kept sets
+    dv = lambda a: torch.from_numpy(a).to(dev)
+    psi, phi = kb.make_psi_phi(dv(s.img), dv(s.var), dv(s.mask), dv(s.psf))
+    vx, vy = dv(s.vx), dv(s.vy)
+    res = kb.search(psi, phi, s.times, vx, vy, sp)
+    pix, slot, count = kb.collect(res, args.n_refine)
+    params0, keep = kb.candidate_params(pix, slot, res, vx, vy)
+    del res
+    # the best n_refine survivors, or all of them when fewer survive
+    n = min(args.n_refine, int(count.item()))
+    params0, keep = params0[:n].contiguous(), keep[:n].contiguous()
+    work = torch.empty_like(params0)
+    gpsi = torch.empty_like(psi)
+    gphi = torch.empty_like(phi)
+    ones = torch.ones(n, dtype=torch.float32, device=dev)
+    lh = torch.empty(n, dtype=torch.float32, device=dev)
+    times = np.ascontiguousarray(s.times, np.float64)
+    def stage_events(steps):
+        out = {k: [torch.cuda.Event(enable_timing=True) for _ in range(2 * steps)]
+               for k in ("refine", "fwd", "bwd")}
+        for lst in out.values():
+            for e in lst:       # torch creates the CUDA event on first record
+                e.record(stream)
+        return out
+
+    ev = stage_events(args.steps)
+
+    def step(p_src, i=None):
+        work.copy_(p_src)
+        if i is not None:
+            ev["refine"][2 * i].record(stream)
+        out = kb.refine(psi, phi, times, work, keep, rp, inplace=True)
+        if i is not None:
+            ev["refine"][2 * i + 1].record(stream)
+            ev["fwd"][2 * i].record(stream)
+        L, A = kb.traj_eval(psi, phi, times, work, keep)
+        if i is not None:
+            ev["fwd"][2 * i + 1].record(stream)
+        gpsi.zero_()
+        gphi.zero_()
+        if i is not None:
+            ev["bwd"][2 * i].record(stream)
+        gp, _, _ = kb.traj_eval_backward(psi, phi, times, work, keep, ones, None, True,
+                                         grad_psi=gpsi, grad_phi=gphi)
+        if i is not None:
+            ev["bwd"][2 * i + 1].record(stream)
+        return out, L, A, gp
+
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.warmup):
+        step(params0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if args.auto_steps:
+        # a step takes a few ms: time enough of them to span ~1.5 s, so that the clock sampler
+        # (200 ms period) sees the timed region
+        per = e0.elapsed_time(e1) / max(1, args.warmup)
+        args.steps = max(3, int(math.ceil(1500.0 / max(per, 1e-3))))
+        if world > 1:   # every rank times the same number of steps
+            t = torch.tensor([args.steps], dtype=torch.int64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            args.steps = int(t.item())
+        ev = stage_events(args.steps)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    launches0 = kb.launch_count()
+    with ClockSampler(local) as clk:
+        barrier()
+        e0.record(stream)
+        for i in range(args.steps):
+            out = step(params0, i)
+        e1.record(stream)
+        barrier()
+    launches = kb.launch_count() - launches0
+    ms = e0.elapsed_time(e1)
+    clocks = clk.summary()
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    evals = rp.n_steps + 1 + 2
+    te_step = n * T * evals
+    value = world * te_step * args.steps / (ms_max / 1e3)
+    part = {k: statistics.mean(ev[k][2 * i].elapsed_time(ev[k][2 * i + 1])
+                               for i in range(args.steps)) for k in ev}
+
+    # recovery of the injected movers: grid search vs refined
+    _, L1, _, L0 = out[0]
+    P0, P1 = params0.cpu().numpy(), out[0][0].cpu().numpy()
+    L0, L1 = L0.cpu().numpy(), L1.cpu().numpy()
+    i0 = _match_movers(P0, L0, s.movers, s.times)
+    i1 = _match_movers(P1, L1, s.movers, s.times)
+    both = (i0 >= 0) & (i1 >= 0)
+    tv = np.stack([s.movers["vx"], s.movers["vy"]], 1)
+    tp = np.stack([s.movers["x0"], s.movers["y0"]], 1)
+    ev0 = np.hypot(*(P0[i0[both], 2:] - tv[both]).T)
+    ev1 = np.hypot(*(P1[i1[both], 2:] - tv[both]).T)
+    ep0 = np.hypot(*(P0[i0[both], :2] - tp[both]).T)
+    ep1 = np.hypot(*(P1[i1[both], :2] - tp[both]).T)
+    gain = L1[i1[both]] / L0[i0[both]] - 1.0
+    fin = np.isfinite(L0) & np.isfinite(L1)
+    recovery = {
+        "movers": int(len(s.movers["x0"])), "matched": int(both.sum()),
+        "velocity_err_px_per_day": {"grid_median": float(np.median(ev0)),
+                                    "refined_median": float(np.median(ev1)),
+                                    "grid_p90": float(np.percentile(ev0, 90)),
+                                    "refined_p90": float(np.percentile(ev1, 90))},
+        "start_err_px": {"grid_median": float(np.median(ep0)),
+                         "refined_median": float(np.median(ep1))},
+        "lh_gain_median": float(np.median(gain)),
+        "all_candidates": {"n": int(n), "finite": int(fin.sum()),
+                           "lh_gain_median": float(np.median(L1[fin] / L0[fin] - 1.0)),
+                           "frac_improved": float((L1[fin] > L0[fin]).mean())}}
+
+    # end to end through the C ABI: candidates from pinned host memory, refined tracks and their
+    # L, alpha back to the host (psi/phi stay resident; they are the search's device output)
+    e2e = None
+    if not args.no_e2e:
+        host_p = params0.cpu().pin_memory()
+        host_k = keep.cpu().pin_memory()
+        h2d = host_p.numel() * 4 + host_k.numel() * 4
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            p_d = host_p.to(dev, non_blocking=True)
+            k_d = host_k.to(dev, non_blocking=True)
+            pr, L, A, L0_ = kb.refine(psi, phi, times, p_d, k_d, rp, inplace=True)
+            Lf, Af = kb.traj_eval(psi, phi, times, pr, k_d)
+            gpsi.zero_()
+            gphi.zero_()
+            gp, _, _ = kb.traj_eval_backward(psi, phi, times, pr, k_d, ones, None, True,
+                                             grad_psi=gpsi, grad_phi=gphi)
+            back = [x.to("cpu", non_blocking=True) for x in (pr, Lf, Af, gp)]
+        e1.record(stream)
+        barrier()
+        d2h = sum(x.numel() * 4 for x in back)
+        t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * te_step * args.steps / (float(t.item()) / 1e3), "unit": "TE/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    peaks, peaks_src = measured_peaks()
+    r_ms = part["refine"]
+    te_refine = n * T * (rp.n_steps + 1)
+    # 8 float32 taps (4 of psi, 4 of phi) per trajectory-epoch evaluation
+    achieved = te_refine * 32 / (r_ms / 1e3) / 1e9
+    line = {
+        "metric": "refine trajectory-epoch evals/sec", "value": value, "unit": "TE/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded DECam-shaped stack, "
+                                                    "movers off the grid)",
+        "config": dict(refine_config(args), candidates=int(n), survivors=int(count.item()),
+                       parallelism="one independent stack per GPU" if world > 1 else "1 GPU",
+                       l2="psi+phi %.2f GB, above L2; candidates' taps re-read every step" %
+                          (2 * 4 * T * H * W / 1e9)),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "kernel": "refine_kernel", "kernel_ms": r_ms,
+                     "peak_source": "hbm_gbs (%s)" % peaks_src,
+                     "algorithmic_bytes_per_te": 32,
+                     "note": "gather rate of the bilinear taps (8 x 4 B per trajectory-epoch, "
+                             "%d evaluations per candidate) against the HBM copy peak" %
+                             (rp.n_steps + 1)},
+        "stage_ms": part, "recovery": recovery,
+        "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
+    }
+    if not args.no_cpu_baseline:
+        r = oracle_refine_rate(args.cpu_seconds, args.workload, rp.n_steps)
+        line["cpu_baseline"] = {
+            "value": r["value"], "unit": "TE/s", "cores": r["threads"], "kind": "oracle",
+            "sample": "FP64 C oracle Adam refine (%d steps, one candidate per call, one thread) "
+                      "of %d candidate tracks x %d epochs of the workload's likelihood planes, "
+                      "%.1f s" % (rp.n_steps, r["n"], r["T"], r["seconds"])}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
+    auto_steps = args.steps is None
+    if auto_steps:
+        args.steps = 3
+    args.auto_steps = auto_steps and args.workload == "decam_refine" and args.impl == "ours"
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "decam_refine":
+        run_refine(args)
     else:
         run_ours(args)
 

@@ -255,8 +255,9 @@ KB_API int kb_candidate_tracks(const int32_t* cand_pix, const int32_t* cand_slot
  *     Psi = sum_{t kept} psi_t(.),  Phi = sum_{t kept} phi_t(.),
  *     L = Psi / sqrt(Phi),  alpha = Psi / Phi        (Eq. 1 and 2 on the kept epochs).
  * L is piecewise bilinear in (x0, y0, vx, vy); its gradient is the one-sided derivative on the
- * cell containing the position.  Positions are formed in float64 (x0 + vx dt_t with the product
- * and the sum rounded separately), the bilinear weights and the sums in float32.  A candidate
+ * cell containing the position.  Positions x0 + vx dt_t are formed in float-float arithmetic
+ * (about 48 significant bits, so the cell of an epoch is the one of the exact position unless it
+ * lies within ~1e-11 px of a cell edge), the bilinear weights and the sums in float32.  A candidate
  * whose Phi is not > 0 (no kept tap inside the image with phi > 0) gets L = alpha = NaN and a zero
  * gradient.
  *
@@ -307,8 +308,8 @@ KB_API void kb_refine_params_default(kb_refine_params* rp);
  * Step k = 1..n_steps evaluates L and g = dL/dparams at the current params and moves them by
  * lr mhat / (sqrt(vhat) + eps), m = beta1 m + (1 - beta1) g, v = beta2 v + (1 - beta2) g^2,
  * mhat = m / (1 - beta1^k), vhat = v / (1 - beta2^k); lr is lr_pos for x0, y0 and lr_vel for
- * vx, vy.  The gradient and the moments are float32; the parameters are carried in float64
- * between steps and rounded to float32 once at the end.  params are updated in place;
+ * vx, vy.  The gradient and the moments are float32; the parameters are carried in
+ * float-float between steps and rounded to float32 once at the end.  params are updated in place;
  * out_lh, out_flux [n] are L and alpha at the returned (rounded) params; out_lh_start [n]
  * (nullable) is L at the given params.  Where Phi <= 0 is met the ascent of that candidate stops
  * there (params as they were, rounded; L = alpha = NaN).

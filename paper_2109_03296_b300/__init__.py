@@ -314,18 +314,27 @@ def traj_eval(psi, phi, times, params, keep=None, grad=False, stream=None):
 
 
 def traj_eval_backward(psi, phi, times, params, keep, grad_lh=None, grad_flux=None,
-                       want_params=True, want_psi=False, want_phi=False, stream=None):
+                       want_params=True, want_psi=False, want_phi=False, grad_psi=None,
+                       grad_phi=None, stream=None):
     """Vector-Jacobian product of traj_eval: (grad_params [n, 4], grad_psi, grad_phi [T, H, W]),
-    each None unless asked for."""
+    each None unless asked for.  Image gradients go to new zeroed tensors, or are ACCUMULATED into
+    the grad_psi / grad_phi tensors given."""
     T, H, W = _traj_args(psi, phi, params, keep)
     n = params.shape[0]
     dev = psi.device
     for name, g in (("grad_lh", grad_lh), ("grad_flux", grad_flux)):
         if g is not None:
             _dev(g, torch.float32, name, 1)
+    for name, g in (("grad_psi", grad_psi), ("grad_phi", grad_phi)):
+        if g is not None:
+            _dev(g, torch.float32, name, 3)
+            if g.shape != psi.shape:
+                raise ValueError("%s must have the shape of psi" % name)
     gp = torch.empty((n, 4), dtype=torch.float32, device=dev) if want_params else None
-    gpsi = torch.zeros((T, H, W), dtype=torch.float32, device=dev) if want_psi else None
-    gphi = torch.zeros((T, H, W), dtype=torch.float32, device=dev) if want_phi else None
+    gpsi = grad_psi if grad_psi is not None else (
+        torch.zeros((T, H, W), dtype=torch.float32, device=dev) if want_psi else None)
+    gphi = grad_phi if grad_phi is not None else (
+        torch.zeros((T, H, W), dtype=torch.float32, device=dev) if want_phi else None)
     times = _host_times(times)
     check(lib().kb_traj_eval_bwd(_ptr(psi), _ptr(phi), times.ctypes.data_as(C.c_void_p), T, H, W,
                                  _ptr(params), _ptr(keep), n, _ptr(grad_lh), _ptr(grad_flux),

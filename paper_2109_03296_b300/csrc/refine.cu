@@ -11,11 +11,13 @@
 // (x0, y0, vx, vy) (piecewise bilinear) and linear / rational in the psi / phi pixels.
 //
 // One warp per candidate, lanes over epochs (lane l takes epochs l, l+32, ...).  Each lane forms
-// its position in float64 (product and sum rounded separately), splits it into cell and
-// fraction, reads the four taps of psi_t and phi_t through the read-only path, and contributes to
-// ten float32 sums: Psi, Phi and the derivatives of both in the four parameters.  A butterfly
-// reduction leaves the same sums, bit for bit, in every lane, so the Adam update of the refine
-// loop runs redundantly in all lanes with no further communication.
+// its position in float-float arithmetic (an unevaluated sum hi + lo of two float32 values, about
+// 48 significant bits, built from exact two-sum and FMA two-product steps; float64 runs at a small
+// fraction of the float32 rate on this part), splits it into cell and fraction, reads the four
+// taps of psi_t and phi_t through the read-only path, and contributes to ten float32 sums: Psi,
+// Phi and the derivatives of both in the four parameters.  A butterfly reduction leaves the same
+// sums, bit for bit, in every lane, so the Adam update of the refine loop runs redundantly in all
+// lanes with no further communication.
 #include <cmath>
 
 #include "kb_internal.cuh"
@@ -26,8 +28,49 @@ constexpr int RF_WARPS = 8;
 constexpr int RF_THREADS = RF_WARPS * 32;
 
 struct EpochDt {
-  double dt[KB_MAX_T];
+  float hi[KB_MAX_T];  // dt_t = times[t] - times[0] as hi + lo (float-float)
+  float lo[KB_MAX_T];
 };
+
+// Float-float values: hi + lo with |lo| <= ulp(hi)/2.  The _rn intrinsics keep every step a
+// separately rounded IEEE operation (no contraction into FMAs), which the error-free
+// transformations below rely on.
+struct FF {
+  float hi, lo;
+};
+
+// a + b = s + e exactly (Knuth's two-sum)
+__device__ __forceinline__ FF two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return FF{s, e};
+}
+
+// a + b = s + e exactly when |a| >= |b| (Dekker's fast two-sum)
+__device__ __forceinline__ FF fast_two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  return FF{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  FF s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ FF ff_add_f(FF a, float b) {
+  FF s = two_sum(a.hi, b);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+
+// product with the exact error of hi*hi from an FMA; lo*lo is below the format's precision
+__device__ __forceinline__ FF ff_mul(FF a, FF b) {
+  float p = __fmul_rn(a.hi, b.hi);
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return fast_two_sum(p, e);
+}
 
 // The four bilinear taps of one epoch: flat index of the lower-left tap (may point before the
 // image when a tap row or column is outside), fractions, and a validity bit per tap
@@ -38,18 +81,34 @@ struct Taps {
   unsigned valid;
 };
 
-__device__ __forceinline__ Taps make_taps(double x, double y, int H, int W) {
+// cell floor(v) and fraction v - floor(v) of a float-float value, the cell decided by the sign of
+// lo where hi is an integer
+__device__ __forceinline__ void ff_floor_frac(FF v, float& cell, float& frac) {
+  cell = floorf(v.hi);
+  frac = __fadd_rn(__fsub_rn(v.hi, cell), v.lo);   // hi - floor(hi) is exact
+  if (frac < 0.f) {
+    cell -= 1.f;
+    frac = __fadd_rn(frac, 1.f);
+  } else if (frac >= 1.f) {
+    cell += 1.f;
+    frac = __fsub_rn(frac, 1.f);
+  }
+}
+
+__device__ __forceinline__ Taps make_taps(FF x, FF y, int H, int W) {
   Taps tp;
   tp.base = 0;
   tp.ax = 0.f;
   tp.ay = 0.f;
   tp.valid = 0u;
-  double fx = floor(x), fy = floor(y);
+  float fx, fy, ax, ay;
+  ff_floor_frac(x, fx, ax);
+  ff_floor_frac(y, fy, ay);
   // also false for NaN: such a position has no tap inside the image
-  if (!(fx >= -1.0 && fx <= (double)(W - 1) && fy >= -1.0 && fy <= (double)(H - 1))) return tp;
+  if (!(fx >= -1.f && fx <= (float)(W - 1) && fy >= -1.f && fy <= (float)(H - 1))) return tp;
   int ix = (int)fx, iy = (int)fy;
-  tp.ax = (float)(x - fx);
-  tp.ay = (float)(y - fy);
+  tp.ax = ax;
+  tp.ay = ay;
   bool c0 = ix >= 0, c1 = ix + 1 < W, r0 = iy >= 0, r1 = iy + 1 < H;
   tp.valid = (unsigned)(c0 && r0) | (unsigned)(c1 && r0) << 1 | (unsigned)(c0 && r1) << 2 |
              (unsigned)(c1 && r1) << 3;
@@ -83,25 +142,29 @@ __device__ __forceinline__ void bilerp(const Quad& q, float ax, float ay, float&
 // s[0] = Psi, s[1] = Phi, s[2..5] = dPsi/d(x0, y0, vx, vy), s[6..9] = dPhi/d(...)
 constexpr int NSUM = 10;
 
-// Track parameters in float64: the inputs are float32, but the refine loop accumulates its steps
-// in float64 so that the side of a bilinear cell edge on which an epoch falls is decided as in
-// exact arithmetic (float32 parameters near x ~ 4000 px carry 2.4e-4 px of rounding, times dt).
+// Track parameters in float-float: the inputs are float32, but the refine loop accumulates its
+// steps in float-float so that the side of a bilinear cell edge on which an epoch falls is
+// decided as in exact arithmetic (float32 parameters near x ~ 4000 px carry 2.4e-4 px of
+// rounding, times dt for the velocities).
 struct Track {
-  double x0, y0, vx, vy;
+  FF x0, y0, vx, vy;
 };
 
 __device__ __forceinline__ Track to_track(float4 p) {
-  return Track{(double)p.x, (double)p.y, (double)p.z, (double)p.w};
+  return Track{FF{p.x, 0.f}, FF{p.y, 0.f}, FF{p.z, 0.f}, FF{p.w, 0.f}};
 }
 
-__device__ __forceinline__ double track_pos(double p0, double v, double dt) {
-  return __dadd_rn(p0, __dmul_rn(v, dt));
+__device__ __forceinline__ float4 round_track(const Track& p) {
+  return make_float4(__fadd_rn(p.x0.hi, p.x0.lo), __fadd_rn(p.y0.hi, p.y0.lo),
+                     __fadd_rn(p.vx.hi, p.vx.lo), __fadd_rn(p.vy.hi, p.vy.lo));
 }
+
+__device__ __forceinline__ FF track_pos(FF p0, FF v, FF dt) { return ff_add(p0, ff_mul(v, dt)); }
 
 template <int J>
 __device__ __forceinline__ void lane_sums(const float* __restrict__ psi,
                                           const float* __restrict__ phi, int T, int H, int W,
-                                          const double (&dt)[J], unsigned kbits, const Track& p,
+                                          const FF (&dt)[J], unsigned kbits, const Track& p,
                                           float (&s)[NSUM]) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -118,7 +181,7 @@ __device__ __forceinline__ void lane_sums(const float* __restrict__ psi,
     float vp, gpx, gpy, vf, gfx, gfy;
     bilerp(qp, tp.ax, tp.ay, vp, gpx, gpy);
     bilerp(qf, tp.ax, tp.ay, vf, gfx, gfy);
-    float d = (float)dt[j];
+    float d = dt[j].hi;
     s[0] += vp;
     s[1] += vf;
     s[2] += gpx;
@@ -139,24 +202,19 @@ __device__ __forceinline__ void lane_sums(const float* __restrict__ psi,
 // Per-lane state loaded once per candidate: the lane's dt values and its kept bits (bit j for
 // epoch lane + 32 j).
 template <int J>
-__device__ __forceinline__ unsigned lane_setup(const double* s_dt, const uint32_t* __restrict__ keep,
-                                               int MW, long long c, int T, double (&dt)[J]) {
+__device__ __forceinline__ unsigned lane_setup(const EpochDt& e, const uint32_t* __restrict__ keep,
+                                               int MW, long long c, int T, FF (&dt)[J]) {
   const int lane = threadIdx.x & 31;
   unsigned kbits = 0u;
 #pragma unroll
   for (int j = 0; j < J; ++j) {
     int t = lane + 32 * j;
-    dt[j] = t < T ? s_dt[t] : 0.0;
+    dt[j] = t < T ? FF{e.hi[t], e.lo[t]} : FF{0.f, 0.f};
     unsigned b = 0u;
     if (t < T) b = keep ? ((__ldg(keep + c * MW + j) >> lane) & 1u) : 1u;
     kbits |= b << j;
   }
   return kbits;
-}
-
-__device__ __forceinline__ void load_dt(double* s_dt, const EpochDt& e, int T) {
-  for (int t = threadIdx.x; t < T; t += blockDim.x) s_dt[t] = e.dt[t];
-  __syncthreads();
 }
 
 template <int J>
@@ -165,12 +223,10 @@ __global__ void __launch_bounds__(RF_THREADS) traj_fwd_kernel(
     const float4* __restrict__ params, const uint32_t* __restrict__ keep, int MW, int n,
     EpochDt e, float* __restrict__ out_lh, float* __restrict__ out_flux,
     float4* __restrict__ out_grad) {
-  __shared__ double s_dt[KB_MAX_T];
-  load_dt(s_dt, e, T);
   const long long c = (long long)blockIdx.x * RF_WARPS + (threadIdx.x >> 5);
   if (c >= n) return;
-  double dt[J];
-  unsigned kbits = lane_setup<J>(s_dt, keep, MW, c, T, dt);
+  FF dt[J];
+  unsigned kbits = lane_setup<J>(e, keep, MW, c, T, dt);
   const Track p = to_track(__ldg(params + c));
   float s[NSUM];
   lane_sums<J>(psi, phi, T, H, W, dt, kbits, p, s);
@@ -197,13 +253,11 @@ __global__ void __launch_bounds__(RF_THREADS) traj_bwd_kernel(
     const float4* __restrict__ params, const uint32_t* __restrict__ keep, int MW, int n,
     EpochDt e, const float* __restrict__ grad_lh, const float* __restrict__ grad_flux,
     float4* __restrict__ out_grad, float* __restrict__ grad_psi, float* __restrict__ grad_phi) {
-  __shared__ double s_dt[KB_MAX_T];
-  load_dt(s_dt, e, T);
   const long long c = (long long)blockIdx.x * RF_WARPS + (threadIdx.x >> 5);
   if (c >= n) return;
   const int lane = threadIdx.x & 31;
-  double dt[J];
-  unsigned kbits = lane_setup<J>(s_dt, keep, MW, c, T, dt);
+  FF dt[J];
+  unsigned kbits = lane_setup<J>(e, keep, MW, c, T, dt);
   const Track p = to_track(__ldg(params + c));
   float s[NSUM];
   lane_sums<J>(psi, phi, T, H, W, dt, kbits, p, s);
@@ -251,13 +305,11 @@ __global__ void __launch_bounds__(RF_THREADS) refine_kernel(
     float4* __restrict__ params, const uint32_t* __restrict__ keep, int MW, int n, EpochDt e,
     AdamConsts ac, float* __restrict__ out_lh, float* __restrict__ out_flux,
     float* __restrict__ out_lh_start) {
-  __shared__ double s_dt[KB_MAX_T];
-  load_dt(s_dt, e, T);
   const long long c = (long long)blockIdx.x * RF_WARPS + (threadIdx.x >> 5);
   if (c >= n) return;
   const int lane = threadIdx.x & 31;
-  double dt[J];
-  unsigned kbits = lane_setup<J>(s_dt, keep, MW, c, T, dt);
+  FF dt[J];
+  unsigned kbits = lane_setup<J>(e, keep, MW, c, T, dt);
   Track p = to_track(params[c]);
   float m[4] = {0.f, 0.f, 0.f, 0.f}, v[4] = {0.f, 0.f, 0.f, 0.f};
   float b1k = 1.f, b2k = 1.f;
@@ -265,8 +317,7 @@ __global__ void __launch_bounds__(RF_THREADS) refine_kernel(
   bool ok = true;
   for (int k = 0; k <= ac.n_steps; ++k) {
     // the returned params are float32: evaluate the final L and alpha at exactly those
-    if (k == ac.n_steps && k > 0)
-      p = to_track(make_float4((float)p.x0, (float)p.y0, (float)p.vx, (float)p.vy));
+    if (k == ac.n_steps && k > 0) p = to_track(round_track(p));
     lane_sums<J>(psi, phi, T, H, W, dt, kbits, p, s);
     if (!(s[1] > 0.f)) {
       if (k == 0 && out_lh_start && lane == 0) out_lh_start[c] = __int_as_float(0x7fc00000);
@@ -289,13 +340,13 @@ __global__ void __launch_bounds__(RF_THREADS) refine_kernel(
       float mh = m[i] / (1.f - b1k), vh = v[i] / (1.f - b2k);
       step[i] = (i < 2 ? ac.lr_pos : ac.lr_vel) * mh / (sqrtf(vh) + ac.eps);
     }
-    p.x0 += (double)step[0];
-    p.y0 += (double)step[1];
-    p.vx += (double)step[2];
-    p.vy += (double)step[3];
+    p.x0 = ff_add_f(p.x0, step[0]);
+    p.y0 = ff_add_f(p.y0, step[1]);
+    p.vx = ff_add_f(p.vx, step[2]);
+    p.vy = ff_add_f(p.vy, step[3]);
   }
   if (lane != 0) return;
-  params[c] = make_float4((float)p.x0, (float)p.y0, (float)p.vx, (float)p.vy);
+  params[c] = round_track(p);
   if (ok) {
     float rs = sqrtf(s[1]);
     out_lh[c] = s[0] / rs;
@@ -345,7 +396,9 @@ static int check_common(const char* who, const float* psi, const float* phi, con
     return fail(KB_ERR_UNSUPPORTED, "%s: image sides are limited to 2^20 pixels", who);
   for (int t = 0; t < T; ++t) {
     if (!std::isfinite(times[t])) return fail(KB_ERR_INVALID_ARG, "%s: times not finite", who);
-    e.dt[t] = times[t] - times[0];
+    double dt = times[t] - times[0];
+    e.hi[t] = (float)dt;
+    e.lo[t] = (float)(dt - (double)e.hi[t]);
   }
   return KB_OK;
 }
