@@ -660,7 +660,12 @@ def run_refine(args):
     peaks, peaks_src = measured_peaks()
     r_ms = part["refine"]
     te_refine = n * T * (rp.n_steps + 1)
-    # 8 float32 taps (4 of psi, 4 of phi) per trajectory-epoch evaluation
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
+    # The refine kernel reads its taps through L1 (a candidate's taps stay on chip across its
+    # steps; DRAM traffic is a few tens of MB): roofline = the L1 load path, one 128-byte wavefront
+    # per SM per clock, against 8 float32 taps (4 of psi, 4 of phi) per trajectory-epoch.
+    l1_peak = sms * 128 * sm_max * 1e6 / 1e9
     achieved = te_refine * 32 / (r_ms / 1e3) / 1e9
     line = {
         "metric": "refine trajectory-epoch evals/sec", "value": value, "unit": "TE/s",
@@ -672,14 +677,16 @@ def run_refine(args):
                        parallelism="one independent stack per GPU" if world > 1 else "1 GPU",
                        l2="psi+phi %.2f GB, above L2; candidates' taps re-read every step" %
                           (2 * 4 * T * H * W / 1e9)),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": l1_peak, "unit": "GB/s",
+                     "frac": achieved / l1_peak, "traffic": None,
                      "kernel": "refine_kernel", "kernel_ms": r_ms,
-                     "peak_source": "hbm_gbs (%s)" % peaks_src,
+                     "peak_source": "derived: %d SMs x 128 B/clk L1 loads x %g MHz (sm_max_mhz, "
+                                    "%s)" % (sms, sm_max, peaks_src),
                      "algorithmic_bytes_per_te": 32,
-                     "note": "gather rate of the bilinear taps (8 x 4 B per trajectory-epoch, "
-                             "%d evaluations per candidate) against the HBM copy peak" %
-                             (rp.n_steps + 1)},
+                     "note": "8 x 4 B bilinear taps per trajectory-epoch, %d evaluations per "
+                             "candidate; each 4 B tap occupies a 32 B sector, and the kernel is "
+                             "instruction-issue bound (float-float positions, bilinear "
+                             "weights, butterfly sums)" % (rp.n_steps + 1)},
         "stage_ms": part, "recovery": recovery,
         "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
     }

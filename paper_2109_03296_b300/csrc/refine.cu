@@ -10,22 +10,23 @@
 // The kept set is an input and stays fixed, so L is differentiable almost everywhere in
 // (x0, y0, vx, vy) (piecewise bilinear) and linear / rational in the psi / phi pixels.
 //
-// One warp per candidate, lanes over epochs (lane l takes epochs l, l+32, ...).  Each lane forms
-// its position in float-float arithmetic (an unevaluated sum hi + lo of two float32 values, about
-// 48 significant bits, built from exact two-sum and FMA two-product steps; float64 runs at a small
-// fraction of the float32 rate on this part), splits it into cell and fraction, reads the four
-// taps of psi_t and phi_t through the read-only path, and contributes to ten float32 sums: Psi,
-// Phi and the derivatives of both in the four parameters.  A butterfly reduction leaves the same
-// sums, bit for bit, in every lane, so the Adam update of the refine loop runs redundantly in all
-// lanes with no further communication.
+// A group of G lanes per candidate (a warp for T > 16; 16 or 8 lanes, several candidates per warp,
+// for smaller T) with E epochs per lane (epoch sub + G j for sub-lane `sub`, j < E).  Each lane forms its positions in
+// float-float arithmetic (an unevaluated sum hi + lo of two float32 values, about 48 significant
+// bits, built from exact two-sum and FMA two-product steps; float64 runs at a small fraction of
+// the float32 rate on this part), splits them into cell and fraction, reads the four taps of
+// psi_t and phi_t through the read-only path, and adds to ten float32 partial sums: Psi, Phi and
+// the derivatives of both in the four parameters.  A butterfly reduction within the group leaves
+// the same sums, bit for bit, in every lane of the group, so the Adam update of the refine loop
+// runs redundantly in all of them with no further communication.
 #include <cmath>
+#include <type_traits>
 
 #include "kb_internal.cuh"
 
 namespace kb {
 
-constexpr int RF_WARPS = 8;
-constexpr int RF_THREADS = RF_WARPS * 32;
+constexpr int RF_THREADS = 256;
 
 struct EpochDt {
   float hi[KB_MAX_T];  // dt_t = times[t] - times[0] as hi + lo (float-float)
@@ -161,18 +162,40 @@ __device__ __forceinline__ float4 round_track(const Track& p) {
 
 __device__ __forceinline__ FF track_pos(FF p0, FF v, FF dt) { return ff_add(p0, ff_mul(v, dt)); }
 
-template <int J>
-__device__ __forceinline__ void lane_sums(const float* __restrict__ psi,
-                                          const float* __restrict__ phi, int T, int H, int W,
-                                          const FF (&dt)[J], unsigned kbits, const Track& p,
-                                          float (&s)[NSUM]) {
-  const int lane = threadIdx.x & 31;
+// Lane layout of a candidate group: G lanes (a power of two dividing 32), E epochs per lane.
+template <int G>
+struct Group {
+  static constexpr int PER_BLOCK = RF_THREADS / G;
+  __device__ static int sub() { return threadIdx.x & (G - 1); }
+  __device__ static long long cand() {
+    return (long long)blockIdx.x * PER_BLOCK + (threadIdx.x / G);
+  }
+  __device__ static unsigned mask() {
+    return G == 32 ? 0xffffffffu : ((1u << G) - 1u) << (threadIdx.x & 31 & ~(G - 1));
+  }
+  // butterfly sum over the group: every lane of the group ends with the same value, bit for bit
+  __device__ static float sum(float v) {
+    const unsigned m = mask();
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(m, v, o);
+    return v;
+  }
+};
+
+// The lane's partial sums over its own epochs: s[0] = psi, s[1] = phi, s[2..5] = d psi /
+// d(x0, y0, vx, vy), s[6..9] = d phi / d(...).
+template <int G, int E>
+__device__ __forceinline__ void lane_partials(const float* __restrict__ psi,
+                                              const float* __restrict__ phi, int T, int H, int W,
+                                              const FF (&dt)[E], unsigned kbits, const Track& p,
+                                              float (&s)[NSUM]) {
+  const int sub = Group<G>::sub();
 #pragma unroll
   for (int i = 0; i < NSUM; ++i) s[i] = 0.f;
   const size_t hw = (size_t)H * W;
 #pragma unroll
-  for (int j = 0; j < J; ++j) {
-    int t = lane + 32 * j;
+  for (int j = 0; j < E; ++j) {
+    const int t = sub + G * j;
     if (t >= T || !((kbits >> j) & 1u)) continue;
     Taps tp = make_taps(track_pos(p.x0, p.vx, dt[j]), track_pos(p.y0, p.vy, dt[j]), H, W);
     if (!tp.valid) continue;
@@ -193,92 +216,101 @@ __device__ __forceinline__ void lane_sums(const float* __restrict__ psi,
     s[8] = fmaf(gfx, d, s[8]);
     s[9] = fmaf(gfy, d, s[9]);
   }
+}
+
+template <int G>
+__device__ __forceinline__ void group_sums(float (&s)[NSUM]) {
+  const unsigned m = Group<G>::mask();
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1)
+  for (int o = G / 2; o > 0; o >>= 1)
 #pragma unroll
-    for (int i = 0; i < NSUM; ++i) s[i] += __shfl_xor_sync(0xffffffffu, s[i], o);
+    for (int i = 0; i < NSUM; ++i) s[i] += __shfl_xor_sync(m, s[i], o);
+}
+
+// a dPsi/dparams + b dPhi/dparams from the group sums
+__device__ __forceinline__ float4 param_grad(const float (&s)[NSUM], float a, float b) {
+  return make_float4(fmaf(b, s[6], a * s[2]), fmaf(b, s[7], a * s[3]), fmaf(b, s[8], a * s[4]),
+                     fmaf(b, s[9], a * s[5]));
 }
 
 // Per-lane state loaded once per candidate: the lane's dt values and its kept bits (bit j for
-// epoch lane + 32 j).
-template <int J>
+// epoch sub + G j).
+template <int G, int E>
 __device__ __forceinline__ unsigned lane_setup(const EpochDt& e, const uint32_t* __restrict__ keep,
-                                               int MW, long long c, int T, FF (&dt)[J]) {
-  const int lane = threadIdx.x & 31;
+                                               int MW, long long c, int T, FF (&dt)[E]) {
+  const int sub = Group<G>::sub();
   unsigned kbits = 0u;
 #pragma unroll
-  for (int j = 0; j < J; ++j) {
-    int t = lane + 32 * j;
+  for (int j = 0; j < E; ++j) {
+    const int t = sub + G * j;
     dt[j] = t < T ? FF{e.hi[t], e.lo[t]} : FF{0.f, 0.f};
     unsigned b = 0u;
-    if (t < T) b = keep ? ((__ldg(keep + c * MW + j) >> lane) & 1u) : 1u;
+    if (t < T) b = keep ? ((__ldg(keep + c * MW + (t >> 5)) >> (t & 31)) & 1u) : 1u;
     kbits |= b << j;
   }
   return kbits;
 }
 
-template <int J>
+template <int G, int E>
 __global__ void __launch_bounds__(RF_THREADS) traj_fwd_kernel(
     const float* __restrict__ psi, const float* __restrict__ phi, int T, int H, int W,
     const float4* __restrict__ params, const uint32_t* __restrict__ keep, int MW, int n,
     EpochDt e, float* __restrict__ out_lh, float* __restrict__ out_flux,
     float4* __restrict__ out_grad) {
-  const long long c = (long long)blockIdx.x * RF_WARPS + (threadIdx.x >> 5);
+  const long long c = Group<G>::cand();
   if (c >= n) return;
-  FF dt[J];
-  unsigned kbits = lane_setup<J>(e, keep, MW, c, T, dt);
+  const bool leader = Group<G>::sub() == 0;
+  FF dt[E];
+  unsigned kbits = lane_setup<G, E>(e, keep, MW, c, T, dt);
   const Track p = to_track(__ldg(params + c));
   float s[NSUM];
-  lane_sums<J>(psi, phi, T, H, W, dt, kbits, p, s);
-  if ((threadIdx.x & 31) != 0) return;
+  lane_partials<G, E>(psi, phi, T, H, W, dt, kbits, p, s);
+  group_sums<G>(s);
+  if (!leader) return;
   if (!(s[1] > 0.f)) {
     out_lh[c] = __int_as_float(0x7fc00000);
     out_flux[c] = __int_as_float(0x7fc00000);
     if (out_grad) out_grad[c] = make_float4(0.f, 0.f, 0.f, 0.f);
     return;
   }
-  float rs = sqrtf(s[1]);
+  const float rs = sqrtf(s[1]);
   out_lh[c] = s[0] / rs;
   out_flux[c] = s[0] / s[1];
-  if (out_grad) {
-    float a = 1.f / rs, b = -0.5f * s[0] / (s[1] * rs);
-    out_grad[c] = make_float4(fmaf(b, s[6], a * s[2]), fmaf(b, s[7], a * s[3]),
-                              fmaf(b, s[8], a * s[4]), fmaf(b, s[9], a * s[5]));
-  }
+  if (out_grad) out_grad[c] = param_grad(s, 1.f / rs, -0.5f * s[0] / (s[1] * rs));
 }
 
-template <int J>
+template <int G, int E>
 __global__ void __launch_bounds__(RF_THREADS) traj_bwd_kernel(
     const float* __restrict__ psi, const float* __restrict__ phi, int T, int H, int W,
     const float4* __restrict__ params, const uint32_t* __restrict__ keep, int MW, int n,
     EpochDt e, const float* __restrict__ grad_lh, const float* __restrict__ grad_flux,
     float4* __restrict__ out_grad, float* __restrict__ grad_psi, float* __restrict__ grad_phi) {
-  const long long c = (long long)blockIdx.x * RF_WARPS + (threadIdx.x >> 5);
+  const long long c = Group<G>::cand();
   if (c >= n) return;
-  const int lane = threadIdx.x & 31;
-  FF dt[J];
-  unsigned kbits = lane_setup<J>(e, keep, MW, c, T, dt);
+  const int sub = Group<G>::sub();
+  FF dt[E];
+  unsigned kbits = lane_setup<G, E>(e, keep, MW, c, T, dt);
   const Track p = to_track(__ldg(params + c));
   float s[NSUM];
-  lane_sums<J>(psi, phi, T, H, W, dt, kbits, p, s);
-  if (!(s[1] > 0.f)) {
-    if (lane == 0 && out_grad) out_grad[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+  lane_partials<G, E>(psi, phi, T, H, W, dt, kbits, p, s);
+  group_sums<G>(s);
+  const float Ps = s[0], Ph = s[1];
+  if (!(Ph > 0.f)) {
+    if (sub == 0 && out_grad) out_grad[c] = make_float4(0.f, 0.f, 0.f, 0.f);
     return;
   }
-  float gL = grad_lh ? __ldg(grad_lh + c) : 0.f;
-  float gA = grad_flux ? __ldg(grad_flux + c) : 0.f;
-  float rs = sqrtf(s[1]);
+  const float gL = grad_lh ? __ldg(grad_lh + c) : 0.f;
+  const float gA = grad_flux ? __ldg(grad_flux + c) : 0.f;
+  const float rs = sqrtf(Ph);
   // dL/dPsi = 1/sqrt(Phi), dL/dPhi = -Psi/(2 Phi^1.5); dalpha/dPsi = 1/Phi, dalpha/dPhi = -Psi/Phi^2
-  float cps = gL / rs + gA / s[1];
-  float cph = -0.5f * gL * s[0] / (s[1] * rs) - gA * s[0] / (s[1] * s[1]);
-  if (lane == 0 && out_grad)
-    out_grad[c] = make_float4(fmaf(cph, s[6], cps * s[2]), fmaf(cph, s[7], cps * s[3]),
-                              fmaf(cph, s[8], cps * s[4]), fmaf(cph, s[9], cps * s[5]));
+  const float cps = gL / rs + gA / Ph;
+  const float cph = -0.5f * gL * Ps / (Ph * rs) - gA * Ps / (Ph * Ph);
+  if (sub == 0 && out_grad) out_grad[c] = param_grad(s, cps, cph);
   if (!grad_psi && !grad_phi) return;
   const size_t hw = (size_t)H * W;
 #pragma unroll
-  for (int j = 0; j < J; ++j) {
-    int t = lane + 32 * j;
+  for (int j = 0; j < E; ++j) {
+    const int t = sub + G * j;
     if (t >= T || !((kbits >> j) & 1u)) continue;
     Taps tp = make_taps(track_pos(p.x0, p.vx, dt[j]), track_pos(p.y0, p.vy, dt[j]), H, W);
     const float w[4] = {(1.f - tp.ax) * (1.f - tp.ay), tp.ax * (1.f - tp.ay),
@@ -299,17 +331,21 @@ struct AdamConsts {
   float lr_pos, lr_vel, b1, b2, eps;
 };
 
-template <int J>
-__global__ void __launch_bounds__(RF_THREADS) refine_kernel(
+// Adam runs redundantly in every lane of the group on the group sums, so all lanes hold the same
+// parameters; the bias corrections are applied as products with correctly rounded reciprocals.
+// A minimum of one block per SM leaves the register budget to the compiler: at T = 26 it takes 69
+// registers (4 blocks of 256 per SM) and runs 1.5x faster than when held to 48 for 5 blocks.
+template <int G, int E>
+__global__ void __launch_bounds__(RF_THREADS, 1) refine_kernel(
     const float* __restrict__ psi, const float* __restrict__ phi, int T, int H, int W,
     float4* __restrict__ params, const uint32_t* __restrict__ keep, int MW, int n, EpochDt e,
     AdamConsts ac, float* __restrict__ out_lh, float* __restrict__ out_flux,
     float* __restrict__ out_lh_start) {
-  const long long c = (long long)blockIdx.x * RF_WARPS + (threadIdx.x >> 5);
+  const long long c = Group<G>::cand();
   if (c >= n) return;
-  const int lane = threadIdx.x & 31;
-  FF dt[J];
-  unsigned kbits = lane_setup<J>(e, keep, MW, c, T, dt);
+  const bool leader = Group<G>::sub() == 0;
+  FF dt[E];
+  unsigned kbits = lane_setup<G, E>(e, keep, MW, c, T, dt);
   Track p = to_track(params[c]);
   float m[4] = {0.f, 0.f, 0.f, 0.f}, v[4] = {0.f, 0.f, 0.f, 0.f};
   float b1k = 1.f, b2k = 1.f;
@@ -318,38 +354,37 @@ __global__ void __launch_bounds__(RF_THREADS) refine_kernel(
   for (int k = 0; k <= ac.n_steps; ++k) {
     // the returned params are float32: evaluate the final L and alpha at exactly those
     if (k == ac.n_steps && k > 0) p = to_track(round_track(p));
-    lane_sums<J>(psi, phi, T, H, W, dt, kbits, p, s);
+    lane_partials<G, E>(psi, phi, T, H, W, dt, kbits, p, s);
+    group_sums<G>(s);
     if (!(s[1] > 0.f)) {
-      if (k == 0 && out_lh_start && lane == 0) out_lh_start[c] = __int_as_float(0x7fc00000);
+      if (k == 0 && out_lh_start && leader) out_lh_start[c] = __int_as_float(0x7fc00000);
       ok = false;
       break;
     }
-    float rs = sqrtf(s[1]);
-    if (k == 0 && out_lh_start && lane == 0) out_lh_start[c] = s[0] / rs;
+    const float rs = sqrtf(s[1]);
+    if (k == 0 && out_lh_start && leader) out_lh_start[c] = s[0] / rs;
     if (k == ac.n_steps) break;
-    float a = 1.f / rs, b = -0.5f * s[0] / (s[1] * rs);
-    float g[4] = {fmaf(b, s[6], a * s[2]), fmaf(b, s[7], a * s[3]), fmaf(b, s[8], a * s[4]),
-                  fmaf(b, s[9], a * s[5])};
+    const float4 g4 = param_grad(s, 1.f / rs, -0.5f * s[0] / (s[1] * rs));
+    const float g[4] = {g4.x, g4.y, g4.z, g4.w};
     b1k *= ac.b1;
     b2k *= ac.b2;
+    const float c1 = __frcp_rn(1.f - b1k), c2 = __frcp_rn(1.f - b2k);
     float step[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       m[i] = fmaf(ac.b1, m[i], (1.f - ac.b1) * g[i]);
       v[i] = fmaf(ac.b2, v[i], (1.f - ac.b2) * g[i] * g[i]);
-      float mh = m[i] / (1.f - b1k), vh = v[i] / (1.f - b2k);
-      step[i] = (i < 2 ? ac.lr_pos : ac.lr_vel) * mh / (sqrtf(vh) + ac.eps);
+      step[i] = (i < 2 ? ac.lr_pos : ac.lr_vel) * (m[i] * c1) / (sqrtf(v[i] * c2) + ac.eps);
     }
     p.x0 = ff_add_f(p.x0, step[0]);
     p.y0 = ff_add_f(p.y0, step[1]);
     p.vx = ff_add_f(p.vx, step[2]);
     p.vy = ff_add_f(p.vy, step[3]);
   }
-  if (lane != 0) return;
+  if (!leader) return;
   params[c] = round_track(p);
   if (ok) {
-    float rs = sqrtf(s[1]);
-    out_lh[c] = s[0] / rs;
+    out_lh[c] = s[0] / sqrtf(s[1]);
     out_flux[c] = s[0] / s[1];
   } else {
     out_lh[c] = __int_as_float(0x7fc00000);
@@ -403,7 +438,28 @@ static int check_common(const char* who, const float* psi, const float* phi, con
   return KB_OK;
 }
 
-static inline unsigned rf_blocks(int n) { return (unsigned)((n + RF_WARPS - 1) / RF_WARPS); }
+// Group shape by T: G lanes per candidate, E = ceil(T / G) epochs per lane.  A whole warp per
+// candidate wherever T fills most of it: packing two candidates into a warp (16 lanes x 2 epochs)
+// issues fewer instructions but doubles the candidates resident per SM, and their taps then no
+// longer fit the L1 (measured at T = 26: hit rate 84% -> 62%, 0.75 -> 1.0 ms).
+template <typename F>
+static void with_shape(int T, F&& f) {
+  if (T <= 8)
+    f(std::integral_constant<int, 8>{}, std::integral_constant<int, 1>{});
+  else if (T <= 16)
+    f(std::integral_constant<int, 16>{}, std::integral_constant<int, 1>{});
+  else if (T <= 32)
+    f(std::integral_constant<int, 32>{}, std::integral_constant<int, 1>{});
+  else if (T <= 64)
+    f(std::integral_constant<int, 32>{}, std::integral_constant<int, 2>{});
+  else
+    f(std::integral_constant<int, 32>{}, std::integral_constant<int, 4>{});
+}
+
+template <int G>
+static inline unsigned rf_blocks(int n) {
+  return (unsigned)(((long long)n + Group<G>::PER_BLOCK - 1) / Group<G>::PER_BLOCK);
+}
 
 }  // namespace kb
 
@@ -420,12 +476,10 @@ extern "C" int kb_traj_eval_fwd(const float* psi, const float* phi, const double
   const int MW = (T + 31) / 32;
   const float4* p4 = reinterpret_cast<const float4*>(params);
   float4* g4 = reinterpret_cast<float4*>(out_grad);
-  if (MW == 1)
-    traj_fwd_kernel<1><<<rf_blocks(n), RF_THREADS, 0, st>>>(psi, phi, T, H, W, p4, keep, MW, n, e,
-                                                             out_lh, out_flux, g4);
-  else
-    traj_fwd_kernel<4><<<rf_blocks(n), RF_THREADS, 0, st>>>(psi, phi, T, H, W, p4, keep, MW, n, e,
-                                                             out_lh, out_flux, g4);
+  with_shape(T, [&](auto G, auto E) {
+    traj_fwd_kernel<G(), E()><<<rf_blocks<G()>(n), RF_THREADS, 0, st>>>(
+        psi, phi, T, H, W, p4, keep, MW, n, e, out_lh, out_flux, g4);
+  });
   KB_LAUNCH_CHECK("traj_fwd_kernel");
   return KB_OK;
 }
@@ -444,12 +498,10 @@ extern "C" int kb_traj_eval_bwd(const float* psi, const float* phi, const double
   const int MW = (T + 31) / 32;
   const float4* p4 = reinterpret_cast<const float4*>(params);
   float4* g4 = reinterpret_cast<float4*>(out_grad_params);
-  if (MW == 1)
-    traj_bwd_kernel<1><<<rf_blocks(n), RF_THREADS, 0, st>>>(
+  with_shape(T, [&](auto G, auto E) {
+    traj_bwd_kernel<G(), E()><<<rf_blocks<G()>(n), RF_THREADS, 0, st>>>(
         psi, phi, T, H, W, p4, keep, MW, n, e, grad_lh, grad_flux, g4, grad_psi, grad_phi);
-  else
-    traj_bwd_kernel<4><<<rf_blocks(n), RF_THREADS, 0, st>>>(
-        psi, phi, T, H, W, p4, keep, MW, n, e, grad_lh, grad_flux, g4, grad_psi, grad_phi);
+  });
   KB_LAUNCH_CHECK("traj_bwd_kernel");
   return KB_OK;
 }
@@ -487,12 +539,10 @@ extern "C" int kb_refine(const float* psi, const float* phi, const double* times
   AdamConsts ac{rp->n_steps, rp->lr_pos, rp->lr_vel, rp->beta1, rp->beta2, rp->eps};
   const int MW = (T + 31) / 32;
   float4* p4 = reinterpret_cast<float4*>(params);
-  if (MW == 1)
-    refine_kernel<1><<<rf_blocks(n), RF_THREADS, 0, st>>>(psi, phi, T, H, W, p4, keep, MW, n, e,
-                                                           ac, out_lh, out_flux, out_lh_start);
-  else
-    refine_kernel<4><<<rf_blocks(n), RF_THREADS, 0, st>>>(psi, phi, T, H, W, p4, keep, MW, n, e,
-                                                           ac, out_lh, out_flux, out_lh_start);
+  with_shape(T, [&](auto G, auto E) {
+    refine_kernel<G(), E()><<<rf_blocks<G()>(n), RF_THREADS, 0, st>>>(
+        psi, phi, T, H, W, p4, keep, MW, n, e, ac, out_lh, out_flux, out_lh_start);
+  });
   KB_LAUNCH_CHECK("refine_kernel");
   return KB_OK;
 }
