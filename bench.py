@@ -217,7 +217,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    if args.workload == "decam_refine":
+    if args.workload.startswith("decam_refine"):
         return run_reference_refine(args)
     r = None
     for _ in range(args.warmup):
@@ -708,10 +708,11 @@ def main():
     auto_steps = args.steps is None
     if auto_steps:
         args.steps = 3
-    args.auto_steps = auto_steps and args.workload == "decam_refine" and args.impl == "ours"
+    refine = args.workload.startswith("decam_refine")
+    args.auto_steps = auto_steps and refine and args.impl == "ours"
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == "decam_refine":
+    elif refine:
         run_refine(args)
     else:
         run_ours(args)

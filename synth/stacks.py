@@ -15,6 +15,7 @@ Section 4.1).  The DECam NEO data are not available, so these stand in for them:
   refine    the tiny stack with movers at off-grid sub-pixel starts and velocities.
   decam_refine  the decam recipe (own seed) with movers at sub-pixel starts and off-grid
             velocities, uniform between grid points: the workload of the off-grid refinement.
+  decam_refine_half  the same at 2046x2048 with 100 movers (detailed refine profiles).
   decam_small  the decam recipe on 1024x1024 with 50 movers (psi+phi 218 MB, above the 126 MB
             L2).
   decam_half   the decam recipe on 2046x2048 with 100 movers (same mover density; psi+phi
@@ -85,6 +86,13 @@ CONFIGS = {
                          times=("nights", (7, 7, 6, 6)), integer_tracks=False,
                          movers_on_grid=False, start_margin=0, seed=7, K=8, lh_min=10.0,
                          min_obs=15, subpixel_starts=True),
+    "decam_refine_half": dict(T=26, H=2046, W=2048, psf_k=15, psf_sigma=(1.0, 2.0),
+                              var=(0.5, 2.0), mask_frac=0.005, n_movers=100,
+                              snr=("loguniform", 1.5, 10.0), spike_frac=0.1,
+                              grid=(90.0, 500.0, 256, -0.3, 0.3, 128),
+                              times=("nights", (7, 7, 6, 6)), integer_tracks=False,
+                              movers_on_grid=False, start_margin=0, seed=7, K=8, lh_min=10.0,
+                              min_obs=15, subpixel_starts=True),
 }
 
 
