@@ -534,3 +534,42 @@ int kbo_refine_adam(const double* psi, const double* phi, const double* times, i
   return kbo_traj_eval_subpixel(psi, phi, times, T, H, W, keep, params[0], params[1], params[2],
                                 params[3], lh, flux, NULL);
 }
+
+/* ---------------------------------------------------------------------------------------- */
+/* Central moments of a coadded stamp (Section 3.3)                                          */
+/* ---------------------------------------------------------------------------------------- */
+
+/* Moments of stamp S (side = 2r+1, row-major, dy = row - r, dx = col - r measured from the
+ * stamp centre, i.e. the trajectory's position) normalised by its sum (R17):
+ *   out[0] = sum S,  out[1] = x = sum dx S / sum S,  out[2] = y = sum dy S / sum S,
+ *   out[3] = xy = sum dx dy S / sum S,  out[4] = xx = sum dx^2 S / sum S,
+ *   out[5] = yy = sum dy^2 S / sum S.
+ * NaN pixels (no contributing epoch) count as 0.  Returns 1 if the stamp passes the filter:
+ * sum S > 0 and |x| < lim[0], |y| < lim[1], |xy| < lim[2], xx < lim[3], yy < lim[4] (strict),
+ * else 0. */
+int kbo_stamp_moments(const double* S, int r, const double* lim, double* out) {
+  int side = 2 * r + 1;
+  double m0 = 0, mx = 0, my = 0, mxy = 0, mxx = 0, myy = 0;
+  for (int row = 0; row < side; ++row) {
+    for (int col = 0; col < side; ++col) {
+      double v = S[row * side + col];
+      if (isnan(v)) continue;
+      double dx = col - r, dy = row - r;
+      m0 += v;
+      mx += dx * v;
+      my += dy * v;
+      mxy += dx * dy * v;
+      mxx += dx * dx * v;
+      myy += dy * dy * v;
+    }
+  }
+  out[0] = m0;
+  out[1] = mx / m0;
+  out[2] = my / m0;
+  out[3] = mxy / m0;
+  out[4] = mxx / m0;
+  out[5] = myy / m0;
+  if (!(m0 > 0.0)) return 0;
+  return fabs(out[1]) < lim[0] && fabs(out[2]) < lim[1] && fabs(out[3]) < lim[2] &&
+         out[4] < lim[3] && out[5] < lim[4];
+}

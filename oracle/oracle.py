@@ -47,6 +47,8 @@ def lib():
         _LIB.kbo_traj_eval_subpixel.argtypes = [p, p, p, i, i, i, p, d, d, d, d, p, p, p]
         _LIB.kbo_traj_vjp.restype = i
         _LIB.kbo_traj_vjp.argtypes = [p, p, p, i, i, i, p, d, d, d, d, d, d, p, p, p]
+        _LIB.kbo_stamp_moments.restype = i
+        _LIB.kbo_stamp_moments.argtypes = [p, i, p, p]
         _LIB.kbo_refine_adam.restype = i
         _LIB.kbo_refine_adam.argtypes = [p, p, p, i, i, i, p, p, i, d, d, d, d, d, p, p]
     return _LIB
@@ -250,3 +252,21 @@ def refine_adam(psi, phi, times, keep, params, n_steps, lr_pos, lr_vel, b1=0.9, 
                           int(n_steps), float(lr_pos), float(lr_vel), float(b1), float(b2),
                           float(eps), C.byref(lh), C.byref(fl))
     return pr, lh.value, fl.value
+
+
+PAPER_MOMENT_LIMITS = (0.5, 0.5, 1.5, 36.5, 36.5)   # x, y, xy, xx, yy (Section 3.3)
+
+
+def stamp_moments(stamps, limits=PAPER_MOMENT_LIMITS):
+    """Moments (sum, x, y, xy, xx, yy) [n][6] of stamps [n][2r+1][2r+1] about their centres and
+    the filter decision [n] (bool)."""
+    st = _f64(stamps)
+    n, side, _ = st.shape
+    r = side // 2
+    lim = np.ascontiguousarray(limits, dtype=np.float64)
+    out = np.zeros((n, 6))
+    ok = np.zeros(n, bool)
+    for i in range(n):
+        s_i = np.ascontiguousarray(st[i])
+        ok[i] = bool(lib().kbo_stamp_moments(_ptr(s_i), r, _ptr(lim), _ptr(out[i])))
+    return out, ok

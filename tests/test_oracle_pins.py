@@ -701,3 +701,71 @@ def test_adam_stops_where_phi_vanishes():
     pr, L, A = oracle.refine_adam(psi, phi, times, keep, [-300.0, -300.0, 0.0, 0.0], 5, 0.1, 0.1)
     assert np.isnan(L) and np.isnan(A)
     assert np.array_equal(pr, [-300.0, -300.0, 0.0, 0.0])
+
+
+# ------------------------------------------------------------------------------------------------
+# Central moments of coadded stamps (Section 3.3)
+# ------------------------------------------------------------------------------------------------
+
+def test_moments_of_single_pixels_and_their_mixtures():
+    r = 10
+    side = 2 * r + 1
+    rng = np.random.default_rng(71)
+    for _ in range(20):
+        dx, dy = rng.integers(-r, r + 1, 2)
+        s = np.zeros((side, side))
+        s[dy + r, dx + r] = rng.uniform(0.5, 3.0)
+        m, ok = oracle.stamp_moments(s[None])
+        assert np.allclose(m[0, 1:], [dx, dy, dx * dy, dx * dx, dy * dy], atol=1e-12)
+        assert ok[0] == (abs(dx) < 0.5 and abs(dy) < 0.5)
+    # two lit pixels: moments are the weight-averaged ones
+    s = np.zeros((side, side))
+    s[r + 2, r - 3] = 1.0          # dx = -3, dy = +2
+    s[r - 1, r + 4] = 3.0          # dx = +4, dy = -1
+    m, _ = oracle.stamp_moments(s[None])
+    w = np.array([0.25, 0.75])
+    dxs, dys = np.array([-3, 4]), np.array([2, -1])
+    assert np.allclose(m[0], [4.0, w @ dxs, w @ dys, w @ (dxs * dys), w @ dxs ** 2,
+                              w @ dys ** 2], atol=1e-12)
+
+
+def test_moments_of_a_flat_stamp_and_the_paper_limits():
+    # the mean of dx^2 over -r..r is r(r+1)/3: 36.67 for the paper's 21x21 stamps, just above the
+    # 36.5 limit, so a flat (noise-like) stamp is rejected
+    for r in (3, 7, 10):
+        side = 2 * r + 1
+        m, ok = oracle.stamp_moments(np.full((1, side, side), 0.37))
+        assert np.allclose(m[0, 1:], [0, 0, 0, r * (r + 1) / 3, r * (r + 1) / 3], atol=1e-12)
+    assert not ok[0] and abs(m[0, 4] - 110.0 / 3) < 1e-12
+    # empty, negative-sum and NaN stamps
+    assert not oracle.stamp_moments(np.zeros((1, 21, 21)))[1][0]
+    assert not oracle.stamp_moments(-np.ones((1, 21, 21)))[1][0]
+    s = np.full((1, 21, 21), np.nan)
+    s[0, 10, 10] = 2.0
+    m, ok = oracle.stamp_moments(s)
+    assert ok[0] and m[0, 0] == 2.0 and np.allclose(m[0, 1:], 0)
+
+
+def test_moments_of_a_sampled_gaussian():
+    r = 10
+    u = np.arange(-r, r + 1, dtype=np.float64)
+    yy, xx = np.meshgrid(u, u, indexing="ij")
+    for cx, cy, sig in ((0.2, -0.3, 1.5), (0.0, 0.0, 2.0), (0.7, 0.1, 1.2), (-2.0, 1.0, 1.4)):
+        g = np.exp(-((xx - cx) ** 2 + (yy - cy) ** 2) / (2 * sig ** 2))
+        m, ok = oracle.stamp_moments(g[None])
+        # a Gaussian well inside the stamp: centroid = centre, second moments = sig^2 + centre^2
+        assert np.allclose(m[0, 1:3], [cx, cy], atol=1e-6)
+        assert abs(m[0, 3] - cx * cy) < 1e-6
+        assert abs(m[0, 4] - (sig ** 2 + cx ** 2)) < 1e-3
+        assert abs(m[0, 5] - (sig ** 2 + cy ** 2)) < 1e-3
+        assert ok[0] == (abs(cx) < 0.5 and abs(cy) < 0.5)
+    # symmetric stamps have zero odd moments
+    g = np.exp(-(xx ** 2 + 2 * yy ** 2) / 8.0) + 0.1 * (np.abs(xx) + np.abs(yy))
+    m, _ = oracle.stamp_moments(g[None])
+    assert np.allclose(m[0, 1:4], 0, atol=1e-12)
+    # limits are strict
+    s = np.zeros((1, 21, 21))
+    s[0, 10, 10] = 1.0
+    s[0, 10, 11] = 1.0      # x = 0.5 exactly
+    assert not oracle.stamp_moments(s)[1][0]
+    assert oracle.stamp_moments(s, limits=(0.5000001, 0.5, 1.5, 36.5, 36.5))[1][0]
