@@ -3,7 +3,8 @@
 
 One step = the whole hot path over one stack resident in HBM: psi/phi formation, the exhaustive
 integer-track search with the in-line sigma-G clip and per-pixel top-K, the survivor handoff
-(best n_stamps slots), and 21 x 21 mean/median coadded stamps for them.  The metric is
+(best n_stamps slots), 21 x 21 mean/median coadded stamps for them and the central-moment filter
+of the median stamps.  The metric is
 trajectory-epoch evaluations per second: start pixels x trajectories x epochs of the step, over
 the step's device time.
 
@@ -346,8 +347,9 @@ def run_ours(args):
         x0, y0, cvx, cvy, traj = kb.candidate_tracks(pix, slot, res, vx, vy)
         mean, med = kb.stamps(inp["img"], inp["var"], inp["mask"], s.times, x0, y0, cvx, cvy,
                               radius=10)
+        moments, passed = kb.stamp_filter(med)
         return dict(pix=pix, slot=slot, count=count, x0=x0, y0=y0, vx=cvx, vy=cvy, traj=traj,
-                    mean=mean, median=med)
+                    mean=mean, median=med, moments=moments, passed=passed)
 
     for _ in range(args.warmup):
         step(d)

@@ -214,6 +214,27 @@ KB_API int kb_stamps(const float* img, const float* var, const uint8_t* mask, co
               float* out_median, void* stream);
 
 /*
+ * kb_stamp_filter -- central-moment filter of coadded stamps (Section 3.3: a candidate is kept
+ * only if the moments of its median coadd are those of a compact source at the trajectory's
+ * position; the paper's limits are 0.5, 0.5, 1.5, 36.5, 36.5 for x, y, xy, xx, yy, strictly).
+ * With S the stamp, (dx, dy) = (column - radius, row - radius), NaN pixels (no contributing
+ * epoch) left out and the weights w = S - min S (the smallest non-NaN pixel):
+ *   M0 = sum w,  x = sum dx w / M0,  y = sum dy w / M0,  xy = sum dx dy w / M0,
+ *   xx = sum dx^2 w / M0,  yy = sum dy^2 w / M0   (sums in float64)
+ * and the stamp passes iff M0 > 0, |x| < lim[0], |y| < lim[1], |xy| < lim[2], xx < lim[3] and
+ * yy < lim[4].  (Uniform weights over 21 x 21 give xx = yy = 36.67: a flat or noise-like stamp
+ * sits just above the paper's 36.5, and light concentrated at the centre pulls it below.)
+ *
+ *   stamps       [n][2r+1][2r+1] float32 (device), e.g. kb_stamps' out_median.
+ *   limits       [5] float32 HOST array, or NULL for the paper's limits.
+ *   out_moments  [n][6] float32 (device, nullable): M0, x, y, xy, xx, yy.
+ *   out_pass     [n] uint8 (device): 1 = passes.
+ * Errors: KB_ERR_INVALID_ARG (null pointers, n < 0, radius outside 0..15, NaN limits).
+ */
+KB_API int kb_stamp_filter(const float* stamps, int n, int radius, const float* limits,
+                           float* out_moments, uint8_t* out_pass, void* stream);
+
+/*
  * kb_collect -- GPU-to-host handoff of the survivors (Section 3.1 reworked handoff; Section 3.2
  * returns the per-pixel results to the CPU): gathers every filled slot of a kb_search result
  * and orders them by LH' descending, then start pixel, then slot; the first n_max are written.

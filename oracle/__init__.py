@@ -21,9 +21,10 @@ the pins live in tests/test_oracle_pins.py):
                     single psi/phi pixels; tap support; Euler's theorem for the homogeneity
                     degrees of L and alpha in psi and phi
   stamp_moments     closed forms: a single lit pixel at (dx, dy) gives x = dx, y = dy, xy = dx dy,
-                    xx = dx^2, yy = dy^2; a flat stamp gives xx = yy = r(r+1)/3 (36.67 > 36.5 for
-                    r = 10); symmetric stamps give zero odd moments; a sampled Gaussian gives
-                    its centre and variance
+                    xx = dx^2, yy = dy^2; a flat stamp with one dark pixel at its centre gives
+                    xx = yy = side r(r+1)(2r+1) / (3 (side^2 - 1)) (36.75 > 36.5 for r = 10);
+                    invariance to a constant offset; symmetric stamps give zero odd moments; a
+                    sampled Gaussian gives its centre and variance
   refine_adam       closed form of Adam's first step; convergence to a noiseless off-grid mover;
                     stop where Phi vanishes
 """

@@ -539,28 +539,32 @@ int kbo_refine_adam(const double* psi, const double* phi, const double* times, i
 /* Central moments of a coadded stamp (Section 3.3)                                          */
 /* ---------------------------------------------------------------------------------------- */
 
-/* Moments of stamp S (side = 2r+1, row-major, dy = row - r, dx = col - r measured from the
- * stamp centre, i.e. the trajectory's position) normalised by its sum (R17):
- *   out[0] = sum S,  out[1] = x = sum dx S / sum S,  out[2] = y = sum dy S / sum S,
- *   out[3] = xy = sum dx dy S / sum S,  out[4] = xx = sum dx^2 S / sum S,
- *   out[5] = yy = sum dy^2 S / sum S.
- * NaN pixels (no contributing epoch) count as 0.  Returns 1 if the stamp passes the filter:
- * sum S > 0 and |x| < lim[0], |y| < lim[1], |xy| < lim[2], xx < lim[3], yy < lim[4] (strict),
- * else 0. */
+/* Moments of stamp S (side = 2r+1, row-major) about its centre, the trajectory's position
+ * (R17): with dy = row - r, dx = col - r, NaN pixels (no contributing epoch) left out, and the
+ * weights w = S - min S (the smallest non-NaN pixel, so every weight is >= 0):
+ *   out[0] = sum w,  out[1] = x = sum dx w / sum w,  out[2] = y = sum dy w / sum w,
+ *   out[3] = xy = sum dx dy w / sum w,  out[4] = xx = sum dx^2 w / sum w,
+ *   out[5] = yy = sum dy^2 w / sum w.
+ * Returns 1 if the stamp passes the filter: sum w > 0 and |x| < lim[0], |y| < lim[1],
+ * |xy| < lim[2], xx < lim[3], yy < lim[4] (strict), else 0. */
 int kbo_stamp_moments(const double* S, int r, const double* lim, double* out) {
   int side = 2 * r + 1;
+  double lo = INFINITY;
+  for (int i = 0; i < side * side; ++i)
+    if (!isnan(S[i]) && S[i] < lo) lo = S[i];
   double m0 = 0, mx = 0, my = 0, mxy = 0, mxx = 0, myy = 0;
   for (int row = 0; row < side; ++row) {
     for (int col = 0; col < side; ++col) {
       double v = S[row * side + col];
       if (isnan(v)) continue;
+      double w = v - lo;
       double dx = col - r, dy = row - r;
-      m0 += v;
-      mx += dx * v;
-      my += dy * v;
-      mxy += dx * dy * v;
-      mxx += dx * dx * v;
-      myy += dy * dy * v;
+      m0 += w;
+      mx += dx * w;
+      my += dy * w;
+      mxy += dx * dy * w;
+      mxx += dx * dx * w;
+      myy += dy * dy * w;
     }
   }
   out[0] = m0;

@@ -8,6 +8,7 @@ Every step of the computation runs in the library's sm_103a kernels; CPU tensors
     res = search(psi, phi, times, vx, vy, SearchParams(...))      # Sections 3, 3.1, 3.2
     pix, slot, count = collect(res, n_max)                        # GPU -> host handoff
     mean, median = stamps(img, var, mask, times, x0, y0, vx, vy)  # Section 3.3
+    moments, passed = stamp_filter(median)                        # Section 3.3 moment filter
     params, keep = candidate_params(pix, slot, res, vx, vy)       # off-grid refinement:
     params, L, alpha, L0 = refine(psi, phi, times, params, keep)  #   Section 4.1, bilinear
     L, alpha = traj_likelihood(params, psi, phi, times, keep)     # differentiable (autograd)
@@ -24,7 +25,8 @@ from ._lib import (KB_MAX_K, KB_MAX_T, KB_WORKSPACE_ALIGN, KbError, RefineParams
 __all__ = ["SearchParams", "make_psi_phi", "search", "search_workspace_size", "search_stats",
            "stamps", "collect", "candidate_tracks", "launch_count", "profile_events", "KbError",
            "search_no_alloc", "RefineParams", "traj_eval", "traj_eval_backward", "TrajEval",
-           "traj_likelihood", "refine", "candidate_params",
+           "traj_likelihood", "refine", "candidate_params", "stamp_filter",
+           "PAPER_MOMENT_LIMITS",
            "KB_MAX_T", "KB_MAX_K", "lib", "version", "alloc_workspace"]
 
 
@@ -179,6 +181,26 @@ def stamps(img, var, mask, times, x0, y0, vx, vy, radius=10, keep_mask=None, str
                           T, H, W, _ptr(x0), _ptr(y0), _ptr(vx), _ptr(vy), _ptr(keep_mask), n,
                           radius, _ptr(mean), _ptr(med), _stream(stream)))
     return mean, med
+
+
+PAPER_MOMENT_LIMITS = (0.5, 0.5, 1.5, 36.5, 36.5)   # x, y, xy, xx, yy (Section 3.3)
+
+
+def stamp_filter(stamps_, limits=None, stream=None):
+    """Central moments (M0, x, y, xy, xx, yy) [n, 6] of stamps [n, 2r+1, 2r+1] and the moment
+    filter's decision [n] (bool tensor); limits default to the paper's."""
+    _dev(stamps_, torch.float32, "stamps", 3)
+    n, side, side2 = stamps_.shape
+    if side != side2 or side % 2 != 1:
+        raise ValueError("stamps must be [n, 2r+1, 2r+1]")
+    mom = torch.empty((n, 6), dtype=torch.float32, device=stamps_.device)
+    ok = torch.empty(n, dtype=torch.uint8, device=stamps_.device)
+    lim = None
+    if limits is not None:
+        lim = (C.c_float * 5)(*[float(v) for v in limits])
+    check(lib().kb_stamp_filter(_ptr(stamps_), n, side // 2, lim, _ptr(mom), _ptr(ok),
+                                _stream(stream)))
+    return mom, ok.view(torch.bool)
 
 
 def collect(result, n_max, workspace=None, stream=None):

@@ -24,7 +24,7 @@ EXPORTS = ("kb_version", "kb_last_error", "kb_search_params_default", "kb_make_p
            "kb_search_workspace_size", "kb_search", "kb_search_stats", "kb_stamps",
            "kb_collect_workspace_size", "kb_collect", "kb_candidate_tracks", "kb_launch_count",
            "kb_profile_events", "kb_search_no_alloc", "kb_traj_eval_fwd", "kb_traj_eval_bwd",
-           "kb_refine_params_default", "kb_refine", "kb_candidate_params")
+           "kb_refine_params_default", "kb_refine", "kb_candidate_params", "kb_stamp_filter")
 
 
 class KbError(RuntimeError):
@@ -97,6 +97,8 @@ def lib():
     L.kb_refine_params_default.argtypes = [C.POINTER(RefineParamsC)]
     L.kb_refine.restype = i
     L.kb_refine.argtypes = [p, p, p, i, i, i, p, p, i, C.POINTER(RefineParamsC), p, p, p, p]
+    L.kb_stamp_filter.restype = i
+    L.kb_stamp_filter.argtypes = [p, i, i, p, p, p, p]
     L.kb_candidate_params.restype = i
     L.kb_candidate_params.argtypes = [p, p, i, p, p, i, i, p, p, i, i, i, p, p, p]
     _LIB = L

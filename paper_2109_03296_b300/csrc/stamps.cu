@@ -170,3 +170,90 @@ extern "C" int kb_stamps(const float* img, const float* var, const uint8_t* mask
   KB_LAUNCH_CHECK("stamps_kernel");
   return KB_OK;
 }
+
+// ------------------------------------------------------------------------------------------------
+// Central-moment filter of coadded stamps (Section 3.3): moments about the stamp centre of the
+// weights w = S - min S (NaN pixels left out), normalised by their sum; a stamp passes when they
+// are those of a compact source at the centre.  One warp per stamp, lanes striding over the
+// pixels: a warp minimum, then the six weighted sums in float64 (a few hundred terms per stamp,
+// so the cost is negligible), so that a decision differs from the exact one only for moments
+// within ~1e-15 relative of a limit.
+// ------------------------------------------------------------------------------------------------
+namespace kb {
+
+struct MomentLimits {
+  double x, y, xy, xx, yy;
+};
+
+__global__ void stamp_moments_kernel(const float* __restrict__ stamps, int n, int radius,
+                                     MomentLimits lim, float* __restrict__ out_moments,
+                                     uint8_t* __restrict__ out_pass) {
+  const long long c = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (c >= n) return;
+  const int lane = threadIdx.x & 31;
+  const int side = 2 * radius + 1, npx = side * side;
+  const float* S = stamps + c * npx;
+  float lo = INFINITY;
+  for (int i = lane; i < npx; i += 32) {
+    float v = __ldg(S + i);
+    if (!isnan(v)) lo = fminf(lo, v);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+  double m[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int i = lane; i < npx; i += 32) {
+    float v = __ldg(S + i);
+    if (isnan(v)) continue;
+    double dv = (double)v - (double)lo;
+    double dx = (double)(i % side - radius), dy = (double)(i / side - radius);
+    m[0] += dv;
+    m[1] += dx * dv;
+    m[2] += dy * dv;
+    m[3] += dx * dy * dv;
+    m[4] += dx * dx * dv;
+    m[5] += dy * dy * dv;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) m[k] += __shfl_xor_sync(0xffffffffu, m[k], o);
+  if (lane != 0) return;
+  const double x = m[1] / m[0], y = m[2] / m[0], xy = m[3] / m[0], xx = m[4] / m[0],
+               yy = m[5] / m[0];
+  if (out_moments) {
+    float* o = out_moments + c * 6;
+    o[0] = (float)m[0];
+    o[1] = (float)x;
+    o[2] = (float)y;
+    o[3] = (float)xy;
+    o[4] = (float)xx;
+    o[5] = (float)yy;
+  }
+  const bool pass = m[0] > 0.0 && fabs(x) < lim.x && fabs(y) < lim.y && fabs(xy) < lim.xy &&
+                    xx < lim.xx && yy < lim.yy;
+  out_pass[c] = pass ? 1 : 0;
+}
+
+}  // namespace kb
+
+extern "C" int kb_stamp_filter(const float* stamps, int n, int radius, const float* limits,
+                               float* out_moments, uint8_t* out_pass, void* stream) {
+  using namespace kb;
+  if (n < 0) return fail(KB_ERR_INVALID_ARG, "kb_stamp_filter: n < 0");
+  if (radius < 0 || radius > 15)
+    return fail(KB_ERR_INVALID_ARG, "kb_stamp_filter: radius outside 0..15");
+  if (n == 0) return KB_OK;
+  if (!stamps || !out_pass) return fail(KB_ERR_INVALID_ARG, "kb_stamp_filter: null pointer");
+  MomentLimits lim{0.5, 0.5, 1.5, 36.5, 36.5};
+  if (limits) {
+    lim = MomentLimits{limits[0], limits[1], limits[2], limits[3], limits[4]};
+    for (int k = 0; k < 5; ++k)
+      if (std::isnan(limits[k])) return fail(KB_ERR_INVALID_ARG, "kb_stamp_filter: NaN limit");
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int warps = 8;
+  stamp_moments_kernel<<<(unsigned)((n + warps - 1) / warps), warps * 32, 0, st>>>(
+      stamps, n, radius, lim, out_moments, out_pass);
+  KB_LAUNCH_CHECK("stamp_moments_kernel");
+  return KB_OK;
+}

@@ -730,20 +730,33 @@ def test_moments_of_single_pixels_and_their_mixtures():
 
 
 def test_moments_of_a_flat_stamp_and_the_paper_limits():
-    # the mean of dx^2 over -r..r is r(r+1)/3: 36.67 for the paper's 21x21 stamps, just above the
-    # 36.5 limit, so a flat (noise-like) stamp is rejected
+    # a flat stamp with one dark pixel at its centre: every other pixel has weight 1, so
+    # xx = sum dx^2 / (side^2 - 1) = side r(r+1)(2r+1)/3 / (side^2 - 1): 36.75 for the paper's
+    # 21 x 21 stamps, just above the 36.5 limit (a flat, noise-like stamp is rejected)
     for r in (3, 7, 10):
         side = 2 * r + 1
-        m, ok = oracle.stamp_moments(np.full((1, side, side), 0.37))
-        assert np.allclose(m[0, 1:], [0, 0, 0, r * (r + 1) / 3, r * (r + 1) / 3], atol=1e-12)
-    assert not ok[0] and abs(m[0, 4] - 110.0 / 3) < 1e-12
-    # empty, negative-sum and NaN stamps
+        s = np.full((1, side, side), 0.37)
+        s[0, r, r] = -0.2
+        m, ok = oracle.stamp_moments(s)
+        xx = side * r * (r + 1) * (2 * r + 1) / 3 / (side * side - 1)
+        assert np.allclose(m[0], [(side * side - 1) * 0.57, 0, 0, 0, xx, xx], atol=1e-12)
+    assert not ok[0] and abs(m[0, 4] - 16170.0 / 440) < 1e-12
+    # a constant offset changes nothing (the weights are taken above the stamp's minimum)
+    rng = np.random.default_rng(72)
+    s = rng.normal(size=(1, 21, 21))
+    m1, ok1 = oracle.stamp_moments(s)
+    m2, ok2 = oracle.stamp_moments(s + 7.25)
+    assert np.allclose(m1, m2, rtol=1e-9, atol=1e-9) and ok1[0] == ok2[0]
+    # flat, empty and all-NaN stamps have no weight and are rejected
     assert not oracle.stamp_moments(np.zeros((1, 21, 21)))[1][0]
-    assert not oracle.stamp_moments(-np.ones((1, 21, 21)))[1][0]
+    assert not oracle.stamp_moments(np.full((1, 21, 21), -3.0))[1][0]
+    assert not oracle.stamp_moments(np.full((1, 21, 21), np.nan))[1][0]
+    # NaN pixels are left out of both the minimum and the sums
     s = np.full((1, 21, 21), np.nan)
     s[0, 10, 10] = 2.0
+    s[0, 10, 12] = 1.0      # the minimum: weight 0
     m, ok = oracle.stamp_moments(s)
-    assert ok[0] and m[0, 0] == 2.0 and np.allclose(m[0, 1:], 0)
+    assert ok[0] and m[0, 0] == 1.0 and np.allclose(m[0, 1:], 0)
 
 
 def test_moments_of_a_sampled_gaussian():
