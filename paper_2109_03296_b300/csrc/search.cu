@@ -79,6 +79,7 @@ __host__ __device__ constexpr int stage_width(int mode) {
 }
 __host__ __device__ constexpr int stage_height(int h) { return 64 + 16 * h; }
 
+constexpr int S_ORDER_MAX = 16384;       // tiles ordered by predicted cost (one-block sort)
 constexpr int HILBERT_BITS = 8;          // 256 x 256 velocity cells
 constexpr int N_CELLS = 1 << (2 * HILBERT_BITS);
 
@@ -102,7 +103,7 @@ struct EvalParams {
 
 // Workspace layout (offsets in bytes from the workspace base).
 struct WsLayout {
-  size_t ctrl, vbox, keys, counts, cursor, sorted, orig, offs, plan, bound, total;
+  size_t ctrl, vbox, keys, counts, cursor, sorted, orig, offs, plan, bound, tkeys, torder, total;
   int n_pad, nchunk, Wp;
 };
 
@@ -127,6 +128,8 @@ static WsLayout ws_layout(int T, int H, int W, int n_traj) {
   L.offs = take(sizeof(int2) * (size_t)L.n_pad * T);
   L.plan = take(sizeof(PlanRec) * (size_t)L.nchunk * T);
   L.bound = take(sizeof(uint32_t) * (size_t)T * (H + 1) * L.Wp);
+  L.tkeys = take(sizeof(unsigned long long) * S_ORDER_MAX);
+  L.torder = take(sizeof(int32_t) * S_ORDER_MAX);
   L.total = o;
   return L;
 }
@@ -363,6 +366,80 @@ __global__ void bound_prep_kernel(const float* __restrict__ psi, const float* __
     const unsigned short hi = half_round_up(nu2_at(psi, phi, H, W, plane, r, x));
     bound[i] = (uint32_t)lo | ((uint32_t)hi << 16);
   }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Tile order.  A start pixel near a bright source in an epoch whose offsets are all small (the
+// first night) gets a candidate pair from nearly every trajectory, so the few tiles around such
+// sources carry most of the full evaluations; handed out last, they leave most SMs idle at the
+// end.  The score of a tile is the number of pixels with nu2 >= tau in its footprint at each
+// epoch whose offsets span at most S_SCORE_SPAN pixels; tiles are handed out in decreasing score
+// (ties and unscored tiles in row-major order).  The order only schedules work: the results do
+// not depend on it.
+// ---------------------------------------------------------------------------------------------
+constexpr int S_SCORE_SPAN = 64;
+
+__global__ void __launch_bounds__(256) tile_score_kernel(
+    const uint32_t* __restrict__ bound, int T, int H, int W, int Wp, const float4* vbox,
+    SearchConsts cs, int x_lo, int y_lo, int x_hi, int y_hi, int ntx, int ntiles, float tau,
+    unsigned long long* __restrict__ keys) {
+  const int tile = blockIdx.x;
+  if (tile >= ntiles) return;
+  __shared__ unsigned int s_count;
+  if (threadIdx.x == 0) s_count = 0u;
+  __syncthreads();
+  const float4 b = *vbox;  // vx min, vx max, vy min, vy max
+  const int tx0 = x_lo + (tile % ntx) * S_TX, ty0 = y_lo + (tile / ntx) * S_TY;
+  const int tx1 = min(tx0 + S_TX, x_hi), ty1 = min(ty0 + S_TY, y_hi);
+  unsigned int cnt = 0u;
+  for (int t = 0; t < T; ++t) {
+    const int oxa = track_offset(b.x, cs.dt[t]), oxb = track_offset(b.y, cs.dt[t]);
+    const int oya = track_offset(b.z, cs.dt[t]), oyb = track_offset(b.w, cs.dt[t]);
+    if (oxb - oxa > S_SCORE_SPAN || oyb - oya > S_SCORE_SPAN) continue;
+    const int xa = max(tx0 + oxa, 0), xb = min(tx1 - 1 + oxb, W - 1);
+    const int ya = max(ty0 + oya, 0), yb = min(ty1 - 1 + oyb, H - 1);
+    if (xa > xb || ya > yb) continue;
+    const int w = xb - xa + 1, n = w * (yb - ya + 1);
+    const uint32_t* plane = bound + (size_t)t * (H + 1) * Wp;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const int y = ya + i / w, x = xa + i % w;
+      // image row y is the high half of word row y
+      const float v = __half2float(__ushort_as_half((unsigned short)(__ldg(plane + (size_t)y * Wp + x) >> 16)));
+      cnt += v >= tau ? 1u : 0u;
+    }
+  }
+  atomicAdd(&s_count, cnt);
+  __syncthreads();
+  if (threadIdx.x == 0)
+    keys[tile] = ((unsigned long long)(0xffffffffu - s_count) << 32) | (unsigned int)tile;
+}
+
+// One block sorts the ntiles keys (ntiles <= S_ORDER_MAX) in shared memory with a bitonic
+// network and writes the tile order.
+__global__ void __launch_bounds__(1024) tile_order_kernel(const unsigned long long* __restrict__ keys,
+                                                          int ntiles, int32_t* __restrict__ order) {
+  extern __shared__ unsigned long long sk[];
+  int n = 1;
+  while (n < ntiles) n <<= 1;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) sk[i] = i < ntiles ? keys[i] : ~0ull;
+  __syncthreads();
+  for (int k = 2; k <= n; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int l = i ^ j;
+        if (l > i) {
+          const unsigned long long a = sk[i], c = sk[l];
+          const bool up = (i & k) == 0;
+          if ((a > c) == up) {
+            sk[i] = c;
+            sk[l] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < ntiles; i += blockDim.x) order[i] = (int32_t)(sk[i] & 0xffffffffu);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -640,6 +717,7 @@ struct SearchArgs {
   uint16_t* out_nkept;
   uint32_t* out_mask;
   Ctrl* ctrl;
+  const int32_t* order;  // tile order (nullptr: row-major)
   EvalParams ep;
   int n_traj, nchunk, Wp;
   int x_lo, x_hi, y_lo, y_hi, ntx, nty, ntiles;
@@ -734,6 +812,7 @@ __device__ void producer_loop(const TmapSet& maps, const SearchArgs& A, unsigned
     if (pw == 0) {
       if (lane == 0) {
         tile = (int)atomicAdd(&A.ctrl->tile_counter, 1u);
+        if (A.order && tile < A.ntiles) tile = __ldg(A.order + tile);
         tr->tile[k & 3] = tile;
         __threadfence_block();
         *(volatile unsigned int*)&tr->published = (unsigned int)(k + 1);
@@ -1339,6 +1418,24 @@ extern "C" int kb_search(const float* psi, const float* phi, const double* times
     KB_LAUNCH_CHECK("bound_prep_kernel");
   }
 
+  const int ntx = (p->x_hi - p->x_lo + S_TX - 1) / S_TX;
+  const int ntiles = ntx * ((p->y_hi - p->y_lo + S_TY - 1) / S_TY);
+  int32_t* torder = nullptr;
+  if (ntiles > 1 && ntiles <= S_ORDER_MAX) {
+    unsigned long long* tkeys = reinterpret_cast<unsigned long long*>(ws + L.tkeys);
+    torder = reinterpret_cast<int32_t*>(ws + L.torder);
+    tile_score_kernel<<<ntiles, 256, 0, st>>>(bound, T, H, W, L.Wp, vbox, cs, p->x_lo, p->y_lo,
+                                              p->x_hi, p->y_hi, ntx, ntiles, 16.0f, tkeys);
+    KB_LAUNCH_CHECK("tile_score_kernel");
+    int n2 = 1;
+    while (n2 < ntiles) n2 <<= 1;
+    const size_t osm = sizeof(unsigned long long) * (size_t)n2;
+    KB_CUDA_TRY(cudaFuncSetAttribute(tile_order_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)osm));
+    tile_order_kernel<<<1, 1024, osm, st>>>(tkeys, ntiles, torder);
+    KB_LAUNCH_CHECK("tile_order_kernel");
+  }
+
   TmapSet maps;
   for (int w = 1; w <= S_NW; ++w)
     for (int h = 0; h < S_NH; ++h) {
@@ -1368,6 +1465,7 @@ extern "C" int kb_search(const float* psi, const float* phi, const double* times
   A.out_nkept = out_nkept;
   A.out_mask = out_mask;
   A.ctrl = ctrl;
+  A.order = torder;
   A.ep.T = T;
   A.ep.H = H;
   A.ep.W = W;
