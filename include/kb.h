@@ -214,6 +214,84 @@ KB_API int kb_stamps(const float* img, const float* var, const uint8_t* mask, co
               float* out_median, void* stream);
 
 /*
+ * Batched search -- many stacks (CCDs, pointings) in one persistent launch.  The paper searches
+ * each CCD's stack on its own (Section 2: 2580 independent searches, Section 4.1); here the tiles
+ * of all stacks are handed out from one counter to one persistent kernel, so that no SM idles at
+ * the end of a small stack, and the whole sequence (per-stack preparation + the search) can be
+ * replayed as one CUDA graph.  Each stack's results are exactly those of kb_search on it.
+ *
+ *   kb_stack       one stack: the arguments of kb_search (psi, phi, times, sizes, velocities,
+ *                  search parameters and the six output arrays), with the same meaning, layout
+ *                  and ownership; each stack has its own T (up to KB_MAX_T), H, W and n_traj.
+ *   kb_schedule    scheduling knobs; the results never depend on them:
+ *                    tile_order   1: each stack's tiles in decreasing predicted cost (pixels
+ *                                 with psi^2/phi >= hot_nu2 in the footprints of the epochs
+ *                                 whose offsets span at most score_span pixels); 0: row-major.
+ *                    stack_order  1: stacks in decreasing trajectory-epoch count; 0: as given.
+ *                  kb_schedule_default: {tile_order 1, hot_nu2 16, score_span 64, stack_order 1}
+ *                  (kb_search uses the same tile order).
+ *   kb_batch       opaque handle: kb_batch_create validates every stack (the checks of
+ *                  kb_search), lays out the workspace and writes the batch tables to the device
+ *                  (synchronous copies); the stacks' buffers must stay valid while it is used.
+ *
+ * kb_batch_workspace_size: bytes of the caller-owned workspace (KB_WORKSPACE_ALIGN-aligned).
+ * kb_batch_run: enqueues the batch on `stream` (kernel launches only).
+ * kb_batch_run_graph: on first use captures kb_batch_run into a CUDA graph on a stream of the
+ *   batch's own; every call replays it, ordered after the work already on `stream` and before
+ *   the work enqueued on it later.  A schedule change drops the graph (re-captured on the next
+ *   call).
+ * kb_batch_set_schedule / kb_batch_get_schedule: knobs above (set waits for the device).
+ * kb_batch_autotune: times the batch (kb_batch_run, best of `reps`) under schedules chosen by
+ *   coordinate descent from the default (stack order, tile order, hot_nu2 in {16, 9, 36},
+ *   score_span in {64, 32, 128}), keeps the fastest and returns it in *best (nullable).  Runs
+ *   the batch about 8 x reps times; its outputs are those of a normal run.
+ * kb_batch_stats: after a run, done_ns[i] = ns from the start of the run to the completion of
+ *   stack i's last tile (the caller's order), totals[4] = {trajectory-epochs, full evaluations,
+ *   insertions, error flags} of the run (blocks the host).
+ * kb_batch_destroy: frees the handle (not the workspace or the stacks' buffers).
+ * Errors: as kb_search per stack (the message names the stack), KB_ERR_INVALID_ARG for bad
+ * schedules, KB_ERR_WORKSPACE, KB_ERR_CUDA.
+ */
+typedef struct kb_stack {
+  const float* psi;
+  const float* phi;
+  const double* times; /* HOST */
+  int T, H, W;
+  const float* vx;
+  const float* vy;
+  int n_traj;
+  kb_search_params params;
+  float* out_lh;
+  float* out_flux;
+  int32_t* out_idx;
+  uint16_t* out_nvalid;
+  uint16_t* out_nkept;
+  uint32_t* out_mask;
+} kb_stack;
+
+typedef struct kb_schedule {
+  int tile_order;
+  float hot_nu2;
+  int score_span;
+  int stack_order;
+} kb_schedule;
+
+typedef struct kb_batch kb_batch;
+
+KB_API void kb_schedule_default(kb_schedule* s);
+KB_API int kb_batch_workspace_size(const kb_stack* stacks, int n, size_t* bytes);
+KB_API int kb_batch_create(const kb_stack* stacks, int n, void* workspace, size_t ws_bytes,
+                           kb_batch** out);
+KB_API int kb_batch_run(kb_batch* b, void* stream);
+KB_API int kb_batch_run_graph(kb_batch* b, void* stream);
+KB_API int kb_batch_set_schedule(kb_batch* b, const kb_schedule* s);
+KB_API int kb_batch_get_schedule(const kb_batch* b, kb_schedule* s);
+KB_API int kb_batch_autotune(kb_batch* b, void* stream, int reps, kb_schedule* best);
+KB_API int kb_batch_stats(kb_batch* b, unsigned long long* done_ns, unsigned long long* totals,
+                          void* stream);
+KB_API void kb_batch_destroy(kb_batch* b);
+
+/*
  * kb_stamp_filter -- central-moment filter of coadded stamps (Section 3.3: a candidate is kept
  * only if the moments of its median coadd are those of a compact source at the trajectory's
  * position; the paper's limits are 0.5, 0.5, 1.5, 36.5, 36.5 for x, y, xy, xx, yy, strictly).

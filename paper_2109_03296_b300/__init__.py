@@ -6,6 +6,8 @@ Every step of the computation runs in the library's sm_103a kernels; CPU tensors
 
     psi, phi = make_psi_phi(img, var, mask, psf)                  # Section 3
     res = search(psi, phi, times, vx, vy, SearchParams(...))      # Sections 3, 3.1, 3.2
+    batch = Batch([dict(psi=..., phi=..., times=..., vx=..., vy=..., params=...), ...])
+    batch.run(graph=True); batch.results[i]                       # many stacks, one launch
     pix, slot, count = collect(res, n_max)                        # GPU -> host handoff
     mean, median = stamps(img, var, mask, times, x0, y0, vx, vy)  # Section 3.3
     moments, passed = stamp_filter(median)                        # Section 3.3 moment filter
@@ -19,14 +21,14 @@ from dataclasses import dataclass
 import numpy as np
 import torch
 
-from ._lib import (KB_MAX_K, KB_MAX_T, KB_WORKSPACE_ALIGN, KbError, RefineParamsC, SearchParamsC,
-                   check, lib)
+from ._lib import (KB_MAX_K, KB_MAX_T, KB_WORKSPACE_ALIGN, KbError, RefineParamsC, ScheduleC,
+                   SearchParamsC, StackC, check, lib)
 
 __all__ = ["SearchParams", "make_psi_phi", "search", "search_workspace_size", "search_stats",
            "stamps", "collect", "candidate_tracks", "launch_count", "profile_events", "KbError",
            "search_no_alloc", "RefineParams", "traj_eval", "traj_eval_backward", "TrajEval",
            "traj_likelihood", "refine", "candidate_params", "stamp_filter",
-           "PAPER_MOMENT_LIMITS",
+           "PAPER_MOMENT_LIMITS", "Schedule", "Batch",
            "KB_MAX_T", "KB_MAX_K", "lib", "version", "alloc_workspace"]
 
 
@@ -428,3 +430,120 @@ def candidate_params(pix, slot, result, vx, vy, window=None, stream=None):
                                     _ptr(vx), _ptr(vy), int(x_lo), int(y_lo), wx, _ptr(params),
                                     _ptr(keep), _stream(stream)))
     return params, keep
+
+
+# ------------------------------------------------------------------------------------------------
+# Batched search: many stacks in one persistent launch (optionally replayed as a CUDA graph)
+# ------------------------------------------------------------------------------------------------
+
+@dataclass
+class Schedule:
+    """kb_schedule (include/kb.h): scheduling knobs of a batch; results never depend on them."""
+    tile_order: int = 1
+    hot_nu2: float = 16.0
+    score_span: int = 64
+    stack_order: int = 1
+
+    def to_c(self):
+        return ScheduleC(int(self.tile_order), float(self.hot_nu2), int(self.score_span),
+                         int(self.stack_order))
+
+    @staticmethod
+    def from_c(c):
+        return Schedule(c.tile_order, c.hot_nu2, c.score_span, c.stack_order)
+
+
+class Batch:
+    """A batch of stacks searched by one persistent launch (kb_batch_*).
+
+    stacks: list of dicts with psi, phi ([T, H, W] float32 CUDA tensors), times (host array),
+    vx, vy (float32 CUDA tensors) and params (SearchParams, optional).  Allocates each stack's
+    outputs (``results[i]``, the dict kb.search returns) and the workspace."""
+
+    def __init__(self, stacks, device=None):
+        if not stacks:
+            raise ValueError("empty batch")
+        n = len(stacks)
+        self._keep = []                    # host times and tensors referenced by the C structs
+        arr = (StackC * n)()
+        self.results = []
+        self.te = []
+        for i, st in enumerate(stacks):
+            psi, phi, vx, vy = st["psi"], st["phi"], st["vx"], st["vy"]
+            _dev(psi, torch.float32, "psi", 3)
+            _dev(phi, torch.float32, "phi", 3)
+            _dev(vx, torch.float32, "vx", 1)
+            _dev(vy, torch.float32, "vy", 1)
+            T, H, W = psi.shape
+            sp = st.get("params") or SearchParams()
+            pc = sp.to_c(H, W)
+            x_lo, x_hi, y_lo, y_hi = pc.x_lo, pc.x_hi, pc.y_lo, pc.y_hi
+            wy, wx, K = y_hi - y_lo, x_hi - x_lo, pc.k_per_pixel
+            mw = (T + 31) // 32
+            dev = psi.device
+            out = dict(lh=torch.empty((wy, wx, K), dtype=torch.float32, device=dev),
+                       flux=torch.empty((wy, wx, K), dtype=torch.float32, device=dev),
+                       idx=torch.empty((wy, wx, K), dtype=torch.int32, device=dev),
+                       nvalid=torch.empty((wy, wx, K), dtype=torch.int16, device=dev),
+                       nkept=torch.empty((wy, wx, K), dtype=torch.int16, device=dev),
+                       mask=torch.empty((wy, wx, K, mw), dtype=torch.int32, device=dev))
+            times = _host_times(st["times"])
+            self._keep += [times, psi, phi, vx, vy]
+            arr[i] = StackC(psi.data_ptr(), phi.data_ptr(), times.ctypes.data, T, H, W,
+                            vx.data_ptr(), vy.data_ptr(), vx.numel(), pc,
+                            out["lh"].data_ptr(), out["flux"].data_ptr(), out["idx"].data_ptr(),
+                            out["nvalid"].data_ptr(), out["nkept"].data_ptr(),
+                            out["mask"].data_ptr())
+            self.results.append(out)
+            self.te.append(wy * wx * vx.numel() * T)
+        self._arr = arr
+        nbytes = C.c_size_t(0)
+        check(lib().kb_batch_workspace_size(arr, n, C.byref(nbytes)))
+        self.workspace = alloc_workspace(nbytes.value, stacks[0]["psi"].device)
+        h = C.c_void_p()
+        check(lib().kb_batch_create(arr, n, _ptr(self.workspace), self.workspace.numel(),
+                                    C.byref(h)))
+        self._h = h
+        self.n = n
+
+    def run(self, graph=False, stream=None):
+        fn = lib().kb_batch_run_graph if graph else lib().kb_batch_run
+        check(fn(self._h, _stream(stream)))
+        return self.results
+
+    @property
+    def schedule(self):
+        c = ScheduleC()
+        check(lib().kb_batch_get_schedule(self._h, C.byref(c)))
+        return Schedule.from_c(c)
+
+    @schedule.setter
+    def schedule(self, s):
+        c = s.to_c()
+        check(lib().kb_batch_set_schedule(self._h, C.byref(c)))
+
+    def autotune(self, reps=1, stream=None):
+        c = ScheduleC()
+        check(lib().kb_batch_autotune(self._h, _stream(stream), int(reps), C.byref(c)))
+        return Schedule.from_c(c)
+
+    def stats(self, stream=None):
+        """(done_ns [n] numpy uint64: completion of each stack from the start of the last run,
+        totals {te, evals, inserts, err})."""
+        done = np.zeros(self.n, np.uint64)
+        tot = np.zeros(4, np.uint64)
+        check(lib().kb_batch_stats(self._h, done.ctypes.data_as(C.c_void_p),
+                                   tot.ctypes.data_as(C.c_void_p), _stream(stream)))
+        return done, dict(te=int(tot[0]), evals=int(tot[1]), inserts=int(tot[2]),
+                          err=int(tot[3]))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().kb_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

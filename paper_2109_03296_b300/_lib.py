@@ -24,7 +24,10 @@ EXPORTS = ("kb_version", "kb_last_error", "kb_search_params_default", "kb_make_p
            "kb_search_workspace_size", "kb_search", "kb_search_stats", "kb_stamps",
            "kb_collect_workspace_size", "kb_collect", "kb_candidate_tracks", "kb_launch_count",
            "kb_profile_events", "kb_search_no_alloc", "kb_traj_eval_fwd", "kb_traj_eval_bwd",
-           "kb_refine_params_default", "kb_refine", "kb_candidate_params", "kb_stamp_filter")
+           "kb_refine_params_default", "kb_refine", "kb_candidate_params", "kb_stamp_filter",
+           "kb_schedule_default", "kb_batch_workspace_size", "kb_batch_create", "kb_batch_run",
+           "kb_batch_run_graph", "kb_batch_set_schedule", "kb_batch_get_schedule",
+           "kb_batch_autotune", "kb_batch_stats", "kb_batch_destroy")
 
 
 class KbError(RuntimeError):
@@ -44,6 +47,20 @@ class SearchParamsC(C.Structure):
 class RefineParamsC(C.Structure):
     _fields_ = [("n_steps", C.c_int32), ("lr_pos", C.c_float), ("lr_vel", C.c_float),
                 ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float)]
+
+
+class StackC(C.Structure):
+    _fields_ = [("psi", C.c_void_p), ("phi", C.c_void_p), ("times", C.c_void_p),
+                ("T", C.c_int32), ("H", C.c_int32), ("W", C.c_int32),
+                ("vx", C.c_void_p), ("vy", C.c_void_p), ("n_traj", C.c_int32),
+                ("params", SearchParamsC),
+                ("out_lh", C.c_void_p), ("out_flux", C.c_void_p), ("out_idx", C.c_void_p),
+                ("out_nvalid", C.c_void_p), ("out_nkept", C.c_void_p), ("out_mask", C.c_void_p)]
+
+
+class ScheduleC(C.Structure):
+    _fields_ = [("tile_order", C.c_int32), ("hot_nu2", C.c_float), ("score_span", C.c_int32),
+                ("stack_order", C.c_int32)]
 
 
 _LIB = None
@@ -97,6 +114,27 @@ def lib():
     L.kb_refine_params_default.argtypes = [C.POINTER(RefineParamsC)]
     L.kb_refine.restype = i
     L.kb_refine.argtypes = [p, p, p, i, i, i, p, p, i, C.POINTER(RefineParamsC), p, p, p, p]
+    SP, SCP = C.POINTER(StackC), C.POINTER(ScheduleC)
+    L.kb_schedule_default.restype = None
+    L.kb_schedule_default.argtypes = [SCP]
+    L.kb_batch_workspace_size.restype = i
+    L.kb_batch_workspace_size.argtypes = [SP, i, C.POINTER(sz)]
+    L.kb_batch_create.restype = i
+    L.kb_batch_create.argtypes = [SP, i, p, sz, C.POINTER(p)]
+    L.kb_batch_run.restype = i
+    L.kb_batch_run.argtypes = [p, p]
+    L.kb_batch_run_graph.restype = i
+    L.kb_batch_run_graph.argtypes = [p, p]
+    L.kb_batch_set_schedule.restype = i
+    L.kb_batch_set_schedule.argtypes = [p, SCP]
+    L.kb_batch_get_schedule.restype = i
+    L.kb_batch_get_schedule.argtypes = [p, SCP]
+    L.kb_batch_autotune.restype = i
+    L.kb_batch_autotune.argtypes = [p, p, i, SCP]
+    L.kb_batch_stats.restype = i
+    L.kb_batch_stats.argtypes = [p, p, p, p]
+    L.kb_batch_destroy.restype = None
+    L.kb_batch_destroy.argtypes = [p]
     L.kb_stamp_filter.restype = i
     L.kb_stamp_filter.argtypes = [p, i, i, p, p, p, p]
     L.kb_candidate_params.restype = i

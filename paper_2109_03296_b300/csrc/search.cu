@@ -41,10 +41,14 @@
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <climits>
+#include <cstdio>
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
+#include <vector>
 
 #include "kb_internal.cuh"
 
@@ -373,16 +377,14 @@ __global__ void bound_prep_kernel(const float* __restrict__ psi, const float* __
 // first night) gets a candidate pair from nearly every trajectory, so the few tiles around such
 // sources carry most of the full evaluations; handed out last, they leave most SMs idle at the
 // end.  The score of a tile is the number of pixels with nu2 >= tau in its footprint at each
-// epoch whose offsets span at most S_SCORE_SPAN pixels; tiles are handed out in decreasing score
+// epoch whose offsets span at most `span` pixels; tiles are handed out in decreasing score
 // (ties and unscored tiles in row-major order).  The order only schedules work: the results do
 // not depend on it.
 // ---------------------------------------------------------------------------------------------
-constexpr int S_SCORE_SPAN = 64;
-
 __global__ void __launch_bounds__(256) tile_score_kernel(
     const uint32_t* __restrict__ bound, int T, int H, int W, int Wp, const float4* vbox,
     SearchConsts cs, int x_lo, int y_lo, int x_hi, int y_hi, int ntx, int ntiles, float tau,
-    unsigned long long* __restrict__ keys) {
+    int span, unsigned long long* __restrict__ keys) {
   const int tile = blockIdx.x;
   if (tile >= ntiles) return;
   __shared__ unsigned int s_count;
@@ -395,7 +397,7 @@ __global__ void __launch_bounds__(256) tile_score_kernel(
   for (int t = 0; t < T; ++t) {
     const int oxa = track_offset(b.x, cs.dt[t]), oxb = track_offset(b.y, cs.dt[t]);
     const int oya = track_offset(b.z, cs.dt[t]), oyb = track_offset(b.w, cs.dt[t]);
-    if (oxb - oxa > S_SCORE_SPAN || oyb - oya > S_SCORE_SPAN) continue;
+    if (oxb - oxa > span || oyb - oya > span) continue;
     const int xa = max(tx0 + oxa, 0), xb = min(tx1 - 1 + oxb, W - 1);
     const int ya = max(ty0 + oya, 0), yb = min(ty1 - 1 + oyb, H - 1);
     if (xa > xb || ya > yb) continue;
@@ -727,6 +729,35 @@ struct TmapSet {
   CUtensorMap m[S_NW * S_NH];  // box (width class w, height class h) at m[(w-1)*S_NH + h]
 };
 
+// A batch of stacks searched by one launch: the tiles of stack s (in schedule order) are the
+// global tiles tile_base[s] .. tile_base[s+1]-1; the tile counter and statistics are shared.
+struct BatchArgs {
+  const SearchArgs* stacks;     // [nstacks], device memory
+  const TmapSet* maps;          // [nstacks], device memory (64-byte aligned)
+  const int* tile_base;         // [nstacks + 1]
+  int nstacks, total_tiles;
+  Ctrl* ctrl;
+  unsigned int* done_tiles;     // [nstacks] tiles finished
+  unsigned long long* done_ns;  // [nstacks] %globaltimer when the stack's last tile finished
+};
+
+// Stack of global tile g (binary search of the tile prefix).
+__device__ __forceinline__ int batch_stack_of(const BatchArgs& B, int g) {
+  int lo = 0, hi = B.nstacks - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(B.tile_base + mid) <= g) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void tmap_acquire(const void* tmap) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                   reinterpret_cast<uint64_t>(tmap))
+               : "memory");
+}
+
 struct SmemLayout {
   static constexpr size_t arena = 0;
   static constexpr size_t rec = arena + S_ARENA_BYTES;             // [S_QCAP][S_REC_WORDS]
@@ -740,7 +771,8 @@ struct SmemLayout {
   static constexpr size_t full = sinfo + S_D * sizeof(int4);       // S_D mbarriers: data landed
   static constexpr size_t empty = full + S_D * sizeof(uint64_t);   // S_D mbarriers: slot released
   static constexpr size_t misc = empty + S_D * sizeof(uint64_t);
-  static constexpr size_t total = misc + 64;
+  static constexpr size_t sargs = misc + 64;  // consumers' copy of the tile's stack arguments
+  static constexpr size_t total = sargs + (sizeof(SearchArgs) + 15) / 16 * 16;
 };
 static_assert(SmemLayout::total <= 232448, "shared memory budget");
 static_assert(SmemLayout::slots % 16 == 0 && SmemLayout::full % 8 == 0, "alignment");
@@ -797,22 +829,23 @@ struct TileRing {
 // its own TMA operations keeps the per-thread issue cost of TMA off the critical path.  The plan
 // records of the next 32 iterations are loaded by the 32 lanes at once.  The slot after the last
 // tile carries tile -1.
-__device__ void producer_loop(const TmapSet& maps, const SearchArgs& A, unsigned char* ring,
-                              int ring_base, PlanRec* slots, int4* sinfo, uint64_t* full,
-                              uint64_t* empty, unsigned int* s_abort, TileRing* tr,
-                              long long* issued_out, int pw, int lane) {
-  const int T = A.ep.T;
-  const int n_it_tile = A.nchunk * T;
+template <bool BATCH>
+__device__ void producer_loop(const TmapSet& pmaps, const SearchArgs& A0, const BatchArgs& B,
+                              unsigned char* ring, int ring_base, PlanRec* slots, int4* sinfo,
+                              uint64_t* full, uint64_t* empty, unsigned int* s_abort,
+                              TileRing* tr, long long* issued_out, int pw, int lane) {
+  Ctrl* const ctrl = BATCH ? B.ctrl : A0.ctrl;
+  const int total_tiles = BATCH ? B.total_tiles : A0.ntiles;
+  int cur_stack = -1;
   long long it_base = 0;        // global iteration number of the current tile's first iteration
   long long oldest = pw;        // oldest unretired iteration of this producer
   long long last_issued = -1;
   int head = 0, tail = 0, live = 0;  // ring: [tail, head) cyclically, `live` regions
   for (int k = 0;; ++k) {
-    int tile = 0;
+    int tile = 0;  // the global tile (counter value) first; resolved below
     if (pw == 0) {
       if (lane == 0) {
-        tile = (int)atomicAdd(&A.ctrl->tile_counter, 1u);
-        if (A.order && tile < A.ntiles) tile = __ldg(A.order + tile);
+        tile = (int)atomicAdd(&ctrl->tile_counter, 1u);
         tr->tile[k & 3] = tile;
         __threadfence_block();
         *(volatile unsigned int*)&tr->published = (unsigned int)(k + 1);
@@ -833,13 +866,34 @@ __device__ void producer_loop(const TmapSet& maps, const SearchArgs& A, unsigned
     }
     tile = __shfl_sync(0xffffffffu, tile, 0);
     if (tile == -2) {
-      if (lane == 0 && atomicExch(s_abort, 1u) == 0u) atomicOr(&A.ctrl->err, kErrTimeout);
+      if (lane == 0 && atomicExch(s_abort, 1u) == 0u) atomicOr(&ctrl->err, kErrTimeout);
       break;
     }
-    const bool last = tile >= A.ntiles;
-    const int n_it = last ? 1 : n_it_tile;
-    const int tx0 = last ? 0 : A.x_lo + (tile % A.ntx) * S_TX;
-    const int ty0 = last ? 0 : A.y_lo + (tile / A.ntx) * S_TY;
+    const bool last = tile >= total_tiles;
+    // the tile's stack, its arguments and its tile within the stack (in the stack's tile order)
+    int stack = 0;
+    const SearchArgs* Sp = &A0;
+    const TmapSet* maps = &pmaps;
+    if (BATCH && !last) {
+      stack = batch_stack_of(B, tile);
+      Sp = B.stacks + stack;
+      maps = B.maps + stack;
+      tile -= __ldg(B.tile_base + stack);
+      if (stack != cur_stack) {  // the stack's tensor maps were written before the launch
+        if (lane < S_NW * S_NH) {
+          tmap_acquire(&maps->m[lane]);
+          prefetch_tmap(&maps->m[lane]);
+        }
+        __syncwarp();
+        cur_stack = stack;
+      }
+    }
+    const PlanRec* const plan = Sp->plan;
+    const int T = last ? 1 : Sp->ep.T;
+    if (!last && Sp->order) tile = __ldg(Sp->order + tile);
+    const int n_it = last ? 1 : Sp->nchunk * T;
+    const int tx0 = last ? 0 : Sp->x_lo + (tile % Sp->ntx) * S_TX;
+    const int ty0 = last ? 0 : Sp->y_lo + (tile / Sp->ntx) * S_TY;
     // this producer's iterations of the tile: q = first_q, first_q + S_PWARPS, ...
     const int first_q = (int)(((pw - it_base) % S_PWARPS + S_PWARPS) % S_PWARPS);
     for (int qb = first_q; qb < n_it; qb += 32 * S_PWARPS) {
@@ -848,7 +902,7 @@ __device__ void producer_loop(const TmapSet& maps, const SearchArgs& A, unsigned
       for (int i = 0; i < (int)(sizeof(PlanRec) / 16); ++i) rec[i] = make_int4(0, 0, 0, 0);
       const int my_q = qb + lane * S_PWARPS;
       if (!last && my_q < n_it) {
-        const int4* src = reinterpret_cast<const int4*>(A.plan + my_q);
+        const int4* src = reinterpret_cast<const int4*>(plan + my_q);
 #pragma unroll
         for (int i = 0; i < (int)(sizeof(PlanRec) / 16); ++i) rec[i] = __ldg(src + i);
       }
@@ -887,7 +941,7 @@ __device__ void producer_loop(const TmapSet& maps, const SearchArgs& A, unsigned
           const bool ok = *(volatile unsigned int*)s_abort == 0u &&
                           mbar_wait_parity(&empty[oldest % S_D], (uint32_t)((oldest / S_D) & 1));
           if (!__all_sync(0xffffffffu, ok)) {
-            if (lane == 0 && atomicExch(s_abort, 1u) == 0u) atomicOr(&A.ctrl->err, kErrTimeout);
+            if (lane == 0 && atomicExch(s_abort, 1u) == 0u) atomicOr(&ctrl->err, kErrTimeout);
             *issued_out = last_issued;
             return;
           }
@@ -917,12 +971,12 @@ __device__ void producer_loop(const TmapSet& maps, const SearchArgs& A, unsigned
         }
         __syncwarp();
         if (lane == 0) {
-          sinfo[slot] = make_int4(ring_base + pos, last ? -1 : tile, sz, 0);
+          sinfo[slot] = make_int4(ring_base + pos, last ? -1 : tile, sz, stack);
           if (sz == 0) {
             mbar_arrive(&full[slot]);
           } else {  // word row r = image row + 1 (the pair planes carry one leading row)
             mbar_arrive_expect_tx(&full[slot], (uint32_t)sz);
-            tma_load_3d(ring + pos, &maps.m[(b.w - 1) * S_NH + b.z], &full[slot], tx0 + b.x,
+            tma_load_3d(ring + pos, &maps->m[(b.w - 1) * S_NH + b.z], &full[slot], tx0 + b.x,
                         ty0 + b.y + 1, t);
           }
         }
@@ -988,9 +1042,12 @@ __device__ __noinline__ bool insert_sorted(const SearchArgs& A, size_t wp, int K
 
 // NT > 0: thread-per-pair evaluation with an NT-wide sorting network (T <= NT <= 32);
 // NT == 0: warp-per-pair evaluation with J epochs per lane (32 < T <= 32 J).
-template <int NT, int J>
+//
+// BATCH: the tiles of several stacks (BatchArgs), each with its own T; the evaluation path is
+// chosen per tile from the stack's T (the template arguments are unused).
+template <int NT, int J, bool BATCH>
 __global__ void __launch_bounds__(S_THREADS, 1)
-search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A) {
+search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const BatchArgs B) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* arena = smem + SmemLayout::arena;
   uint32_t* recs = reinterpret_cast<uint32_t*>(smem + SmemLayout::rec);
@@ -1009,10 +1066,12 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A) {
   unsigned int* s_abort = s_qcount + 3;
   int* s_tile = reinterpret_cast<int*>(s_qcount + 4);
   TileRing* tr = reinterpret_cast<TileRing*>(s_qcount + 5);       // 20 bytes
+  int* s_stack = reinterpret_cast<int*>(s_qcount + 10);
   long long* s_issued = reinterpret_cast<long long*>(smem + SmemLayout::misc + 48);  // [2]
+  SearchArgs* s_args = reinterpret_cast<SearchArgs*>(smem + SmemLayout::sargs);
+  Ctrl* const ctrl = BATCH ? B.ctrl : A0.ctrl;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int T = A.ep.T, K = A.ep.K, mw = A.ep.mw;
 
   for (int i = tid; i < S_NPIX; i += S_THREADS) head[i] = -1;
   if (tid == 0) {
@@ -1034,29 +1093,42 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A) {
   if (warp >= S_CWARPS) {
     // ------------------------------- producer warps --------------------------------------
     const int pw = warp - S_CWARPS;
-    if (pw == 0 && lane < S_NW * S_NH) prefetch_tmap(&maps.m[lane]);
+    if (!BATCH && pw == 0 && lane < S_NW * S_NH) prefetch_tmap(&maps.m[lane]);
     long long issued = -1;
-    producer_loop(maps, A, arena + pw * S_RING_BYTES, pw * S_RING_BYTES, slots, sinfo, full,
-                  empty, s_abort, tr, &issued, pw, lane);
+    producer_loop<BATCH>(maps, A0, B, arena + pw * S_RING_BYTES, pw * S_RING_BYTES, slots, sinfo,
+                         full, empty, s_abort, tr, &issued, pw, lane);
     if (lane == 0) s_issued[pw] = issued;
   } else {
     // ------------------------------- consumer warps --------------------------------------
-    const float lh_min = A.ep.lh_min;
-    const size_t wx = (size_t)(A.x_hi - A.x_lo);
     long long it = 0;
     for (;;) {
-      // the first slot of the next tile names it (-1: none left); decided by one thread
+      // the first slot of the next tile names it (-1: none left) and its stack; decided by one
+      // thread
       consumer_sync();
       if (tid == 0) {
         const int slot0 = (int)(it % S_D);
         const bool ok = *(volatile unsigned int*)s_abort == 0u &&
                         mbar_wait_parity(&full[slot0], (uint32_t)((it / S_D) & 1));
-        if (!ok && atomicExch(s_abort, 1u) == 0u) atomicOr(&A.ctrl->err, kErrTimeout);
+        if (!ok && atomicExch(s_abort, 1u) == 0u) atomicOr(&ctrl->err, kErrTimeout);
         *s_tile = ok ? sinfo[slot0].y : -1;
+        *s_stack = ok ? sinfo[slot0].w : 0;
       }
       consumer_sync();
       const int tile = *s_tile;
       if (tile < 0) break;
+      const int stack = *s_stack;
+      if (BATCH) {  // the stack's arguments, copied once per tile
+        if (warp == 0) {
+          const uint32_t* src = reinterpret_cast<const uint32_t*>(B.stacks + stack);
+          uint32_t* dst = reinterpret_cast<uint32_t*>(s_args);
+          for (int i = lane; i < (int)(sizeof(SearchArgs) / 4); i += 32) dst[i] = __ldg(src + i);
+        }
+        consumer_sync();
+      }
+      const SearchArgs& A = BATCH ? *s_args : A0;
+      const int T = A.ep.T, K = A.ep.K, mw = A.ep.mw;
+      const float lh_min = A.ep.lh_min;
+      const size_t wx = (size_t)(A.x_hi - A.x_lo);
       const int tx0 = A.x_lo + (tile % A.ntx) * S_TX;
       const int ty0 = A.y_lo + (tile / A.ntx) * S_TY;
       const int px = tx0 + lane;
@@ -1088,16 +1160,29 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A) {
       // consumer barrier.
       auto flush = [&]() {
         const int nq = min((int)*s_qcount, S_QCAP);
-        if (NT > 0) {
+        auto by_thread = [&](auto nt) {
           for (int e = tid; e < nq; e += S_CTHREADS)
-            eval_pair_thread<(NT > 0 ? NT : 1)>(A.psi, A.phi, A.ep, tx0 + (q_pix[e] & 31),
+            eval_pair_thread<decltype(nt)::value>(A.psi, A.phi, A.ep, tx0 + (q_pix[e] & 31),
+                                                  ty0 + (q_pix[e] >> 5),
+                                                  A.offs + (size_t)q_traj[e] * T,
+                                                  recs + e * S_REC_WORDS);
+        };
+        auto by_warp = [&](auto jj) {
+          for (int e = warp; e < nq; e += S_CWARPS)
+            eval_pair_warp<decltype(jj)::value>(A.psi, A.phi, A.ep, tx0 + (q_pix[e] & 31),
                                                 ty0 + (q_pix[e] >> 5),
                                                 A.offs + (size_t)q_traj[e] * T,
-                                                recs + e * S_REC_WORDS);
+                                                recs + e * S_REC_WORDS, lane);
+        };
+        if (BATCH) {
+          if (T <= 16) by_thread(std::integral_constant<int, 16>{});
+          else if (T <= 32) by_thread(std::integral_constant<int, 32>{});
+          else if (T <= 64) by_warp(std::integral_constant<int, 2>{});
+          else by_warp(std::integral_constant<int, 4>{});
+        } else if (NT > 0) {
+          by_thread(std::integral_constant<int, (NT > 0 ? NT : 1)>{});
         } else {
-          for (int e = warp; e < nq; e += S_CWARPS)
-            eval_pair_warp<J>(A.psi, A.phi, A.ep, tx0 + (q_pix[e] & 31), ty0 + (q_pix[e] >> 5),
-                              A.offs + (size_t)q_traj[e] * T, recs + e * S_REC_WORDS, lane);
+          by_warp(std::integral_constant<int, J>{});
         }
         consumer_sync();
 #pragma unroll 1
@@ -1175,7 +1260,7 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A) {
               }
             }
           } else if (lane == 0 && atomicExch(s_abort, 1u) == 0u) {
-            atomicOr(&A.ctrl->err, kErrTimeout);
+            atomicOr(&ctrl->err, kErrTimeout);
           }
           __syncwarp();  // every lane's reads of the slot come before the warp's release
           if (lane == 0) mbar_arrive(&empty[slot]);
@@ -1254,13 +1339,18 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A) {
       }
       consumer_sync();
       if (*(volatile unsigned int*)s_qcount > 0u) flush();
+      if (BATCH && tid == 0) {  // completion time of the stack whose last tile this was
+        __threadfence();
+        if (atomicAdd(B.done_tiles + stack, 1u) + 1u == (unsigned int)A.ntiles)
+          B.done_ns[stack] = globaltimer_ns();
+      }
     }
   }
 
   __syncthreads();
   if (tid == 0) {
-    atomicAdd(&A.ctrl->evals, (unsigned long long)*s_evals);
-    atomicAdd(&A.ctrl->inserts, (unsigned long long)*s_ins);
+    atomicAdd(&ctrl->evals, (unsigned long long)*s_evals);
+    atomicAdd(&ctrl->inserts, (unsigned long long)*s_ins);
   }
   if (warp >= S_CWARPS && lane == 0 && *(volatile unsigned int*)s_abort != 0u) {
     // a wait gave up: wait (bounded) for this producer's last copies
@@ -1353,119 +1443,87 @@ extern "C" int kb_search_workspace_size(int T, int H, int W, int n_traj,
   return KB_OK;
 }
 
-extern "C" int kb_search(const float* psi, const float* phi, const double* times, int T, int H,
-                         int W, const float* vx, const float* vy, int n_traj,
+namespace kb {
+
+// Everything kb_search needs to know about one stack: its arguments for the search kernel, its
+// tensor maps, and the inputs of its preparation kernels.
+struct StackPrep {
+  SearchArgs A;
+  TmapSet maps;
+  SearchConsts cs;
+  WsLayout L;
+  const float *psi, *phi, *vx, *vy;
+  int T, H, W, n_traj;
+  int x_lo, x_hi, y_lo, y_hi;
+  char* ws;
+  unsigned long long te;
+};
+
+// Validates one stack, lays out its workspace, encodes its tensor maps and fills its kernel
+// arguments (no launch).  ctrl: the control block the search kernel will use.
+static int prepare_stack(const char* who, const float* psi, const float* phi, const double* times,
+                         int T, int H, int W, const float* vx, const float* vy, int n_traj,
                          const kb_search_params* p, float* out_lh, float* out_flux,
                          int32_t* out_idx, uint16_t* out_nvalid, uint16_t* out_nkept,
-                         uint32_t* out_mask, void* workspace, size_t ws_bytes, void* stream) {
-  using namespace kb;
+                         uint32_t* out_mask, char* ws, size_t ws_bytes, StackPrep& sp) {
   int rc = validate(psi, phi, times, T, H, W, vx, vy, n_traj, p);
   if (rc != KB_OK) return rc;
   if (!out_lh || !out_flux || !out_idx || !out_nvalid || !out_nkept || !out_mask)
-    return fail(KB_ERR_INVALID_ARG, "kb_search: null output pointer");
+    return fail(KB_ERR_INVALID_ARG, "%s: null output pointer", who);
   const WsLayout L = ws_layout(T, H, W, n_traj);
-  if (!workspace || ws_bytes < L.total)
-    return fail(KB_ERR_WORKSPACE, "kb_search: workspace of %zu bytes, %zu needed", ws_bytes, L.total);
-  if (reinterpret_cast<uintptr_t>(workspace) % KB_WORKSPACE_ALIGN)
-    return fail(KB_ERR_WORKSPACE, "kb_search: workspace not %d-byte aligned", KB_WORKSPACE_ALIGN);
+  if (!ws || ws_bytes < L.total)
+    return fail(KB_ERR_WORKSPACE, "%s: workspace of %zu bytes, %zu needed", who, ws_bytes, L.total);
+  if (reinterpret_cast<uintptr_t>(ws) % KB_WORKSPACE_ALIGN)
+    return fail(KB_ERR_WORKSPACE, "%s: workspace not %d-byte aligned", who, KB_WORKSPACE_ALIGN);
   auto enc = get_encode_fn();
-  if (!enc) return fail(KB_ERR_CUDA, "kb_search: cuTensorMapEncodeTiled unavailable");
-  if (g_num_sms == 0) {
-    int dev = 0;
-    KB_CUDA_TRY(cudaGetDevice(&dev));
-    KB_CUDA_TRY(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
-  }
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  char* ws = static_cast<char*>(workspace);
-  Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws + L.ctrl);
-  float4* vbox = reinterpret_cast<float4*>(ws + L.vbox);
-  uint32_t* keys = reinterpret_cast<uint32_t*>(ws + L.keys);
-  uint32_t* counts = reinterpret_cast<uint32_t*>(ws + L.counts);
-  uint32_t* cursor = reinterpret_cast<uint32_t*>(ws + L.cursor);
-  int32_t* sorted = reinterpret_cast<int32_t*>(ws + L.sorted);
-  int32_t* orig = reinterpret_cast<int32_t*>(ws + L.orig);
-  int2* offs = reinterpret_cast<int2*>(ws + L.offs);
-  PlanRec* plan = reinterpret_cast<PlanRec*>(ws + L.plan);
+  if (!enc) return fail(KB_ERR_CUDA, "%s: cuTensorMapEncodeTiled unavailable", who);
+  sp.L = L;
+  sp.ws = ws;
+  sp.psi = psi;
+  sp.phi = phi;
+  sp.vx = vx;
+  sp.vy = vy;
+  sp.T = T;
+  sp.H = H;
+  sp.W = W;
+  sp.n_traj = n_traj;
+  sp.x_lo = p->x_lo;
+  sp.x_hi = p->x_hi;
+  sp.y_lo = p->y_lo;
+  sp.y_hi = p->y_hi;
+  sp.cs = SearchConsts{};
+  for (int t = 0; t < T; ++t) sp.cs.dt[t] = (float)(times[t] - times[0]);
+  sp.te = (unsigned long long)(p->x_hi - p->x_lo) * (p->y_hi - p->y_lo) * n_traj * T;
   uint32_t* bound = reinterpret_cast<uint32_t*>(ws + L.bound);
-
-  SearchConsts cs{};
-  for (int t = 0; t < T; ++t) cs.dt[t] = (float)(times[t] - times[0]);
-
-  const int npix_w = (p->x_hi - p->x_lo) * (p->y_hi - p->y_lo);
-  const unsigned long long te = (unsigned long long)npix_w * n_traj * T;
-
-  plan_reset_kernel<<<N_CELLS / 256, 256, 0, st>>>(ctrl, counts, te);
-  KB_LAUNCH_CHECK("plan_reset_kernel");
-  plan_minmax_kernel<<<1, 1024, 0, st>>>(vx, vy, n_traj, vbox);
-  KB_LAUNCH_CHECK("plan_minmax_kernel");
-  plan_hist_kernel<<<(n_traj + 255) / 256, 256, 0, st>>>(vx, vy, n_traj, vbox, keys, counts);
-  KB_LAUNCH_CHECK("plan_hist_kernel");
-  plan_scan_kernel<<<1, 1024, 0, st>>>(counts, cursor);
-  KB_LAUNCH_CHECK("plan_scan_kernel");
-  plan_scatter_kernel<<<(n_traj + 255) / 256, 256, 0, st>>>(keys, n_traj, cursor, sorted);
-  KB_LAUNCH_CHECK("plan_scatter_kernel");
-  plan_cellsort_kernel<<<N_CELLS / 256, 256, 0, st>>>(counts, cursor, sorted);
-  KB_LAUNCH_CHECK("plan_cellsort_kernel");
-  plan_offsets_kernel<<<(L.n_pad + 255) / 256, 256, 0, st>>>(vx, vy, sorted, n_traj, L.n_pad, T,
-                                                               cs, orig, offs);
-  KB_LAUNCH_CHECK("plan_offsets_kernel");
-  plan_boxes_kernel<<<(L.nchunk * T + 255) / 256, 256, 0, st>>>(offs, L.nchunk, T, p->x_lo, plan);
-  KB_LAUNCH_CHECK("plan_boxes_kernel");
-  {
-    size_t total = (size_t)T * (H + 1) * L.Wp;
-    int blocks = (int)std::min<size_t>((total + 255) / 256, (size_t)g_num_sms * 16);
-    bound_prep_kernel<<<blocks, 256, 0, st>>>(psi, phi, T, H, W, L.Wp, bound);
-    KB_LAUNCH_CHECK("bound_prep_kernel");
-  }
-
-  const int ntx = (p->x_hi - p->x_lo + S_TX - 1) / S_TX;
-  const int ntiles = ntx * ((p->y_hi - p->y_lo + S_TY - 1) / S_TY);
-  int32_t* torder = nullptr;
-  if (ntiles > 1 && ntiles <= S_ORDER_MAX) {
-    unsigned long long* tkeys = reinterpret_cast<unsigned long long*>(ws + L.tkeys);
-    torder = reinterpret_cast<int32_t*>(ws + L.torder);
-    tile_score_kernel<<<ntiles, 256, 0, st>>>(bound, T, H, W, L.Wp, vbox, cs, p->x_lo, p->y_lo,
-                                              p->x_hi, p->y_hi, ntx, ntiles, 16.0f, tkeys);
-    KB_LAUNCH_CHECK("tile_score_kernel");
-    int n2 = 1;
-    while (n2 < ntiles) n2 <<= 1;
-    const size_t osm = sizeof(unsigned long long) * (size_t)n2;
-    KB_CUDA_TRY(cudaFuncSetAttribute(tile_order_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)osm));
-    tile_order_kernel<<<1, 1024, osm, st>>>(tkeys, ntiles, torder);
-    KB_LAUNCH_CHECK("tile_order_kernel");
-  }
-
-  TmapSet maps;
   for (int w = 1; w <= S_NW; ++w)
     for (int h = 0; h < S_NH; ++h) {
       cuuint64_t dims[3] = {(cuuint64_t)L.Wp, (cuuint64_t)H + 1, (cuuint64_t)T};
       cuuint64_t strides[2] = {(cuuint64_t)L.Wp * 4, (cuuint64_t)L.Wp * (H + 1) * 4};
       cuuint32_t boxd[3] = {(cuuint32_t)stage_width(w), (cuuint32_t)stage_height(h), 1u};
       cuuint32_t estr[3] = {1u, 1u, 1u};
-      CUresult r = enc(&maps.m[(w - 1) * S_NH + h], CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, bound,
+      CUresult r = enc(&sp.maps.m[(w - 1) * S_NH + h], CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, bound,
                        dims, strides, boxd, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
       if (r != CUDA_SUCCESS)
-        return fail(KB_ERR_CUDA, "kb_search: cuTensorMapEncodeTiled failed (%d)", (int)r);
+        return fail(KB_ERR_CUDA, "%s: cuTensorMapEncodeTiled failed (%d)", who, (int)r);
     }
-
-  SearchArgs A{};
+  SearchArgs& A = sp.A;
+  A = SearchArgs{};
   A.psi = psi;
   A.phi = phi;
   A.bound = bound;
-  A.orig = orig;
-  A.offs = offs;
-  A.plan = plan;
+  A.orig = reinterpret_cast<int32_t*>(ws + L.orig);
+  A.offs = reinterpret_cast<int2*>(ws + L.offs);
+  A.plan = reinterpret_cast<PlanRec*>(ws + L.plan);
   A.out_lh = out_lh;
   A.out_flux = out_flux;
   A.out_idx = out_idx;
   A.out_nvalid = out_nvalid;
   A.out_nkept = out_nkept;
   A.out_mask = out_mask;
-  A.ctrl = ctrl;
-  A.order = torder;
+  A.ctrl = reinterpret_cast<Ctrl*>(ws + L.ctrl);
+  A.order = nullptr;
   A.ep.T = T;
   A.ep.H = H;
   A.ep.W = W;
@@ -1494,13 +1552,118 @@ extern "C" int kb_search(const float* psi, const float* phi, const double* times
   A.ntx = (p->x_hi - p->x_lo + S_TX - 1) / S_TX;
   A.nty = (p->y_hi - p->y_lo + S_TY - 1) / S_TY;
   A.ntiles = A.ntx * A.nty;
+  return KB_OK;
+}
+
+// Enqueues a stack's preparation: velocity ordering, track offsets, staging plan, bound planes
+// and (when sch.tile_order and the stack has at most S_ORDER_MAX tiles) its tile order.  Sets
+// sp.A.order accordingly.
+static int launch_prep(StackPrep& sp, const kb_schedule& sch, cudaStream_t st) {
+  const WsLayout& L = sp.L;
+  char* ws = sp.ws;
+  const int T = sp.T, H = sp.H, W = sp.W, n_traj = sp.n_traj;
+  Ctrl* ctrl = reinterpret_cast<Ctrl*>(ws + L.ctrl);
+  float4* vbox = reinterpret_cast<float4*>(ws + L.vbox);
+  uint32_t* keys = reinterpret_cast<uint32_t*>(ws + L.keys);
+  uint32_t* counts = reinterpret_cast<uint32_t*>(ws + L.counts);
+  uint32_t* cursor = reinterpret_cast<uint32_t*>(ws + L.cursor);
+  int32_t* sorted = reinterpret_cast<int32_t*>(ws + L.sorted);
+  int32_t* orig = reinterpret_cast<int32_t*>(ws + L.orig);
+  int2* offs = reinterpret_cast<int2*>(ws + L.offs);
+  PlanRec* plan = reinterpret_cast<PlanRec*>(ws + L.plan);
+  uint32_t* bound = reinterpret_cast<uint32_t*>(ws + L.bound);
+  if (g_num_sms == 0) {
+    int dev = 0;
+    KB_CUDA_TRY(cudaGetDevice(&dev));
+    KB_CUDA_TRY(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  plan_reset_kernel<<<N_CELLS / 256, 256, 0, st>>>(ctrl, counts, sp.te);
+  KB_LAUNCH_CHECK("plan_reset_kernel");
+  plan_minmax_kernel<<<1, 1024, 0, st>>>(sp.vx, sp.vy, n_traj, vbox);
+  KB_LAUNCH_CHECK("plan_minmax_kernel");
+  plan_hist_kernel<<<(n_traj + 255) / 256, 256, 0, st>>>(sp.vx, sp.vy, n_traj, vbox, keys, counts);
+  KB_LAUNCH_CHECK("plan_hist_kernel");
+  plan_scan_kernel<<<1, 1024, 0, st>>>(counts, cursor);
+  KB_LAUNCH_CHECK("plan_scan_kernel");
+  plan_scatter_kernel<<<(n_traj + 255) / 256, 256, 0, st>>>(keys, n_traj, cursor, sorted);
+  KB_LAUNCH_CHECK("plan_scatter_kernel");
+  plan_cellsort_kernel<<<N_CELLS / 256, 256, 0, st>>>(counts, cursor, sorted);
+  KB_LAUNCH_CHECK("plan_cellsort_kernel");
+  plan_offsets_kernel<<<(L.n_pad + 255) / 256, 256, 0, st>>>(sp.vx, sp.vy, sorted, n_traj, L.n_pad,
+                                                               T, sp.cs, orig, offs);
+  KB_LAUNCH_CHECK("plan_offsets_kernel");
+  plan_boxes_kernel<<<(L.nchunk * T + 255) / 256, 256, 0, st>>>(offs, L.nchunk, T, sp.x_lo, plan);
+  KB_LAUNCH_CHECK("plan_boxes_kernel");
+  {
+    size_t total = (size_t)T * (H + 1) * L.Wp;
+    int blocks = (int)std::min<size_t>((total + 255) / 256, (size_t)g_num_sms * 16);
+    bound_prep_kernel<<<blocks, 256, 0, st>>>(sp.psi, sp.phi, T, H, W, L.Wp, bound);
+    KB_LAUNCH_CHECK("bound_prep_kernel");
+  }
+  const int ntiles = sp.A.ntiles;
+  sp.A.order = nullptr;
+  if (sch.tile_order && ntiles > 1 && ntiles <= S_ORDER_MAX) {
+    unsigned long long* tkeys = reinterpret_cast<unsigned long long*>(ws + L.tkeys);
+    int32_t* torder = reinterpret_cast<int32_t*>(ws + L.torder);
+    tile_score_kernel<<<ntiles, 256, 0, st>>>(bound, T, H, W, L.Wp, vbox, sp.cs, sp.x_lo, sp.y_lo,
+                                              sp.x_hi, sp.y_hi, sp.A.ntx, ntiles, sch.hot_nu2,
+                                              sch.score_span, tkeys);
+    KB_LAUNCH_CHECK("tile_score_kernel");
+    int n2 = 1;
+    while (n2 < ntiles) n2 <<= 1;
+    const size_t osm = sizeof(unsigned long long) * (size_t)n2;
+    KB_CUDA_TRY(cudaFuncSetAttribute(tile_order_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)osm));
+    tile_order_kernel<<<1, 1024, osm, st>>>(tkeys, ntiles, torder);
+    KB_LAUNCH_CHECK("tile_order_kernel");
+    sp.A.order = torder;
+  }
+  return KB_OK;
+}
+
+static const kb_schedule kDefaultSchedule = {1, 16.0f, 64, 1};
+
+static int check_schedule(const kb_schedule* s) {
+  if (!s) return fail(KB_ERR_INVALID_ARG, "schedule: null pointer");
+  if (s->tile_order != 0 && s->tile_order != 1)
+    return fail(KB_ERR_INVALID_ARG, "schedule: tile_order must be 0 or 1");
+  if (s->stack_order != 0 && s->stack_order != 1)
+    return fail(KB_ERR_INVALID_ARG, "schedule: stack_order must be 0 or 1");
+  if (!(s->hot_nu2 > 0.0f) || !std::isfinite(s->hot_nu2))
+    return fail(KB_ERR_INVALID_ARG, "schedule: hot_nu2 must be finite and > 0");
+  if (s->score_span < 0 || s->score_span > (1 << 20))
+    return fail(KB_ERR_INVALID_ARG, "schedule: score_span outside 0..2^20");
+  return KB_OK;
+}
+
+}  // namespace kb
+
+extern "C" void kb_schedule_default(kb_schedule* s) {
+  if (s) *s = kb::kDefaultSchedule;
+}
+
+extern "C" int kb_search(const float* psi, const float* phi, const double* times, int T, int H,
+                         int W, const float* vx, const float* vy, int n_traj,
+                         const kb_search_params* p, float* out_lh, float* out_flux,
+                         int32_t* out_idx, uint16_t* out_nvalid, uint16_t* out_nkept,
+                         uint32_t* out_mask, void* workspace, size_t ws_bytes, void* stream) {
+  using namespace kb;
+  StackPrep sp;
+  int rc = prepare_stack("kb_search", psi, phi, times, T, H, W, vx, vy, n_traj, p, out_lh,
+                         out_flux, out_idx, out_nvalid, out_nkept, out_mask,
+                         static_cast<char*>(workspace), ws_bytes, sp);
+  if (rc != KB_OK) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  rc = launch_prep(sp, kDefaultSchedule, st);
+  if (rc != KB_OK) return rc;
+  const SearchArgs& A = sp.A;
   const int grid = std::min(A.ntiles, g_num_sms);
   const size_t smem = SmemLayout::total;
 #define KB_SEARCH_LAUNCH(NT, JJ)                                                               \
   do {                                                                                         \
-    KB_CUDA_TRY(cudaFuncSetAttribute(search_kernel<NT, JJ>,                                    \
+    KB_CUDA_TRY(cudaFuncSetAttribute(search_kernel<NT, JJ, false>,                             \
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-    search_kernel<NT, JJ><<<grid, S_THREADS, smem, st>>>(maps, A);                             \
+    search_kernel<NT, JJ, false><<<grid, S_THREADS, smem, st>>>(sp.maps, A, BatchArgs{});      \
   } while (0)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   profile_events(&ev0, &ev1);
@@ -1513,6 +1676,387 @@ extern "C" int kb_search(const float* psi, const float* phi, const double* times
   KB_LAUNCH_CHECK("search_kernel");
   if (ev0 && ev1) KB_CUDA_TRY(cudaEventRecord(ev1, st));
   return KB_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Batched search: many stacks, one persistent launch
+// ---------------------------------------------------------------------------------------------
+namespace kb {
+
+__global__ void batch_reset_kernel(Ctrl* ctrl, unsigned int* done_tiles,
+                                   unsigned long long* done_ns, unsigned long long* start_ns,
+                                   int n, unsigned long long te) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    done_tiles[i] = 0u;
+    done_ns[i] = 0ull;
+  }
+  if (i == 0) {
+    ctrl->err = 0u;
+    ctrl->tile_counter = 0u;
+    ctrl->te = te;
+    ctrl->evals = 0ull;
+    ctrl->inserts = 0ull;
+    *start_ns = globaltimer_ns();
+  }
+}
+
+struct BatchTables {
+  size_t args, maps, tile_base, done_tiles, done_ns, start_ns, ctrl, total;
+};
+
+static BatchTables batch_tables(int n) {
+  BatchTables b{};
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = align_up(o + bytes, KB_WORKSPACE_ALIGN);
+    return at;
+  };
+  b.args = take(sizeof(SearchArgs) * (size_t)n);
+  b.maps = take(sizeof(TmapSet) * (size_t)n);
+  b.tile_base = take(sizeof(int) * (size_t)(n + 1));
+  b.done_tiles = take(sizeof(unsigned int) * (size_t)n);
+  b.done_ns = take(sizeof(unsigned long long) * (size_t)n);
+  b.start_ns = take(sizeof(unsigned long long));
+  b.ctrl = take(256);
+  b.total = o;
+  return b;
+}
+
+}  // namespace kb
+
+struct kb_batch {
+  int n = 0;
+  std::vector<kb::StackPrep> sp;   // in the caller's order
+  std::vector<int> order;          // schedule position -> caller's index
+  kb_schedule sch{};
+  char* ws = nullptr;
+  kb::BatchTables tb{};
+  int total_tiles = 0;
+  unsigned long long te_total = 0;
+  int device = 0;
+  cudaStream_t gstream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  unsigned int graph_kernels = 0;
+};
+
+namespace kb {
+
+static size_t stack_ws_bytes(const kb_stack& s) {
+  return ws_layout(s.T, s.H, s.W, s.n_traj).total;
+}
+
+static void drop_graph(kb_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+}
+
+// Writes the schedule-ordered tables (stack arguments, tensor maps, tile prefix) to the device.
+// The tile orders themselves are computed on the device by each run.
+static int write_tables(kb_batch* b) {
+  const int n = b->n;
+  std::vector<int> idx(n);
+  for (int i = 0; i < n; ++i) idx[i] = i;
+  if (b->sch.stack_order == 1)  // predicted cost (trajectory-epochs), largest first
+    std::stable_sort(idx.begin(), idx.end(),
+                     [&](int a, int c) { return b->sp[a].te > b->sp[c].te; });
+  b->order = idx;
+  std::vector<SearchArgs> args(n);
+  std::vector<TmapSet> maps(n);
+  std::vector<int> base(n + 1, 0);
+  Ctrl* ctrl = reinterpret_cast<Ctrl*>(b->ws + b->tb.ctrl);
+  for (int k = 0; k < n; ++k) {
+    StackPrep& sp = b->sp[idx[k]];
+    args[k] = sp.A;
+    args[k].ctrl = ctrl;
+    // the tile order lives in the stack's own workspace; used when it was computed
+    const bool ordered = b->sch.tile_order && sp.A.ntiles > 1 && sp.A.ntiles <= S_ORDER_MAX;
+    args[k].order = ordered ? reinterpret_cast<int32_t*>(sp.ws + sp.L.torder) : nullptr;
+    maps[k] = sp.maps;
+    base[k + 1] = base[k] + sp.A.ntiles;
+  }
+  b->total_tiles = base[n];
+  KB_CUDA_TRY(cudaMemcpy(b->ws + b->tb.args, args.data(), sizeof(SearchArgs) * n,
+                         cudaMemcpyHostToDevice));
+  KB_CUDA_TRY(cudaMemcpy(b->ws + b->tb.maps, maps.data(), sizeof(TmapSet) * n,
+                         cudaMemcpyHostToDevice));
+  KB_CUDA_TRY(cudaMemcpy(b->ws + b->tb.tile_base, base.data(), sizeof(int) * (n + 1),
+                         cudaMemcpyHostToDevice));
+  return KB_OK;
+}
+
+static int batch_enqueue(kb_batch* b, cudaStream_t st) {
+  const int n = b->n;
+  Ctrl* ctrl = reinterpret_cast<Ctrl*>(b->ws + b->tb.ctrl);
+  unsigned int* done_tiles = reinterpret_cast<unsigned int*>(b->ws + b->tb.done_tiles);
+  unsigned long long* done_ns = reinterpret_cast<unsigned long long*>(b->ws + b->tb.done_ns);
+  unsigned long long* start_ns = reinterpret_cast<unsigned long long*>(b->ws + b->tb.start_ns);
+  batch_reset_kernel<<<(n + 255) / 256, 256, 0, st>>>(ctrl, done_tiles, done_ns, start_ns, n,
+                                                      b->te_total);
+  KB_LAUNCH_CHECK("batch_reset_kernel");
+  for (int k = 0; k < n; ++k) {
+    int rc = launch_prep(b->sp[b->order[k]], b->sch, st);
+    if (rc != KB_OK) return rc;
+  }
+  BatchArgs B{};
+  B.stacks = reinterpret_cast<const SearchArgs*>(b->ws + b->tb.args);
+  B.maps = reinterpret_cast<const TmapSet*>(b->ws + b->tb.maps);
+  B.tile_base = reinterpret_cast<const int*>(b->ws + b->tb.tile_base);
+  B.nstacks = n;
+  B.total_tiles = b->total_tiles;
+  B.ctrl = ctrl;
+  B.done_tiles = done_tiles;
+  B.done_ns = done_ns;
+  const size_t smem = SmemLayout::total;
+  KB_CUDA_TRY(cudaFuncSetAttribute(search_kernel<0, 1, true>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int grid = std::min(b->total_tiles, g_num_sms);
+  static const TmapSet kNoMaps{};
+  search_kernel<0, 1, true><<<grid, S_THREADS, smem, st>>>(kNoMaps, SearchArgs{}, B);
+  KB_LAUNCH_CHECK("search_kernel (batch)");
+  return KB_OK;
+}
+
+}  // namespace kb
+
+extern "C" int kb_batch_workspace_size(const kb_stack* stacks, int n, size_t* bytes) {
+  using namespace kb;
+  if (!stacks || !bytes || n < 1) return fail(KB_ERR_INVALID_ARG, "kb_batch_workspace_size: bad arguments");
+  size_t total = batch_tables(n).total;
+  for (int i = 0; i < n; ++i) {
+    const kb_stack& s = stacks[i];
+    if (s.T < 1 || s.H < 1 || s.W < 1 || s.n_traj < 1)
+      return fail(KB_ERR_INVALID_ARG, "kb_batch_workspace_size: stack %d has bad sizes", i);
+    if (s.T > KB_MAX_T) return fail(KB_ERR_UNSUPPORTED, "kb_batch_workspace_size: stack %d: T > KB_MAX_T", i);
+    if (s.n_traj > (1 << 24))
+      return fail(KB_ERR_UNSUPPORTED, "kb_batch_workspace_size: stack %d: n_traj > 2^24", i);
+    total = align_up(total + stack_ws_bytes(s), KB_WORKSPACE_ALIGN);
+  }
+  *bytes = total;
+  return KB_OK;
+}
+
+extern "C" int kb_batch_create(const kb_stack* stacks, int n, void* workspace, size_t ws_bytes,
+                               kb_batch** out) {
+  using namespace kb;
+  if (!out) return fail(KB_ERR_INVALID_ARG, "kb_batch_create: null output handle");
+  *out = nullptr;
+  size_t need = 0;
+  int rc = kb_batch_workspace_size(stacks, n, &need);
+  if (rc != KB_OK) return rc;
+  if (!workspace || ws_bytes < need)
+    return fail(KB_ERR_WORKSPACE, "kb_batch_create: workspace of %zu bytes, %zu needed", ws_bytes, need);
+  if (reinterpret_cast<uintptr_t>(workspace) % KB_WORKSPACE_ALIGN)
+    return fail(KB_ERR_WORKSPACE, "kb_batch_create: workspace not %d-byte aligned", KB_WORKSPACE_ALIGN);
+  kb_batch* b = new kb_batch();
+  b->n = n;
+  b->sp.resize(n);
+  b->sch = kDefaultSchedule;
+  b->ws = static_cast<char*>(workspace);
+  b->tb = batch_tables(n);
+  size_t off = b->tb.total;
+  for (int i = 0; i < n; ++i) {
+    const kb_stack& s = stacks[i];
+    const size_t sz = stack_ws_bytes(s);
+    char who[48];
+    snprintf(who, sizeof(who), "kb_batch_create (stack %d)", i);
+    rc = prepare_stack(who, s.psi, s.phi, s.times, s.T, s.H, s.W, s.vx, s.vy, s.n_traj,
+                       &s.params, s.out_lh, s.out_flux, s.out_idx, s.out_nvalid, s.out_nkept,
+                       s.out_mask, b->ws + off, sz, b->sp[i]);
+    if (rc != KB_OK) {
+      delete b;
+      char msg[256];
+      snprintf(msg, sizeof(msg), "%s", kb_last_error());
+      return fail(rc, "kb_batch_create: stack %d: %s", i, msg);
+    }
+    b->te_total += b->sp[i].te;
+    off = align_up(off + sz, KB_WORKSPACE_ALIGN);
+  }
+  cudaError_t e = cudaGetDevice(&b->device);
+  if (e == cudaSuccess && g_num_sms == 0)
+    e = cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, b->device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->gstream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    kb_batch_destroy(b);
+    return fail(KB_ERR_CUDA, "kb_batch_create: %s", cudaGetErrorString(e));
+  }
+  rc = write_tables(b);
+  if (rc != KB_OK) {
+    kb_batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return KB_OK;
+}
+
+extern "C" int kb_batch_run(kb_batch* b, void* stream) {
+  using namespace kb;
+  if (!b) return fail(KB_ERR_INVALID_ARG, "kb_batch_run: null batch");
+  return batch_enqueue(b, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int kb_batch_run_graph(kb_batch* b, void* stream) {
+  using namespace kb;
+  if (!b) return fail(KB_ERR_INVALID_ARG, "kb_batch_run_graph: null batch");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!b->exec) {
+    const unsigned long long before = kb_launch_count();
+    KB_CUDA_TRY(cudaStreamBeginCapture(b->gstream, cudaStreamCaptureModeThreadLocal));
+    int rc = batch_enqueue(b, b->gstream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->gstream, &g);
+    if (rc != KB_OK) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e != cudaSuccess) return fail(KB_ERR_CUDA, "kb_batch_run_graph: capture failed: %s", cudaGetErrorString(e));
+    b->graph = g;
+    e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e != cudaSuccess) {
+      drop_graph(b);
+      return fail(KB_ERR_CUDA, "kb_batch_run_graph: instantiation failed: %s", cudaGetErrorString(e));
+    }
+    // the capture counted the graph's kernels once; each replay launches them again
+    b->graph_kernels = (unsigned int)(kb_launch_count() - before);
+  }
+  KB_CUDA_TRY(cudaEventRecord(b->ev_in, st));
+  KB_CUDA_TRY(cudaStreamWaitEvent(b->gstream, b->ev_in, 0));
+  KB_CUDA_TRY(cudaGraphLaunch(b->exec, b->gstream));
+  KB_CUDA_TRY(cudaEventRecord(b->ev_out, b->gstream));
+  KB_CUDA_TRY(cudaStreamWaitEvent(st, b->ev_out, 0));
+  count_launch(b->graph_kernels);
+  return KB_OK;
+}
+
+extern "C" int kb_batch_get_schedule(const kb_batch* b, kb_schedule* s) {
+  using namespace kb;
+  if (!b || !s) return fail(KB_ERR_INVALID_ARG, "kb_batch_get_schedule: null pointer");
+  *s = b->sch;
+  return KB_OK;
+}
+
+extern "C" int kb_batch_set_schedule(kb_batch* b, const kb_schedule* s) {
+  using namespace kb;
+  if (!b) return fail(KB_ERR_INVALID_ARG, "kb_batch_set_schedule: null batch");
+  int rc = check_schedule(s);
+  if (rc != KB_OK) return rc;
+  // the tables may be in use by work already enqueued
+  KB_CUDA_TRY(cudaDeviceSynchronize());
+  b->sch = *s;
+  drop_graph(b);
+  return write_tables(b);
+}
+
+extern "C" int kb_batch_autotune(kb_batch* b, void* stream, int reps, kb_schedule* best) {
+  using namespace kb;
+  if (!b) return fail(KB_ERR_INVALID_ARG, "kb_batch_autotune: null batch");
+  if (reps < 1 || reps > 100) return fail(KB_ERR_INVALID_ARG, "kb_batch_autotune: reps outside 1..100");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  KB_CUDA_TRY(cudaEventCreate(&e0));
+  KB_CUDA_TRY(cudaEventCreate(&e1));
+  auto time_of = [&](const kb_schedule& s, float* ms) -> int {
+    int rc = kb_batch_set_schedule(b, &s);
+    if (rc != KB_OK) return rc;
+    float bestt = 1e30f;
+    for (int r = 0; r < reps; ++r) {
+      KB_CUDA_TRY(cudaEventRecord(e0, st));
+      rc = batch_enqueue(b, st);
+      if (rc != KB_OK) return rc;
+      KB_CUDA_TRY(cudaEventRecord(e1, st));
+      KB_CUDA_TRY(cudaEventSynchronize(e1));
+      float t = 0.0f;
+      KB_CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+      bestt = std::min(bestt, t);
+    }
+    *ms = bestt;
+    return KB_OK;
+  };
+  // coordinate descent over the scheduling knobs, starting from the defaults
+  kb_schedule cur = kDefaultSchedule;
+  float cur_ms = 0.0f;
+  int rc = time_of(cur, &cur_ms);
+  const float hot[] = {16.0f, 9.0f, 36.0f};
+  const int span[] = {64, 32, 128};
+  for (int pass = 0; rc == KB_OK && pass < 4; ++pass) {
+    std::vector<kb_schedule> cand;
+    if (pass == 0) {
+      kb_schedule c = cur;
+      c.stack_order = 1 - cur.stack_order;
+      cand.push_back(c);
+    } else if (pass == 1) {
+      kb_schedule c = cur;
+      c.tile_order = 1 - cur.tile_order;
+      cand.push_back(c);
+    } else if (pass == 2 && cur.tile_order) {
+      for (float h : hot)
+        if (h != cur.hot_nu2) {
+          kb_schedule c = cur;
+          c.hot_nu2 = h;
+          cand.push_back(c);
+        }
+    } else if (pass == 3 && cur.tile_order) {
+      for (int sp : span)
+        if (sp != cur.score_span) {
+          kb_schedule c = cur;
+          c.score_span = sp;
+          cand.push_back(c);
+        }
+    }
+    for (const kb_schedule& c : cand) {
+      float ms = 0.0f;
+      rc = time_of(c, &ms);
+      if (rc != KB_OK) break;
+      if (ms < cur_ms) {
+        cur = c;
+        cur_ms = ms;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != KB_OK) return rc;
+  rc = kb_batch_set_schedule(b, &cur);
+  if (rc != KB_OK) return rc;
+  if (best) *best = cur;
+  return KB_OK;
+}
+
+extern "C" int kb_batch_stats(kb_batch* b, unsigned long long* done_ns, unsigned long long* totals,
+                              void* stream) {
+  using namespace kb;
+  if (!b || !done_ns || !totals) return fail(KB_ERR_INVALID_ARG, "kb_batch_stats: null pointer");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::vector<unsigned long long> dn(b->n);
+  unsigned long long start = 0;
+  Ctrl c{};
+  KB_CUDA_TRY(cudaMemcpyAsync(dn.data(), b->ws + b->tb.done_ns, sizeof(unsigned long long) * b->n,
+                              cudaMemcpyDeviceToHost, st));
+  KB_CUDA_TRY(cudaMemcpyAsync(&start, b->ws + b->tb.start_ns, sizeof(start), cudaMemcpyDeviceToHost, st));
+  KB_CUDA_TRY(cudaMemcpyAsync(&c, b->ws + b->tb.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+  KB_CUDA_TRY(cudaStreamSynchronize(st));
+  for (int k = 0; k < b->n; ++k) done_ns[b->order[k]] = dn[k] >= start ? dn[k] - start : 0ull;
+  totals[0] = c.te;
+  totals[1] = c.evals;
+  totals[2] = c.inserts;
+  totals[3] = c.err;
+  return KB_OK;
+}
+
+extern "C" void kb_batch_destroy(kb_batch* b) {
+  if (!b) return;
+  kb::drop_graph(b);
+  if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->ev_out) cudaEventDestroy(b->ev_out);
+  if (b->gstream) cudaStreamDestroy(b->gstream);
+  delete b;
 }
 
 extern "C" int kb_search_stats(const void* workspace, unsigned long long* stats, void* stream) {

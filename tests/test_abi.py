@@ -169,3 +169,35 @@ def test_comparison_harness_catches_planted_mistakes():
             g["nkept"][y, x, 0] += 1
         with pytest.raises(AssertionError):
             compare_search(g, o, 0.5)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of the header's structs have the C sizes and field offsets (gcc)."""
+    import ctypes as C
+    import subprocess
+    from paper_2109_03296_b300 import _lib
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = tmp_path / "layout.c"
+    src.write_text(r"""
+#include <stddef.h>
+#include <stdio.h>
+#include "kb.h"
+int main(void) {
+  printf("%zu %zu %zu %zu\n", sizeof(kb_search_params), sizeof(kb_refine_params),
+         sizeof(kb_schedule), sizeof(kb_stack));
+  printf("%zu %zu %zu %zu %zu\n", offsetof(kb_stack, vx), offsetof(kb_stack, n_traj),
+         offsetof(kb_stack, params), offsetof(kb_stack, out_lh), offsetof(kb_stack, out_mask));
+  return 0;
+}
+""")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(root, "include"), str(src), "-o",
+                           str(exe)])
+    out = subprocess.check_output([str(exe)]).decode().split()
+    sizes = [int(v) for v in out[:4]]
+    offs = [int(v) for v in out[4:]]
+    assert sizes == [C.sizeof(_lib.SearchParamsC), C.sizeof(_lib.RefineParamsC),
+                     C.sizeof(_lib.ScheduleC), C.sizeof(_lib.StackC)]
+    S = _lib.StackC
+    assert offs == [S.vx.offset, S.n_traj.offset, S.params.offset, S.out_lh.offset,
+                    S.out_mask.offset]
