@@ -1160,18 +1160,25 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
       // consumer barrier.
       auto flush = [&]() {
         const int nq = min((int)*s_qcount, S_QCAP);
+        // a batch's arguments live in shared memory: the evaluations read theirs from registers
+        EvalParams ep_copy;
+        if (BATCH) ep_copy = A.ep;
+        const EvalParams& EP = BATCH ? ep_copy : A.ep;
+        const float* const e_psi = A.psi;
+        const float* const e_phi = A.phi;
+        const int2* const e_offs = A.offs;
         auto by_thread = [&](auto nt) {
           for (int e = tid; e < nq; e += S_CTHREADS)
-            eval_pair_thread<decltype(nt)::value>(A.psi, A.phi, A.ep, tx0 + (q_pix[e] & 31),
+            eval_pair_thread<decltype(nt)::value>(e_psi, e_phi, EP, tx0 + (q_pix[e] & 31),
                                                   ty0 + (q_pix[e] >> 5),
-                                                  A.offs + (size_t)q_traj[e] * T,
+                                                  e_offs + (size_t)q_traj[e] * T,
                                                   recs + e * S_REC_WORDS);
         };
         auto by_warp = [&](auto jj) {
           for (int e = warp; e < nq; e += S_CWARPS)
-            eval_pair_warp<decltype(jj)::value>(A.psi, A.phi, A.ep, tx0 + (q_pix[e] & 31),
+            eval_pair_warp<decltype(jj)::value>(e_psi, e_phi, EP, tx0 + (q_pix[e] & 31),
                                                 ty0 + (q_pix[e] >> 5),
-                                                A.offs + (size_t)q_traj[e] * T,
+                                                e_offs + (size_t)q_traj[e] * T,
                                                 recs + e * S_REC_WORDS, lane);
         };
         if (BATCH) {
