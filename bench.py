@@ -285,6 +285,21 @@ def refine_config(args):
     return cfg
 
 
+def search_traffic(version, workload):
+    """DRAM bytes per search_kernel launch on this workload, from the ncu summary in profiles/
+    (a line `traffic: <workload> <bytes> kernel_version <v>`); None if absent or taken on another
+    kernel version."""
+    import re
+    p = os.path.join(ROOT, "profiles", "search_kernel_decam.md")
+    if not os.path.exists(p):
+        return None
+    for line in open(p):
+        m = re.match(r"\s*traffic:\s+(\S+)\s+([0-9.e+]+)\s+kernel_version\s+(\d+)", line)
+        if m and m.group(1) == workload and int(m.group(3)) == version:
+            return float(m.group(2))
+    return None
+
+
 def workload_config(name):
     from synth import CONFIGS
     c = CONFIGS[name]
@@ -431,13 +446,7 @@ def run_ours(args):
     smem_peak = sms * 128 * sm_max * 1e6 / 1e9                 # GB/s
     te_per_s_kernel = te_step / (k_ms / 1e3)
     achieved = te_per_s_kernel * 2 / 1e9
-    traffic = None
-    tp = os.path.join(ROOT, "profiles", "search_kernel_traffic.json")
-    if os.path.exists(tp):
-        with open(tp) as f:
-            tj = json.load(f)
-        if tj.get("kernel_version") == kb.version():
-            traffic = tj.get("bytes_per_launch")
+    traffic = search_traffic(kb.version(), args.workload)
     line = {
         "metric": "trajectory-epoch evals/sec", "value": value, "unit": "TE/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
