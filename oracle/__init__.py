@@ -25,6 +25,11 @@ the pins live in tests/test_oracle_pins.py):
                     xx = yy = side r(r+1)(2r+1) / (3 (side^2 - 1)) (36.75 > 36.5 for r = 10);
                     invariance to a constant offset; symmetric stamps give zero odd moments; a
                     sampled Gaussian gives its centre and variance
+  cluster           hand-worked cases (identical tracks, a chain where greedy order matters,
+                    tracks that part before the last epoch, invalid entries); on random inputs
+                    the properties that fix the greedy result uniquely: kept candidates are
+                    pairwise distinct, every other valid one duplicates a kept one of lower
+                    index and names the first such as its representative
   refine_adam       closed form of Adam's first step; convergence to a noiseless off-grid mover;
                     stop where Phi vanishes
 """

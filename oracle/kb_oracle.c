@@ -577,3 +577,42 @@ int kbo_stamp_moments(const double* S, int r, const double* lim, double* out) {
   return fabs(out[1]) < lim[0] && fabs(out[2]) < lim[1] && fabs(out[3]) < lim[2] &&
          out[4] < lim[3] && out[5] < lim[4];
 }
+
+/* ---------------------------------------------------------------------------------------- */
+/* Clustering of candidates (Fig. 3 caption names it; reading R19)                          */
+/* ---------------------------------------------------------------------------------------- */
+
+/* Greedy de-duplication in priority order (index 0 first): candidate i (start (x0, y0), velocity
+ * (vx, vy)) is a duplicate of j when their positions agree within r at the first epoch and at
+ * t0 + dt (the last epoch): |p_i - p_j| <= r at both, with p(dt) = (x0 + vx dt, y0 + vy dt).
+ * Walking the candidates in order, i is kept unless it duplicates an already kept j; rep[i] is i
+ * when kept, else the first (lowest-index) kept j it duplicates.  valid (nullable): candidates
+ * with valid[i] == 0 take no part (keep 0, rep -1). */
+static int kbo_dup(const int32_t* x0, const int32_t* y0, const float* vx, const float* vy,
+                   int i, int j, double dt, double r2) {
+  double dx0 = (double)x0[i] - (double)x0[j], dy0 = (double)y0[i] - (double)y0[j];
+  if (dx0 * dx0 + dy0 * dy0 > r2) return 0;
+  double xi = (double)x0[i] + (double)vx[i] * dt, yi = (double)y0[i] + (double)vy[i] * dt;
+  double xj = (double)x0[j] + (double)vx[j] * dt, yj = (double)y0[j] + (double)vy[j] * dt;
+  double dx1 = xi - xj, dy1 = yi - yj;
+  return dx1 * dx1 + dy1 * dy1 <= r2;
+}
+
+void kbo_cluster(const int32_t* x0, const int32_t* y0, const float* vx, const float* vy,
+                 const uint8_t* valid, int n, double dt, double r, uint8_t* keep, int32_t* rep) {
+  double r2 = r * r;
+  for (int i = 0; i < n; ++i) {
+    keep[i] = 0;
+    rep[i] = -1;
+    if (valid && !valid[i]) continue;
+    int found = -1;
+    for (int j = 0; j < i && found < 0; ++j)
+      if (keep[j] && kbo_dup(x0, y0, vx, vy, i, j, dt, r2)) found = j;
+    if (found < 0) {
+      keep[i] = 1;
+      rep[i] = i;
+    } else {
+      rep[i] = found;
+    }
+  }
+}

@@ -47,6 +47,8 @@ def lib():
         _LIB.kbo_traj_eval_subpixel.argtypes = [p, p, p, i, i, i, p, d, d, d, d, p, p, p]
         _LIB.kbo_traj_vjp.restype = i
         _LIB.kbo_traj_vjp.argtypes = [p, p, p, i, i, i, p, d, d, d, d, d, d, p, p, p]
+        _LIB.kbo_cluster.restype = None
+        _LIB.kbo_cluster.argtypes = [p, p, p, p, p, i, d, d, p, p]
         _LIB.kbo_stamp_moments.restype = i
         _LIB.kbo_stamp_moments.argtypes = [p, i, p, p]
         _LIB.kbo_refine_adam.restype = i
@@ -270,3 +272,18 @@ def stamp_moments(stamps, limits=PAPER_MOMENT_LIMITS):
         s_i = np.ascontiguousarray(st[i])
         ok[i] = bool(lib().kbo_stamp_moments(_ptr(s_i), r, _ptr(lim), _ptr(out[i])))
     return out, ok
+
+
+def cluster(x0, y0, vx, vy, dt, radius, valid=None):
+    """Greedy de-duplication in index order: (keep [n] bool, rep [n] int32)."""
+    x0 = np.ascontiguousarray(x0, np.int32)
+    y0 = np.ascontiguousarray(y0, np.int32)
+    vx = np.ascontiguousarray(vx, np.float32)
+    vy = np.ascontiguousarray(vy, np.float32)
+    n = len(x0)
+    va = None if valid is None else np.ascontiguousarray(valid, np.uint8)
+    keep = np.zeros(n, np.uint8)
+    rep = np.zeros(n, np.int32)
+    lib().kbo_cluster(_ptr(x0), _ptr(y0), _ptr(vx), _ptr(vy), _ptr(va), n, float(dt),
+                      float(radius), _ptr(keep), _ptr(rep))
+    return keep.astype(bool), rep

@@ -782,3 +782,66 @@ def test_moments_of_a_sampled_gaussian():
     s[0, 10, 11] = 1.0      # x = 0.5 exactly
     assert not oracle.stamp_moments(s)[1][0]
     assert oracle.stamp_moments(s, limits=(0.5000001, 0.5, 1.5, 36.5, 36.5))[1][0]
+
+
+# ------------------------------------------------------------------------------------------------
+# Clustering of candidates (greedy de-duplication, reading of the Fig. 3 step)
+# ------------------------------------------------------------------------------------------------
+
+def test_cluster_hand_cases():
+    dt, r = 3.0, 4.0
+    # identical tracks: the second duplicates the first
+    keep, rep = oracle.cluster([10, 10], [20, 20], [100.0, 100.0], [5.0, 5.0], dt, r)
+    assert keep.tolist() == [True, False] and rep.tolist() == [0, 0]
+    # a chain a - b - c (a~b, b~c, a!~c): greedy keeps a, drops b, keeps c (b was not kept)
+    keep, rep = oracle.cluster([0, 3, 6], [0, 0, 0], [10.0, 10.0, 10.0], [0.0, 0.0, 0.0], dt, r)
+    assert keep.tolist() == [True, False, True] and rep.tolist() == [0, 0, 2]
+    # the same start but velocities 2 px/day apart: 6 px apart at the last epoch -> distinct
+    keep, rep = oracle.cluster([5, 5], [5, 5], [100.0, 102.0], [0.0, 0.0], dt, r)
+    assert keep.tolist() == [True, True]
+    # exactly r apart at both epochs counts as a duplicate (<= r)
+    keep, _ = oracle.cluster([0, 4], [0, 0], [1.0, 1.0], [0.0, 0.0], dt, r)
+    assert keep.tolist() == [True, False]
+    # an invalid entry takes no part: c is compared with a only
+    keep, rep = oracle.cluster([0, 3, 6], [0, 0, 0], [10.0] * 3, [0.0] * 3, dt, r,
+                               valid=[1, 0, 1])
+    assert keep.tolist() == [True, False, True] and rep.tolist() == [0, -1, 2]
+    # the representative is the first kept duplicate, not the nearest
+    keep, rep = oracle.cluster([0, 6, 3], [0, 0, 0], [0.0] * 3, [0.0] * 3, dt, r)
+    assert keep.tolist() == [True, True, False] and rep.tolist() == [0, 1, 0]
+
+
+def test_cluster_properties_fix_the_greedy_result():
+    rng = np.random.default_rng(91)
+    dt, r = 3.0, 6.0
+    n = 400
+    # clusters of near-identical tracks plus scattered ones
+    cx = rng.uniform(0, 300, 25)
+    cy = rng.uniform(0, 300, 25)
+    k = rng.integers(0, 25, n)
+    x0 = np.round(cx[k] + rng.normal(0, 2.5, n)).astype(np.int32)
+    y0 = np.round(cy[k] + rng.normal(0, 2.5, n)).astype(np.int32)
+    vx = (100 + 3 * k + rng.normal(0, 0.8, n)).astype(np.float32)
+    vy = (rng.normal(0, 0.8, n)).astype(np.float32)
+    valid = rng.random(n) < 0.9
+    keep, rep = oracle.cluster(x0, y0, vx, vy, dt, r, valid=valid)
+
+    def dup(i, j):
+        d0 = np.hypot(float(x0[i]) - x0[j], float(y0[i]) - y0[j])
+        d1 = np.hypot(x0[i] + float(vx[i]) * dt - (x0[j] + float(vx[j]) * dt),
+                      y0[i] + float(vy[i]) * dt - (y0[j] + float(vy[j]) * dt))
+        return d0 <= r and d1 <= r
+
+    kept = np.nonzero(keep)[0]
+    for a in range(len(kept)):               # kept candidates are pairwise distinct
+        for b in range(a):
+            assert not dup(kept[a], kept[b])
+    for i in range(n):
+        if not valid[i]:
+            assert not keep[i] and rep[i] == -1
+        elif keep[i]:
+            assert rep[i] == i
+        else:                                 # the first kept lower-index duplicate
+            firsts = [j for j in range(i) if keep[j] and dup(i, j)]
+            assert firsts and rep[i] == firsts[0]
+    assert 20 <= keep.sum() < valid.sum()
