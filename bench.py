@@ -3,8 +3,8 @@
 
 One step = the whole hot path over one stack resident in HBM: psi/phi formation, the exhaustive
 integer-track search with the in-line sigma-G clip and per-pixel top-K, the survivor handoff
-(best n_stamps slots), 21 x 21 mean/median coadded stamps for them and the central-moment filter
-of the median stamps.  The metric is
+(best n_stamps slots), 21 x 21 mean/median coadded stamps for them, the central-moment filter
+of the median stamps and the de-duplication of the passing candidates.  The metric is
 trajectory-epoch evaluations per second: start pixels x trajectories x epochs of the step, over
 the step's device time.
 
@@ -285,6 +285,13 @@ def refine_config(args):
     return cfg
 
 
+def cluster_ws_bytes(kb, n):
+    import ctypes as C
+    nb = C.c_size_t(0)
+    kb.lib().kb_cluster_workspace_size(int(n), C.byref(nb))
+    return nb.value
+
+
 def search_traffic(version, workload):
     """DRAM bytes per search_kernel launch on this workload, from the ncu summary in profiles/
     (a line `traffic: <workload> <bytes> kernel_version <v>`); None if absent or taken on another
@@ -353,6 +360,7 @@ def run_ours(args):
                nkept=torch.empty((H, W, K), dtype=torch.int16, device=dev),
                mask=torch.empty((H, W, K, mw), dtype=torch.int32, device=dev))
     n_st = args.n_stamps
+    cl_ws = kb.alloc_workspace(cluster_ws_bytes(kb, n_st), dev)
     stream = torch.cuda.current_stream()
     kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
@@ -372,8 +380,10 @@ def run_ours(args):
         mean, med = kb.stamps(inp["img"], inp["var"], inp["mask"], s.times, x0, y0, cvx, cvy,
                               radius=10)
         moments, passed = kb.stamp_filter(med)
+        keep, rep = kb.cluster(x0, y0, cvx, cvy, s.times, radius=8.0, valid=passed & (traj >= 0),
+                               workspace=cl_ws)
         return dict(pix=pix, slot=slot, count=count, x0=x0, y0=y0, vx=cvx, vy=cvy, traj=traj,
-                    mean=mean, median=med, moments=moments, passed=passed)
+                    mean=mean, median=med, moments=moments, passed=passed, keep=keep, rep=rep)
 
     for _ in range(args.warmup):
         step(d)

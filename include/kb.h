@@ -313,6 +313,34 @@ KB_API int kb_stamp_filter(const float* stamps, int n, int radius, const float* 
                            float* out_moments, uint8_t* out_pass, void* stream);
 
 /*
+ * kb_cluster -- de-duplication of candidates (the clustering step that follows the stamp filter
+ * in the paper's pipeline, Fig. 3; the paper does not give its algorithm).  In priority order
+ * (index 0 first, e.g. kb_collect's LH' order), candidate i is kept unless its track agrees
+ * within `radius` pixels, at the first epoch and at the last, with a candidate kept before it:
+ *   |p_i(0) - p_j(0)| <= radius  and  |p_i(dt) - p_j(dt)| <= radius,
+ *   p(t) = (x0 + vx t, y0 + vy t), distances in float64, dt = t_last - t_0.
+ * out_rep[i] = i for a kept candidate, else the first (lowest-index) kept candidate it
+ * duplicates; -1 for candidates that take no part (valid[i] == 0, or a start pixel outside
+ * 0 .. 2^20 - 1, as kb_candidate_tracks gives empty slots).
+ *
+ *   x0, y0       [n] int32 start pixels; vx, vy [n] float32 (device).
+ *   valid        [n] uint8 (device) or NULL: e.g. kb_stamp_filter's out_pass.
+ *   out_keep     [n] uint8 (device): 1 = kept.   out_rep [n] int32 (device).
+ *   workspace    kb_cluster_workspace_size(n) bytes, KB_WORKSPACE_ALIGN-aligned.
+ *   rounds       (nullable, host) the number of parallel rounds run.
+ * The greedy order is resolved in rounds that decide every candidate whose earlier duplicates are
+ * all decided; the call reads a round counter back every 4 rounds, so it BLOCKS the host until
+ * the result is final (it is not capturable in a CUDA graph).
+ * Errors: KB_ERR_INVALID_ARG (null pointers, n < 0, radius < 1 or not finite, dt not finite),
+ * KB_ERR_UNSUPPORTED (n > 2^24), KB_ERR_WORKSPACE.
+ */
+KB_API int kb_cluster_workspace_size(int n, size_t* bytes);
+KB_API int kb_cluster(const int32_t* x0, const int32_t* y0, const float* vx, const float* vy,
+                      const uint8_t* valid, int n, double dt, double radius, uint8_t* out_keep,
+                      int32_t* out_rep, void* workspace, size_t ws_bytes, int* rounds,
+                      void* stream);
+
+/*
  * kb_collect -- GPU-to-host handoff of the survivors (Section 3.1 reworked handoff; Section 3.2
  * returns the per-pixel results to the CPU): gathers every filled slot of a kb_search result
  * and orders them by LH' descending, then start pixel, then slot; the first n_max are written.

@@ -11,6 +11,7 @@ Every step of the computation runs in the library's sm_103a kernels; CPU tensors
     pix, slot, count = collect(res, n_max)                        # GPU -> host handoff
     mean, median = stamps(img, var, mask, times, x0, y0, vx, vy)  # Section 3.3
     moments, passed = stamp_filter(median)                        # Section 3.3 moment filter
+    keep, rep = cluster(x0, y0, vx, vy, times, valid=passed)      # de-duplication (Fig. 3)
     params, keep = candidate_params(pix, slot, res, vx, vy)       # off-grid refinement:
     params, L, alpha, L0 = refine(psi, phi, times, params, keep)  #   Section 4.1, bilinear
     L, alpha = traj_likelihood(params, psi, phi, times, keep)     # differentiable (autograd)
@@ -28,7 +29,7 @@ __all__ = ["SearchParams", "make_psi_phi", "search", "search_workspace_size", "s
            "stamps", "collect", "candidate_tracks", "launch_count", "profile_events", "KbError",
            "search_no_alloc", "RefineParams", "traj_eval", "traj_eval_backward", "TrajEval",
            "traj_likelihood", "refine", "candidate_params", "stamp_filter",
-           "PAPER_MOMENT_LIMITS", "Schedule", "Batch",
+           "PAPER_MOMENT_LIMITS", "Schedule", "Batch", "cluster",
            "KB_MAX_T", "KB_MAX_K", "lib", "version", "alloc_workspace"]
 
 
@@ -203,6 +204,36 @@ def stamp_filter(stamps_, limits=None, stream=None):
     check(lib().kb_stamp_filter(_ptr(stamps_), n, side // 2, lim, _ptr(mom), _ptr(ok),
                                 _stream(stream)))
     return mom, ok.view(torch.bool)
+
+
+def cluster(x0, y0, vx, vy, times, radius=8.0, valid=None, workspace=None, stream=None,
+            return_rounds=False):
+    """De-duplicate candidates in index order (kb_cluster): (keep bool [n], rep int32 [n]).
+    Two tracks are duplicates when they agree within `radius` pixels at the first and the last
+    epoch of `times`.  Blocks the host until the result is final."""
+    _dev(x0, torch.int32, "x0", 1)
+    _dev(y0, torch.int32, "y0", 1)
+    _dev(vx, torch.float32, "vx", 1)
+    _dev(vy, torch.float32, "vy", 1)
+    if valid is not None:
+        if valid.dtype == torch.bool:
+            valid = valid.view(torch.uint8)
+        _dev(valid, torch.uint8, "valid", 1)
+    n = x0.numel()
+    t = _host_times(times)
+    dt = float(t[-1] - t[0]) if len(t) else 0.0
+    if workspace is None:
+        nb = C.c_size_t(0)
+        check(lib().kb_cluster_workspace_size(n, C.byref(nb)))
+        workspace = alloc_workspace(nb.value, x0.device)
+    keep = torch.empty(n, dtype=torch.uint8, device=x0.device)
+    rep = torch.empty(n, dtype=torch.int32, device=x0.device)
+    rounds = C.c_int(0)
+    check(lib().kb_cluster(_ptr(x0), _ptr(y0), _ptr(vx), _ptr(vy), _ptr(valid), n, dt,
+                           float(radius), _ptr(keep), _ptr(rep), _ptr(workspace),
+                           workspace.numel(), C.byref(rounds), _stream(stream)))
+    out = (keep.view(torch.bool), rep)
+    return out + (rounds.value,) if return_rounds else out
 
 
 def collect(result, n_max, workspace=None, stream=None):

@@ -27,7 +27,8 @@ EXPORTS = ("kb_version", "kb_last_error", "kb_search_params_default", "kb_make_p
            "kb_refine_params_default", "kb_refine", "kb_candidate_params", "kb_stamp_filter",
            "kb_schedule_default", "kb_batch_workspace_size", "kb_batch_create", "kb_batch_run",
            "kb_batch_run_graph", "kb_batch_set_schedule", "kb_batch_get_schedule",
-           "kb_batch_autotune", "kb_batch_stats", "kb_batch_destroy")
+           "kb_batch_autotune", "kb_batch_stats", "kb_batch_destroy",
+           "kb_cluster_workspace_size", "kb_cluster")
 
 
 class KbError(RuntimeError):
@@ -135,6 +136,11 @@ def lib():
     L.kb_batch_stats.argtypes = [p, p, p, p]
     L.kb_batch_destroy.restype = None
     L.kb_batch_destroy.argtypes = [p]
+    L.kb_cluster_workspace_size.restype = i
+    L.kb_cluster_workspace_size.argtypes = [i, C.POINTER(sz)]
+    L.kb_cluster.restype = i
+    L.kb_cluster.argtypes = [p, p, p, p, p, i, C.c_double, C.c_double, p, p, p, sz,
+                             C.POINTER(C.c_int), p]
     L.kb_stamp_filter.restype = i
     L.kb_stamp_filter.argtypes = [p, i, i, p, p, p, p]
     L.kb_candidate_params.restype = i
