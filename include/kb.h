@@ -328,9 +328,10 @@ KB_API int kb_stamp_filter(const float* stamps, int n, int radius, const float* 
  *   out_keep     [n] uint8 (device): 1 = kept.   out_rep [n] int32 (device).
  *   workspace    kb_cluster_workspace_size(n) bytes, KB_WORKSPACE_ALIGN-aligned.
  *   rounds       (nullable, host) the number of parallel rounds run.
- * The greedy order is resolved in rounds that decide every candidate whose earlier duplicates are
- * all decided; the call reads a round counter back every 4 rounds, so it BLOCKS the host until
- * the result is final (it is not capturable in a CUDA graph).
+ * The greedy order is resolved in rounds: a candidate is dropped as soon as an earlier duplicate
+ * is kept, and kept once its earlier duplicates are all decided and none is kept (a group of
+ * mutual duplicates takes two rounds).  The call reads a round counter back every 4 rounds, so
+ * it BLOCKS the host until the result is final (it is not capturable in a CUDA graph).
  * Errors: KB_ERR_INVALID_ARG (null pointers, n < 0, radius < 1 or not finite, dt not finite),
  * KB_ERR_UNSUPPORTED (n > 2^24), KB_ERR_WORKSPACE.
  */

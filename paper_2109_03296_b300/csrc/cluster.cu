@@ -5,11 +5,12 @@
 //
 // The greedy order is resolved in parallel rounds.  Candidates are bucketed by their start
 // position on a grid of r-sized cells (a duplicate starts within r, so in the same or an adjacent
-// cell), the (cell, index) keys are sorted, and each round decides every candidate whose
-// higher-priority duplicates are all decided: kept if none of them is kept, else suppressed with
-// the first kept one as representative.  That is exactly the greedy result (by induction over the
-// priority order); the number of rounds is the longest chain of pending duplicates, a handful in
-// practice.  Distances are compared in float64 with separately rounded operations, the same
+// cell) and the (cell, index) keys are sorted.  Each round suppresses every candidate with an
+// earlier duplicate already kept, and keeps every candidate whose earlier duplicates are all
+// decided and none kept; decisions are final, so this is exactly the greedy result (by induction
+// over the priority order).  A group of mutual duplicates is settled in two rounds; only chains of
+// duplicates that are not duplicates of each other take longer.  A last pass names each
+// suppressed candidate's representative, the first kept duplicate.  Distances are compared in float64 with separately rounded operations, the same
 // decisions as a plain double-precision loop.
 #include <algorithm>
 
@@ -84,27 +85,20 @@ __device__ __forceinline__ double sq_dist(double ax, double ay, double bx, doubl
   return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
 }
 
-__global__ void cluster_round_kernel(const int32_t* __restrict__ x0,
-                                     const int32_t* __restrict__ y0,
-                                     const float* __restrict__ vx, const float* __restrict__ vy,
-                                     int n, double dt, double r, const unsigned long long* keys,
-                                     int P, const uint8_t* __restrict__ st_in,
-                                     uint8_t* __restrict__ st_out, int32_t* __restrict__ rep,
-                                     unsigned int* undecided) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const uint8_t s = st_in[i];
-  if (s != CL_UNDECIDED) {
-    st_out[i] = s;
-    return;
-  }
+// Scans candidate i's earlier duplicates in states st: returns the first kept one (INT_MAX if
+// none) and whether any is still undecided.
+__device__ __forceinline__ int scan_earlier(const int32_t* __restrict__ x0,
+                                            const int32_t* __restrict__ y0,
+                                            const float* __restrict__ vx,
+                                            const float* __restrict__ vy, int i, double dt,
+                                            double r, const unsigned long long* keys, int P,
+                                            const uint8_t* __restrict__ st, bool& pending) {
   const double r2 = __dmul_rn(r, r);
   const double xi = (double)x0[i], yi = (double)y0[i];
   const double xi1 = __dadd_rn(xi, __dmul_rn((double)vx[i], dt));
   const double yi1 = __dadd_rn(yi, __dmul_rn((double)vy[i], dt));
   const long long cx = (long long)floor(xi / r), cy = (long long)floor(yi / r);
   int first_kept = INT_MAX;
-  bool pending = false;
   for (long long yy = cy - 1; yy <= cy + 1; ++yy) {
     if (yy < 0 || yy >= (1LL << 20)) continue;
     for (long long xx = cx - 1; xx <= cx + 1; ++xx) {
@@ -122,30 +116,57 @@ __global__ void cluster_round_kernel(const int32_t* __restrict__ x0,
         const double xj1 = __dadd_rn(xj, __dmul_rn((double)vx[j], dt));
         const double yj1 = __dadd_rn(yj, __dmul_rn((double)vy[j], dt));
         if (sq_dist(xi1, yi1, xj1, yj1) > r2) continue;
-        const uint8_t sj = st_in[j];
+        const uint8_t sj = st[j];
         if (sj == CL_KEPT) first_kept = min(first_kept, j);
         else if (sj == CL_UNDECIDED) pending = true;
       }
     }
   }
-  if (pending) {
+  return first_kept;
+}
+
+__global__ void cluster_round_kernel(const int32_t* __restrict__ x0,
+                                     const int32_t* __restrict__ y0,
+                                     const float* __restrict__ vx, const float* __restrict__ vy,
+                                     int n, double dt, double r, const unsigned long long* keys,
+                                     int P, const uint8_t* __restrict__ st_in,
+                                     uint8_t* __restrict__ st_out, unsigned int* undecided) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint8_t s = st_in[i];
+  if (s != CL_UNDECIDED) {
+    st_out[i] = s;
+    return;
+  }
+  bool pending = false;
+  const int first_kept = scan_earlier(x0, y0, vx, vy, i, dt, r, keys, P, st_in, pending);
+  if (first_kept != INT_MAX) {
+    st_out[i] = CL_SUPPRESSED;       // an earlier duplicate is kept: final
+  } else if (pending) {
     st_out[i] = CL_UNDECIDED;
     atomicAdd(undecided, 1u);
-  } else if (first_kept != INT_MAX) {
-    st_out[i] = CL_SUPPRESSED;
-    rep[i] = first_kept;
   } else {
     st_out[i] = CL_KEPT;
-    rep[i] = i;
   }
 }
 
-__global__ void cluster_out_kernel(const uint8_t* __restrict__ st, int n, uint8_t* __restrict__ keep,
-                                   int32_t* __restrict__ rep) {
+__global__ void cluster_out_kernel(const int32_t* __restrict__ x0, const int32_t* __restrict__ y0,
+                                   const float* __restrict__ vx, const float* __restrict__ vy,
+                                   int n, double dt, double r, const unsigned long long* keys,
+                                   int P, const uint8_t* __restrict__ st,
+                                   uint8_t* __restrict__ keep, int32_t* __restrict__ rep) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  keep[i] = st[i] == CL_KEPT ? 1 : 0;
-  if (st[i] == CL_IGNORED) rep[i] = -1;
+  const uint8_t s = st[i];
+  keep[i] = s == CL_KEPT ? 1 : 0;
+  if (s == CL_IGNORED) {
+    rep[i] = -1;
+  } else if (s == CL_KEPT) {
+    rep[i] = i;
+  } else {
+    bool pending = false;
+    rep[i] = scan_earlier(x0, y0, vx, vy, i, dt, r, keys, P, st, pending);
+  }
 }
 
 }  // namespace kb
@@ -193,12 +214,13 @@ extern "C" int kb_cluster(const int32_t* x0, const int32_t* y0, const float* vx,
     }
   // rounds in groups of CL_ROUNDS_PER_CHECK, with one host read of the undecided counts per
   // group; every round decides at least the first undecided candidate, so n rounds suffice
+  // (in practice a few: rounds grow only with chains of duplicates that are not mutual)
   int done_rounds = 0;
   for (;;) {
     KB_CUDA_TRY(cudaMemsetAsync(und, 0, sizeof(unsigned int) * CL_ROUNDS_PER_CHECK, st));
     for (int q = 0; q < CL_ROUNDS_PER_CHECK; ++q) {
       cluster_round_kernel<<<(n + 255) / 256, 256, 0, st>>>(x0, y0, vx, vy, n, dt, radius, keys,
-                                                            P, s0, s1, out_rep, und + q);
+                                                            P, s0, s1, und + q);
       KB_LAUNCH_CHECK("cluster_round_kernel");
       std::swap(s0, s1);
     }
@@ -211,7 +233,8 @@ extern "C" int kb_cluster(const int32_t* x0, const int32_t* y0, const float* vx,
       return fail(KB_ERR_CUDA, "kb_cluster: no progress after %d rounds", done_rounds);
   }
   if (rounds) *rounds = done_rounds;
-  cluster_out_kernel<<<(n + 255) / 256, 256, 0, st>>>(s0, n, out_keep, out_rep);
+  cluster_out_kernel<<<(n + 255) / 256, 256, 0, st>>>(x0, y0, vx, vy, n, dt, radius, keys, P, s0,
+                                                      out_keep, out_rep);
   KB_LAUNCH_CHECK("cluster_out_kernel");
   return KB_OK;
 }

@@ -48,6 +48,24 @@ def test_cluster_matches_oracle(cuda_device, seed, n, groups, spx, sv, r):
     assert 1 <= rounds <= 64
 
 
+def test_cluster_rounds_stay_few_on_dense_groups(cuda_device):
+    # 3000 candidates in 3 groups of mutual duplicates, as a bright mover's survivors are: the
+    # greedy result needs two rounds per group, not one per member
+    rng = np.random.default_rng(9)
+    n = 3000
+    g = rng.integers(0, 3, n)
+    x0 = (np.array([100, 900, 2000])[g] + rng.integers(-1, 2, n)).astype(np.int32)
+    y0 = (np.array([50, 700, 1500])[g] + rng.integers(-1, 2, n)).astype(np.int32)
+    vx = (np.array([120.0, 300.0, 450.0])[g] + rng.normal(0, 0.2, n)).astype(np.float32)
+    vy = (np.array([10.0, -40.0, 90.0])[g] + rng.normal(0, 0.2, n)).astype(np.float32)
+    keep, rep, rounds = kb.cluster(_d(x0), _d(y0), _d(vx), _d(vy), [0.0, 3.0], radius=8.0,
+                                   return_rounds=True)
+    ok, orep = oracle.cluster(x0, y0, vx, vy, 3.0, 8.0)
+    assert np.array_equal(keep.cpu().numpy(), ok) and np.array_equal(rep.cpu().numpy(), orep)
+    assert ok.sum() == 3
+    assert rounds <= 4
+
+
 def test_cluster_edges(cuda_device):
     e = torch.empty(0, dtype=torch.int32, device="cuda")
     ef = torch.empty(0, dtype=torch.float32, device="cuda")
