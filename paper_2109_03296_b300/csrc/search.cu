@@ -614,6 +614,15 @@ __device__ __forceinline__ void thread_bitonic_sort(float (&v)[NT]) {
 }
 
 // Percentile of the n smallest of the ascending values in loc[] (linear interpolation, h = (n-1) q).
+// Element idx of a register array (selects, no dynamically indexed local memory).
+template <int NT>
+__device__ __forceinline__ float sel_sorted(const float (&v)[NT], int idx) {
+  float r = v[0];
+#pragma unroll
+  for (int k = 1; k < NT; ++k) r = (k == idx) ? v[k] : r;
+  return r;
+}
+
 template <int NT>
 __device__ __forceinline__ float sorted_percentile(const float (&loc)[NT], int n, float q) {
   const float h = (float)(n - 1) * q;
@@ -621,7 +630,7 @@ __device__ __forceinline__ float sorted_percentile(const float (&loc)[NT], int n
   lo = max(0, min(lo, n - 1));
   const int hi = min(lo + 1, n - 1);
   const float f = h - (float)lo;
-  const float a = loc[lo], b = loc[hi];
+  const float a = sel_sorted<NT>(loc, lo), b = sel_sorted<NT>(loc, hi);
   return a + f * (b - a);
 }
 
@@ -1282,12 +1291,17 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
           const __half2 th = __halves2half2(half_round_down(thr2[2 * pp]),
                                             half_round_down(thr2[2 * pp + 1]));
           uint32_t b0 = 0u, b1 = 0u;
+          // most chunks have no candidate in the whole warp: test the maxima first
+          __half2 mx = acc[pp][0];
 #pragma unroll
-          for (int v = 0; v < S_C; ++v) {
-            const uint32_t m = __hge2_mask(acc[pp][v], th);
-            b0 |= (m & 1u) << v;
-            b1 |= ((m >> 16) & 1u) << v;
-          }
+          for (int v = 1; v < S_C; ++v) mx = __hmax2(mx, acc[pp][v]);
+          if (__any_sync(0xffffffffu, __hge2_mask(mx, th) != 0u))
+#pragma unroll
+            for (int v = 0; v < S_C; ++v) {
+              const uint32_t m = __hge2_mask(acc[pp][v], th);
+              b0 |= (m & 1u) << v;
+              b1 |= ((m >> 16) & 1u) << v;
+            }
           cb[2 * pp] = ((active >> (2 * pp)) & 1u) ? (b0 & vmask) : 0u;
           cb[2 * pp + 1] = ((active >> (2 * pp + 1)) & 1u) ? (b1 & vmask) : 0u;
         }
