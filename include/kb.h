@@ -214,11 +214,12 @@ KB_API int kb_stamps(const float* img, const float* var, const uint8_t* mask, co
               float* out_median, void* stream);
 
 /*
- * Batched search -- many stacks (CCDs, pointings) in one persistent launch.  The paper searches
- * each CCD's stack on its own (Section 2: 2580 independent searches, Section 4.1); here the tiles
- * of all stacks are handed out from one counter to one persistent kernel, so that no SM idles at
- * the end of a small stack, and the whole sequence (per-stack preparation + the search) can be
- * replayed as one CUDA graph.  Each stack's results are exactly those of kb_search on it.
+ * Batched search -- many stacks (CCDs, pointings) searched as one unit.  The paper searches each
+ * CCD's stack on its own (Section 2: 2580 independent searches, Section 4.1); here either the
+ * tiles of all stacks are handed out from one counter to one persistent kernel, or the stacks'
+ * kernels run concurrently on a few streams (schedule mode), so that no SM idles at the end of
+ * a stack, and the whole sequence (per-stack preparation + the search) can be replayed as one
+ * CUDA graph.  Each stack's results are exactly those of kb_search on it.
  *
  *   kb_stack       one stack: the arguments of kb_search (psi, phi, times, sizes, velocities,
  *                  search parameters and the six output arrays), with the same meaning, layout
@@ -228,8 +229,13 @@ KB_API int kb_stamps(const float* img, const float* var, const uint8_t* mask, co
  *                                 with psi^2/phi >= hot_nu2 in the footprints of the epochs
  *                                 whose offsets span at most score_span pixels); 0: row-major.
  *                    stack_order  1: stacks in decreasing trajectory-epoch count; 0: as given.
- *                  kb_schedule_default: {tile_order 1, hot_nu2 16, score_span 64, stack_order 1}
- *                  (kb_search uses the same tile order).
+ *                    mode         0: one persistent launch over the tiles of all stacks;
+ *                                 1: one launch per stack (the single-stack kernel, whose
+ *                                 arguments live in parameter space), spread over four
+ *                                 streams of the batch, so that a stack's kernel starts on the
+ *                                 SMs that the previous one's last tiles leave idle.
+ *                  kb_schedule_default: {tile_order 1, hot_nu2 16, score_span 64, stack_order 1,
+ *                  mode 1} (kb_search uses the same tile order).
  *   kb_batch       opaque handle: kb_batch_create validates every stack (the checks of
  *                  kb_search), lays out the workspace and writes the batch tables to the device
  *                  (synchronous copies); the stacks' buffers must stay valid while it is used.
@@ -242,9 +248,9 @@ KB_API int kb_stamps(const float* img, const float* var, const uint8_t* mask, co
  *   call).
  * kb_batch_set_schedule / kb_batch_get_schedule: knobs above (set waits for the device).
  * kb_batch_autotune: times the batch (kb_batch_run, best of `reps`) under schedules chosen by
- *   coordinate descent from the default (stack order, tile order, hot_nu2 in {16, 9, 36},
- *   score_span in {64, 32, 128}), keeps the fastest and returns it in *best (nullable).  Runs
- *   the batch about 8 x reps times; its outputs are those of a normal run.
+ *   coordinate descent from the default (mode and stack order, tile order, hot_nu2 in
+ *   {16, 9, 36}, score_span in {64, 32, 128}), keeps the fastest and returns it in *best
+ *   (nullable).  Runs the batch about 9 x reps times; its outputs are those of a normal run.
  * kb_batch_stats: after a run, done_ns[i] = ns from the start of the run to the completion of
  *   stack i's last tile (the caller's order), totals[4] = {trajectory-epochs, full evaluations,
  *   insertions, error flags} of the run (blocks the host).
@@ -274,6 +280,7 @@ typedef struct kb_schedule {
   float hot_nu2;
   int score_span;
   int stack_order;
+  int mode;
 } kb_schedule;
 
 typedef struct kb_batch kb_batch;

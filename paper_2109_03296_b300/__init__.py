@@ -474,18 +474,20 @@ class Schedule:
     hot_nu2: float = 16.0
     score_span: int = 64
     stack_order: int = 1
+    mode: int = 1           # 0: one persistent launch; 1: concurrent per-stack launches
 
     def to_c(self):
         return ScheduleC(int(self.tile_order), float(self.hot_nu2), int(self.score_span),
-                         int(self.stack_order))
+                         int(self.stack_order), int(self.mode))
 
     @staticmethod
     def from_c(c):
-        return Schedule(c.tile_order, c.hot_nu2, c.score_span, c.stack_order)
+        return Schedule(c.tile_order, c.hot_nu2, c.score_span, c.stack_order, c.mode)
 
 
 class Batch:
-    """A batch of stacks searched by one persistent launch (kb_batch_*).
+    """A batch of stacks searched as one unit (kb_batch_*): one persistent launch or concurrent
+    per-stack launches (Schedule.mode), optionally replayed as one CUDA graph.
 
     stacks: list of dicts with psi, phi ([T, H, W] float32 CUDA tensors), times (host array),
     vx, vy (float32 CUDA tensors) and params (SearchParams, optional).  Allocates each stack's

@@ -61,7 +61,7 @@ class StackC(C.Structure):
 
 class ScheduleC(C.Structure):
     _fields_ = [("tile_order", C.c_int32), ("hot_nu2", C.c_float), ("score_span", C.c_int32),
-                ("stack_order", C.c_int32)]
+                ("stack_order", C.c_int32), ("mode", C.c_int32)]
 
 
 _LIB = None

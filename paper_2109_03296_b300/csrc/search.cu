@@ -645,22 +645,27 @@ __device__ __forceinline__ bool gather_pair(const float* __restrict__ psi,
   return f > 0.0f && isfinite(p) && isfinite(f);
 }
 
+// One pair, one thread.  psi_t and phi_t stay in registers from the single gather; the
+// lightcurve value of an epoch (flux psi/phi, or psi/sqrt(phi) when clip_on) is recomputed with
+// the same IEEE operations where it is needed (sort input, clip test), so no epoch is read twice.
 template <int NT>
 __device__ void eval_pair_thread(const float* __restrict__ psi, const float* __restrict__ phi,
                                  const EvalParams& ep, int x0, int y0,
                                  const int2* __restrict__ off, uint32_t* rec) {
-  float a[NT];
+  float pv[NT], fv[NT];
   uint32_t vm = 0u;
   const size_t plane = (size_t)ep.H * ep.W;
 #pragma unroll
   for (int t = 0; t < NT; ++t) {
-    a[t] = INFINITY;
+    pv[t] = 0.0f;
+    fv[t] = 0.0f;
     if (t < ep.T) {
       const int2 o = __ldg(off + t);
       float p, f;
       if (gather_pair(psi, phi, ep, plane, t, x0 + o.x, y0 + o.y, p, f)) {
         vm |= 1u << t;
-        a[t] = ep.clip_on ? __fdiv_rn(p, __fsqrt_rn(f)) : __fdiv_rn(p, f);
+        pv[t] = p;
+        fv[t] = f;
       }
     }
   }
@@ -670,11 +675,15 @@ __device__ void eval_pair_thread(const float* __restrict__ psi, const float* __r
     rec[2] = (uint32_t)nvalid;
     return;
   }
+  const bool on_lh = ep.clip_on != 0;
+  auto curve = [&](int t) {
+    return on_lh ? __fdiv_rn(pv[t], __fsqrt_rn(fv[t])) : __fdiv_rn(pv[t], fv[t]);
+  };
   uint32_t km = vm;
   if (ep.clip) {
     float loc[NT];
 #pragma unroll
-    for (int t = 0; t < NT; ++t) loc[t] = a[t];
+    for (int t = 0; t < NT; ++t) loc[t] = ((vm >> t) & 1u) ? curve(t) : INFINITY;
     thread_bitonic_sort<NT>(loc);
     const float x_lo = sorted_percentile<NT>(loc, nvalid, ep.q_lo);
     const float x_mid = sorted_percentile<NT>(loc, nvalid, ep.q_mid);
@@ -683,19 +692,20 @@ __device__ void eval_pair_thread(const float* __restrict__ psi, const float* __r
     const float lo_b = x_mid - ep.n_sigma * sg, hi_b = x_mid + ep.n_sigma * sg;
     km = 0u;
 #pragma unroll
-    for (int t = 0; t < NT; ++t)
-      if (((vm >> t) & 1u) && a[t] >= lo_b && a[t] <= hi_b) km |= 1u << t;
+    for (int t = 0; t < NT; ++t) {
+      if ((vm >> t) & 1u) {
+        const float a = curve(t);
+        if (a >= lo_b && a <= hi_b) km |= 1u << t;
+      }
+    }
   }
-  // sums over the kept epochs, in epoch order (second gather: the lines are in L1)
+  // sums over the kept epochs, in epoch order
   float sp = 0.0f, sf = 0.0f;
 #pragma unroll
   for (int t = 0; t < NT; ++t) {
     if ((km >> t) & 1u) {
-      const int2 o = __ldg(off + t);
-      float p = 0.0f, f = 0.0f;
-      gather_pair(psi, phi, ep, plane, t, x0 + o.x, y0 + o.y, p, f);
-      sp += p;
-      sf += f;
+      sp += pv[t];
+      sf += fv[t];
     }
   }
   const int nkept = __popc(km);
@@ -1642,7 +1652,28 @@ static int launch_prep(StackPrep& sp, const kb_schedule& sch, cudaStream_t st) {
   return KB_OK;
 }
 
-static const kb_schedule kDefaultSchedule = {1, 16.0f, 64, 1};
+// The search kernel of one stack (its arguments and tensor maps in parameter space).
+static int launch_search_single(const StackPrep& sp, cudaStream_t st) {
+  const SearchArgs& A = sp.A;
+  const int T = sp.T;
+  const int grid = std::min(A.ntiles, g_num_sms);
+  const size_t smem = SmemLayout::total;
+#define KB_SEARCH_LAUNCH(NT, JJ)                                                               \
+  do {                                                                                         \
+    KB_CUDA_TRY(cudaFuncSetAttribute(search_kernel<NT, JJ, false>,                             \
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+    search_kernel<NT, JJ, false><<<grid, S_THREADS, smem, st>>>(sp.maps, A, BatchArgs{});      \
+  } while (0)
+  if (T <= 16) KB_SEARCH_LAUNCH(16, 1);
+  else if (T <= 32) KB_SEARCH_LAUNCH(32, 1);
+  else if (T <= 64) KB_SEARCH_LAUNCH(0, 2);
+  else KB_SEARCH_LAUNCH(0, 4);
+#undef KB_SEARCH_LAUNCH
+  KB_LAUNCH_CHECK("search_kernel");
+  return KB_OK;
+}
+
+static const kb_schedule kDefaultSchedule = {1, 16.0f, 64, 1, 1};
 
 static int check_schedule(const kb_schedule* s) {
   if (!s) return fail(KB_ERR_INVALID_ARG, "schedule: null pointer");
@@ -1654,6 +1685,7 @@ static int check_schedule(const kb_schedule* s) {
     return fail(KB_ERR_INVALID_ARG, "schedule: hot_nu2 must be finite and > 0");
   if (s->score_span < 0 || s->score_span > (1 << 20))
     return fail(KB_ERR_INVALID_ARG, "schedule: score_span outside 0..2^20");
+  if (s->mode != 0 && s->mode != 1) return fail(KB_ERR_INVALID_ARG, "schedule: mode must be 0 or 1");
   return KB_OK;
 }
 
@@ -1677,24 +1709,11 @@ extern "C" int kb_search(const float* psi, const float* phi, const double* times
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   rc = launch_prep(sp, kDefaultSchedule, st);
   if (rc != KB_OK) return rc;
-  const SearchArgs& A = sp.A;
-  const int grid = std::min(A.ntiles, g_num_sms);
-  const size_t smem = SmemLayout::total;
-#define KB_SEARCH_LAUNCH(NT, JJ)                                                               \
-  do {                                                                                         \
-    KB_CUDA_TRY(cudaFuncSetAttribute(search_kernel<NT, JJ, false>,                             \
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-    search_kernel<NT, JJ, false><<<grid, S_THREADS, smem, st>>>(sp.maps, A, BatchArgs{});      \
-  } while (0)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   profile_events(&ev0, &ev1);
   if (ev0 && ev1) KB_CUDA_TRY(cudaEventRecord(ev0, st));
-  if (T <= 16) KB_SEARCH_LAUNCH(16, 1);
-  else if (T <= 32) KB_SEARCH_LAUNCH(32, 1);
-  else if (T <= 64) KB_SEARCH_LAUNCH(0, 2);
-  else KB_SEARCH_LAUNCH(0, 4);
-#undef KB_SEARCH_LAUNCH
-  KB_LAUNCH_CHECK("search_kernel");
+  rc = launch_search_single(sp, st);
+  if (rc != KB_OK) return rc;
   if (ev0 && ev1) KB_CUDA_TRY(cudaEventRecord(ev1, st));
   return KB_OK;
 }
@@ -1722,8 +1741,24 @@ __global__ void batch_reset_kernel(Ctrl* ctrl, unsigned int* done_tiles,
   }
 }
 
+__global__ void stack_done_kernel(unsigned long long* done_ns) { *done_ns = globaltimer_ns(); }
+
+// Totals of the concurrent mode: each stack's search counted into its own control block.
+__global__ void batch_sum_kernel(Ctrl* const* __restrict__ ctrls, int n, Ctrl* total) {
+  unsigned long long ev = 0, ins = 0;
+  unsigned int err = 0;
+  for (int k = 0; k < n; ++k) {
+    ev += ctrls[k]->evals;
+    ins += ctrls[k]->inserts;
+    err |= ctrls[k]->err;
+  }
+  total->evals = ev;
+  total->inserts = ins;
+  total->err = err;
+}
+
 struct BatchTables {
-  size_t args, maps, tile_base, done_tiles, done_ns, start_ns, ctrl, total;
+  size_t args, maps, tile_base, done_tiles, done_ns, start_ns, ctrl, ctrls, total;
 };
 
 static BatchTables batch_tables(int n) {
@@ -1741,6 +1776,7 @@ static BatchTables batch_tables(int n) {
   b.done_ns = take(sizeof(unsigned long long) * (size_t)n);
   b.start_ns = take(sizeof(unsigned long long));
   b.ctrl = take(256);
+  b.ctrls = take(sizeof(Ctrl*) * (size_t)n);
   b.total = o;
   return b;
 }
@@ -1762,6 +1798,9 @@ struct kb_batch {
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   unsigned int graph_kernels = 0;
+  static constexpr int NS = 4;     // streams of the concurrent mode
+  cudaStream_t cs[NS] = {};
+  cudaEvent_t fork = nullptr, join[NS] = {};
 };
 
 namespace kb {
@@ -1790,6 +1829,7 @@ static int write_tables(kb_batch* b) {
   std::vector<SearchArgs> args(n);
   std::vector<TmapSet> maps(n);
   std::vector<int> base(n + 1, 0);
+  std::vector<Ctrl*> ctrls(n);
   Ctrl* ctrl = reinterpret_cast<Ctrl*>(b->ws + b->tb.ctrl);
   for (int k = 0; k < n; ++k) {
     StackPrep& sp = b->sp[idx[k]];
@@ -1799,6 +1839,7 @@ static int write_tables(kb_batch* b) {
     const bool ordered = b->sch.tile_order && sp.A.ntiles > 1 && sp.A.ntiles <= S_ORDER_MAX;
     args[k].order = ordered ? reinterpret_cast<int32_t*>(sp.ws + sp.L.torder) : nullptr;
     maps[k] = sp.maps;
+    ctrls[k] = sp.A.ctrl;
     base[k + 1] = base[k] + sp.A.ntiles;
   }
   b->total_tiles = base[n];
@@ -1807,6 +1848,8 @@ static int write_tables(kb_batch* b) {
   KB_CUDA_TRY(cudaMemcpy(b->ws + b->tb.maps, maps.data(), sizeof(TmapSet) * n,
                          cudaMemcpyHostToDevice));
   KB_CUDA_TRY(cudaMemcpy(b->ws + b->tb.tile_base, base.data(), sizeof(int) * (n + 1),
+                         cudaMemcpyHostToDevice));
+  KB_CUDA_TRY(cudaMemcpy(b->ws + b->tb.ctrls, ctrls.data(), sizeof(Ctrl*) * n,
                          cudaMemcpyHostToDevice));
   return KB_OK;
 }
@@ -1820,6 +1863,28 @@ static int batch_enqueue(kb_batch* b, cudaStream_t st) {
   batch_reset_kernel<<<(n + 255) / 256, 256, 0, st>>>(ctrl, done_tiles, done_ns, start_ns, n,
                                                       b->te_total);
   KB_LAUNCH_CHECK("batch_reset_kernel");
+  if (b->sch.mode == 1) {
+    // concurrent per-stack launches on the batch's streams: a stack's kernel starts on the SMs
+    // that the previous one's last tiles leave idle
+    KB_CUDA_TRY(cudaEventRecord(b->fork, st));
+    for (int q = 0; q < kb_batch::NS; ++q) KB_CUDA_TRY(cudaStreamWaitEvent(b->cs[q], b->fork, 0));
+    for (int k = 0; k < n; ++k) {
+      cudaStream_t q = b->cs[k % kb_batch::NS];
+      StackPrep& sp = b->sp[b->order[k]];
+      int rc = launch_prep(sp, b->sch, q);
+      if (rc == KB_OK) rc = launch_search_single(sp, q);
+      if (rc != KB_OK) return rc;
+      stack_done_kernel<<<1, 1, 0, q>>>(done_ns + k);
+      KB_LAUNCH_CHECK("stack_done_kernel");
+    }
+    for (int q = 0; q < kb_batch::NS; ++q) {
+      KB_CUDA_TRY(cudaEventRecord(b->join[q], b->cs[q]));
+      KB_CUDA_TRY(cudaStreamWaitEvent(st, b->join[q], 0));
+    }
+    batch_sum_kernel<<<1, 1, 0, st>>>(reinterpret_cast<Ctrl* const*>(b->ws + b->tb.ctrls), n, ctrl);
+    KB_LAUNCH_CHECK("batch_sum_kernel");
+    return KB_OK;
+  }
   for (int k = 0; k < n; ++k) {
     int rc = launch_prep(b->sp[b->order[k]], b->sch, st);
     if (rc != KB_OK) return rc;
@@ -1904,6 +1969,11 @@ extern "C" int kb_batch_create(const kb_stack* stacks, int n, void* workspace, s
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->gstream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  for (int q = 0; q < kb_batch::NS && e == cudaSuccess; ++q) {
+    e = cudaStreamCreateWithFlags(&b->cs[q], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[q], cudaEventDisableTiming);
+  }
   if (e != cudaSuccess) {
     kb_batch_destroy(b);
     return fail(KB_ERR_CUDA, "kb_batch_create: %s", cudaGetErrorString(e));
@@ -2010,6 +2080,9 @@ extern "C" int kb_batch_autotune(kb_batch* b, void* stream, int reps, kb_schedul
     std::vector<kb_schedule> cand;
     if (pass == 0) {
       kb_schedule c = cur;
+      c.mode = 1 - cur.mode;
+      cand.push_back(c);
+      c = cur;
       c.stack_order = 1 - cur.stack_order;
       cand.push_back(c);
     } else if (pass == 1) {
@@ -2077,6 +2150,11 @@ extern "C" void kb_batch_destroy(kb_batch* b) {
   if (b->ev_in) cudaEventDestroy(b->ev_in);
   if (b->ev_out) cudaEventDestroy(b->ev_out);
   if (b->gstream) cudaStreamDestroy(b->gstream);
+  if (b->fork) cudaEventDestroy(b->fork);
+  for (int q = 0; q < kb_batch::NS; ++q) {
+    if (b->cs[q]) cudaStreamDestroy(b->cs[q]);
+    if (b->join[q]) cudaEventDestroy(b->join[q]);
+  }
   delete b;
 }
 

@@ -84,8 +84,8 @@ def test_batch_equals_per_stack_search(cuda_device, batch_case):
 def test_batch_graph_replay_and_schedules(cuda_device, batch_case):
     stacks, ref = batch_case
     b = kb.Batch(stacks)
-    for sched in (kb.Schedule(), kb.Schedule(tile_order=0, stack_order=0),
-                  kb.Schedule(hot_nu2=9.0, score_span=128, stack_order=0),
+    for sched in (kb.Schedule(), kb.Schedule(mode=0), kb.Schedule(tile_order=0, stack_order=0),
+                  kb.Schedule(mode=0, hot_nu2=9.0, score_span=128, stack_order=0),
                   kb.Schedule(score_span=0)):
         b.schedule = sched
         assert b.schedule == sched
@@ -107,6 +107,8 @@ def test_batch_graph_replay_and_schedules(cuda_device, batch_case):
         b.schedule = kb.Schedule(tile_order=2)
     with pytest.raises(kb.KbError):
         b.schedule = kb.Schedule(hot_nu2=0.0)
+    with pytest.raises(kb.KbError):
+        b.schedule = kb.Schedule(mode=3)
 
 
 def test_batch_stacks_against_oracle(cuda_device, batch_case):
@@ -123,9 +125,11 @@ def test_batch_stacks_against_oracle(cuda_device, batch_case):
         compare_search(gpu_result_numpy(res[i]), o, sp.lh_min)
 
 
-def test_batch_completion_times(cuda_device, batch_case):
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_completion_times(cuda_device, batch_case, mode):
     stacks, _ = batch_case
     b = kb.Batch(stacks)
+    b.schedule = kb.Schedule(mode=mode)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     b.run()
