@@ -842,8 +842,8 @@ def run_batch(args):
         "config": {"workload": "batch64: 64 stacks, sizes uniform in {512x512, 1024x2048, "
                                "2046x4094}, T uniform in 10..40, grids of 4096..32768 "
                                "trajectories (90-500 px/day, +-0.3 rad), K=8, LH'>=10, "
-                               "min_obs=min(15, T/2); one persistent launch per step, "
-                               "CUDA-graph replay, autotuned schedule",
+                               "min_obs=min(15, T/2); CUDA-graph replay of the batch, "
+                               "autotuned schedule",
                    "stacks": len(stacks), "sizes": sizes, "te_per_step": te_step,
                    "l2": "inputs larger than L2 (psi+phi %.1f GB)" %
                          (sum(2 * s["psi"].numel() * 4 for s in stacks) / 1e9),
@@ -857,7 +857,9 @@ def run_batch(args):
                                  "p99": float(np.percentile(pl, 99)), "max": float(pl.max())},
                        "definition": "completion of each stack's search from the start of the "
                                      "step (batch: device timestamps; plain: CUDA events)"},
-        "schedule": {"tile_order": sched.tile_order, "hot_nu2": sched.hot_nu2,
+        "schedule": {"mode": ("concurrent per-stack launches" if sched.mode == 1 else
+                              "one persistent launch"),
+                     "tile_order": sched.tile_order, "hot_nu2": sched.hot_nu2,
                      "score_span": sched.score_span, "stack_order": sched.stack_order,
                      "autotune_s": tune_s},
         "results_identical_to_plain": bool(same),
