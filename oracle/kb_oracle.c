@@ -587,7 +587,8 @@ int kbo_stamp_moments(const double* S, int r, const double* lim, double* out) {
  * t0 + dt (the last epoch): |p_i - p_j| <= r at both, with p(dt) = (x0 + vx dt, y0 + vy dt).
  * Walking the candidates in order, i is kept unless it duplicates an already kept j; rep[i] is i
  * when kept, else the first (lowest-index) kept j it duplicates.  valid (nullable): candidates
- * with valid[i] == 0 take no part (keep 0, rep -1). */
+ * with valid[i] == 0 take no part (keep 0, rep -1), nor do candidates whose start pixel lies
+ * outside 0 .. 2^20 - 1 on either axis (the placeholders of empty survivor slots). */
 static int kbo_dup(const int32_t* x0, const int32_t* y0, const float* vx, const float* vy,
                    int i, int j, double dt, double r2) {
   double dx0 = (double)x0[i] - (double)x0[j], dy0 = (double)y0[i] - (double)y0[j];
@@ -605,6 +606,7 @@ void kbo_cluster(const int32_t* x0, const int32_t* y0, const float* vx, const fl
     keep[i] = 0;
     rep[i] = -1;
     if (valid && !valid[i]) continue;
+    if (x0[i] < 0 || x0[i] >= (1 << 20) || y0[i] < 0 || y0[i] >= (1 << 20)) continue;
     int found = -1;
     for (int j = 0; j < i && found < 0; ++j)
       if (keep[j] && kbo_dup(x0, y0, vx, vy, i, j, dt, r2)) found = j;
