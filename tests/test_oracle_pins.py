@@ -806,6 +806,10 @@ def test_cluster_hand_cases():
     keep, rep = oracle.cluster([0, 3, 6], [0, 0, 0], [10.0] * 3, [0.0] * 3, dt, r,
                                valid=[1, 0, 1])
     assert keep.tolist() == [True, False, True] and rep.tolist() == [0, -1, 2]
+    # a placeholder start far outside any image takes no part, even at a duplicate's position
+    keep, rep = oracle.cluster([-(1 << 28), -(1 << 28), 5], [-(1 << 28), -(1 << 28), 5],
+                               [1.0] * 3, [0.0] * 3, dt, r)
+    assert keep.tolist() == [False, False, True] and rep.tolist() == [-1, -1, 2]
     # the representative is the first kept duplicate, not the nearest
     keep, rep = oracle.cluster([0, 6, 3], [0, 0, 0], [0.0] * 3, [0.0] * 3, dt, r)
     assert keep.tolist() == [True, True, False] and rep.tolist() == [0, 1, 0]
