@@ -67,6 +67,22 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x, world, device):
+    """The largest of the ranks' values of x (every rank gets it); x itself when world == 1."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_seed(base, rank, stride=100):
+    """Seed of rank `rank`'s own stack: ranks search independent stacks (weak scaling)."""
+    return base + stride * rank
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -337,7 +353,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     c = CONFIGS[args.workload]
-    s = make_stack(args.workload, seed=c["seed"] + 100 * rank)
+    s = make_stack(args.workload, seed=rank_seed(c["seed"], rank))
     T, H, W = s.img.shape
     n_traj = len(s.vx)
     K = c["K"]
@@ -411,10 +427,7 @@ def run_ours(args):
     launches = kb.launch_count() - launches0
     ms = e0.elapsed_time(e1)
     clocks = clk.summary()
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, world, dev)
     value = world * te_step * args.steps / (ms_max / 1e3)
     stats = kb.search_stats(ws)
 
@@ -434,10 +447,8 @@ def run_ours(args):
         barrier()
         e2e_ms = e0.elapsed_time(e1)
         d2h = sum(v.numel() * v.element_size() for v in res_host.values())
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * te_step * args.steps / (float(t.item()) / 1e3), "unit": "TE/s",
+        e2e_max = max_over_ranks(e2e_ms, world, dev)
+        e2e = {"value": world * te_step * args.steps / (e2e_max / 1e3), "unit": "TE/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "survivors_per_step": int(res_host["count"].item())}
 
@@ -527,7 +538,7 @@ def run_refine(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     c = CONFIGS[args.workload]
-    s = make_stack(args.workload, seed=c["seed"] + 100 * rank)
+    s = make_stack(args.workload, seed=rank_seed(c["seed"], rank))
     T, H, W = s.img.shape
     sp = kb.SearchParams(k=c["K"], lh_min=c["lh_min"], min_obs=c["min_obs"])
     rp = kb.RefineParams(n_steps=args.refine_steps)
@@ -594,10 +605,7 @@ def run_refine(args):
         # (200 ms period) sees the timed region
         per = e0.elapsed_time(e1) / max(1, args.warmup)
         args.steps = max(3, int(math.ceil(1500.0 / max(per, 1e-3))))
-        if world > 1:   # every rank times the same number of steps
-            t = torch.tensor([args.steps], dtype=torch.int64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            args.steps = int(t.item())
+        args.steps = int(max_over_ranks(args.steps, world, dev))  # the same on every rank
         ev = stage_events(args.steps)
 
     def barrier():
@@ -616,10 +624,7 @@ def run_refine(args):
     launches = kb.launch_count() - launches0
     ms = e0.elapsed_time(e1)
     clocks = clk.summary()
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, world, dev)
     evals = rp.n_steps + 1 + 2
     te_step = n * T * evals
     value = world * te_step * args.steps / (ms_max / 1e3)
@@ -676,10 +681,8 @@ def run_refine(args):
         e1.record(stream)
         barrier()
         d2h = sum(x.numel() * 4 for x in back)
-        t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * te_step * args.steps / (float(t.item()) / 1e3), "unit": "TE/s",
+        e2e_max = max_over_ranks(e0.elapsed_time(e1), world, dev)
+        e2e = {"value": world * te_step * args.steps / (e2e_max / 1e3), "unit": "TE/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     if rank != 0:
@@ -753,7 +756,7 @@ def run_batch(args):
     specs = batch_specs()
     stacks = []
     for (H, W, T, ns, na, nm, seed) in specs:
-        st = make_stack_torch(H, W, T, ns, na, nm, seed + 100000 * rank, dev)
+        st = make_stack_torch(H, W, T, ns, na, nm, rank_seed(seed, rank, 100000), dev)
         psi, phi = kb.make_psi_phi(st["img"], st["var"], st["mask"], st["psf"])
         stacks.append(dict(psi=psi, phi=phi, times=st["times"], vx=st["vx"], vy=st["vy"],
                            params=kb.SearchParams(k=8, lh_min=10.0, min_obs=min(15, T // 2))))

@@ -1,0 +1,79 @@
+"""The bench's multi-rank host logic on CPU with the gloo backend (world size 2): each rank
+searches its own stack (weak scaling, no collective on the data path), the timed region's
+duration is the maximum over ranks, every rank agrees on the step count, and under torchrun the
+reference arm runs on rank 0 only."""
+import os
+import socket
+import sys
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    r, w, lr = bench.dist_env()
+    got = {"env": (r, w, lr),
+           "ms_max": bench.max_over_ranks(10.0 + 5.0 * rank, world, "cpu"),
+           "steps": bench.max_over_ranks(3 + rank, world, "cpu"),
+           "seed": bench.rank_seed(5, rank)}
+    dist.barrier()
+    dist.destroy_process_group()
+    out.put((rank, got))
+
+
+def test_max_over_ranks_and_rank_seeds_gloo():
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = dict(q.get(timeout=120) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for r in range(world):
+        assert res[r]["env"] == (r, world, r)
+        assert res[r]["ms_max"] == 15.0          # the slowest rank's time, on every rank
+        assert res[r]["steps"] == 4.0
+    assert res[0]["seed"] != res[1]["seed"]       # independent stacks
+
+
+def test_single_rank_needs_no_process_group():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(7.5, 1, "cpu") == 7.5
+    assert bench.rank_seed(5, 0) == 5
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+
+    class A:
+        workload = "decam"
+        warmup = 1
+        steps = 1
+        cpu_seconds = 0.1
+        gpus = 2
+
+    bench.run_reference(A())   # returns at once: no oracle work, nothing printed
+    assert capsys.readouterr().out == ""
