@@ -187,7 +187,7 @@ def oracle_rate(target_s, workload):
         if dt * 2 > target_s or side >= 64:
             break
         side *= 2
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    threads = oracle.get_threads()
     return dict(value=te / dt, seconds=dt, te=te, side=side, threads=threads, T=T,
                 n_traj=len(vx), H=H, W=W)
 
@@ -459,7 +459,8 @@ def run_ours(args):
         return
 
     peaks, peaks_src = measured_peaks()
-    k_ms = statistics.mean(kernel_ms)
+    k_ms = statistics.median(kernel_ms)
+    l2_gbs = kb.l2_read_bandwidth(device=dev)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_max = float(peaks.get("sm_max_mhz", 2032.0))
     # Shared-memory load roofline of the bound pass: one 128-byte wavefront per SM per clock;
@@ -486,18 +487,35 @@ def run_ours(args):
                                           "hbm_peak_gbs": peaks["hbm_gbs"],
                                           "note": "8 B/TE psi+phi gather rate vs the measured HBM "
                                                   "copy peak (%s); above 1 because the bound "
-                                                  "pass reuses staged tiles on chip" % peaks_src}},
+                                                  "pass reuses staged tiles on chip" % peaks_src},
+                     "l2_gather": {"bytes_per_te": 8, "l2_read_gbs": l2_gbs,
+                                   "achieved_gbs": te_per_s_kernel * 8 / 1e9,
+                                   "frac": te_per_s_kernel * 8 / 1e9 / l2_gbs,
+                                   "note": "the naive gather roofline (8 B of psi+phi per "
+                                           "trajectory-epoch against the L2 read bandwidth "
+                                           "measured by kb_l2_probe at bench start); above 1 "
+                                           "because the exact bound reads 2 B per "
+                                           "trajectory-epoch from staged shared memory and only "
+                                           "0.2% of pairs are gathered in full"}},
         "search_stats": {"te": stats[0], "full_evals": stats[1], "inserts": stats[2],
                          "full_eval_frac": stats[1] / max(1, stats[0] / T)},
         "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
     }
     if not args.no_cpu_baseline:
+        import oracle
         r = oracle_rate(args.cpu_seconds, args.workload)
+        n_thr = oracle.get_threads()
+        oracle.set_threads(1)
+        r1 = oracle_rate(args.cpu_seconds / 3, args.workload)
+        oracle.set_threads(n_thr)
         line["cpu_baseline"] = {
             "value": r["value"], "unit": "TE/s", "cores": r["threads"], "kind": "oracle",
             "sample": "FP64 C oracle search on a %dx%d start-pixel window (x %d trajectories x %d "
                       "epochs) of the workload's likelihood planes, %.1f s" %
-                      (r["side"], r["side"], r["n_traj"], r["T"], r["seconds"])}
+                      (r["side"], r["side"], r["n_traj"], r["T"], r["seconds"]),
+            "single_thread": {"value": r1["value"], "unit": "TE/s",
+                              "sample": "%dx%d window, one thread, %.1f s" %
+                                        (r1["side"], r1["side"], r1["seconds"])}}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()

@@ -465,6 +465,16 @@ KB_API int kb_candidate_params(const int32_t* cand_pix, const int32_t* cand_slot
                                const float* vx, const float* vy, int x_lo, int y_lo, int wx,
                                float* out_params, uint32_t* out_keep, void* stream);
 
+/*
+ * kb_l2_probe -- measurement utility, not part of the method: reads the device buffer `buf`
+ * (`bytes`, 16-byte aligned; choose it smaller than the L2 so that it stays resident) `reps`
+ * times with 16-byte loads cached in L2 only, from `blocks` blocks of 512 threads.  The caller
+ * times the call (CUDA events): bytes x reps / time is the L2 read bandwidth.  scratch: `blocks`
+ * floats (device), written only in a case that the probe data never meet.
+ */
+KB_API int kb_l2_probe(const void* buf, size_t bytes, int reps, float* scratch, int blocks,
+                       void* stream);
+
 /* Number of kernels this library has launched in the process so far (all entry points). */
 KB_API unsigned long long kb_launch_count(void);
 

@@ -31,6 +31,7 @@
  *   R13 bilinear sampling: pixel centres at integer coordinates, cell = floor of the position.
  */
 #include <math.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -618,3 +619,7 @@ void kbo_cluster(const int32_t* x0, const int32_t* y0, const float* vx, const fl
     }
   }
 }
+
+/* Thread count of the OpenMP loops (timing of the CPU baseline). */
+void kbo_set_threads(int n) { omp_set_num_threads(n > 0 ? n : 1); }
+int kbo_get_threads(void) { return omp_get_max_threads(); }

@@ -47,6 +47,10 @@ def lib():
         _LIB.kbo_traj_eval_subpixel.argtypes = [p, p, p, i, i, i, p, d, d, d, d, p, p, p]
         _LIB.kbo_traj_vjp.restype = i
         _LIB.kbo_traj_vjp.argtypes = [p, p, p, i, i, i, p, d, d, d, d, d, d, p, p, p]
+        _LIB.kbo_set_threads.restype = None
+        _LIB.kbo_set_threads.argtypes = [i]
+        _LIB.kbo_get_threads.restype = i
+        _LIB.kbo_get_threads.argtypes = []
         _LIB.kbo_cluster.restype = None
         _LIB.kbo_cluster.argtypes = [p, p, p, p, p, i, d, d, p, p]
         _LIB.kbo_stamp_moments.restype = i
@@ -287,3 +291,12 @@ def cluster(x0, y0, vx, vy, dt, radius, valid=None):
     lib().kbo_cluster(_ptr(x0), _ptr(y0), _ptr(vx), _ptr(vy), _ptr(va), n, float(dt),
                       float(radius), _ptr(keep), _ptr(rep))
     return keep.astype(bool), rep
+
+
+def set_threads(n):
+    """OpenMP threads of the oracle's parallel loops."""
+    lib().kbo_set_threads(int(n))
+
+
+def get_threads():
+    return int(lib().kbo_get_threads())

@@ -275,6 +275,27 @@ def candidate_tracks(pix, slot, result, vx, vy, window=None, stream=None):
     return x0, y0, ovx, ovy, traj
 
 
+def l2_read_bandwidth(mbytes=64, reps=40, device=None):
+    """L2 read bandwidth in GB/s from kb_l2_probe on a resident buffer of `mbytes` MB (best of 3
+    timed calls after a warm-up)."""
+    dev = torch.device("cuda") if device is None else device
+    buf = torch.ones(mbytes * (1 << 20) // 4, dtype=torch.float32, device=dev)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks = sms * 4
+    scratch = torch.zeros(blocks, dtype=torch.float32, device=dev)
+    s = _stream(None)
+    check(lib().kb_l2_probe(_ptr(buf), buf.numel() * 4, 2, _ptr(scratch), blocks, s))
+    best = 0.0
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        check(lib().kb_l2_probe(_ptr(buf), buf.numel() * 4, reps, _ptr(scratch), blocks, s))
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, buf.numel() * 4 * reps / (e0.elapsed_time(e1) / 1e3) / 1e9)
+    return best
+
+
 def launch_count():
     """Kernels launched by the library in this process so far."""
     return int(lib().kb_launch_count())

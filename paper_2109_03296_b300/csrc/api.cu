@@ -69,3 +69,38 @@ extern "C" void kb_search_params_default(kb_search_params* p, int H, int W) {
   p->y_lo = 0;
   p->y_hi = H;
 }
+
+// ------------------------------------------------------------------------------------------------
+// L2 read probe (measurement utility): reads an L2-resident buffer `reps` times with 16-byte
+// loads from a persistent grid; the caller times it (bytes * reps / time = L2 read bandwidth).
+// ------------------------------------------------------------------------------------------------
+namespace kb {
+__global__ void l2_probe_kernel(const float4* __restrict__ buf, size_t n_vec, int reps,
+                                float* __restrict__ out) {
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (int r = 0; r < reps; ++r)
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_vec; i += stride) {
+      const float4 v = __ldcg(buf + i);  // cached in L2 only
+      acc.x += v.x;
+      acc.y += v.y;
+      acc.z += v.z;
+      acc.w += v.w;
+    }
+  const float s = acc.x + acc.y + acc.z + acc.w;
+  if (s == 1.2345678e-30f) out[blockIdx.x] = s;  // keeps the loads; never true for the probe data
+}
+}  // namespace kb
+
+extern "C" int kb_l2_probe(const void* buf, size_t bytes, int reps, float* scratch, int blocks,
+                           void* stream) {
+  using namespace kb;
+  if (!buf || !scratch || bytes < 16 || reps < 1 || blocks < 1)
+    return fail(KB_ERR_INVALID_ARG, "kb_l2_probe: bad arguments");
+  if (reinterpret_cast<uintptr_t>(buf) % 16)
+    return fail(KB_ERR_INVALID_ARG, "kb_l2_probe: buffer not 16-byte aligned");
+  l2_probe_kernel<<<blocks, 512, 0, static_cast<cudaStream_t>(stream)>>>(
+      static_cast<const float4*>(buf), bytes / 16, reps, scratch);
+  KB_LAUNCH_CHECK("l2_probe_kernel");
+  return KB_OK;
+}
