@@ -211,6 +211,41 @@ def test_search_parity_decam_full_size(cuda_device):
     assert filled > 0
 
 
+def test_search_parity_full_config_grid(cuda_device):
+    """The full-scale configuration's shape -- T = 100 over five nights (warp-per-pair
+    evaluation, four epochs per lane), the paper's 512 x 256 velocity grid (131072 trajectories,
+    92-550 px/day, +-pi/10), 1% masked pixels, min_obs 50 -- on a 384 x 2560 image (wide
+    enough that movers stay in it for most of the 4 days); the oracle on windows around the
+    brightest movers that start in the left third, and at a corner."""
+    name = "full"
+    psi, phi, times, vx, vy, movers = make_likelihood_stack(name, H=384, W=2560, n_movers=60)
+    c = CONFIGS[name]
+    sp = kb.SearchParams(k=c["K"], lh_min=c["lh_min"], min_obs=c["min_obs"])
+    T, H, W = psi.shape
+    assert T == 100 and len(vx) == 131072
+    res = kb.search(_cuda(psi), _cuda(phi), times, _cuda(vx), _cuda(vy), sp)
+    torch.cuda.synchronize()
+    assert kb.search_stats(res["workspace"])[3] == 0
+    g_all = gpu_result_numpy(res)
+    del res
+    torch.cuda.empty_cache()
+    inside = (movers["x0"] > 8) & (movers["x0"] < W // 3) & (movers["y0"] > 8) & \
+        (movers["y0"] < H - 8)
+    order = [i for i in np.argsort(-movers["snr"]) if inside[i]]
+    wins = []
+    for i in order[:2]:
+        x0, y0 = int(movers["x0"][i]), int(movers["y0"][i])
+        wins.append((x0 - 3, x0 + 3, y0 - 3, y0 + 3))
+    wins.append((0, 5, H - 5, H))
+    filled = 0
+    for (xa, xb, ya, yb) in wins:
+        o = oracle.search(psi, phi, times, vx, vy, _oracle_params(sp), window=(xa, xb, ya, yb))
+        g = {k: v[ya:yb, xa:xb] for k, v in g_all.items()}
+        compare_search(g, o, sp.lh_min)
+        filled += int((o["idx"] >= 0).sum())
+    assert filled > 0
+
+
 # ------------------------------------------------------------------------------------------------
 # stamps and the handoff
 # ------------------------------------------------------------------------------------------------
