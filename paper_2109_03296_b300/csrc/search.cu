@@ -29,14 +29,14 @@
 //    back to direct global loads.
 //
 //  * Full evaluation.  After each chunk, the pairs whose bound passes are appended to a queue
-//    in shared memory (with a per-pixel linked list); the queue is evaluated in one batch once
+//    in shared memory; the queue is evaluated in one batch once
 //    it holds S_FLUSH_MIN pairs (and at the end of a tile), so every thread has work and no
 //    warp idles at a barrier for a lone candidate.  For T <= 32 one thread evaluates one pair:
 //    gather into registers, bitonic sorting network on the lightcurve, percentiles, clip, sums in
 //    epoch order (identical tracks give bit-identical LH').  For T > 32 one warp evaluates one
-//    pair with lanes over epochs.  The owner thread of each start pixel then walks its list and
-//    inserts the results into the pixel's output list (LH' descending, trajectory index
-//    ascending).
+//    pair with lanes over epochs.  Results that reach lh_min (a small fraction) are pushed onto
+//    a per-pixel list; the owner thread of each start pixel then walks its list and inserts
+//    them into the pixel's output list (LH' descending, trajectory index ascending).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
@@ -107,7 +107,8 @@ struct EvalParams {
 
 // Workspace layout (offsets in bytes from the workspace base).
 struct WsLayout {
-  size_t ctrl, vbox, keys, counts, cursor, sorted, orig, offs, plan, bound, tkeys, torder, total;
+  size_t ctrl, vbox, keys, counts, cursor, sorted, orig, offs, vsort, dtf, plan, bound, pairs, tkeys,
+      torder, total;
   int n_pad, nchunk, Wp;
 };
 
@@ -130,8 +131,11 @@ static WsLayout ws_layout(int T, int H, int W, int n_traj) {
   L.sorted = take(sizeof(int32_t) * (size_t)n_traj);
   L.orig = take(sizeof(int32_t) * (size_t)L.n_pad);
   L.offs = take(sizeof(int2) * (size_t)L.n_pad * T);
+  L.vsort = take(sizeof(float2) * (size_t)L.n_pad);
+  L.dtf = take(sizeof(float) * KB_MAX_T);
   L.plan = take(sizeof(PlanRec) * (size_t)L.nchunk * T);
   L.bound = take(sizeof(uint32_t) * (size_t)T * (H + 1) * L.Wp);
+  L.pairs = take(sizeof(float2) * (size_t)T * H * W);
   L.tkeys = take(sizeof(unsigned long long) * S_ORDER_MAX);
   L.torder = take(sizeof(int32_t) * S_ORDER_MAX);
   L.total = o;
@@ -286,12 +290,16 @@ __device__ __forceinline__ int track_offset(float v, float dt) {
 
 __global__ void plan_offsets_kernel(const float* __restrict__ vx, const float* __restrict__ vy,
                                     const int32_t* __restrict__ sorted, int n, int n_pad, int T,
-                                    SearchConsts cs, int32_t* orig, int2* offs) {
+                                    SearchConsts cs, int32_t* orig, int2* offs, float2* vsort,
+                                    float* dtf) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s == 0)
+    for (int t = 0; t < T; ++t) dtf[t] = cs.dt[t];
   if (s >= n_pad) return;
   int j = sorted[s < n ? s : n - 1];
   orig[s] = s < n ? j : -1;
   float x = vx[j], y = vy[j];
+  vsort[s] = make_float2(x, y);
   for (int t = 0; t < T; ++t)
     offs[(size_t)s * T + t] = make_int2(track_offset(x, cs.dt[t]), track_offset(y, cs.dt[t]));
 }
@@ -370,6 +378,15 @@ __global__ void bound_prep_kernel(const float* __restrict__ psi, const float* __
     const unsigned short hi = half_round_up(nu2_at(psi, phi, H, W, plane, r, x));
     bound[i] = (uint32_t)lo | ((uint32_t)hi << 16);
   }
+}
+
+// (psi, phi) interleaved, [T][H][W] float2: a full evaluation gathers both with one 8-byte load
+// per epoch (one sector per lane instead of two).
+__global__ void pair_planes_kernel(const float* __restrict__ psi, const float* __restrict__ phi,
+                                   size_t n, float2* __restrict__ pairs) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    pairs[i] = make_float2(__ldg(psi + i), __ldg(phi + i));
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -506,10 +523,10 @@ __device__ __forceinline__ float warp_sum(float v) {
 }
 
 // Writes rec[0..7]: L' (NaN when the pair is not eligible), alpha, nvalid | nkept << 16,
-// mask words.  All lanes take part; lane 0 writes.
+// mask words.  All lanes take part; lane 0 writes and gets L' back (the other lanes get NaN).
 template <int J>
-__device__ void eval_pair_warp(const float* __restrict__ psi, const float* __restrict__ phi,
-                               const EvalParams& ep, int x0, int y0,
+__device__ float eval_pair_warp(const float2* __restrict__ pairs, const EvalParams& ep, int x0,
+                               int y0,
                                const int2* __restrict__ off, uint32_t* rec, int lane) {
   float ps[J], ph[J], a[J];
   bool valid[J];
@@ -524,8 +541,8 @@ __device__ void eval_pair_warp(const float* __restrict__ psi, const float* __res
       const int2 o = __ldg(off + t);
       const int x = x0 + o.x, y = y0 + o.y;
       if (x >= 0 && x < ep.W && y >= 0 && y < ep.H) {
-        const size_t i = (size_t)t * plane + (size_t)y * ep.W + x;
-        const float p = __ldg(psi + i), f = __ldg(phi + i);
+        const float2 pf = __ldg(pairs + (size_t)t * plane + (size_t)y * ep.W + x);
+        const float p = pf.x, f = pf.y;
         if (f > 0.0f && isfinite(p) && isfinite(f)) {
           ps[j] = p;
           ph[j] = f;
@@ -542,7 +559,7 @@ __device__ void eval_pair_warp(const float* __restrict__ psi, const float* __res
       rec[0] = __float_as_uint(NAN);
       rec[2] = (uint32_t)nvalid;
     }
-    return;
+    return NAN;
   }
   bool keep[J];
   if (ep.clip) {
@@ -578,8 +595,9 @@ __device__ void eval_pair_warp(const float* __restrict__ psi, const float* __res
   }
   sp = warp_sum(sp);
   sf = warp_sum(sf);
+  float L = NAN;
   if (lane == 0) {
-    float L = NAN, alpha = 0.0f;
+    float alpha = 0.0f;
     if (nkept > 0 && sf > 0.0f) {
       L = __fdiv_rn(sp, __fsqrt_rn(sf));
       alpha = __fdiv_rn(sp, sf);
@@ -590,6 +608,7 @@ __device__ void eval_pair_warp(const float* __restrict__ psi, const float* __res
 #pragma unroll
     for (int j = 0; j < 4; ++j) rec[3 + j] = mw[j];
   }
+  return L;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -634,24 +653,28 @@ __device__ __forceinline__ float sorted_percentile(const float (&loc)[NT], int n
   return a + f * (b - a);
 }
 
-__device__ __forceinline__ bool gather_pair(const float* __restrict__ psi,
-                                            const float* __restrict__ phi, const EvalParams& ep,
-                                            size_t plane, int t, int x, int y, float& p,
-                                            float& f) {
+__device__ __forceinline__ bool gather_pair(const float2* __restrict__ pairs,
+                                            const EvalParams& ep, size_t plane, int t, int x,
+                                            int y, float& p, float& f) {
   if (x < 0 || x >= ep.W || y < 0 || y >= ep.H) return false;
-  const size_t i = (size_t)t * plane + (size_t)y * ep.W + x;
-  p = __ldg(psi + i);
-  f = __ldg(phi + i);
+  const float2 pf = __ldg(pairs + (size_t)t * plane + (size_t)y * ep.W + x);
+  p = pf.x;
+  f = pf.y;
   return f > 0.0f && isfinite(p) && isfinite(f);
 }
 
 // One pair, one thread.  psi_t and phi_t stay in registers from the single gather; the
 // lightcurve value of an epoch (flux psi/phi, or psi/sqrt(phi) when clip_on) is recomputed with
 // the same IEEE operations where it is needed (sort input, clip test), so no epoch is read twice.
+//
+// The track offsets are recomputed from the pair's velocity with the plan's own arithmetic
+// (track_offset on the same float dt), so they equal the stored ones bit for bit; this replaces
+// T scattered offset loads per pair (one per lane and epoch) by one velocity load and broadcast
+// loads of dt.  Returns L' (NaN when the pair is not eligible).
 template <int NT>
-__device__ void eval_pair_thread(const float* __restrict__ psi, const float* __restrict__ phi,
-                                 const EvalParams& ep, int x0, int y0,
-                                 const int2* __restrict__ off, uint32_t* rec) {
+__device__ float eval_pair_thread(const float2* __restrict__ pairs,
+                                  const EvalParams& ep, int x0, int y0, float2 v,
+                                  const float* __restrict__ dtf, uint32_t* rec) {
   float pv[NT], fv[NT];
   uint32_t vm = 0u;
   const size_t plane = (size_t)ep.H * ep.W;
@@ -660,9 +683,10 @@ __device__ void eval_pair_thread(const float* __restrict__ psi, const float* __r
     pv[t] = 0.0f;
     fv[t] = 0.0f;
     if (t < ep.T) {
-      const int2 o = __ldg(off + t);
+      const float dt = __ldg(dtf + t);
+      const int ox = track_offset(v.x, dt), oy = track_offset(v.y, dt);
       float p, f;
-      if (gather_pair(psi, phi, ep, plane, t, x0 + o.x, y0 + o.y, p, f)) {
+      if (gather_pair(pairs, ep, plane, t, x0 + ox, y0 + oy, p, f)) {
         vm |= 1u << t;
         pv[t] = p;
         fv[t] = f;
@@ -673,7 +697,7 @@ __device__ void eval_pair_thread(const float* __restrict__ psi, const float* __r
   if (nvalid < ep.min_obs || nvalid == 0) {
     rec[0] = __float_as_uint(NAN);
     rec[2] = (uint32_t)nvalid;
-    return;
+    return NAN;
   }
   const bool on_lh = ep.clip_on != 0;
   auto curve = [&](int t) {
@@ -719,6 +743,7 @@ __device__ void eval_pair_thread(const float* __restrict__ psi, const float* __r
   rec[2] = (uint32_t)nvalid | ((uint32_t)nkept << 16);
   rec[3] = km;
   rec[4] = rec[5] = rec[6] = 0u;
+  return L;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -727,9 +752,12 @@ __device__ void eval_pair_thread(const float* __restrict__ psi, const float* __r
 struct SearchArgs {
   const float* psi;
   const float* phi;
+  const float2* pairs;  // (psi, phi) interleaved, [T][H][W]
   const uint32_t* bound;
   const int32_t* orig;
   const int2* offs;
+  const float2* vsort;  // velocities in list order (thread evaluation recomputes the offsets)
+  const float* dtf;     // [T] epoch offsets t_t - t_0 as float, as used for the track offsets
   const PlanRec* plan;
   float* out_lh;
   float* out_flux;
@@ -783,8 +811,8 @@ struct SmemLayout {
   static constexpr size_t qtraj = rec + S_QCAP * S_REC_WORDS * sizeof(uint32_t);
   static constexpr size_t qpix = qtraj + S_QCAP * sizeof(int32_t);
   static constexpr size_t qnext = qpix + S_QCAP * sizeof(uint16_t);
-  static constexpr size_t head = qnext + S_QCAP * sizeof(int16_t);  // [pixel] list of queued pairs
-  static constexpr size_t filled = head + S_NPIX * sizeof(int16_t);
+  static constexpr size_t head = (qnext + S_QCAP * sizeof(int16_t) + 15) / 16 * 16;  // [pixel]
+  static constexpr size_t filled = head + S_NPIX * sizeof(int32_t);
   static constexpr size_t slots = (filled + S_NPIX + 15) / 16 * 16;          // S_D plan records
   static constexpr size_t sinfo = slots + S_D * sizeof(PlanRec);  // S_D x {offset, tile, bytes}
   static constexpr size_t full = sinfo + S_D * sizeof(int4);       // S_D mbarriers: data landed
@@ -1077,7 +1105,7 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
   int4* sinfo = reinterpret_cast<int4*>(smem + SmemLayout::sinfo);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + SmemLayout::full);
   uint64_t* empty = reinterpret_cast<uint64_t*>(smem + SmemLayout::empty);
-  int16_t* head = reinterpret_cast<int16_t*>(smem + SmemLayout::head);
+  int* head = reinterpret_cast<int*>(smem + SmemLayout::head);
   uint8_t* s_filled = reinterpret_cast<uint8_t*>(smem + SmemLayout::filled);
   unsigned int* s_qcount = reinterpret_cast<unsigned int*>(smem + SmemLayout::misc);
   unsigned int* s_evals = s_qcount + 1;
@@ -1183,22 +1211,30 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
         EvalParams ep_copy;
         if (BATCH) ep_copy = A.ep;
         const EvalParams& EP = BATCH ? ep_copy : A.ep;
-        const float* const e_psi = A.psi;
-        const float* const e_phi = A.phi;
+        const float2* const e_pairs = A.pairs;
         const int2* const e_offs = A.offs;
+        const float2* const e_vs = A.vsort;
+        const float* const e_dt = A.dtf;
+        // a result that reaches lh_min joins its pixel's list (pushed with one shared atomic);
+        // the others (almost all of them) are never looked at again
+        auto link = [&](int e, int pl) { q_next[e] = (int16_t)atomicExch(&head[pl], e); };
         auto by_thread = [&](auto nt) {
-          for (int e = tid; e < nq; e += S_CTHREADS)
-            eval_pair_thread<decltype(nt)::value>(e_psi, e_phi, EP, tx0 + (q_pix[e] & 31),
-                                                  ty0 + (q_pix[e] >> 5),
-                                                  e_offs + (size_t)q_traj[e] * T,
-                                                  recs + e * S_REC_WORDS);
+          for (int e = tid; e < nq; e += S_CTHREADS) {
+            const int pl = q_pix[e], j = q_traj[e];
+            const float L = eval_pair_thread<decltype(nt)::value>(
+                e_pairs, EP, tx0 + (pl & 31), ty0 + (pl >> 5), __ldg(e_vs + j), e_dt,
+                recs + e * S_REC_WORDS);
+            if (L >= lh_min) link(e, pl);
+          }
         };
         auto by_warp = [&](auto jj) {
-          for (int e = warp; e < nq; e += S_CWARPS)
-            eval_pair_warp<decltype(jj)::value>(e_psi, e_phi, EP, tx0 + (q_pix[e] & 31),
-                                                ty0 + (q_pix[e] >> 5),
-                                                e_offs + (size_t)q_traj[e] * T,
-                                                recs + e * S_REC_WORDS, lane);
+          for (int e = warp; e < nq; e += S_CWARPS) {
+            const int pl = q_pix[e];
+            const float L = eval_pair_warp<decltype(jj)::value>(
+                e_pairs, EP, tx0 + (pl & 31), ty0 + (pl >> 5),
+                e_offs + (size_t)q_traj[e] * T, recs + e * S_REC_WORDS, lane);
+            if (lane == 0 && L >= lh_min) link(e, pl);
+          }
         };
         if (BATCH) {
           if (T <= 16) by_thread(std::integral_constant<int, 16>{});
@@ -1211,6 +1247,11 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
           by_warp(std::integral_constant<int, J>{});
         }
         consumer_sync();
+        // every thread read the count before the evaluations: reset it while the lists are walked
+        if (tid == 0) {
+          atomicAdd(s_evals, (unsigned int)nq);
+          *s_qcount = 0u;
+        }
 #pragma unroll 1
         for (int i = 0; i < S_ROWS; ++i) {
           const int row = warp * S_ROWS + i;
@@ -1239,9 +1280,6 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
               if (ii == i) thr2[ii] = t2;
           }
         }
-        if (tid == 0) atomicAdd(s_evals, (unsigned int)nq);
-        consumer_sync();
-        if (tid == 0) *s_qcount = 0u;
         consumer_sync();
       };
 
@@ -1342,11 +1380,8 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
                 const int v = __ffs(bits) - 1;
                 bits &= bits - 1u;
                 if (pos < S_QCAP) {
-                  const int pl = ((warp * S_ROWS + i) << 5) | lane;
                   q_traj[pos] = c * S_C + v;
-                  q_pix[pos] = (uint16_t)pl;
-                  q_next[pos] = head[pl];  // this thread owns pixel pl
-                  head[pl] = (int16_t)pos;
+                  q_pix[pos] = (uint16_t)(((warp * S_ROWS + i) << 5) | lane);
                 } else {
                   left |= 1u << v;
                   deferred = true;
@@ -1543,9 +1578,12 @@ static int prepare_stack(const char* who, const float* psi, const float* phi, co
   A = SearchArgs{};
   A.psi = psi;
   A.phi = phi;
+  A.pairs = reinterpret_cast<float2*>(ws + L.pairs);
   A.bound = bound;
   A.orig = reinterpret_cast<int32_t*>(ws + L.orig);
   A.offs = reinterpret_cast<int2*>(ws + L.offs);
+  A.vsort = reinterpret_cast<float2*>(ws + L.vsort);
+  A.dtf = reinterpret_cast<float*>(ws + L.dtf);
   A.plan = reinterpret_cast<PlanRec*>(ws + L.plan);
   A.out_lh = out_lh;
   A.out_flux = out_flux;
@@ -1601,6 +1639,8 @@ static int launch_prep(StackPrep& sp, const kb_schedule& sch, cudaStream_t st) {
   int32_t* sorted = reinterpret_cast<int32_t*>(ws + L.sorted);
   int32_t* orig = reinterpret_cast<int32_t*>(ws + L.orig);
   int2* offs = reinterpret_cast<int2*>(ws + L.offs);
+  float2* vsort = reinterpret_cast<float2*>(ws + L.vsort);
+  float* dtf = reinterpret_cast<float*>(ws + L.dtf);
   PlanRec* plan = reinterpret_cast<PlanRec*>(ws + L.plan);
   uint32_t* bound = reinterpret_cast<uint32_t*>(ws + L.bound);
   if (g_num_sms == 0) {
@@ -1621,7 +1661,7 @@ static int launch_prep(StackPrep& sp, const kb_schedule& sch, cudaStream_t st) {
   plan_cellsort_kernel<<<N_CELLS / 256, 256, 0, st>>>(counts, cursor, sorted);
   KB_LAUNCH_CHECK("plan_cellsort_kernel");
   plan_offsets_kernel<<<(L.n_pad + 255) / 256, 256, 0, st>>>(sp.vx, sp.vy, sorted, n_traj, L.n_pad,
-                                                               T, sp.cs, orig, offs);
+                                                               T, sp.cs, orig, offs, vsort, dtf);
   KB_LAUNCH_CHECK("plan_offsets_kernel");
   plan_boxes_kernel<<<(L.nchunk * T + 255) / 256, 256, 0, st>>>(offs, L.nchunk, T, sp.x_lo, plan);
   KB_LAUNCH_CHECK("plan_boxes_kernel");
@@ -1629,6 +1669,10 @@ static int launch_prep(StackPrep& sp, const kb_schedule& sch, cudaStream_t st) {
     size_t total = (size_t)T * (H + 1) * L.Wp;
     int blocks = (int)std::min<size_t>((total + 255) / 256, (size_t)g_num_sms * 16);
     bound_prep_kernel<<<blocks, 256, 0, st>>>(sp.psi, sp.phi, T, H, W, L.Wp, bound);
+    KB_LAUNCH_CHECK("bound_prep_kernel");
+    const size_t npx = (size_t)T * H * W;
+    pair_planes_kernel<<<(int)std::min<size_t>((npx + 255) / 256, (size_t)g_num_sms * 16), 256, 0,
+                         st>>>(sp.psi, sp.phi, npx, reinterpret_cast<float2*>(ws + L.pairs));
     KB_LAUNCH_CHECK("bound_prep_kernel");
   }
   const int ntiles = sp.A.ntiles;

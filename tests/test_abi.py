@@ -96,8 +96,10 @@ def test_workspace_size_query(L):
     p = _params(L, 2046, 4094)
     n = C.c_size_t()
     assert L.kb_search_workspace_size(26, 2046, 4094, 32768, C.byref(p), C.byref(n)) == 0
-    # dominated by the [T][H][Wp] bound planes (Wp = 4096)
-    assert 26 * 2046 * 4096 * 4 < n.value < 26 * 2046 * 4096 * 4 + 64 * 2 ** 20
+    # dominated by the [T][H+1][Wp] bound planes (Wp = 4096) and the interleaved (psi, phi)
+    # planes [T][H][W] of 8-byte pairs
+    planes = 26 * 2047 * 4096 * 4 + 26 * 2046 * 4094 * 8
+    assert planes < n.value < planes + 64 * 2 ** 20
     assert L.kb_search_workspace_size(200, 10, 10, 5, C.byref(p), C.byref(n)) == 2
 
 
