@@ -308,7 +308,8 @@ __global__ void plan_offsets_kernel(const float* __restrict__ vx, const float* _
 // box = {x offset of the rectangle from the tile origin (x_lo + dxmin - xshift is a multiple
 // of 4 so that the TMA x coordinate is 16-byte aligned), y offset, height class, mode} with
 // mode 1..4 = rows of 48/64/96/128 words: the narrowest, then lowest, TMA box that holds the
-// rectangle; mode 0 = no box within S_REGION_MAX (direct loads).
+// rectangle; mode 0 = no box within S_REGION_MAX (direct loads); bit 3 of the last field set
+// when all of the chunk's offsets are equal in this epoch.
 __global__ void plan_boxes_kernel(const int2* __restrict__ offs, int nchunk, int T, int x_lo,
                                   PlanRec* plan) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -335,7 +336,10 @@ __global__ void plan_boxes_kernel(const int2* __restrict__ offs, int nchunk, int
         break;
       }
   PlanRec& pr = plan[i];
-  pr.box = make_int4(dxmin - xshift, dymin, hcls, mode);
+  // bit 3 of box.w: every trajectory of the chunk has the same offset in this epoch (always
+  // at t = 0, often in the first hours), so one load per row pair serves all of them
+  const int uniform = (dxmin == dxmax && dymin == dymax) ? 8 : 0;
+  pr.box = make_int4(dxmin - xshift, dymin, hcls, mode | uniform);
   for (int v = 0; v < S_C; ++v) {
     int2 o = offs[(size_t)(c * S_C + v) * T + t];
     pr.rel[v] = mode ? ((o.y - dymin) * pitch + (o.x - dxmin + xshift)) * 4 : 0;
@@ -965,7 +969,8 @@ __device__ void producer_loop(const TmapSet& pmaps, const SearchArgs& A0, const 
         b.y = __shfl_sync(0xffffffffu, mine.y, kk);
         b.z = __shfl_sync(0xffffffffu, mine.z, kk);
         b.w = __shfl_sync(0xffffffffu, mine.w, kk);
-        const int sz = (!last && b.w) ? stage_width(b.w) * stage_height(b.z) * 4 : 0;
+        const int mode = b.w & 7;
+        const int sz = (!last && mode) ? stage_width(mode) * stage_height(b.z) * 4 : 0;
         int pos = 0;
         for (;;) {
           bool room = it - oldest < S_D;
@@ -1023,7 +1028,7 @@ __device__ void producer_loop(const TmapSet& pmaps, const SearchArgs& A0, const 
             mbar_arrive(&full[slot]);
           } else {  // word row r = image row + 1 (the pair planes carry one leading row)
             mbar_arrive_expect_tx(&full[slot], (uint32_t)sz);
-            tma_load_3d(ring + pos, &maps->m[(b.w - 1) * S_NH + b.z], &full[slot], tx0 + b.x,
+            tma_load_3d(ring + pos, &maps->m[(mode - 1) * S_NH + b.z], &full[slot], tx0 + b.x,
                         ty0 + b.y + 1, t);
           }
         }
@@ -1056,6 +1061,24 @@ __device__ __forceinline__ void accumulate_stage(__half2 (&acc)[2][S_C], const u
         acc[pp][vq * 4 + u] = __hadd2(acc[pp][vq * 4 + u], *reinterpret_cast<const __half2*>(&w));
       }
     }
+  }
+}
+
+// A staged (chunk, epoch) in which all trajectories share one offset: one load per row pair,
+// added to every accumulator (the same values in the same order as the general path).
+template <int PITCH>
+__device__ __forceinline__ void accumulate_uniform(__half2 (&acc)[2][S_C],
+                                                   const unsigned char* st, const PlanRec* slot,
+                                                   int warp, int lane) {
+  const uint32_t* q = reinterpret_cast<const uint32_t*>(
+      st + (size_t)(warp * S_ROWS * PITCH + lane) * 4 + slot->rel[0]);
+  const uint32_t w0 = q[0], w1 = q[2 * PITCH];
+  const __half2 h0 = *reinterpret_cast<const __half2*>(&w0);
+  const __half2 h1 = *reinterpret_cast<const __half2*>(&w1);
+#pragma unroll
+  for (int v = 0; v < S_C; ++v) {
+    acc[0][v] = __hadd2(acc[0][v], h0);
+    acc[1][v] = __hadd2(acc[1][v], h1);
   }
 }
 
@@ -1296,9 +1319,14 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
                           mbar_wait_parity(&full[slot], (uint32_t)((it / S_D) & 1));
           if (ok) {
             const PlanRec* rec = &slots[slot];
-            const int mode = rec->box.w;
+            const int mode = rec->box.w & 7;
             const unsigned char* st = arena + sinfo[slot].x;
-            if (mode == 1) {
+            if (mode != 0 && (rec->box.w & 8)) {
+              if (mode == 1) accumulate_uniform<stage_width(1)>(acc, st, rec, warp, lane);
+              else if (mode == 2) accumulate_uniform<stage_width(2)>(acc, st, rec, warp, lane);
+              else if (mode == 3) accumulate_uniform<stage_width(3)>(acc, st, rec, warp, lane);
+              else accumulate_uniform<stage_width(4)>(acc, st, rec, warp, lane);
+            } else if (mode == 1) {
               accumulate_stage<stage_width(1)>(acc, st, rec, warp, lane);
             } else if (mode == 2) {
               accumulate_stage<stage_width(2)>(acc, st, rec, warp, lane);
