@@ -1042,24 +1042,43 @@ __device__ void producer_loop(const TmapSet& pmaps, const SearchArgs& A0, const 
   *issued_out = last_issued;
 }
 
+// Shared-memory loads with 32-bit shared-window addresses (the staged regions are addressed
+// through offsets read from shared memory; explicit forms keep the loop on 32-bit arithmetic).
+__device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+  return v;
+}
+template <int OFF>
+__device__ __forceinline__ uint32_t lds_u32_off(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1+%2];" : "=r"(v) : "r"(addr), "n"(OFF));
+  return v;
+}
+__device__ __forceinline__ int4 lds_v4(uint32_t addr) {
+  int4 v;
+  asm volatile("ld.shared.v4.s32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "r"(addr));
+  return v;
+}
+
 // Sums one staged (chunk, epoch) into the fp16 row-pair accumulators.
 template <int PITCH>
 __device__ __forceinline__ void accumulate_stage(__half2 (&acc)[2][S_C], const unsigned char* st,
                                                  const PlanRec* slot, int warp, int lane) {
-  const unsigned char* base = st + (size_t)(warp * S_ROWS * PITCH + lane) * 4;
-  const int4* relv = reinterpret_cast<const int4*>(slot->rel);
+  const uint32_t base = smem_u32(st) + (uint32_t)(warp * S_ROWS * PITCH + lane) * 4u;
+  const uint32_t relv = smem_u32(slot->rel);
 #pragma unroll
   for (int vq = 0; vq < S_C / 4; ++vq) {
-    const int4 r4 = relv[vq];
+    const int4 r4 = lds_v4(relv + 16u * vq);
     const int rr[4] = {r4.x, r4.y, r4.z, r4.w};
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const uint32_t* q = reinterpret_cast<const uint32_t*>(base + rr[u]);
-#pragma unroll
-      for (int pp = 0; pp < 2; ++pp) {
-        const uint32_t w = q[2 * pp * PITCH];
-        acc[pp][vq * 4 + u] = __hadd2(acc[pp][vq * 4 + u], *reinterpret_cast<const __half2*>(&w));
-      }
+      const uint32_t q = base + (uint32_t)rr[u];
+      const uint32_t w0 = lds_u32(q), w1 = lds_u32_off<8 * PITCH>(q);
+      acc[0][vq * 4 + u] = __hadd2(acc[0][vq * 4 + u], *reinterpret_cast<const __half2*>(&w0));
+      acc[1][vq * 4 + u] = __hadd2(acc[1][vq * 4 + u], *reinterpret_cast<const __half2*>(&w1));
     }
   }
 }
@@ -1070,9 +1089,9 @@ template <int PITCH>
 __device__ __forceinline__ void accumulate_uniform(__half2 (&acc)[2][S_C],
                                                    const unsigned char* st, const PlanRec* slot,
                                                    int warp, int lane) {
-  const uint32_t* q = reinterpret_cast<const uint32_t*>(
-      st + (size_t)(warp * S_ROWS * PITCH + lane) * 4 + slot->rel[0]);
-  const uint32_t w0 = q[0], w1 = q[2 * PITCH];
+  const uint32_t q = smem_u32(st) + (uint32_t)(warp * S_ROWS * PITCH + lane) * 4u +
+                     (uint32_t)slot->rel[0];
+  const uint32_t w0 = lds_u32(q), w1 = lds_u32_off<8 * PITCH>(q);
   const __half2 h0 = *reinterpret_cast<const __half2*>(&w0);
   const __half2 h1 = *reinterpret_cast<const __half2*>(&w1);
 #pragma unroll
