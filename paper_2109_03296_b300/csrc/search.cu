@@ -1049,12 +1049,6 @@ __device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
   asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
   return v;
 }
-template <int OFF>
-__device__ __forceinline__ uint32_t lds_u32_off(uint32_t addr) {
-  uint32_t v;
-  asm volatile("ld.shared.u32 %0, [%1+%2];" : "=r"(v) : "r"(addr), "n"(OFF));
-  return v;
-}
 __device__ __forceinline__ int4 lds_v4(uint32_t addr) {
   int4 v;
   asm volatile("ld.shared.v4.s32 {%0, %1, %2, %3}, [%4];"
@@ -1063,11 +1057,25 @@ __device__ __forceinline__ int4 lds_v4(uint32_t addr) {
   return v;
 }
 
-// Sums one staged (chunk, epoch) into the fp16 row-pair accumulators.
-template <int PITCH>
+// Sums one staged (chunk, epoch), a rectangle of `pitch`-word rows, into the fp16 row-pair
+// accumulators.  One code path for every box width (the pitch only moves the two row bases),
+// which keeps the hot loop small.  uniform: all trajectories share rel[0] (one load per row
+// pair, added to every accumulator: the same values in the same order as the general path).
 __device__ __forceinline__ void accumulate_stage(__half2 (&acc)[2][S_C], const unsigned char* st,
-                                                 const PlanRec* slot, int warp, int lane) {
-  const uint32_t base = smem_u32(st) + (uint32_t)(warp * S_ROWS * PITCH + lane) * 4u;
+                                                 int pitch, bool uniform, const PlanRec* slot,
+                                                 int warp, int lane) {
+  const uint32_t base = smem_u32(st) + (uint32_t)(warp * S_ROWS * pitch + lane) * 4u;
+  const uint32_t base1 = base + 8u * (uint32_t)pitch;  // two rows further: the second pair
+  if (uniform) {
+    const uint32_t w0 = lds_u32(base + (uint32_t)slot->rel[0]);
+    const uint32_t w1 = lds_u32(base1 + (uint32_t)slot->rel[0]);
+#pragma unroll
+    for (int v = 0; v < S_C; ++v) {
+      acc[0][v] = __hadd2(acc[0][v], *reinterpret_cast<const __half2*>(&w0));
+      acc[1][v] = __hadd2(acc[1][v], *reinterpret_cast<const __half2*>(&w1));
+    }
+    return;
+  }
   const uint32_t relv = smem_u32(slot->rel);
 #pragma unroll
   for (int vq = 0; vq < S_C / 4; ++vq) {
@@ -1075,29 +1083,11 @@ __device__ __forceinline__ void accumulate_stage(__half2 (&acc)[2][S_C], const u
     const int rr[4] = {r4.x, r4.y, r4.z, r4.w};
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const uint32_t q = base + (uint32_t)rr[u];
-      const uint32_t w0 = lds_u32(q), w1 = lds_u32_off<8 * PITCH>(q);
+      const uint32_t w0 = lds_u32(base + (uint32_t)rr[u]);
+      const uint32_t w1 = lds_u32(base1 + (uint32_t)rr[u]);
       acc[0][vq * 4 + u] = __hadd2(acc[0][vq * 4 + u], *reinterpret_cast<const __half2*>(&w0));
       acc[1][vq * 4 + u] = __hadd2(acc[1][vq * 4 + u], *reinterpret_cast<const __half2*>(&w1));
     }
-  }
-}
-
-// A staged (chunk, epoch) in which all trajectories share one offset: one load per row pair,
-// added to every accumulator (the same values in the same order as the general path).
-template <int PITCH>
-__device__ __forceinline__ void accumulate_uniform(__half2 (&acc)[2][S_C],
-                                                   const unsigned char* st, const PlanRec* slot,
-                                                   int warp, int lane) {
-  const uint32_t q = smem_u32(st) + (uint32_t)(warp * S_ROWS * PITCH + lane) * 4u +
-                     (uint32_t)slot->rel[0];
-  const uint32_t w0 = lds_u32(q), w1 = lds_u32_off<8 * PITCH>(q);
-  const __half2 h0 = *reinterpret_cast<const __half2*>(&w0);
-  const __half2 h1 = *reinterpret_cast<const __half2*>(&w1);
-#pragma unroll
-  for (int v = 0; v < S_C; ++v) {
-    acc[0][v] = __hadd2(acc[0][v], h0);
-    acc[1][v] = __hadd2(acc[1][v], h1);
   }
 }
 
@@ -1340,19 +1330,9 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
             const PlanRec* rec = &slots[slot];
             const int mode = rec->box.w & 7;
             const unsigned char* st = arena + sinfo[slot].x;
-            if (mode != 0 && (rec->box.w & 8)) {
-              if (mode == 1) accumulate_uniform<stage_width(1)>(acc, st, rec, warp, lane);
-              else if (mode == 2) accumulate_uniform<stage_width(2)>(acc, st, rec, warp, lane);
-              else if (mode == 3) accumulate_uniform<stage_width(3)>(acc, st, rec, warp, lane);
-              else accumulate_uniform<stage_width(4)>(acc, st, rec, warp, lane);
-            } else if (mode == 1) {
-              accumulate_stage<stage_width(1)>(acc, st, rec, warp, lane);
-            } else if (mode == 2) {
-              accumulate_stage<stage_width(2)>(acc, st, rec, warp, lane);
-            } else if (mode == 3) {
-              accumulate_stage<stage_width(3)>(acc, st, rec, warp, lane);
-            } else if (mode == 4) {
-              accumulate_stage<stage_width(4)>(acc, st, rec, warp, lane);
+            if (mode != 0) {
+              accumulate_stage(acc, st, stage_width(mode), (rec->box.w & 8) != 0, rec, warp,
+                               lane);
             } else {
               // direct loads from the pair planes (word row = image row + 1)
               const uint32_t* bp = A.bound + (size_t)t * (A.ep.H + 1) * A.Wp;
