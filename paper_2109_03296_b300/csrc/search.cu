@@ -75,11 +75,11 @@ constexpr int S_FLUSH_MIN = S_CTHREADS;  // evaluate the queue once it holds one
 constexpr int S_REC_WORDS = 8;           // L', alpha, nvalid|nkept<<16, mask[4], pad
 constexpr float S_PRUNE_MARGIN = 1.0f - 1e-4f;
 static_assert(S_D % S_PWARPS == 0 && S_REGION_MAX <= S_RING_BYTES, "pipeline configuration");
-// A staged rectangle is one TMA box: width class w = 1..4 (rows of 48/64/96/128 words) and
+// A staged rectangle is one TMA box: width class w = 1..3 (rows of 64/96/128 words) and
 // height class h = 0..4 (64/80/96/112/128 word rows); mode 0 = direct global loads.
-constexpr int S_NW = 4, S_NH = 5;
+constexpr int S_NW = 3, S_NH = 5;
 __host__ __device__ constexpr int stage_width(int mode) {
-  return mode == 1 ? 48 : mode == 2 ? 64 : mode == 3 ? 96 : 128;
+  return mode == 1 ? 64 : mode == 2 ? 96 : 128;
 }
 __host__ __device__ constexpr int stage_height(int h) { return 64 + 16 * h; }
 
@@ -307,7 +307,7 @@ __global__ void plan_offsets_kernel(const float* __restrict__ vx, const float* _
 // One thread per (chunk, epoch): staging rectangle and per-trajectory byte offsets into it.
 // box = {x offset of the rectangle from the tile origin (x_lo + dxmin - xshift is a multiple
 // of 4 so that the TMA x coordinate is 16-byte aligned), y offset, height class, mode} with
-// mode 1..4 = rows of 48/64/96/128 words: the narrowest, then lowest, TMA box that holds the
+// mode 1..3 = rows of 64/96/128 words: the narrowest, then lowest, TMA box that holds the
 // rectangle; mode 0 = no box within S_REGION_MAX (direct loads); bit 3 of the last field set
 // when all of the chunk's offsets are equal in this epoch.
 __global__ void plan_boxes_kernel(const int2* __restrict__ offs, int nchunk, int T, int x_lo,
@@ -1049,6 +1049,12 @@ __device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
   asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
   return v;
 }
+template <int OFF>
+__device__ __forceinline__ uint32_t lds_u32_off(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1+%2];" : "=r"(v) : "r"(addr), "n"(OFF));
+  return v;
+}
 __device__ __forceinline__ int4 lds_v4(uint32_t addr) {
   int4 v;
   asm volatile("ld.shared.v4.s32 {%0, %1, %2, %3}, [%4];"
@@ -1057,18 +1063,19 @@ __device__ __forceinline__ int4 lds_v4(uint32_t addr) {
   return v;
 }
 
-// Sums one staged (chunk, epoch), a rectangle of `pitch`-word rows, into the fp16 row-pair
-// accumulators.  One code path for every box width (the pitch only moves the two row bases),
-// which keeps the hot loop small.  uniform: all trajectories share rel[0] (one load per row
-// pair, added to every accumulator: the same values in the same order as the general path).
+// Sums one staged (chunk, epoch), a rectangle of PITCH-word rows, into the fp16 row-pair
+// accumulators: per trajectory one address add and two shared loads (the second row pair at an
+// immediate offset of two rows).  uniform: all trajectories share rel[0] (one load per row pair,
+// added to every accumulator: the same values in the same order as the general path).  Three
+// box widths keep both the instruction count (immediate row offsets) and the hot code small.
+template <int PITCH>
 __device__ __forceinline__ void accumulate_stage(__half2 (&acc)[2][S_C], const unsigned char* st,
-                                                 int pitch, bool uniform, const PlanRec* slot,
-                                                 int warp, int lane) {
-  const uint32_t base = smem_u32(st) + (uint32_t)(warp * S_ROWS * pitch + lane) * 4u;
-  const uint32_t base1 = base + 8u * (uint32_t)pitch;  // two rows further: the second pair
+                                                 bool uniform, const PlanRec* slot, int warp,
+                                                 int lane) {
+  const uint32_t base = smem_u32(st) + (uint32_t)(warp * S_ROWS * PITCH + lane) * 4u;
   if (uniform) {
-    const uint32_t w0 = lds_u32(base + (uint32_t)slot->rel[0]);
-    const uint32_t w1 = lds_u32(base1 + (uint32_t)slot->rel[0]);
+    const uint32_t q = base + (uint32_t)slot->rel[0];
+    const uint32_t w0 = lds_u32(q), w1 = lds_u32_off<8 * PITCH>(q);
 #pragma unroll
     for (int v = 0; v < S_C; ++v) {
       acc[0][v] = __hadd2(acc[0][v], *reinterpret_cast<const __half2*>(&w0));
@@ -1083,8 +1090,8 @@ __device__ __forceinline__ void accumulate_stage(__half2 (&acc)[2][S_C], const u
     const int rr[4] = {r4.x, r4.y, r4.z, r4.w};
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const uint32_t w0 = lds_u32(base + (uint32_t)rr[u]);
-      const uint32_t w1 = lds_u32(base1 + (uint32_t)rr[u]);
+      const uint32_t q = base + (uint32_t)rr[u];
+      const uint32_t w0 = lds_u32(q), w1 = lds_u32_off<8 * PITCH>(q);
       acc[0][vq * 4 + u] = __hadd2(acc[0][vq * 4 + u], *reinterpret_cast<const __half2*>(&w0));
       acc[1][vq * 4 + u] = __hadd2(acc[1][vq * 4 + u], *reinterpret_cast<const __half2*>(&w1));
     }
@@ -1331,8 +1338,10 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
             const int mode = rec->box.w & 7;
             const unsigned char* st = arena + sinfo[slot].x;
             if (mode != 0) {
-              accumulate_stage(acc, st, stage_width(mode), (rec->box.w & 8) != 0, rec, warp,
-                               lane);
+              const bool uni = (rec->box.w & 8) != 0;
+              if (mode == 1) accumulate_stage<stage_width(1)>(acc, st, uni, rec, warp, lane);
+              else if (mode == 2) accumulate_stage<stage_width(2)>(acc, st, uni, rec, warp, lane);
+              else accumulate_stage<stage_width(3)>(acc, st, uni, rec, warp, lane);
             } else {
               // direct loads from the pair planes (word row = image row + 1)
               const uint32_t* bp = A.bound + (size_t)t * (A.ep.H + 1) * A.Wp;
