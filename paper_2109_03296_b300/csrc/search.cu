@@ -73,6 +73,7 @@ constexpr int S_REGION_MAX = 64 * 1024;  // larger rectangles use direct loads
 constexpr int S_QCAP = 1024;             // block queue of full evaluations
 constexpr int S_FLUSH_MIN = S_CTHREADS;  // evaluate the queue once it holds one pair per thread
 constexpr int S_REC_WORDS = 8;           // L', alpha, nvalid|nkept<<16, mask[4], pad
+constexpr int S_REC_BLOCKS = 256;        // most blocks of a launch (records in the workspace)
 constexpr float S_PRUNE_MARGIN = 1.0f - 1e-4f;
 static_assert(S_D % S_PWARPS == 0 && S_REGION_MAX <= S_RING_BYTES, "pipeline configuration");
 // A staged rectangle is one TMA box: width class w = 1..3 (rows of 64/96/128 words) and
@@ -107,8 +108,8 @@ struct EvalParams {
 
 // Workspace layout (offsets in bytes from the workspace base).
 struct WsLayout {
-  size_t ctrl, vbox, keys, counts, cursor, sorted, orig, offs, vsort, dtf, plan, bound, pairs, tkeys,
-      torder, total;
+  size_t ctrl, vbox, keys, counts, cursor, sorted, orig, offs, vsort, dtf, plan, bound, pairs, recs,
+      tkeys, torder, total;
   int n_pad, nchunk, Wp;
 };
 
@@ -136,6 +137,7 @@ static WsLayout ws_layout(int T, int H, int W, int n_traj) {
   L.plan = take(sizeof(PlanRec) * (size_t)L.nchunk * T);
   L.bound = take(sizeof(uint32_t) * (size_t)T * (H + 1) * L.Wp);
   L.pairs = take(sizeof(float2) * (size_t)T * H * W);
+  L.recs = take(sizeof(uint32_t) * S_REC_WORDS * S_QCAP * S_REC_BLOCKS);
   L.tkeys = take(sizeof(unsigned long long) * S_ORDER_MAX);
   L.torder = take(sizeof(int32_t) * S_ORDER_MAX);
   L.total = o;
@@ -757,6 +759,7 @@ struct SearchArgs {
   const float* psi;
   const float* phi;
   const float2* pairs;  // (psi, phi) interleaved, [T][H][W]
+  uint32_t* recs;       // [S_REC_BLOCKS][S_QCAP][S_REC_WORDS] evaluation records, one set per block
   const uint32_t* bound;
   const int32_t* orig;
   const int2* offs;
@@ -811,8 +814,7 @@ __device__ __forceinline__ void tmap_acquire(const void* tmap) {
 
 struct SmemLayout {
   static constexpr size_t arena = 0;
-  static constexpr size_t rec = arena + S_ARENA_BYTES;             // [S_QCAP][S_REC_WORDS]
-  static constexpr size_t qtraj = rec + S_QCAP * S_REC_WORDS * sizeof(uint32_t);
+  static constexpr size_t qtraj = arena + S_ARENA_BYTES;
   static constexpr size_t qpix = qtraj + S_QCAP * sizeof(int32_t);
   static constexpr size_t qnext = qpix + S_QCAP * sizeof(uint16_t);
   static constexpr size_t head = (qnext + S_QCAP * sizeof(int16_t) + 15) / 16 * 16;  // [pixel]
@@ -1136,7 +1138,6 @@ __global__ void __launch_bounds__(S_THREADS, 1)
 search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const BatchArgs B) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* arena = smem + SmemLayout::arena;
-  uint32_t* recs = reinterpret_cast<uint32_t*>(smem + SmemLayout::rec);
   int32_t* q_traj = reinterpret_cast<int32_t*>(smem + SmemLayout::qtraj);
   uint16_t* q_pix = reinterpret_cast<uint16_t*>(smem + SmemLayout::qpix);
   int16_t* q_next = reinterpret_cast<int16_t*>(smem + SmemLayout::qnext);
@@ -1212,6 +1213,8 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
         consumer_sync();
       }
       const SearchArgs& A = BATCH ? *s_args : A0;
+      // evaluation records of this block (global memory, L2-resident: a few MB per launch)
+      uint32_t* const recs = A.recs + (size_t)blockIdx.x * S_QCAP * S_REC_WORDS;
       const int T = A.ep.T, K = A.ep.K, mw = A.ep.mw;
       const float lh_min = A.ep.lh_min;
       const size_t wx = (size_t)(A.x_hi - A.x_lo);
@@ -1615,6 +1618,7 @@ static int prepare_stack(const char* who, const float* psi, const float* phi, co
   A.psi = psi;
   A.phi = phi;
   A.pairs = reinterpret_cast<float2*>(ws + L.pairs);
+  A.recs = reinterpret_cast<uint32_t*>(ws + L.recs);
   A.bound = bound;
   A.orig = reinterpret_cast<int32_t*>(ws + L.orig);
   A.offs = reinterpret_cast<int2*>(ws + L.offs);
@@ -1737,6 +1741,9 @@ static int launch_search_single(const StackPrep& sp, cudaStream_t st) {
   const SearchArgs& A = sp.A;
   const int T = sp.T;
   const int grid = std::min(A.ntiles, g_num_sms);
+  if (grid > S_REC_BLOCKS)
+    return fail(KB_ERR_UNSUPPORTED, "kb_search: %d SMs, at most %d supported", g_num_sms,
+                S_REC_BLOCKS);
   const size_t smem = SmemLayout::total;
 #define KB_SEARCH_LAUNCH(NT, JJ)                                                               \
   do {                                                                                         \
@@ -1982,6 +1989,9 @@ static int batch_enqueue(kb_batch* b, cudaStream_t st) {
   KB_CUDA_TRY(cudaFuncSetAttribute(search_kernel<0, 1, true>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int grid = std::min(b->total_tiles, g_num_sms);
+  if (grid > S_REC_BLOCKS)
+    return fail(KB_ERR_UNSUPPORTED, "kb_batch_run: %d SMs, at most %d supported", g_num_sms,
+                S_REC_BLOCKS);
   static const TmapSet kNoMaps{};
   search_kernel<0, 1, true><<<grid, S_THREADS, smem, st>>>(kNoMaps, SearchArgs{}, B);
   KB_LAUNCH_CHECK("search_kernel (batch)");
