@@ -76,6 +76,7 @@ constexpr int S_REC_WORDS = 8;           // L', alpha, nvalid|nkept<<16, mask[4]
 constexpr int S_REC_BLOCKS = 256;        // most blocks of a launch (records in the workspace)
 constexpr float S_PRUNE_MARGIN = 1.0f - 1e-4f;
 static_assert(S_D % S_PWARPS == 0 && S_REGION_MAX <= S_RING_BYTES, "pipeline configuration");
+static_assert((S_D & (S_D - 1)) == 0, "slot indices from a 32-bit iteration count");
 // A staged rectangle is one TMA box: width class w = 1..3 (rows of 64/96/128 words) and
 // height class h = 0..4 (64/80/96/112/128 word rows); mode 0 = direct global loads.
 constexpr int S_NW = 3, S_NH = 5;
@@ -852,6 +853,19 @@ __device__ __forceinline__ __half half_round_down(float x) {
   return h;
 }
 
+// mbar_wait_parity for the consumers: the flag set by a warp that gave up is checked only while
+// waiting (the fast path is one try_wait), so the other warps stop promptly after a timeout.
+__device__ __forceinline__ bool consumer_wait(uint64_t* bar, uint32_t parity,
+                                              const unsigned int* abort_flag) {
+  if (mbar_try_wait(bar, parity, 20000u)) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  for (;;) {
+    if (*(volatile const unsigned int*)abort_flag != 0u) return false;
+    if (mbar_try_wait(bar, parity, 20000u)) return true;
+    if (globaltimer_ns() - t0 > kWaitLimitNs) return false;
+  }
+}
+
 __device__ __forceinline__ void consumer_sync() {
   asm volatile("bar.sync 1, %0;" ::"r"(S_CTHREADS) : "memory");
 }
@@ -1187,15 +1201,16 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
     if (lane == 0) s_issued[pw] = issued;
   } else {
     // ------------------------------- consumer warps --------------------------------------
-    long long it = 0;
+    // consumer iteration counter: only its low bits (slot, phase parity) are used, and they
+    // agree with the producers' 64-bit count modulo 2^32 (S_D divides 2^32)
+    uint32_t it = 0u;
     for (;;) {
       // the first slot of the next tile names it (-1: none left) and its stack; decided by one
       // thread
       consumer_sync();
       if (tid == 0) {
         const int slot0 = (int)(it % S_D);
-        const bool ok = *(volatile unsigned int*)s_abort == 0u &&
-                        mbar_wait_parity(&full[slot0], (uint32_t)((it / S_D) & 1));
+        const bool ok = consumer_wait(&full[slot0], (it / S_D) & 1u, s_abort);
         if (!ok && atomicExch(s_abort, 1u) == 0u) atomicOr(&ctrl->err, kErrTimeout);
         *s_tile = ok ? sinfo[slot0].y : -1;
         *s_stack = ok ? sinfo[slot0].w : 0;
@@ -1334,8 +1349,7 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
 
         for (int t = 0; t < T; ++t, ++it) {
           const int slot = (int)(it % S_D);
-          const bool ok = *(volatile unsigned int*)s_abort == 0u &&
-                          mbar_wait_parity(&full[slot], (uint32_t)((it / S_D) & 1));
+          const bool ok = consumer_wait(&full[slot], (it / S_D) & 1u, s_abort);
           if (ok) {
             const PlanRec* rec = &slots[slot];
             const int mode = rec->box.w & 7;
