@@ -1272,25 +1272,31 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
         const int2* const e_offs = A.offs;
         const float2* const e_vs = A.vsort;
         const float* const e_dt = A.dtf;
-        // a result that reaches lh_min joins its pixel's list (pushed with one shared atomic);
-        // the others (almost all of them) are never looked at again
-        auto link = [&](int e, int pl) { q_next[e] = (int16_t)atomicExch(&head[pl], e); };
+        // a result that reaches lh_min is written to the block's records and joins its pixel's
+        // list (pushed with one shared atomic); the others (almost all of them) are dropped
+        auto keep = [&](int e, int pl, const uint32_t (&r)[S_REC_WORDS]) {
+          uint4* dst = reinterpret_cast<uint4*>(recs + e * S_REC_WORDS);
+          dst[0] = make_uint4(r[0], r[1], r[2], r[3]);
+          dst[1] = make_uint4(r[4], r[5], r[6], 0u);
+          q_next[e] = (int16_t)atomicExch(&head[pl], e);
+        };
         auto by_thread = [&](auto nt) {
           for (int e = tid; e < nq; e += S_CTHREADS) {
             const int pl = q_pix[e], j = q_traj[e];
+            uint32_t r[S_REC_WORDS];
             const float L = eval_pair_thread<decltype(nt)::value>(
-                e_pairs, EP, tx0 + (pl & 31), ty0 + (pl >> 5), __ldg(e_vs + j), e_dt,
-                recs + e * S_REC_WORDS);
-            if (L >= lh_min) link(e, pl);
+                e_pairs, EP, tx0 + (pl & 31), ty0 + (pl >> 5), __ldg(e_vs + j), e_dt, r);
+            if (L >= lh_min) keep(e, pl, r);
           }
         };
         auto by_warp = [&](auto jj) {
           for (int e = warp; e < nq; e += S_CWARPS) {
             const int pl = q_pix[e];
+            uint32_t r[S_REC_WORDS];
             const float L = eval_pair_warp<decltype(jj)::value>(
                 e_pairs, EP, tx0 + (pl & 31), ty0 + (pl >> 5),
-                e_offs + (size_t)q_traj[e] * T, recs + e * S_REC_WORDS, lane);
-            if (lane == 0 && L >= lh_min) link(e, pl);
+                e_offs + (size_t)q_traj[e] * T, r, lane);
+            if (lane == 0 && L >= lh_min) keep(e, pl, r);
           }
         };
         if (BATCH) {
