@@ -10,23 +10,26 @@
 //    So a (start pixel, trajectory) pair can only enter a top-K list if that bound reaches the
 //    list's current admission threshold (lh_min, or the K-th LH' once the list is full).  The
 //    search therefore runs in two levels:
-//      1. bound pass: B(p, j) = sum_t nu2[t, p + d_t(j)] with nu2 = psi^2/phi (psi > 0, valid),
-//         one float load + one add per trajectory-epoch;
-//      2. full evaluation of the few pairs whose bound reaches the threshold: gather psi/phi,
-//         sigma-G clip, LH', alpha, then insertion into the pixel's list.
-//    Pairs are dropped only when B < thr^2 (1 - 1e-4); the FP32 rounding of B is far below that
-//    margin, so the output equals evaluating every pair.
+//      1. bound pass over blocks of two vertically adjacent start pixels: for block (x, y..y+1),
+//         B2(j) = sum_t max(nu2[t, y + dy_t, x + dx_t], nu2[t, y + 1 + dy_t, x + dx_t]) with
+//         nu2 = psi^2/phi (psi > 0, valid), which bounds the sum of either pixel;
+//      2. full evaluation of both pixels of the few blocks whose bound reaches the smaller of
+//         their two thresholds: gather psi/phi, sigma-G clip, LH', alpha, then insertion into
+//         the pixel's list.
+//    Pairs are dropped only when B2 < thr^2 (1 - 1e-4) (with the fp16 rounding of the sums
+//    accounted for, see admission_threshold), so the output equals evaluating every pair.
 //
-//  * Bound pass layout.  nu2 is written once per call into the workspace as [T][H][Wp] float32
-//    (Wp = W rounded up to 32, zero padded) so that a 3-D TMA tensor map can address it.  A
-//    block owns a tile of 32 x 64 start pixels (lane = x, 8 rows per thread) and sweeps the
-//    velocity list in chunks of 32 trajectories that are close in velocity space (the list is
-//    reordered by a Morton key of (vx, vy) in the plan kernels).  For each (chunk, epoch) the
-//    union of the tile's 32 shifted footprints is one small rectangle; it is fetched with TMA
-//    into a double-buffered shared-memory stage (zero fill outside the image) while the
-//    previous epoch is being summed.  Each thread then does 4 x 32 shared loads + adds per
-//    epoch with immediate row offsets.  A (chunk, epoch) rectangle too large for a stage falls
-//    back to direct global loads.
+//  * Bound pass layout.  The block maxima are written once per call into the workspace as fp16
+//    pairs: word (t, r, x) of a [T][H+3][Wp] uint32 array (Wp = W rounded up to 32) holds the
+//    maxima of image rows (r-3, r-2) and (r-1, r) at column x, each rounded up.  A block owns a
+//    tile of 32 x 56 start pixels (lane = x, 4 rows = two blocks per consumer thread) and sweeps
+//    the velocity list in chunks of 32 trajectories that are close in velocity space (Hilbert
+//    order of (vx, vy) from the plan kernels).  For each (chunk, epoch) the union of the tile's
+//    32 shifted footprints is one small rectangle, fetched with one TMA box into a shared-memory
+//    ring by producer warps while the consumer warps sum earlier ones.  A consumer thread then
+//    does, per trajectory, one address add, one 32-bit shared load (its two blocks) and one
+//    fp16x2 add.  A (chunk, epoch) rectangle too large for a stage falls back to direct global
+//    loads.
 //
 //  * Full evaluation.  After each chunk, the pairs whose bound passes are appended to a queue
 //    in shared memory; the queue is evaluated in one batch once
@@ -136,7 +139,7 @@ static WsLayout ws_layout(int T, int H, int W, int n_traj) {
   L.vsort = take(sizeof(float2) * (size_t)L.n_pad);
   L.dtf = take(sizeof(float) * KB_MAX_T);
   L.plan = take(sizeof(PlanRec) * (size_t)L.nchunk * T);
-  L.bound = take(sizeof(uint32_t) * (size_t)T * (H + 1) * L.Wp);
+  L.bound = take(sizeof(uint32_t) * (size_t)T * (H + 3) * L.Wp);
   L.pairs = take(sizeof(float2) * (size_t)T * H * W);
   L.recs = take(sizeof(uint32_t) * S_REC_WORDS * S_QCAP * S_REC_BLOCKS);
   L.tkeys = take(sizeof(unsigned long long) * S_ORDER_MAX);
@@ -368,21 +371,25 @@ __device__ __forceinline__ unsigned short half_round_up(float v) {
   return u;
 }
 
-// Bound planes as fp16 row pairs, [T][H+1][Wp] 32-bit words: word (t, r, x) holds nu2 of image
-// rows r-1 (low half) and r (high half) at column x, each rounded up to fp16, zero outside the
-// image and in the padding.  A thread summing start-pixel rows y and y+1 at row offset dy reads
-// the single word at r = y + dy + 1.
+// Bound planes of two-row blocks, [T][H+3][Wp] 32-bit words: with M2(y) = max(nu2(y), nu2(y+1))
+// at column x (nu2 = 0 outside the image), word (t, r, x) holds M2(r-3) (low half) and M2(r-1)
+// (high half), each rounded up to fp16; zero in the padding.  A thread summing the blocks
+// (y, y+1) and (y+2, y+3) at row offset dy reads the single word at r = y + dy + 3; with three
+// leading word rows, a word row outside 0 .. H+2 (which TMA fills with zeros) holds no image row.
 __global__ void bound_prep_kernel(const float* __restrict__ psi, const float* __restrict__ phi,
                                   int T, int H, int W, int Wp, uint32_t* __restrict__ bound) {
-  const size_t total = (size_t)T * (H + 1) * Wp;
+  const size_t total = (size_t)T * (H + 3) * Wp;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (size_t)gridDim.x * blockDim.x) {
     const int x = (int)(i % Wp);
-    const size_t row = i / Wp;  // t*(H+1) + r
-    const int t = (int)(row / (H + 1)), r = (int)(row % (H + 1));
+    const size_t row = i / Wp;
+    const int t = (int)(row / (H + 3)), r = (int)(row % (H + 3));
     const size_t plane = (size_t)t * H * W;
-    const unsigned short lo = half_round_up(nu2_at(psi, phi, H, W, plane, r - 1, x));
-    const unsigned short hi = half_round_up(nu2_at(psi, phi, H, W, plane, r, x));
+    auto m2 = [&](int y) {
+      return fmaxf(nu2_at(psi, phi, H, W, plane, y, x), nu2_at(psi, phi, H, W, plane, y + 1, x));
+    };
+    const unsigned short lo = half_round_up(m2(r - 3));
+    const unsigned short hi = half_round_up(m2(r - 1));
     bound[i] = (uint32_t)lo | ((uint32_t)hi << 16);
   }
 }
@@ -426,11 +433,11 @@ __global__ void __launch_bounds__(256) tile_score_kernel(
     const int ya = max(ty0 + oya, 0), yb = min(ty1 - 1 + oyb, H - 1);
     if (xa > xb || ya > yb) continue;
     const int w = xb - xa + 1, n = w * (yb - ya + 1);
-    const uint32_t* plane = bound + (size_t)t * (H + 1) * Wp;
+    const uint32_t* plane = bound + (size_t)t * (H + 3) * Wp;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const int y = ya + i / w, x = xa + i % w;
-      // image row y is the high half of word row y
-      const float v = __half2float(__ushort_as_half((unsigned short)(__ldg(plane + (size_t)y * Wp + x) >> 16)));
+      // the block of image rows (y, y+1) is the high half of word row y + 2
+      const float v = __half2float(__ushort_as_half((unsigned short)(__ldg(plane + (size_t)(y + 2) * Wp + x) >> 16)));
       cnt += v >= tau ? 1u : 0u;
     }
   }
@@ -1042,10 +1049,10 @@ __device__ void producer_loop(const TmapSet& pmaps, const SearchArgs& A0, const 
           sinfo[slot] = make_int4(ring_base + pos, last ? -1 : tile, sz, stack);
           if (sz == 0) {
             mbar_arrive(&full[slot]);
-          } else {  // word row r = image row + 1 (the pair planes carry one leading row)
+          } else {  // word row = first image row + 3 (the planes carry three leading rows)
             mbar_arrive_expect_tx(&full[slot], (uint32_t)sz);
             tma_load_3d(ring + pos, &maps->m[(mode - 1) * S_NH + b.z], &full[slot], tx0 + b.x,
-                        ty0 + b.y + 1, t);
+                        ty0 + b.y + 3, t);
           }
         }
         last_issued = it;
@@ -1065,12 +1072,6 @@ __device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
   asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
   return v;
 }
-template <int OFF>
-__device__ __forceinline__ uint32_t lds_u32_off(uint32_t addr) {
-  uint32_t v;
-  asm volatile("ld.shared.u32 %0, [%1+%2];" : "=r"(v) : "r"(addr), "n"(OFF));
-  return v;
-}
 __device__ __forceinline__ int4 lds_v4(uint32_t addr) {
   int4 v;
   asm volatile("ld.shared.v4.s32 {%0, %1, %2, %3}, [%4];"
@@ -1079,24 +1080,18 @@ __device__ __forceinline__ int4 lds_v4(uint32_t addr) {
   return v;
 }
 
-// Sums one staged (chunk, epoch), a rectangle of PITCH-word rows, into the fp16 row-pair
-// accumulators: per trajectory one address add and two shared loads (the second row pair at an
-// immediate offset of two rows).  uniform: all trajectories share rel[0] (one load per row pair,
-// added to every accumulator: the same values in the same order as the general path).  Three
-// box widths keep both the instruction count (immediate row offsets) and the hot code small.
-template <int PITCH>
-__device__ __forceinline__ void accumulate_stage(__half2 (&acc)[2][S_C], const unsigned char* st,
-                                                 bool uniform, const PlanRec* slot, int warp,
-                                                 int lane) {
-  const uint32_t base = smem_u32(st) + (uint32_t)(warp * S_ROWS * PITCH + lane) * 4u;
+// Sums one staged (chunk, epoch), a rectangle of `pitch`-word rows, into the fp16 block-pair
+// accumulators: per trajectory one address add, one shared load and one fp16x2 add (the two
+// blocks of the thread are the halves of one word).  uniform: all trajectories share rel[0]
+// (one load, added to every accumulator: the same values in the same order as the general path).
+__device__ __forceinline__ void accumulate_stage(__half2 (&acc)[S_C], const unsigned char* st,
+                                                 int pitch, bool uniform, const PlanRec* slot,
+                                                 int warp, int lane) {
+  const uint32_t base = smem_u32(st) + (uint32_t)(warp * S_ROWS * pitch + lane) * 4u;
   if (uniform) {
-    const uint32_t q = base + (uint32_t)slot->rel[0];
-    const uint32_t w0 = lds_u32(q), w1 = lds_u32_off<8 * PITCH>(q);
+    const uint32_t w = lds_u32(base + (uint32_t)slot->rel[0]);
 #pragma unroll
-    for (int v = 0; v < S_C; ++v) {
-      acc[0][v] = __hadd2(acc[0][v], *reinterpret_cast<const __half2*>(&w0));
-      acc[1][v] = __hadd2(acc[1][v], *reinterpret_cast<const __half2*>(&w1));
-    }
+    for (int v = 0; v < S_C; ++v) acc[v] = __hadd2(acc[v], *reinterpret_cast<const __half2*>(&w));
     return;
   }
   const uint32_t relv = smem_u32(slot->rel);
@@ -1106,10 +1101,8 @@ __device__ __forceinline__ void accumulate_stage(__half2 (&acc)[2][S_C], const u
     const int rr[4] = {r4.x, r4.y, r4.z, r4.w};
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const uint32_t q = base + (uint32_t)rr[u];
-      const uint32_t w0 = lds_u32(q), w1 = lds_u32_off<8 * PITCH>(q);
-      acc[0][vq * 4 + u] = __hadd2(acc[0][vq * 4 + u], *reinterpret_cast<const __half2*>(&w0));
-      acc[1][vq * 4 + u] = __hadd2(acc[1][vq * 4 + u], *reinterpret_cast<const __half2*>(&w1));
+      const uint32_t w = lds_u32(base + (uint32_t)rr[u]);
+      acc[vq * 4 + u] = __hadd2(acc[vq * 4 + u], *reinterpret_cast<const __half2*>(&w));
     }
   }
 }
@@ -1347,11 +1340,9 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
       };
 
       for (int c = 0; c < A.nchunk; ++c) {
-        __half2 acc[2][S_C];
+        __half2 acc[S_C];  // per trajectory: (block rows 0-1, block rows 2-3) of this thread
 #pragma unroll
-        for (int pp = 0; pp < 2; ++pp)
-#pragma unroll
-          for (int v = 0; v < S_C; ++v) acc[pp][v] = __float2half2_rn(0.0f);
+        for (int v = 0; v < S_C; ++v) acc[v] = __float2half2_rn(0.0f);
 
         for (int t = 0; t < T; ++t, ++it) {
           const int slot = (int)(it % S_D);
@@ -1361,24 +1352,19 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
             const int mode = rec->box.w & 7;
             const unsigned char* st = arena + sinfo[slot].x;
             if (mode != 0) {
-              const bool uni = (rec->box.w & 8) != 0;
-              if (mode == 1) accumulate_stage<stage_width(1)>(acc, st, uni, rec, warp, lane);
-              else if (mode == 2) accumulate_stage<stage_width(2)>(acc, st, uni, rec, warp, lane);
-              else accumulate_stage<stage_width(3)>(acc, st, uni, rec, warp, lane);
+              accumulate_stage(acc, st, stage_width(mode), (rec->box.w & 8) != 0, rec, warp,
+                               lane);
             } else {
-              // direct loads from the pair planes (word row = image row + 1)
-              const uint32_t* bp = A.bound + (size_t)t * (A.ep.H + 1) * A.Wp;
+              // direct loads from the block planes (word row = first image row + 3)
+              const uint32_t* bp = A.bound + (size_t)t * (A.ep.H + 3) * A.Wp;
 #pragma unroll
               for (int v = 0; v < S_C; ++v) {
                 const int2 o = __ldg(A.offs + (size_t)(c * S_C + v) * T + t);
                 const int x = px + o.x;
-#pragma unroll
-                for (int pp = 0; pp < 2; ++pp) {
-                  const int r = ty0 + warp * S_ROWS + 2 * pp + o.y + 1;
-                  if (x >= 0 && x < A.Wp && r >= 0 && r <= A.ep.H) {
-                    const uint32_t w = __ldg(bp + (size_t)r * A.Wp + x);
-                    acc[pp][v] = __hadd2(acc[pp][v], *reinterpret_cast<const __half2*>(&w));
-                  }
+                const int r = ty0 + warp * S_ROWS + o.y + 3;
+                if (x >= 0 && x < A.Wp && r >= 0 && r < A.ep.H + 3) {
+                  const uint32_t w = __ldg(bp + (size_t)r * A.Wp + x);
+                  acc[v] = __hadd2(acc[v], *reinterpret_cast<const __half2*>(&w));
                 }
               }
             }
@@ -1392,25 +1378,26 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
         // ---- pairs whose bound reaches the admission threshold join the block queue ----
         const int nv = min(S_C, A.n_traj - c * S_C);
         const uint32_t vmask = nv >= 32 ? 0xffffffffu : ((1u << nv) - 1u);
+        // a block passes against the smaller threshold of its two pixels; both are then queued
         uint32_t cb[S_ROWS];
-#pragma unroll
-        for (int pp = 0; pp < 2; ++pp) {
-          const __half2 th = __halves2half2(half_round_down(thr2[2 * pp]),
-                                            half_round_down(thr2[2 * pp + 1]));
+        {
+          const __half2 th = __halves2half2(half_round_down(fminf(thr2[0], thr2[1])),
+                                            half_round_down(fminf(thr2[2], thr2[3])));
           uint32_t b0 = 0u, b1 = 0u;
-          // most chunks have no candidate in the whole warp: test the maxima first
-          __half2 mx = acc[pp][0];
+          __half2 mx = acc[0];
 #pragma unroll
-          for (int v = 1; v < S_C; ++v) mx = __hmax2(mx, acc[pp][v]);
+          for (int v = 1; v < S_C; ++v) mx = __hmax2(mx, acc[v]);
           if (__any_sync(0xffffffffu, __hge2_mask(mx, th) != 0u))
 #pragma unroll
             for (int v = 0; v < S_C; ++v) {
-              const uint32_t m = __hge2_mask(acc[pp][v], th);
+              const uint32_t m = __hge2_mask(acc[v], th);
               b0 |= (m & 1u) << v;
               b1 |= ((m >> 16) & 1u) << v;
             }
-          cb[2 * pp] = ((active >> (2 * pp)) & 1u) ? (b0 & vmask) : 0u;
-          cb[2 * pp + 1] = ((active >> (2 * pp + 1)) & 1u) ? (b1 & vmask) : 0u;
+          cb[0] = (active & 1u) ? (b0 & vmask) : 0u;
+          cb[1] = (active & 2u) ? (b0 & vmask) : 0u;
+          cb[2] = (active & 4u) ? (b1 & vmask) : 0u;
+          cb[3] = (active & 8u) ? (b1 & vmask) : 0u;
         }
         // Append without a barrier: each warp reserves queue positions with one atomic; pairs
         // beyond the capacity stay in cb and are appended after a flush.
@@ -1622,8 +1609,8 @@ static int prepare_stack(const char* who, const float* psi, const float* phi, co
   uint32_t* bound = reinterpret_cast<uint32_t*>(ws + L.bound);
   for (int w = 1; w <= S_NW; ++w)
     for (int h = 0; h < S_NH; ++h) {
-      cuuint64_t dims[3] = {(cuuint64_t)L.Wp, (cuuint64_t)H + 1, (cuuint64_t)T};
-      cuuint64_t strides[2] = {(cuuint64_t)L.Wp * 4, (cuuint64_t)L.Wp * (H + 1) * 4};
+      cuuint64_t dims[3] = {(cuuint64_t)L.Wp, (cuuint64_t)H + 3, (cuuint64_t)T};
+      cuuint64_t strides[2] = {(cuuint64_t)L.Wp * 4, (cuuint64_t)L.Wp * (H + 3) * 4};
       cuuint32_t boxd[3] = {(cuuint32_t)stage_width(w), (cuuint32_t)stage_height(h), 1u};
       cuuint32_t estr[3] = {1u, 1u, 1u};
       CUresult r = enc(&sp.maps.m[(w - 1) * S_NH + h], CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, bound,
@@ -1726,7 +1713,7 @@ static int launch_prep(StackPrep& sp, const kb_schedule& sch, cudaStream_t st) {
   plan_boxes_kernel<<<(L.nchunk * T + 255) / 256, 256, 0, st>>>(offs, L.nchunk, T, sp.x_lo, plan);
   KB_LAUNCH_CHECK("plan_boxes_kernel");
   {
-    size_t total = (size_t)T * (H + 1) * L.Wp;
+    size_t total = (size_t)T * (H + 3) * L.Wp;
     int blocks = (int)std::min<size_t>((total + 255) / 256, (size_t)g_num_sms * 16);
     bound_prep_kernel<<<blocks, 256, 0, st>>>(sp.psi, sp.phi, T, H, W, L.Wp, bound);
     KB_LAUNCH_CHECK("bound_prep_kernel");
