@@ -40,6 +40,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "decam"
+# Shared-memory bytes the bound pass reads per trajectory-epoch: one 32-bit word per (consumer
+# thread, trajectory, epoch) holds the fp16 maxima of two 2-row blocks, i.e. covers 4 start
+# pixels.
+SEARCH_SMEM_BYTES_PER_TE = 1
 
 
 def parse():
@@ -464,10 +468,10 @@ def run_ours(args):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_max = float(peaks.get("sm_max_mhz", 2032.0))
     # Shared-memory load roofline of the bound pass: one 128-byte wavefront per SM per clock;
-    # the bound pass reads one fp16 bound term (2 B) per trajectory-epoch from shared memory.
+    # the bound pass reads SEARCH_SMEM_BYTES_PER_TE from shared memory per trajectory-epoch.
     smem_peak = sms * 128 * sm_max * 1e6 / 1e9                 # GB/s
     te_per_s_kernel = te_step / (k_ms / 1e3)
-    achieved = te_per_s_kernel * 2 / 1e9
+    achieved = te_per_s_kernel * SEARCH_SMEM_BYTES_PER_TE / 1e9
     traffic = search_traffic(kb.version(), args.workload)
     line = {
         "metric": "trajectory-epoch evals/sec", "value": value, "unit": "TE/s",
@@ -481,7 +485,7 @@ def run_ours(args):
                      "kernel": "search_kernel", "kernel_ms": k_ms,
                      "peak_source": "derived: %d SMs x 128 B/clk shared-memory loads x %g MHz "
                                     "(sm_max_mhz, %s)" % (sms, sm_max, peaks_src),
-                     "algorithmic_bytes_per_te": 2,
+                     "algorithmic_bytes_per_te": SEARCH_SMEM_BYTES_PER_TE,
                      "hbm_gather_equiv": {"bytes_per_te": 8,
                                           "achieved_gbs": te_per_s_kernel * 8 / 1e9,
                                           "hbm_peak_gbs": peaks["hbm_gbs"],
@@ -494,7 +498,7 @@ def run_ours(args):
                                    "note": "the naive gather roofline (8 B of psi+phi per "
                                            "trajectory-epoch against the L2 read bandwidth "
                                            "measured by kb_l2_probe at bench start); above 1 "
-                                           "because the exact bound reads 2 B per "
+                                           "because the exact bound reads 1 B per "
                                            "trajectory-epoch from staged shared memory and only "
                                            "0.2% of pairs are gathered in full"}},
         "search_stats": {"te": stats[0], "full_evals": stats[1], "inserts": stats[2],
@@ -851,7 +855,7 @@ def run_batch(args):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_max = float(peaks.get("sm_max_mhz", 2032.0))
     smem_peak = sms * 128 * sm_max * 1e6 / 1e9
-    achieved = te_step * 2 / (ms / 1e3) / 1e9
+    achieved = te_step * SEARCH_SMEM_BYTES_PER_TE / (ms / 1e3) / 1e9
     sizes = {}
     for (H, W, T, ns, na, nm, seed) in specs:
         sizes["%dx%d" % (H, W)] = sizes.get("%dx%d" % (H, W), 0) + 1
@@ -889,7 +893,7 @@ def run_batch(args):
                      "kernel": "search_kernel (batch) + per-stack preparation", "kernel_ms": ms,
                      "peak_source": "derived: %d SMs x 128 B/clk shared-memory loads x %g MHz "
                                     "(sm_max_mhz, %s)" % (sms, sm_max, peaks_src),
-                     "algorithmic_bytes_per_te": 2},
+                     "algorithmic_bytes_per_te": SEARCH_SMEM_BYTES_PER_TE},
         "search_stats": tot, "clocks": clocks, "gpu_launches": launches,
         "e2e": None,
         "e2e_note": "the stacks' psi/phi are device-resident outputs of kb_make_psi_phi; the "
