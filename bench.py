@@ -436,16 +436,39 @@ def run_ours(args):
     stats = kb.search_stats(ws)
 
     # ---- end to end through the C ABI from pinned host buffers ----
+    # Every step copies its inputs from pinned host memory and reads its results back inside the
+    # timed region.  The copy of step i+1 runs on a second stream into the other of two device
+    # input buffers while step i computes (a stream of stacks in production overlaps the same
+    # way); only the first copy is exposed.
     e2e = None
     if not args.no_e2e:
         h2d = sum(v.numel() * v.element_size() for v in host.values())
-        out_host = None
+        copy_stream = torch.cuda.Stream(device=dev)
+        bufs = [{k: torch.empty_like(v) for k, v in d.items()} for _ in range(2)]
+        ev_copied = [torch.cuda.Event() for _ in range(2)]
+        ev_used = [torch.cuda.Event() for _ in range(2)]
+        ev_start = torch.cuda.Event()
+
+        def fetch(i):
+            b = i % 2
+            with torch.cuda.stream(copy_stream):
+                if i >= 2:
+                    copy_stream.wait_event(ev_used[b])  # step i-2 is done with this buffer
+                for k, v in host.items():
+                    bufs[b][k].copy_(v, non_blocking=True)
+                ev_copied[b].record(copy_stream)
+
         barrier()
-        t0 = time.perf_counter()
         e0.record(stream)
-        for _ in range(args.steps):
-            dd = {k: v.to(dev, non_blocking=True) for k, v in host.items()}
-            r = step(dd)
+        ev_start.record(stream)
+        copy_stream.wait_event(ev_start)
+        fetch(0)
+        for i in range(args.steps):
+            if i + 1 < args.steps:
+                fetch(i + 1)
+            stream.wait_event(ev_copied[i % 2])
+            r = step(bufs[i % 2])
+            ev_used[i % 2].record(stream)
             res_host = {k: v.to("cpu", non_blocking=True) for k, v in r.items()}
         e1.record(stream)
         barrier()

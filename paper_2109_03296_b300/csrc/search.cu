@@ -371,13 +371,18 @@ __device__ __forceinline__ unsigned short half_round_up(float v) {
   return u;
 }
 
-// Bound planes of two-row blocks, [T][H+3][Wp] 32-bit words: with M2(y) = max(nu2(y), nu2(y+1))
-// at column x (nu2 = 0 outside the image), word (t, r, x) holds M2(r-3) (low half) and M2(r-1)
-// (high half), each rounded up to fp16; zero in the padding.  A thread summing the blocks
-// (y, y+1) and (y+2, y+3) at row offset dy reads the single word at r = y + dy + 3; with three
-// leading word rows, a word row outside 0 .. H+2 (which TMA fills with zeros) holds no image row.
+// Bound planes, [T][H+3][Wp] 32-bit words of two fp16 values, each rounded up, zero in the
+// padding (nu2 = 0 outside the image):
+//  * pool = 1 (two-row blocks): with M2(y) = max(nu2(y), nu2(y+1)) at column x, word (t, r, x)
+//    holds M2(r-3) (low half) and M2(r-1) (high half).  A thread summing the blocks (y, y+1)
+//    and (y+2, y+3) at row offset dy reads the single word at r = y + dy + 3.
+//  * pool = 0 (single rows): word (t, r, x) holds nu2(r-3) and nu2(r-2).  A thread summing rows
+//    y .. y+3 reads the words at r = y + dy + 3 and r + 2.
+// With three leading word rows, a word row outside 0 .. H+2 (which TMA fills with zeros) holds
+// no image row.
 __global__ void bound_prep_kernel(const float* __restrict__ psi, const float* __restrict__ phi,
-                                  int T, int H, int W, int Wp, uint32_t* __restrict__ bound) {
+                                  int T, int H, int W, int Wp, int pool,
+                                  uint32_t* __restrict__ bound) {
   const size_t total = (size_t)T * (H + 3) * Wp;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (size_t)gridDim.x * blockDim.x) {
@@ -388,8 +393,10 @@ __global__ void bound_prep_kernel(const float* __restrict__ psi, const float* __
     auto m2 = [&](int y) {
       return fmaxf(nu2_at(psi, phi, H, W, plane, y, x), nu2_at(psi, phi, H, W, plane, y + 1, x));
     };
-    const unsigned short lo = half_round_up(m2(r - 3));
-    const unsigned short hi = half_round_up(m2(r - 1));
+    const unsigned short lo =
+        half_round_up(pool ? m2(r - 3) : nu2_at(psi, phi, H, W, plane, r - 3, x));
+    const unsigned short hi =
+        half_round_up(pool ? m2(r - 1) : nu2_at(psi, phi, H, W, plane, r - 2, x));
     bound[i] = (uint32_t)lo | ((uint32_t)hi << 16);
   }
 }
@@ -436,8 +443,8 @@ __global__ void __launch_bounds__(256) tile_score_kernel(
     const uint32_t* plane = bound + (size_t)t * (H + 3) * Wp;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const int y = ya + i / w, x = xa + i % w;
-      // the block of image rows (y, y+1) is the high half of word row y + 2
-      const float v = __half2float(__ushort_as_half((unsigned short)(__ldg(plane + (size_t)(y + 2) * Wp + x) >> 16)));
+      // image row y (pool = 0) or the block of rows (y, y+1) (pool = 1): low half of word row y+3
+      const float v = __half2float(__ushort_as_half((unsigned short)(__ldg(plane + (size_t)(y + 3) * Wp + x) & 0xffffu)));
       cnt += v >= tau ? 1u : 0u;
     }
   }
@@ -1080,18 +1087,29 @@ __device__ __forceinline__ int4 lds_v4(uint32_t addr) {
   return v;
 }
 
-// Sums one staged (chunk, epoch), a rectangle of `pitch`-word rows, into the fp16 block-pair
-// accumulators: per trajectory one address add, one shared load and one fp16x2 add (the two
-// blocks of the thread are the halves of one word).  uniform: all trajectories share rel[0]
-// (one load, added to every accumulator: the same values in the same order as the general path).
-__device__ __forceinline__ void accumulate_stage(__half2 (&acc)[S_C], const unsigned char* st,
-                                                 int pitch, bool uniform, const PlanRec* slot,
-                                                 int warp, int lane) {
+// Sums one staged (chunk, epoch), a rectangle of `pitch`-word rows, into the fp16 accumulators.
+// POOL: per trajectory one address add, one shared load and one fp16x2 add (the thread's two
+// blocks are the halves of one word; acc[0]).  Otherwise two loads, two rows apart, and two adds
+// (rows 0-1 into acc[0], rows 2-3 into acc[1]).  One code path for every box width (the pitch
+// only moves the row bases).  uniform: all trajectories share rel[0] (the same values in the
+// same order as the general path).
+template <bool POOL>
+__device__ __forceinline__ void accumulate_stage(__half2 (&acc)[POOL ? 1 : 2][S_C],
+                                                 const unsigned char* st, int pitch, bool uniform,
+                                                 const PlanRec* slot, int warp, int lane) {
   const uint32_t base = smem_u32(st) + (uint32_t)(warp * S_ROWS * pitch + lane) * 4u;
+  const uint32_t base1 = base + 8u * (uint32_t)pitch;  // two rows further (single rows only)
   if (uniform) {
-    const uint32_t w = lds_u32(base + (uint32_t)slot->rel[0]);
+    const uint32_t w0 = lds_u32(base + (uint32_t)slot->rel[0]);
+    uint32_t w1 = 0u;
+    if (!POOL) w1 = lds_u32(base1 + (uint32_t)slot->rel[0]);
 #pragma unroll
-    for (int v = 0; v < S_C; ++v) acc[v] = __hadd2(acc[v], *reinterpret_cast<const __half2*>(&w));
+    for (int v = 0; v < S_C; ++v) {
+      acc[0][v] = __hadd2(acc[0][v], *reinterpret_cast<const __half2*>(&w0));
+      if (!POOL)
+        acc[POOL ? 0 : 1][v] =
+            __hadd2(acc[POOL ? 0 : 1][v], *reinterpret_cast<const __half2*>(&w1));
+    }
     return;
   }
   const uint32_t relv = smem_u32(slot->rel);
@@ -1101,8 +1119,13 @@ __device__ __forceinline__ void accumulate_stage(__half2 (&acc)[S_C], const unsi
     const int rr[4] = {r4.x, r4.y, r4.z, r4.w};
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const uint32_t w = lds_u32(base + (uint32_t)rr[u]);
-      acc[vq * 4 + u] = __hadd2(acc[vq * 4 + u], *reinterpret_cast<const __half2*>(&w));
+      const uint32_t w0 = lds_u32(base + (uint32_t)rr[u]);
+      acc[0][vq * 4 + u] = __hadd2(acc[0][vq * 4 + u], *reinterpret_cast<const __half2*>(&w0));
+      if (!POOL) {
+        const uint32_t w1 = lds_u32(base1 + (uint32_t)rr[u]);
+        acc[POOL ? 0 : 1][vq * 4 + u] =
+            __hadd2(acc[POOL ? 0 : 1][vq * 4 + u], *reinterpret_cast<const __half2*>(&w1));
+      }
     }
   }
 }
@@ -1140,7 +1163,11 @@ __device__ __noinline__ bool insert_sorted(const SearchArgs& A, size_t wp, int K
 //
 // BATCH: the tiles of several stacks (BatchArgs), each with its own T; the evaluation path is
 // chosen per tile from the stack's T (the template arguments are unused).
-template <int NT, int J, bool BATCH>
+//
+// POOL: the bound planes hold two-row block maxima (see bound_prep_kernel); a passing block
+// queues both of its pixels.  Otherwise the planes hold single rows and each pixel is tested on
+// its own sum.
+template <int NT, int J, bool BATCH, bool POOL>
 __global__ void __launch_bounds__(S_THREADS, 1)
 search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const BatchArgs B) {
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -1340,9 +1367,13 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
       };
 
       for (int c = 0; c < A.nchunk; ++c) {
-        __half2 acc[S_C];  // per trajectory: (block rows 0-1, block rows 2-3) of this thread
+        // per trajectory: POOL: (block of rows 0-1, block of rows 2-3) of this thread in acc[0];
+        // otherwise (row 0, row 1) in acc[0] and (row 2, row 3) in acc[1]
+        __half2 acc[POOL ? 1 : 2][S_C];
 #pragma unroll
-        for (int v = 0; v < S_C; ++v) acc[v] = __float2half2_rn(0.0f);
+        for (int pp = 0; pp < (POOL ? 1 : 2); ++pp)
+#pragma unroll
+          for (int v = 0; v < S_C; ++v) acc[pp][v] = __float2half2_rn(0.0f);
 
         for (int t = 0; t < T; ++t, ++it) {
           const int slot = (int)(it % S_D);
@@ -1352,8 +1383,8 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
             const int mode = rec->box.w & 7;
             const unsigned char* st = arena + sinfo[slot].x;
             if (mode != 0) {
-              accumulate_stage(acc, st, stage_width(mode), (rec->box.w & 8) != 0, rec, warp,
-                               lane);
+              accumulate_stage<POOL>(acc, st, stage_width(mode), (rec->box.w & 8) != 0, rec,
+                                     warp, lane);
             } else {
               // direct loads from the block planes (word row = first image row + 3)
               const uint32_t* bp = A.bound + (size_t)t * (A.ep.H + 3) * A.Wp;
@@ -1361,10 +1392,13 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
               for (int v = 0; v < S_C; ++v) {
                 const int2 o = __ldg(A.offs + (size_t)(c * S_C + v) * T + t);
                 const int x = px + o.x;
-                const int r = ty0 + warp * S_ROWS + o.y + 3;
-                if (x >= 0 && x < A.Wp && r >= 0 && r < A.ep.H + 3) {
-                  const uint32_t w = __ldg(bp + (size_t)r * A.Wp + x);
-                  acc[v] = __hadd2(acc[v], *reinterpret_cast<const __half2*>(&w));
+#pragma unroll
+                for (int pp = 0; pp < (POOL ? 1 : 2); ++pp) {
+                  const int r = ty0 + warp * S_ROWS + 2 * pp + o.y + 3;
+                  if (x >= 0 && x < A.Wp && r >= 0 && r < A.ep.H + 3) {
+                    const uint32_t w = __ldg(bp + (size_t)r * A.Wp + x);
+                    acc[pp][v] = __hadd2(acc[pp][v], *reinterpret_cast<const __half2*>(&w));
+                  }
                 }
               }
             }
@@ -1378,26 +1412,36 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
         // ---- pairs whose bound reaches the admission threshold join the block queue ----
         const int nv = min(S_C, A.n_traj - c * S_C);
         const uint32_t vmask = nv >= 32 ? 0xffffffffu : ((1u << nv) - 1u);
-        // a block passes against the smaller threshold of its two pixels; both are then queued
+        // POOL: a block passes against the smaller threshold of its two pixels; both are then
+        // queued.  Otherwise each row against its own threshold.
         uint32_t cb[S_ROWS];
-        {
-          const __half2 th = __halves2half2(half_round_down(fminf(thr2[0], thr2[1])),
-                                            half_round_down(fminf(thr2[2], thr2[3])));
-          uint32_t b0 = 0u, b1 = 0u;
-          __half2 mx = acc[0];
 #pragma unroll
-          for (int v = 1; v < S_C; ++v) mx = __hmax2(mx, acc[v]);
+        for (int pp = 0; pp < (POOL ? 1 : 2); ++pp) {
+          const __half2 th =
+              POOL ? __halves2half2(half_round_down(fminf(thr2[0], thr2[1])),
+                                    half_round_down(fminf(thr2[2], thr2[3])))
+                   : __halves2half2(half_round_down(thr2[2 * pp]), half_round_down(thr2[2 * pp + 1]));
+          uint32_t b0 = 0u, b1 = 0u;
+          // most chunks have no candidate in the whole warp: test the maxima first
+          __half2 mx = acc[pp][0];
+#pragma unroll
+          for (int v = 1; v < S_C; ++v) mx = __hmax2(mx, acc[pp][v]);
           if (__any_sync(0xffffffffu, __hge2_mask(mx, th) != 0u))
 #pragma unroll
             for (int v = 0; v < S_C; ++v) {
-              const uint32_t m = __hge2_mask(acc[v], th);
+              const uint32_t m = __hge2_mask(acc[pp][v], th);
               b0 |= (m & 1u) << v;
               b1 |= ((m >> 16) & 1u) << v;
             }
-          cb[0] = (active & 1u) ? (b0 & vmask) : 0u;
-          cb[1] = (active & 2u) ? (b0 & vmask) : 0u;
-          cb[2] = (active & 4u) ? (b1 & vmask) : 0u;
-          cb[3] = (active & 8u) ? (b1 & vmask) : 0u;
+          if (POOL) {
+            cb[0] = (active & 1u) ? (b0 & vmask) : 0u;
+            cb[1] = (active & 2u) ? (b0 & vmask) : 0u;
+            cb[2] = (active & 4u) ? (b1 & vmask) : 0u;
+            cb[3] = (active & 8u) ? (b1 & vmask) : 0u;
+          } else {
+            cb[2 * pp] = ((active >> (2 * pp)) & 1u) ? (b0 & vmask) : 0u;
+            cb[2 * pp + 1] = ((active >> (2 * pp + 1)) & 1u) ? (b1 & vmask) : 0u;
+          }
         }
         // Append without a barrier: each warp reserves queue positions with one atomic; pairs
         // beyond the capacity stay in cb and are appended after a flush.
@@ -1569,7 +1613,18 @@ struct StackPrep {
   int x_lo, x_hi, y_lo, y_hi;
   char* ws;
   unsigned long long te;
+  bool pool;  // sum two-row blocks (see pool_blocks)
 };
+
+// Whether the bound pass sums two-row blocks.  A block's sum bounds both of its pixels, at the
+// price of looser sums: for an epoch of pure noise, psi/sqrt(phi) ~ N(0, 1), a pixel adds
+// nu2 = z^2 (z > 0) with mean 1/2 and a block the maximum of two (correlated) such terms, about
+// 3/4.  Blocks pay while their expected noise sum stays well below the admission threshold,
+// taken as 1.5 T <= lh_min^2 (the decam workload: 39 <= 100); at T = 100 (75 against 100) they
+// evaluate 38x more pairs and the search runs 10x slower, so single rows are summed there.
+static bool pool_blocks(int T, float lh_min) {
+  return !(lh_min > 0.0f) || 1.5 * T <= (double)lh_min * lh_min;
+}
 
 // Validates one stack, lays out its workspace, encodes its tensor maps and fills its kernel
 // arguments (no launch).  ctrl: the control block the search kernel will use.
@@ -1605,6 +1660,7 @@ static int prepare_stack(const char* who, const float* psi, const float* phi, co
   sp.y_hi = p->y_hi;
   sp.cs = SearchConsts{};
   for (int t = 0; t < T; ++t) sp.cs.dt[t] = (float)(times[t] - times[0]);
+  sp.pool = pool_blocks(T, p->lh_min);
   sp.te = (unsigned long long)(p->x_hi - p->x_lo) * (p->y_hi - p->y_lo) * n_traj * T;
   uint32_t* bound = reinterpret_cast<uint32_t*>(ws + L.bound);
   for (int w = 1; w <= S_NW; ++w)
@@ -1674,7 +1730,7 @@ static int prepare_stack(const char* who, const float* psi, const float* phi, co
 // Enqueues a stack's preparation: velocity ordering, track offsets, staging plan, bound planes
 // and (when sch.tile_order and the stack has at most S_ORDER_MAX tiles) its tile order.  Sets
 // sp.A.order accordingly.
-static int launch_prep(StackPrep& sp, const kb_schedule& sch, cudaStream_t st) {
+static int launch_prep(StackPrep& sp, const kb_schedule& sch, bool pool, cudaStream_t st) {
   const WsLayout& L = sp.L;
   char* ws = sp.ws;
   const int T = sp.T, H = sp.H, W = sp.W, n_traj = sp.n_traj;
@@ -1715,7 +1771,8 @@ static int launch_prep(StackPrep& sp, const kb_schedule& sch, cudaStream_t st) {
   {
     size_t total = (size_t)T * (H + 3) * L.Wp;
     int blocks = (int)std::min<size_t>((total + 255) / 256, (size_t)g_num_sms * 16);
-    bound_prep_kernel<<<blocks, 256, 0, st>>>(sp.psi, sp.phi, T, H, W, L.Wp, bound);
+    bound_prep_kernel<<<blocks, 256, 0, st>>>(sp.psi, sp.phi, T, H, W, L.Wp, pool ? 1 : 0,
+                                              bound);
     KB_LAUNCH_CHECK("bound_prep_kernel");
     const size_t npx = (size_t)T * H * W;
     pair_planes_kernel<<<(int)std::min<size_t>((npx + 255) / 256, (size_t)g_num_sms * 16), 256, 0,
@@ -1752,16 +1809,22 @@ static int launch_search_single(const StackPrep& sp, cudaStream_t st) {
     return fail(KB_ERR_UNSUPPORTED, "kb_search: %d SMs, at most %d supported", g_num_sms,
                 S_REC_BLOCKS);
   const size_t smem = SmemLayout::total;
-#define KB_SEARCH_LAUNCH(NT, JJ)                                                               \
+#define KB_SEARCH_LAUNCH(NT, JJ, PL)                                                           \
   do {                                                                                         \
-    KB_CUDA_TRY(cudaFuncSetAttribute(search_kernel<NT, JJ, false>,                             \
+    KB_CUDA_TRY(cudaFuncSetAttribute(search_kernel<NT, JJ, false, PL>,                         \
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-    search_kernel<NT, JJ, false><<<grid, S_THREADS, smem, st>>>(sp.maps, A, BatchArgs{});      \
+    search_kernel<NT, JJ, false, PL><<<grid, S_THREADS, smem, st>>>(sp.maps, A, BatchArgs{});  \
   } while (0)
-  if (T <= 16) KB_SEARCH_LAUNCH(16, 1);
-  else if (T <= 32) KB_SEARCH_LAUNCH(32, 1);
-  else if (T <= 64) KB_SEARCH_LAUNCH(0, 2);
-  else KB_SEARCH_LAUNCH(0, 4);
+#define KB_SEARCH_LAUNCH_T(PL)                  \
+  do {                                          \
+    if (T <= 16) KB_SEARCH_LAUNCH(16, 1, PL);   \
+    else if (T <= 32) KB_SEARCH_LAUNCH(32, 1, PL); \
+    else if (T <= 64) KB_SEARCH_LAUNCH(0, 2, PL);  \
+    else KB_SEARCH_LAUNCH(0, 4, PL);            \
+  } while (0)
+  if (sp.pool) KB_SEARCH_LAUNCH_T(true);
+  else KB_SEARCH_LAUNCH_T(false);
+#undef KB_SEARCH_LAUNCH_T
 #undef KB_SEARCH_LAUNCH
   KB_LAUNCH_CHECK("search_kernel");
   return KB_OK;
@@ -1801,7 +1864,7 @@ extern "C" int kb_search(const float* psi, const float* phi, const double* times
                          static_cast<char*>(workspace), ws_bytes, sp);
   if (rc != KB_OK) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  rc = launch_prep(sp, kDefaultSchedule, st);
+  rc = launch_prep(sp, kDefaultSchedule, sp.pool, st);
   if (rc != KB_OK) return rc;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   profile_events(&ev0, &ev1);
@@ -1965,7 +2028,7 @@ static int batch_enqueue(kb_batch* b, cudaStream_t st) {
     for (int k = 0; k < n; ++k) {
       cudaStream_t q = b->cs[k % kb_batch::NS];
       StackPrep& sp = b->sp[b->order[k]];
-      int rc = launch_prep(sp, b->sch, q);
+      int rc = launch_prep(sp, b->sch, sp.pool, q);
       if (rc == KB_OK) rc = launch_search_single(sp, q);
       if (rc != KB_OK) return rc;
       stack_done_kernel<<<1, 1, 0, q>>>(done_ns + k);
@@ -1979,8 +2042,12 @@ static int batch_enqueue(kb_batch* b, cudaStream_t st) {
     KB_LAUNCH_CHECK("batch_sum_kernel");
     return KB_OK;
   }
+  // one persistent launch: one kind of bound planes for all stacks (blocks only if every stack
+  // takes them)
+  bool pool = true;
+  for (int k = 0; k < n; ++k) pool = pool && b->sp[k].pool;
   for (int k = 0; k < n; ++k) {
-    int rc = launch_prep(b->sp[b->order[k]], b->sch, st);
+    int rc = launch_prep(b->sp[b->order[k]], b->sch, pool, st);
     if (rc != KB_OK) return rc;
   }
   BatchArgs B{};
@@ -1993,14 +2060,14 @@ static int batch_enqueue(kb_batch* b, cudaStream_t st) {
   B.done_tiles = done_tiles;
   B.done_ns = done_ns;
   const size_t smem = SmemLayout::total;
-  KB_CUDA_TRY(cudaFuncSetAttribute(search_kernel<0, 1, true>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  auto kern = pool ? search_kernel<0, 1, true, true> : search_kernel<0, 1, true, false>;
+  KB_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int grid = std::min(b->total_tiles, g_num_sms);
   if (grid > S_REC_BLOCKS)
     return fail(KB_ERR_UNSUPPORTED, "kb_batch_run: %d SMs, at most %d supported", g_num_sms,
                 S_REC_BLOCKS);
   static const TmapSet kNoMaps{};
-  search_kernel<0, 1, true><<<grid, S_THREADS, smem, st>>>(kNoMaps, SearchArgs{}, B);
+  kern<<<grid, S_THREADS, smem, st>>>(kNoMaps, SearchArgs{}, B);
   KB_LAUNCH_CHECK("search_kernel (batch)");
   return KB_OK;
 }
