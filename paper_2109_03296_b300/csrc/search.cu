@@ -1079,6 +1079,12 @@ __device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
   asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
   return v;
 }
+template <int OFF>
+__device__ __forceinline__ uint32_t lds_u32_off(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1+%2];" : "=r"(v) : "r"(addr), "n"(OFF));
+  return v;
+}
 __device__ __forceinline__ int4 lds_v4(uint32_t addr) {
   int4 v;
   asm volatile("ld.shared.v4.s32 {%0, %1, %2, %3}, [%4];"
@@ -1091,12 +1097,15 @@ __device__ __forceinline__ int4 lds_v4(uint32_t addr) {
 // POOL: per trajectory one address add, one shared load and one fp16x2 add (the thread's two
 // blocks are the halves of one word; acc[0]).  Otherwise two loads, two rows apart, and two adds
 // (rows 0-1 into acc[0], rows 2-3 into acc[1]).  One code path for every box width (the pitch
-// only moves the row bases).  uniform: all trajectories share rel[0] (the same values in the
-// same order as the general path).
-template <bool POOL>
+// only moves the row bases; single rows take the pitch as a template constant PITCH, so that the
+// second load is at an immediate offset and costs no address add).  uniform: all trajectories
+// share rel[0] (the same values in the same order as the general path).
+template <bool POOL, int PITCH>
 __device__ __forceinline__ void accumulate_stage(__half2 (&acc)[POOL ? 1 : 2][S_C],
-                                                 const unsigned char* st, int pitch, bool uniform,
-                                                 const PlanRec* slot, int warp, int lane) {
+                                                 const unsigned char* st, int pitch_rt,
+                                                 bool uniform, const PlanRec* slot, int warp,
+                                                 int lane) {
+  const int pitch = PITCH > 0 ? PITCH : pitch_rt;
   const uint32_t base = smem_u32(st) + (uint32_t)(warp * S_ROWS * pitch + lane) * 4u;
   const uint32_t base1 = base + 8u * (uint32_t)pitch;  // two rows further (single rows only)
   if (uniform) {
@@ -1119,10 +1128,12 @@ __device__ __forceinline__ void accumulate_stage(__half2 (&acc)[POOL ? 1 : 2][S_
     const int rr[4] = {r4.x, r4.y, r4.z, r4.w};
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const uint32_t w0 = lds_u32(base + (uint32_t)rr[u]);
+      const uint32_t q = base + (uint32_t)rr[u];
+      const uint32_t w0 = lds_u32(q);
       acc[0][vq * 4 + u] = __hadd2(acc[0][vq * 4 + u], *reinterpret_cast<const __half2*>(&w0));
       if (!POOL) {
-        const uint32_t w1 = lds_u32(base1 + (uint32_t)rr[u]);
+        const uint32_t w1 = PITCH > 0 ? lds_u32_off<8 * (PITCH > 0 ? PITCH : 1)>(q)
+                                      : lds_u32(base1 + (uint32_t)rr[u]);
         acc[POOL ? 0 : 1][vq * 4 + u] =
             __hadd2(acc[POOL ? 0 : 1][vq * 4 + u], *reinterpret_cast<const __half2*>(&w1));
       }
@@ -1383,8 +1394,15 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
             const int mode = rec->box.w & 7;
             const unsigned char* st = arena + sinfo[slot].x;
             if (mode != 0) {
-              accumulate_stage<POOL>(acc, st, stage_width(mode), (rec->box.w & 8) != 0, rec,
-                                     warp, lane);
+              const bool uni = (rec->box.w & 8) != 0;
+              if (POOL)
+                accumulate_stage<POOL, 0>(acc, st, stage_width(mode), uni, rec, warp, lane);
+              else if (mode == 1)
+                accumulate_stage<POOL, stage_width(1)>(acc, st, 0, uni, rec, warp, lane);
+              else if (mode == 2)
+                accumulate_stage<POOL, stage_width(2)>(acc, st, 0, uni, rec, warp, lane);
+              else
+                accumulate_stage<POOL, stage_width(3)>(acc, st, 0, uni, rec, warp, lane);
             } else {
               // direct loads from the block planes (word row = first image row + 3)
               const uint32_t* bp = A.bound + (size_t)t * (A.ep.H + 3) * A.Wp;
