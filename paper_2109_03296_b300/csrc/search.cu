@@ -108,6 +108,10 @@ struct EvalParams {
   int T, H, W, min_obs, clip, clip_on, K, mw;
   float q_lo, q_mid, q_hi, n_sigma, c_sigma, lh_min;
   float prune_scale, prune_slack;  // fp16 bound sums: see admission_threshold()
+  // a pair whose fp32 sum of psi^2/phi over its valid epochs with psi > 0 is below this cannot
+  // reach lh_min (Cauchy-Schwarz; lh_min^2 (1 - 1e-3), -inf when lh_min <= 0): the warp-per-pair
+  // evaluation stops before the clip
+  float nu2_floor;
 };
 
 // Workspace layout (offsets in bytes from the workspace base).
@@ -585,11 +589,25 @@ __device__ float eval_pair_warp(const float2* __restrict__ pairs, const EvalPara
   bool keep[J];
   if (ep.clip) {
     float s[J];
+    // the pair's own Cauchy-Schwarz sum comes with the lightcurve: psi^2/phi = psi a for the flux
+    // curve a = psi/phi, a^2 for the likelihood curve a = psi/sqrt(phi).  (A pair per warp
+    // leaves the clip as a whole warp; with a pair per thread the warp would run the clip for
+    // the others anyway, and there the test cost 2%.)
+    float nu2 = 0.0f;
 #pragma unroll
     for (int j = 0; j < J; ++j) {
       a[j] = valid[j] ? (ep.clip_on ? __fdiv_rn(ps[j], __fsqrt_rn(ph[j])) : __fdiv_rn(ps[j], ph[j]))
                       : INFINITY;
       s[j] = a[j];
+      if (valid[j] && ps[j] > 0.0f) nu2 += ep.clip_on ? a[j] * a[j] : ps[j] * a[j];
+    }
+    // lane 0's total decides for the whole warp (lanes may differ in the last bit)
+    if (__shfl_sync(0xffffffffu, warp_sum(nu2), 0) < ep.nu2_floor) {
+      if (lane == 0) {
+        rec[0] = __float_as_uint(NAN);
+        rec[2] = (uint32_t)nvalid;
+      }
+      return NAN;
     }
     warp_bitonic_sort<J>(s, lane);
     const float x_lo = warp_percentile<J>(s, nvalid, ep.q_lo);
@@ -1732,6 +1750,8 @@ static int prepare_stack(const char* who, const float* psi, const float* phi, co
   A.ep.lh_min = p->lh_min;
   A.ep.prune_scale = (float)(1.0 / (std::pow(1.0 + std::ldexp(1.0, -11), T) * (1.0 + 3e-7)));
   A.ep.prune_slack = (float)(T * std::ldexp(1.0, -25) * 2.0);
+  A.ep.nu2_floor = p->lh_min > 0.0f ? (float)((double)p->lh_min * p->lh_min * (1.0 - 1e-3))
+                                    : -INFINITY;
   A.n_traj = n_traj;
   A.nchunk = L.nchunk;
   A.Wp = L.Wp;
