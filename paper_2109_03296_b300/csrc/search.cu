@@ -10,26 +10,28 @@
 //    So a (start pixel, trajectory) pair can only enter a top-K list if that bound reaches the
 //    list's current admission threshold (lh_min, or the K-th LH' once the list is full).  The
 //    search therefore runs in two levels:
-//      1. bound pass over blocks of two vertically adjacent start pixels: for block (x, y..y+1),
-//         B2(j) = sum_t max(nu2[t, y + dy_t, x + dx_t], nu2[t, y + 1 + dy_t, x + dx_t]) with
-//         nu2 = psi^2/phi (psi > 0, valid), which bounds the sum of either pixel;
-//      2. full evaluation of both pixels of the few blocks whose bound reaches the smaller of
-//         their two thresholds: gather psi/phi, sigma-G clip, LH', alpha, then insertion into
-//         the pixel's list.
-//    Pairs are dropped only when B2 < thr^2 (1 - 1e-4) (with the fp16 rounding of the sums
-//    accounted for, see admission_threshold), so the output equals evaluating every pair.
+//      1. bound pass, B(p, j) = sum_t nu2[t, p + d_t(j)] with nu2 = psi^2/phi (psi > 0, valid),
+//         taken either per start pixel or, when that pays (pool_blocks: 1.5 T <= lh_min^2),
+//         over blocks of two vertically adjacent start pixels, B2 = sum_t of the larger nu2 of
+//         the two shifted pixels, which bounds the sum of either;
+//      2. full evaluation of the few pairs (of both pixels of a passing block) whose bound
+//         reaches the admission threshold (a block: the smaller of its pixels' thresholds):
+//         gather psi/phi, sigma-G clip, LH', alpha, then insertion into the pixel's list.
+//    Pairs are dropped only when the sum is below thr^2 (1 - 1e-4) (with the fp16 rounding of
+//    the sums accounted for, see admission_threshold), so the output equals evaluating every
+//    pair.
 //
-//  * Bound pass layout.  The block maxima are written once per call into the workspace as fp16
-//    pairs: word (t, r, x) of a [T][H+3][Wp] uint32 array (Wp = W rounded up to 32) holds the
-//    maxima of image rows (r-3, r-2) and (r-1, r) at column x, each rounded up.  A block owns a
-//    tile of 32 x 56 start pixels (lane = x, 4 rows = two blocks per consumer thread) and sweeps
-//    the velocity list in chunks of 32 trajectories that are close in velocity space (Hilbert
-//    order of (vx, vy) from the plan kernels).  For each (chunk, epoch) the union of the tile's
-//    32 shifted footprints is one small rectangle, fetched with one TMA box into a shared-memory
-//    ring by producer warps while the consumer warps sum earlier ones.  A consumer thread then
-//    does, per trajectory, one address add, one 32-bit shared load (its two blocks) and one
-//    fp16x2 add.  A (chunk, epoch) rectangle too large for a stage falls back to direct global
-//    loads.
+//  * Bound pass layout.  The terms are written once per call into the workspace as fp16 pairs,
+//    rounded up: word (t, r, x) of a [T][H+3][Wp] uint32 array (Wp = W rounded up to 32) holds
+//    rows r-3 and r-2 (single rows) or the maxima of rows (r-3, r-2) and (r-1, r) (blocks) at
+//    column x.  A block owns a tile of 32 x 56 start pixels (lane = x, 4 rows per consumer
+//    thread) and sweeps the velocity list in chunks of 32 trajectories that are close in
+//    velocity space (Hilbert order of (vx, vy) from the plan kernels).  For each (chunk, epoch)
+//    the union of the tile's 32 shifted footprints is one small rectangle, fetched with one TMA
+//    box into a shared-memory ring by producer warps while the consumer warps sum earlier ones.
+//    A consumer thread then does, per trajectory, one address add, one 32-bit shared load and
+//    one fp16x2 add (blocks), or two loads two rows apart and two adds (single rows).  A
+//    (chunk, epoch) rectangle too large for a stage falls back to direct global loads.
 //
 //  * Full evaluation.  After each chunk, the pairs whose bound passes are appended to a queue
 //    in shared memory; the queue is evaluated in one batch once
