@@ -69,6 +69,11 @@ typedef struct kb_search_params {
                           and/or flux values") */
   int32_t x_lo, x_hi;  /* start-pixel window [x_lo, x_hi) x [y_lo, y_hi); the whole image is */
   int32_t y_lo, y_hi;  /* 0..W, 0..H */
+  int32_t bound_rows;  /* start-pixel rows per term of the pruning bound (an implementation
+                          choice; the results do not depend on it): 0 = automatic (2 when
+                          1.5 T <= lh_min^2 or lh_min <= 0, else 1), 1 = every start pixel on its
+                          own, 2 = blocks of two vertically adjacent start pixels, whose sum
+                          bounds both (half the bound-pass work, looser). */
 } kb_search_params;
 
 /* Library version (major*10000 + minor*100 + patch). */

@@ -50,13 +50,14 @@ class SearchParams:
     n_sigma: float = 2.0
     clip_on: int = 0
     window: tuple = None          # (x_lo, x_hi, y_lo, y_hi); None = whole image
+    bound_rows: int = 0           # pruning bound per 1 or 2 start-pixel rows; 0 = automatic
 
     def to_c(self, H, W):
         x_lo, x_hi, y_lo, y_hi = self.window if self.window is not None else (0, W, 0, H)
         return SearchParamsC(int(self.k), float(self.lh_min), int(self.min_obs), int(self.clip),
                              float(self.q_lo), float(self.q_mid), float(self.q_hi),
                              float(self.n_sigma), int(self.clip_on), int(x_lo), int(x_hi),
-                             int(y_lo), int(y_hi))
+                             int(y_lo), int(y_hi), int(self.bound_rows))
 
 
 def _dev(t, dtype, name, ndim=None):

@@ -42,7 +42,7 @@ class SearchParamsC(C.Structure):
                 ("clip", C.c_int32), ("q_lo", C.c_float), ("q_mid", C.c_float),
                 ("q_hi", C.c_float), ("n_sigma", C.c_float), ("clip_on", C.c_int32),
                 ("x_lo", C.c_int32), ("x_hi", C.c_int32), ("y_lo", C.c_int32),
-                ("y_hi", C.c_int32)]
+                ("y_hi", C.c_int32), ("bound_rows", C.c_int32)]
 
 
 class RefineParamsC(C.Structure):

@@ -49,7 +49,7 @@ extern "C" void kb_profile_events(void* start, void* stop) {
   kb::g_prof_stop = static_cast<cudaEvent_t>(stop);
 }
 
-extern "C" int kb_version(void) { return 136; }  // 0.1.4
+extern "C" int kb_version(void) { return 137; }  // 0.1.5
 
 extern "C" const char* kb_last_error(void) { return kb::g_last_error.c_str(); }
 
@@ -68,6 +68,7 @@ extern "C" void kb_search_params_default(kb_search_params* p, int H, int W) {
   p->x_hi = W;
   p->y_lo = 0;
   p->y_hi = H;
+  p->bound_rows = 0;
 }
 
 // ------------------------------------------------------------------------------------------------

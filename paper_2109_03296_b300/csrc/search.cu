@@ -1605,6 +1605,8 @@ static int validate(const float* psi, const float* phi, const double* times, int
   if (p->clip != 0 && p->clip != 1) return fail(KB_ERR_INVALID_ARG, "kb_search: clip must be 0 or 1");
   if (p->clip_on != 0 && p->clip_on != 1)
     return fail(KB_ERR_INVALID_ARG, "kb_search: clip_on must be 0 or 1");
+  if (p->bound_rows < 0 || p->bound_rows > 2)
+    return fail(KB_ERR_INVALID_ARG, "kb_search: bound_rows must be 0, 1 or 2");
   if (p->clip) {
     if (!(p->q_lo >= 0.0f && p->q_lo < p->q_hi && p->q_hi <= 1.0f && p->q_mid >= 0.0f &&
           p->q_mid <= 1.0f))
@@ -1698,7 +1700,7 @@ static int prepare_stack(const char* who, const float* psi, const float* phi, co
   sp.y_hi = p->y_hi;
   sp.cs = SearchConsts{};
   for (int t = 0; t < T; ++t) sp.cs.dt[t] = (float)(times[t] - times[0]);
-  sp.pool = pool_blocks(T, p->lh_min);
+  sp.pool = p->bound_rows == 2 || (p->bound_rows == 0 && pool_blocks(T, p->lh_min));
   sp.te = (unsigned long long)(p->x_hi - p->x_lo) * (p->y_hi - p->y_lo) * n_traj * T;
   uint32_t* bound = reinterpret_cast<uint32_t*>(ws + L.bound);
   for (int w = 1; w <= S_NW; ++w)

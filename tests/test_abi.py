@@ -44,6 +44,7 @@ def test_version_and_defaults(L):
     assert (p.k_per_pixel, p.lh_min, p.min_obs, p.clip) == (8, 10.0, 15, 1)
     assert (p.q_lo, p.q_mid, p.q_hi, p.n_sigma, p.clip_on) == (0.25, 0.5, 0.75, 2.0, 0)
     assert (p.x_lo, p.x_hi, p.y_lo, p.y_hi) == (0, 4094, 0, 2046)
+    assert p.bound_rows == 0
 
 
 def _params(L, H=64, W=64, **kw):
@@ -82,6 +83,8 @@ def test_search_rejects_bad_arguments(L):
     assert _search(L, p=_params(L, q_lo=0.0)) == K.KB_ERR_INVALID_ARG
     assert _search(L, p=_params(L, n_sigma=float("nan"))) == K.KB_ERR_INVALID_ARG
     assert _search(L, p=_params(L, x_hi=65)) == K.KB_ERR_INVALID_ARG
+    assert _search(L, p=_params(L, bound_rows=3)) == K.KB_ERR_INVALID_ARG
+    assert _search(L, p=_params(L, bound_rows=-1)) == K.KB_ERR_INVALID_ARG
     assert _search(L, p=_params(L, y_lo=10, y_hi=10)) == K.KB_ERR_INVALID_ARG
     assert _search(L, p=_params(L, clip_on=2)) == K.KB_ERR_INVALID_ARG
     assert _search(L, p=_params(L, min_obs=-1)) == K.KB_ERR_INVALID_ARG

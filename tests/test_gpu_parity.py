@@ -1,7 +1,7 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle on the same seeded inputs.
 
 Sizes are chosen so the oracle finishes in seconds while spanning several tiles (the search tile
-is 32 x 64 start pixels, psi/phi tiles 32 x 32) and ragged tails.  The decam-sized case runs the
+is 32 x 56 start pixels, psi/phi tiles 32 x 32) and ragged tails.  The decam-sized case runs the
 search at full size in the bench's launch configuration and checks sampled windows.
 """
 import math
@@ -151,6 +151,29 @@ def test_search_parity_cases(cuda_device, seed, T, H, W, n_traj, K, lh, min_obs,
     sp = kb.SearchParams(k=K, lh_min=lh, min_obs=min_obs, clip=clip, clip_on=clip_on)
     g, o, stats = _run_both(psi, phi, times, vx, vy, sp, window=window)
     compare_search(g, o, lh)
+
+
+@pytest.mark.parametrize("seed,T,H,W,n_traj,K,lh,min_obs,clip_on", [
+    (21, 13, 101, 77, 70, 4, 1.5, 3, 0),     # ragged tiles, many candidates
+    (22, 26, 90, 64, 96, 8, 3.0, 10, 0),     # the decam epoch count, K = 8
+    (23, 40, 65, 40, 50, 3, 2.0, 10, 1),     # warp-per-pair evaluation, likelihood clip
+])
+def test_search_bound_rows_equivalent(cuda_device, seed, T, H, W, n_traj, K, lh, min_obs,
+                                      clip_on):
+    """The pruning bound per start pixel (bound_rows=1) and per block of two rows
+    (bound_rows=2) are both exact: the oracle's results, and bit-identical to each other."""
+    psi, phi, times, vx, vy = _likelihood_case(seed, T, H, W, n_traj)
+    sp = kb.SearchParams(k=K, lh_min=lh, min_obs=min_obs, clip_on=clip_on, bound_rows=1)
+    g1, o, _ = _run_both(psi, phi, times, vx, vy, sp)
+    compare_search(g1, o, lh)
+    sp2 = kb.SearchParams(k=K, lh_min=lh, min_obs=min_obs, clip_on=clip_on, bound_rows=2)
+    res = kb.search(_cuda(psi), _cuda(phi), times, _cuda(vx), _cuda(vy), sp2)
+    torch.cuda.synchronize()
+    assert kb.search_stats(res["workspace"])[3] == 0
+    g2 = gpu_result_numpy(res)
+    for key in g1:
+        assert np.array_equal(g1[key], g2[key], equal_nan=True), key
+    assert int((g1["idx"] >= 0).sum()) > 0
 
 
 def test_search_fast_movers_fallback(cuda_device):
