@@ -144,6 +144,7 @@ def _likelihood_case(seed, T, H, W, n_traj, mask_frac=0.05, spread=40.0, dup=Tru
     (5, 9, 90, 90, 40, 5, 1.0, 2, 0, 0, (3, 70, 5, 83)),   # clip off, window with x_lo % 4 != 0
     (6, 1, 20, 20, 5, 2, 0.5, 1, 1, 0, None),              # a single epoch
     (7, 17, 64, 32, 1, 1, 1.0, 5, 1, 0, None),             # a single trajectory, exact tile
+    (8, 128, 24, 36, 16, 2, 2.0, 40, 1, 0, None),          # T = KB_MAX_T: four full mask words
 ])
 def test_search_parity_cases(cuda_device, seed, T, H, W, n_traj, K, lh, min_obs, clip, clip_on,
                              window):
