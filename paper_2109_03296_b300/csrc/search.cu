@@ -349,7 +349,7 @@ __global__ void plan_boxes_kernel(const int2* __restrict__ offs, int nchunk, int
       }
   PlanRec& pr = plan[i];
   // bit 3 of box.w: every trajectory of the chunk has the same offset in this epoch (always
-  // at t = 0, often in the first hours), so one load per row pair serves all of them
+  // at t = 0, often in the first hours), so one load (per row pair) serves all of them
   const int uniform = (dxmin == dxmax && dymin == dymax) ? 8 : 0;
   pr.box = make_int4(dxmin - xshift, dymin, hcls, mode | uniform);
   for (int v = 0; v < S_C; ++v) {
