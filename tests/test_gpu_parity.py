@@ -177,10 +177,12 @@ def test_search_bound_rows_equivalent(cuda_device, seed, T, H, W, n_traj, K, lh,
     assert int((g1["idx"] >= 0).sum()) > 0
 
 
-def test_search_fast_movers_fallback(cuda_device):
-    """Velocities spread so widely that the staged rectangle overflows: the direct-load path."""
+@pytest.mark.parametrize("bound_rows", [1, 2])
+def test_search_fast_movers_fallback(cuda_device, bound_rows):
+    """Velocities spread so widely that the staged rectangle overflows: the direct-load path,
+    with single-row sums and with two-row blocks."""
     psi, phi, times, vx, vy = _likelihood_case(11, 8, 80, 90, 48, spread=400.0)
-    sp = kb.SearchParams(k=3, lh_min=1.0, min_obs=2)
+    sp = kb.SearchParams(k=3, lh_min=1.0, min_obs=2, bound_rows=bound_rows)
     g, o, _ = _run_both(psi, phi, times, vx, vy, sp)
     compare_search(g, o, 1.0)
 
