@@ -1313,8 +1313,12 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
       // Evaluate every queued pair (all consumer threads), insert the results (owner threads
       // walk their pixels' lists), empty the queue.  Called by all consumer threads after a
       // consumer barrier.
-      auto flush = [&]() {
-        const int nq = min((int)*s_qcount, S_QCAP);
+      // all = false: evaluate only whole rounds (a multiple of the evaluating threads or warps)
+      // and keep the remainder queued for the next flush, so no round leaves most threads idle.
+      auto flush = [&](bool all) {
+        const int nq_all = min((int)*s_qcount, S_QCAP);
+        const int round = (NT > 0 || (BATCH && T <= 32)) ? S_CTHREADS : S_CWARPS;
+        const int nq = all ? nq_all : nq_all - nq_all % round;
         // a batch's arguments live in shared memory: the evaluations read theirs from registers
         EvalParams ep_copy;
         if (BATCH) ep_copy = A.ep;
@@ -1361,11 +1365,7 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
           by_warp(std::integral_constant<int, J>{});
         }
         consumer_sync();
-        // every thread read the count before the evaluations: reset it while the lists are walked
-        if (tid == 0) {
-          atomicAdd(s_evals, (unsigned int)nq);
-          *s_qcount = 0u;
-        }
+        if (tid == 0) atomicAdd(s_evals, (unsigned int)nq);
 #pragma unroll 1
         for (int i = 0; i < S_ROWS; ++i) {
           const int row = warp * S_ROWS + i;
@@ -1394,6 +1394,14 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
               if (ii == i) thr2[ii] = t2;
           }
         }
+        consumer_sync();
+        // the remainder moves to the front (it lies above nq > remainder: no overlap)
+        const int rem = nq_all - nq;
+        for (int i = tid; i < rem; i += S_CTHREADS) {
+          q_traj[i] = q_traj[nq + i];
+          q_pix[i] = q_pix[nq + i];
+        }
+        if (tid == 0) *s_qcount = (unsigned int)rem;
         consumer_sync();
       };
 
@@ -1525,14 +1533,14 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
           // one barrier per chunk decides, for all consumer threads alike, whether to flush
           const bool full_q = consumer_sync_or(deferred);
           if (full_q || *(volatile unsigned int*)s_qcount >= (unsigned int)S_FLUSH_MIN) {
-            flush();
+            flush(false);
             if (full_q) continue;  // append the pairs that did not fit
           }
           break;
         }
       }
       consumer_sync();
-      if (*(volatile unsigned int*)s_qcount > 0u) flush();
+      if (*(volatile unsigned int*)s_qcount > 0u) flush(true);
       if (BATCH && tid == 0) {  // completion time of the stack whose last tile this was
         __threadfence();
         if (atomicAdd(B.done_tiles + stack, 1u) + 1u == (unsigned int)A.ntiles)
