@@ -34,9 +34,10 @@
 //    (chunk, epoch) rectangle too large for a stage falls back to direct global loads.
 //
 //  * Full evaluation.  After each chunk, the pairs whose bound passes are appended to a queue
-//    in shared memory; the queue is evaluated in one batch once
-//    it holds S_FLUSH_MIN pairs (and at the end of a tile), so every thread has work and no
-//    warp idles at a barrier for a lone candidate.  For T <= 32 one thread evaluates one pair:
+//    in shared memory; once it holds S_FLUSH_MIN pairs the largest whole number of rounds (one
+//    pair per consumer thread, or per warp) is evaluated and the rest stays queued, and at the
+//    end of a tile everything, so no round leaves threads idle and no warp waits at a barrier for
+//    a lone candidate.  For T <= 32 one thread evaluates one pair:
 //    gather into registers, bitonic sorting network on the lightcurve, percentiles, clip, sums in
 //    epoch order (identical tracks give bit-identical LH').  For T > 32 one warp evaluates one
 //    pair with lanes over epochs.  Results that reach lh_min (a small fraction) are pushed onto
@@ -75,8 +76,8 @@ constexpr int S_D = 8;                   // pipeline slots (iterations in flight
 constexpr int S_ARENA_BYTES = 168 * 1024;  // rings of staged rectangles, one per producer
 constexpr int S_RING_BYTES = S_ARENA_BYTES / S_PWARPS;
 constexpr int S_REGION_MAX = 64 * 1024;  // larger rectangles use direct loads
-constexpr int S_QCAP = 1024;             // block queue of full evaluations
-constexpr int S_FLUSH_MIN = S_CTHREADS;  // evaluate the queue once it holds one pair per thread
+constexpr int S_QCAP = 2048;             // block queue of full evaluations
+constexpr int S_FLUSH_MIN = 2 * S_CTHREADS;  // evaluate once the queue holds two pairs per thread
 constexpr int S_REC_WORDS = 8;           // L', alpha, nvalid|nkept<<16, mask[4], pad
 constexpr int S_REC_BLOCKS = 256;        // most blocks of a launch (records in the workspace)
 constexpr float S_PRUNE_MARGIN = 1.0f - 1e-4f;
