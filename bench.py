@@ -33,6 +33,7 @@ import math
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -106,7 +107,10 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % gpu_index)
+        # raw samples go to a scratch file (KB_CLOCKS_DIR, else the system's temporary folder);
+        # the line carries their summary
+        self.path = os.path.join(os.environ.get("KB_CLOCKS_DIR", tempfile.gettempdir()),
+                                 "kb_bench_clocks_%d_%d.csv" % (gpu_index, os.getpid()))
 
     def __enter__(self):
         try:
