@@ -4,6 +4,8 @@ differs), under every schedule, through the CUDA graph and on replay; two stacks
 against the FP64 oracle.  Stacks mix T (thread- and warp-evaluated), sizes, windows, K, clip
 settings and velocity counts.  Inputs are seeded likelihood planes (no input comes from the CUDA
 path)."""
+import dataclasses
+
 import numpy as np
 import pytest
 import torch
@@ -79,6 +81,22 @@ def test_batch_equals_per_stack_search(cuda_device, batch_case):
     assert tot["err"] == 0
     assert tot["te"] == sum(b.te)
     assert np.all(done > 0)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_two_row_blocks(cuda_device, batch_case, mode):
+    """Every stack summed over two-row blocks (bound_rows = 2; the automatic choice takes single
+    rows for these small thresholds), so one persistent launch (mode 0) runs the block kernel:
+    results still bit-identical to kb_search with single rows."""
+    stacks, ref = batch_case
+    blocks = [dict(s, params=dataclasses.replace(s["params"], bound_rows=2)) for s in stacks]
+    b = kb.Batch(blocks)
+    b.schedule = kb.Schedule(mode=mode)
+    res = b.run(graph=True)
+    torch.cuda.synchronize()
+    for i, (r, g) in enumerate(zip(ref, res)):
+        assert _equal(r, g), "stack %d differs (mode %d)" % (i, mode)
+    assert b.stats()[1]["err"] == 0
 
 
 def test_batch_graph_replay_and_schedules(cuda_device, batch_case):
