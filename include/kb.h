@@ -239,7 +239,7 @@ KB_API int kb_stamps(const float* img, const float* var, const uint8_t* mask, co
  *                                 arguments live in parameter space), spread over four
  *                                 streams of the batch, so that a stack's kernel starts on the
  *                                 SMs that the previous one's last tiles leave idle.
- *                  kb_schedule_default: {tile_order 1, hot_nu2 16, score_span 64, stack_order 1,
+ *                  kb_schedule_default: {tile_order 1, hot_nu2 64, score_span 64, stack_order 1,
  *                  mode 1} (kb_search uses the same tile order).
  *   kb_batch       opaque handle: kb_batch_create validates every stack (the checks of
  *                  kb_search), lays out the workspace and writes the batch tables to the device
@@ -254,7 +254,7 @@ KB_API int kb_stamps(const float* img, const float* var, const uint8_t* mask, co
  * kb_batch_set_schedule / kb_batch_get_schedule: knobs above (set waits for the device).
  * kb_batch_autotune: times the batch (kb_batch_run, best of `reps`) under schedules chosen by
  *   coordinate descent from the default (mode and stack order, tile order, hot_nu2 in
- *   {16, 9, 36}, score_span in {64, 32, 128}), keeps the fastest and returns it in *best
+ *   {64, 16, 144}, score_span in {64, 32, 128}), keeps the fastest and returns it in *best
  *   (nullable).  Runs the batch about 9 x reps times; its outputs are those of a normal run.
  * kb_batch_stats: after a run, done_ns[i] = ns from the start of the run to the completion of
  *   stack i's last tile (the caller's order), totals[4] = {trajectory-epochs, full evaluations,

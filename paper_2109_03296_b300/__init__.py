@@ -493,7 +493,7 @@ def candidate_params(pix, slot, result, vx, vy, window=None, stream=None):
 class Schedule:
     """kb_schedule (include/kb.h): scheduling knobs of a batch; results never depend on them."""
     tile_order: int = 1
-    hot_nu2: float = 16.0
+    hot_nu2: float = 64.0
     score_span: int = 64
     stack_order: int = 1
     mode: int = 1           # 0: one persistent launch; 1: concurrent per-stack launches

@@ -1881,7 +1881,9 @@ static int launch_search_single(const StackPrep& sp, cudaStream_t st) {
   return KB_OK;
 }
 
-static const kb_schedule kDefaultSchedule = {1, 16.0f, 64, 1, 1};
+// hot_nu2 64: with block maxima in the planes a lower threshold counts noise; on decam_half
+// 16 -> 64 took the search from 276.5 to 272.7 ms (25..100 all within 0.5%)
+static const kb_schedule kDefaultSchedule = {1, 64.0f, 64, 1, 1};
 
 static int check_schedule(const kb_schedule* s) {
   if (!s) return fail(KB_ERR_INVALID_ARG, "schedule: null pointer");
@@ -2289,7 +2291,7 @@ extern "C" int kb_batch_autotune(kb_batch* b, void* stream, int reps, kb_schedul
   kb_schedule cur = kDefaultSchedule;
   float cur_ms = 0.0f;
   int rc = time_of(cur, &cur_ms);
-  const float hot[] = {16.0f, 9.0f, 36.0f};
+  const float hot[] = {64.0f, 16.0f, 144.0f};
   const int span[] = {64, 32, 128};
   for (int pass = 0; rc == KB_OK && pass < 4; ++pass) {
     std::vector<kb_schedule> cand;
