@@ -206,3 +206,12 @@ int main(void) {
     S = _lib.StackC
     assert offs == [S.vx.offset, S.n_traj.offset, S.params.offset, S.out_lh.offset,
                     S.out_mask.offset]
+
+
+def test_bench_traffic_line_matches_library_version(L):
+    """The bench's roofline carries the DRAM traffic measured on this library version (a line in
+    profiles/search_kernel_decam.md); a kernel change without a new capture would leave it null."""
+    import bench
+    v = L.kb_version()
+    assert bench.search_traffic(v, "decam") is not None
+    assert bench.search_traffic(v, "decam_half") is not None
