@@ -150,8 +150,9 @@ KB_API int kb_search_workspace_size(int T, int H, int W, int n_traj, const kb_se
  * Velocities must be finite; a track offset beyond +-2^24 pixels is clamped there (it is off
  * the image either way).
  * Errors: KB_ERR_INVALID_ARG (null pointers, sizes, non-finite times or parameters, bad window,
- * K outside 1..KB_MAX_K), KB_ERR_UNSUPPORTED (T > KB_MAX_T, n_traj > 2^24, H or W > 2^20, an
- * image plane beyond 2^31 pixels), KB_ERR_WORKSPACE, KB_ERR_CUDA.
+ * K outside 1..KB_MAX_K, bound_rows outside 0..2), KB_ERR_UNSUPPORTED (T > KB_MAX_T,
+ * n_traj > 2^24, H or W > 2^20, an image plane beyond 2^31 pixels, a device of more than 256
+ * SMs), KB_ERR_WORKSPACE, KB_ERR_CUDA.
  */
 KB_API int kb_search(const float* psi, const float* phi, const double* times, int T, int H, int W,
               const float* vx, const float* vy, int n_traj, const kb_search_params* p,
