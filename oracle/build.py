@@ -13,12 +13,16 @@ SRC = os.path.join(HERE, "kb_oracle.c")
 LIB = os.path.join(HERE, "libkb_oracle.so")
 
 
+def command(src: str = SRC, out: str = LIB) -> list:
+    """The gcc command line that builds the oracle source ``src`` into the library ``out``."""
+    return ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+            "-fno-fast-math", "-Wall", "-o", out, src, "-lm"]
+
+
 def build(force: bool = False) -> str:
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
         return LIB
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-           "-fno-fast-math", "-Wall", "-o", LIB, SRC, "-lm"]
-    subprocess.check_call(cmd)
+    subprocess.check_call(command())
     return LIB
 
 

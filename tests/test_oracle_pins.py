@@ -199,6 +199,30 @@ def test_psi_phi_at_matches_full():
     assert np.array_equal(ph, phi[tyx[:, 0], tyx[:, 1], tyx[:, 2]])
 
 
+def test_psi_phi_match_scipy_correlate_with_varying_variance():
+    # With masked pixels zeroed, psi_t and phi_t are the zero-padded correlations of I w and w
+    # with P_t and P_t^2 (scipy.ndimage.correlate, a routine the oracle does not use), and 0 at
+    # masked pixels.  The variance varies per pixel, so each tap must take its own pixel's weight.
+    import scipy.ndimage
+    rng = np.random.default_rng(8)
+    T, H, W, k = 3, 26, 21, 7
+    psf = rng.uniform(0.0, 1.0, (T, k, k)).astype(np.float32)   # asymmetric
+    img = rng.normal(size=(T, H, W)).astype(np.float32)
+    var = rng.uniform(0.3, 3.0, (T, H, W)).astype(np.float32)
+    mask = (rng.random((T, H, W)) < 0.08).astype(np.uint8)
+    psi, phi = oracle.psi_phi(img, var, mask, psf)
+    good = mask == 0
+    w = np.where(good, 1.0 / var.astype(np.float64), 0.0)
+    for t in range(T):
+        P = psf[t].astype(np.float64)
+        ref_psi = scipy.ndimage.correlate(img[t] * w[t], P, mode="constant", cval=0.0)
+        ref_phi = scipy.ndimage.correlate(w[t], P * P, mode="constant", cval=0.0)
+        ref_psi[~good[t]] = 0.0
+        ref_phi[~good[t]] = 0.0
+        assert np.allclose(psi[t], ref_psi, rtol=1e-12, atol=1e-12)
+        assert np.allclose(phi[t], ref_phi, rtol=1e-12, atol=1e-12)
+
+
 # ------------------------------------------------------------------------------------------------
 # Search closed form: one noiseless mover, L = SNR sqrt(T), alpha = F  (Section 3: nu = Psi/sqrt Phi)
 # ------------------------------------------------------------------------------------------------
@@ -434,6 +458,26 @@ def test_min_obs_and_off_image():
     assert e["nvalid"] == 1
 
 
+def test_threshold_is_inclusive_at_an_exact_likelihood():
+    # psi = phi = 1 on every pixel: a trajectory with all T = 16 epochs on the image has
+    # Psi = Phi = 16 and L = 16 / sqrt(16) = 4 exactly (and a constant lightcurve keeps every
+    # epoch), one with n < 16 epochs on the image has L = sqrt(n) < 4.  A threshold of exactly 4
+    # keeps the former (ties to the lower trajectory index first); the next float32 above 4
+    # keeps nothing anywhere.
+    T, H, W = 16, 9, 12
+    psi = np.ones((T, H, W))
+    phi = np.ones((T, H, W))
+    times = 0.05 * np.arange(T)
+    vx = np.array([0.0, 10.0], np.float32)      # offsets 0 and round-half-up(0.5 t) <= 8
+    vy = np.zeros(2, np.float32)
+    r = oracle.search(psi, phi, times, vx, vy, dict(k=2, lh_min=4.0, min_obs=1))
+    assert r["idx"][5, 1].tolist() == [0, 1] and r["lh"][5, 1].tolist() == [4.0, 4.0]
+    assert r["idx"][5, 8].tolist() == [0, -1]   # trajectory 1 leaves the image from x0 = 8
+    above = float(np.nextafter(np.float32(4.0), np.float32(5.0)))
+    r = oracle.search(psi, phi, times, vx, vy, dict(k=2, lh_min=above, min_obs=1))
+    assert (r["idx"] < 0).all()
+
+
 # ------------------------------------------------------------------------------------------------
 # Stamps (Section 3.3)
 # ------------------------------------------------------------------------------------------------
@@ -492,15 +536,17 @@ def test_stamps_against_numpy_gather():
 def test_subpixel_eval_equals_integer_eval_on_integer_tracks():
     rng = np.random.default_rng(12)
     T, H, W = 6, 40, 40
-    times = np.arange(T) * 0.25
     phi = rng.uniform(0.2, 1.0, (T, H, W))
     psi = rng.normal(size=(T, H, W)) * np.sqrt(phi)
     vx, vy = np.float32(8.0), np.float32(-4.0)        # integer positions at every epoch
     keep = np.array([(1 << T) - 1], np.uint32)
-    L, a, g = oracle.traj_eval_subpixel(psi, phi, times, keep, 10.0, 20.0, vx, vy)
-    e = oracle.eval_one(psi, phi, times, 10, 20, vx, vy, dict(clip=0, min_obs=0))
-    assert abs(L - e["lh"]) < 1e-12 * abs(e["lh"])
-    assert abs(a - e["flux"]) < 1e-12 * abs(e["flux"])
+    # epochs counted from 0 and as MJDs: both paths measure time from the first epoch
+    for t0 in (0.0, 57000.5):
+        times = t0 + np.arange(T) * 0.25
+        L, a, g = oracle.traj_eval_subpixel(psi, phi, times, keep, 10.0, 20.0, vx, vy)
+        e = oracle.eval_one(psi, phi, times, 10, 20, vx, vy, dict(clip=0, min_obs=0))
+        assert abs(L - e["lh"]) < 1e-12 * abs(e["lh"])
+        assert abs(a - e["flux"]) < 1e-12 * abs(e["flux"])
 
 
 def test_subpixel_gradient_against_finite_differences():
@@ -782,6 +828,24 @@ def test_moments_of_a_sampled_gaussian():
     s[0, 10, 11] = 1.0      # x = 0.5 exactly
     assert not oracle.stamp_moments(s)[1][0]
     assert oracle.stamp_moments(s, limits=(0.5000001, 0.5, 1.5, 36.5, 36.5))[1][0]
+
+
+def test_moment_filter_limits_apply_each_to_its_own_moment():
+    # One lit pixel at (dx, dy) has x = dx, y = dy, xy = dx dy, xx = dx^2, yy = dy^2 exactly.
+    # Limits just above those values pass it; a limit equal to its own moment's magnitude rejects
+    # it (the bounds are strict and act on |x|, |y|, |xy|), and no other limit does.
+    r = 10
+    side = 2 * r + 1
+    for dx, dy in ((2, -3), (-2, 3)):
+        s = np.zeros((1, side, side))
+        s[0, dy + r, dx + r] = 1.5
+        vals = [abs(dx), abs(dy), abs(dx * dy), dx * dx, dy * dy]
+        loose = [v + 1.0 for v in vals]
+        assert oracle.stamp_moments(s, limits=tuple(loose))[1][0]
+        for i in range(5):
+            tight = list(loose)
+            tight[i] = float(vals[i])
+            assert not oracle.stamp_moments(s, limits=tuple(tight))[1][0], (dx, dy, i)
 
 
 # ------------------------------------------------------------------------------------------------
