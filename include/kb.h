@@ -405,15 +405,18 @@ KB_API int kb_candidate_tracks(const int32_t* cand_pix, const int32_t* cand_slot
  * Common arguments:
  *   psi, phi   [T][H][W] float32 (device), as written by kb_make_psi_phi.
  *   times      [T] float64 HOST pointer (finite).
- *   params     [n][4] float32 (device): x0, y0 in pixels, vx, vy in pixels per unit of times.
+ *   params     [n][4] float32 (device, 16-byte aligned: rows are read as float4): x0, y0 in
+ *              pixels, vx, vy in pixels per unit of times.
  *   keep       [n][ceil(T/32)] uint32 (device): bit t of word t/32 set = epoch t kept (the
  *              out_mask layout of kb_search); NULL keeps every epoch.
  * All outputs are caller-owned device arrays.  n = 0 enqueues nothing.
- * Errors: KB_ERR_INVALID_ARG (null pointers, bad sizes, non-finite times or bad refine
- * parameters), KB_ERR_UNSUPPORTED (T > KB_MAX_T, sides > 2^20).
+ * Errors: KB_ERR_INVALID_ARG (null pointers, bad sizes, a params or [n][4] gradient array not
+ * 16-byte aligned, non-finite times or bad refine parameters), KB_ERR_UNSUPPORTED (T > KB_MAX_T,
+ * sides > 2^20).
  */
 
-/* kb_traj_eval_fwd -- out_lh, out_flux [n]; out_grad [n][4] (nullable) receives dL/d(params). */
+/* kb_traj_eval_fwd -- out_lh, out_flux [n]; out_grad [n][4] (nullable, 16-byte aligned)
+ * receives dL/d(params). */
 KB_API int kb_traj_eval_fwd(const float* psi, const float* phi, const double* times, int T, int H,
                             int W, const float* params, const uint32_t* keep, int n,
                             float* out_lh, float* out_flux, float* out_grad, void* stream);
@@ -421,7 +424,8 @@ KB_API int kb_traj_eval_fwd(const float* psi, const float* phi, const double* ti
 /*
  * kb_traj_eval_bwd -- vector-Jacobian product of kb_traj_eval_fwd.  With upstream weights
  * gL = grad_lh[c] and gA = grad_flux[c] (either array nullable, read as zeros):
- *   out_grad_params [n][4] (nullable, overwritten) = gL dL/dparams + gA dalpha/dparams;
+ *   out_grad_params [n][4] (nullable, 16-byte aligned, overwritten) = gL dL/dparams +
+ *   gA dalpha/dparams;
  *   grad_psi, grad_phi [T][H][W] (nullable, ACCUMULATED with atomic adds, in no fixed order):
  *   each kept in-image tap of weight w on epoch t adds cPsi w to grad_psi and cPhi w to grad_phi,
  *   cPsi = gL / sqrt(Phi) + gA / Phi,  cPhi = -gL Psi / (2 Phi^1.5) - gA Psi / Phi^2.
@@ -464,7 +468,8 @@ KB_API int kb_refine(const float* psi, const float* phi, const double* times, in
  * out_params[i] = (x_lo + cand_pix[i] % wx, y_lo + cand_pix[i] / wx, vx[traj], vy[traj]) with
  * traj = idx[cand_pix[i] * K + cand_slot[i]], and out_keep[i] (nullable; needs mask) = that
  * slot's kept-epoch mask from kb_search's out_mask [npix][K][ceil(T/32)].  Other entries get NaN
- * params (kb_refine then reports NaN) and an all-zero mask.  All arrays are device arrays.
+ * params (kb_refine then reports NaN) and an all-zero mask.  All arrays are device arrays;
+ * out_params [n][4] must be 16-byte aligned (KB_ERR_INVALID_ARG otherwise).
  */
 KB_API int kb_candidate_params(const int32_t* cand_pix, const int32_t* cand_slot, int n,
                                const int32_t* idx, const uint32_t* mask, int K, int T,

@@ -421,11 +421,17 @@ __global__ void candidate_params_kernel(const int32_t* __restrict__ cand_pix,
     for (int w = 0; w < MW; ++w) out_keep[i * MW + w] = mask[slot * MW + w];
 }
 
+// params, gradients and out_params are read and written as float4: a row of 4 floats must start on
+// a 16-byte boundary (NULL passes; the callers test it separately).
+static inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
 static int check_common(const char* who, const float* psi, const float* phi, const double* times,
                         int T, int H, int W, const void* params, int n, EpochDt& e) {
   if (!psi || !phi || !times) return fail(KB_ERR_INVALID_ARG, "%s: null pointer argument", who);
   if (n < 0 || T < 1 || H < 1 || W < 1) return fail(KB_ERR_INVALID_ARG, "%s: bad sizes", who);
   if (n > 0 && !params) return fail(KB_ERR_INVALID_ARG, "%s: null params", who);
+  if (n > 0 && !aligned16(params))
+    return fail(KB_ERR_INVALID_ARG, "%s: params not 16-byte aligned", who);
   if (T > KB_MAX_T) return fail(KB_ERR_UNSUPPORTED, "%s: T > KB_MAX_T", who);
   if (H > (1 << 20) || W > (1 << 20))
     return fail(KB_ERR_UNSUPPORTED, "%s: image sides are limited to 2^20 pixels", who);
@@ -471,6 +477,8 @@ extern "C" int kb_traj_eval_fwd(const float* psi, const float* phi, const double
   if (int rc = check_common("kb_traj_eval_fwd", psi, phi, times, T, H, W, params, n, e)) return rc;
   if (n > 0 && (!out_lh || !out_flux))
     return fail(KB_ERR_INVALID_ARG, "kb_traj_eval_fwd: null output");
+  if (n > 0 && !aligned16(out_grad))
+    return fail(KB_ERR_INVALID_ARG, "kb_traj_eval_fwd: out_grad not 16-byte aligned");
   if (n == 0) return KB_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int MW = (T + 31) / 32;
@@ -492,6 +500,8 @@ extern "C" int kb_traj_eval_bwd(const float* psi, const float* phi, const double
   using namespace kb;
   EpochDt e{};
   if (int rc = check_common("kb_traj_eval_bwd", psi, phi, times, T, H, W, params, n, e)) return rc;
+  if (n > 0 && !aligned16(out_grad_params))
+    return fail(KB_ERR_INVALID_ARG, "kb_traj_eval_bwd: out_grad_params not 16-byte aligned");
   if (n == 0) return KB_OK;
   if (!out_grad_params && !grad_psi && !grad_phi) return KB_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -558,6 +568,8 @@ extern "C" int kb_candidate_params(const int32_t* cand_pix, const int32_t* cand_
   if (n == 0) return KB_OK;
   if (!cand_pix || !cand_slot || !idx || !vx || !vy || !out_params || (out_keep && !mask))
     return fail(KB_ERR_INVALID_ARG, "kb_candidate_params: null pointer argument");
+  if (!aligned16(out_params))
+    return fail(KB_ERR_INVALID_ARG, "kb_candidate_params: out_params not 16-byte aligned");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   candidate_params_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
       cand_pix, cand_slot, n, idx, mask, K, (T + 31) / 32, vx, vy, x_lo, y_lo, wx,

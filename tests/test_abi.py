@@ -99,10 +99,10 @@ def test_workspace_size_query(L):
     p = _params(L, 2046, 4094)
     n = C.c_size_t()
     assert L.kb_search_workspace_size(26, 2046, 4094, 32768, C.byref(p), C.byref(n)) == 0
-    # dominated by the [T][H+1][Wp] bound planes (Wp = 4096) and the interleaved (psi, phi)
-    # planes [T][H][W] of 8-byte pairs
-    planes = 26 * 2047 * 4096 * 4 + 26 * 2046 * 4094 * 8
-    assert planes < n.value < planes + 64 * 2 ** 20
+    # dominated by the [T][H+3][Wp] bound planes (Wp = 4096), the interleaved (psi, phi) planes
+    # [T][H][W] of 8-byte pairs and the evaluation records (256 blocks x 2048 x 32 bytes)
+    planes = 26 * 2049 * 4096 * 4 + 26 * 2046 * 4094 * 8 + 256 * 2048 * 32
+    assert planes < n.value < planes + 32 * 2 ** 20
     assert L.kb_search_workspace_size(200, 10, 10, 5, C.byref(p), C.byref(n)) == 2
 
 
@@ -215,3 +215,169 @@ def test_bench_traffic_line_matches_library_version(L):
     v = L.kb_version()
     assert bench.search_traffic(v, "decam") is not None
     assert bench.search_traffic(v, "decam_half") is not None
+
+
+MISALIGNED = C.c_void_p(0x10004)   # 4 bytes past a 16-byte boundary; never dereferenced
+
+
+def _err(L):
+    return L.kb_last_error().decode()
+
+
+def test_refine_entry_points_validate(L):
+    from paper_2109_03296_b300 import _lib as K
+    T = 5
+    times = np.linspace(0, 1, T)
+    tp = times.ctypes.data_as(C.c_void_p)
+
+    def fwd(n=3, params=FAKE, out=FAKE, grad=None, T=T, H=10, W=10, t=tp, psi=FAKE):
+        return L.kb_traj_eval_fwd(psi, FAKE, t, T, H, W, params, None, n, out, out, grad, None)
+
+    assert fwd(n=0, out=None) == K.KB_OK            # nothing to do, no CUDA call
+    assert fwd(psi=None) == K.KB_ERR_INVALID_ARG
+    assert fwd(T=0) == K.KB_ERR_INVALID_ARG
+    assert fwd(n=-1) == K.KB_ERR_INVALID_ARG
+    assert fwd(params=None) == K.KB_ERR_INVALID_ARG
+    assert fwd(out=None) == K.KB_ERR_INVALID_ARG
+    assert fwd(H=(1 << 20) + 1) == K.KB_ERR_UNSUPPORTED
+    long_times = np.linspace(0, 1, K.KB_MAX_T + 1)
+    assert fwd(T=K.KB_MAX_T + 1, t=long_times.ctypes.data_as(C.c_void_p)) == K.KB_ERR_UNSUPPORTED
+    bad = times.copy()
+    bad[2] = np.inf
+    assert fwd(t=bad.ctypes.data_as(C.c_void_p)) == K.KB_ERR_INVALID_ARG
+    # rows of params and of the gradient are float4: a pointer off a 16-byte boundary is refused
+    assert fwd(params=MISALIGNED) == K.KB_ERR_INVALID_ARG and "aligned" in _err(L)
+    assert fwd(grad=MISALIGNED) == K.KB_ERR_INVALID_ARG and "out_grad" in _err(L)
+
+    def bwd(n=3, params=FAKE, gp=None):
+        return L.kb_traj_eval_bwd(FAKE, FAKE, tp, T, 10, 10, params, None, n, None, None, gp,
+                                  FAKE, None, None)
+
+    assert bwd(n=0) == K.KB_OK
+    assert bwd(params=MISALIGNED) == K.KB_ERR_INVALID_ARG
+    assert bwd(gp=MISALIGNED) == K.KB_ERR_INVALID_ARG and "out_grad_params" in _err(L)
+
+    rp0 = K.RefineParamsC()
+    L.kb_refine_params_default(C.byref(rp0))
+    assert (rp0.n_steps, rp0.beta1, rp0.eps) == (20, np.float32(0.9), np.float32(1e-8))
+
+    def refine(rp, n=3, params=FAKE):
+        return L.kb_refine(FAKE, FAKE, tp, T, 10, 10, params, None, n,
+                           None if rp is None else C.byref(rp), FAKE, FAKE, None, None)
+
+    assert refine(rp0, n=0) == K.KB_OK
+    assert refine(None) == K.KB_ERR_INVALID_ARG
+    assert refine(rp0, params=MISALIGNED) == K.KB_ERR_INVALID_ARG
+    for field, value in (("n_steps", -1), ("n_steps", 100001), ("lr_pos", float("nan")),
+                         ("lr_vel", -0.1), ("lr_pos", float("inf")), ("beta1", 1.0),
+                         ("beta2", -0.5), ("eps", 0.0), ("eps", float("inf"))):
+        rp = K.RefineParamsC.from_buffer_copy(rp0)
+        setattr(rp, field, value)
+        assert refine(rp) == K.KB_ERR_INVALID_ARG, (field, value)
+
+    def cand(n=3, K_=8, T_=T, out=FAKE, keep=None, mask=FAKE):
+        return L.kb_candidate_params(FAKE, FAKE, n, FAKE, mask, K_, T_, FAKE, FAKE, 0, 0, 10, out,
+                                     keep, None)
+
+    assert cand(n=0) == K.KB_OK
+    assert cand(K_=0) == K.KB_ERR_INVALID_ARG
+    assert cand(K_=K.KB_MAX_K + 1) == K.KB_ERR_INVALID_ARG
+    assert cand(T_=K.KB_MAX_T + 1) == K.KB_ERR_UNSUPPORTED
+    assert cand(keep=FAKE, mask=None) == K.KB_ERR_INVALID_ARG
+    assert cand(out=MISALIGNED) == K.KB_ERR_INVALID_ARG and "out_params" in _err(L)
+
+
+def test_filter_and_cluster_validate(L):
+    from paper_2109_03296_b300 import _lib as K
+    lim = np.array([0.5, 0.5, 1.5, 36.5, 36.5], np.float32)
+
+    def filt(n=3, radius=10, limits=None, stamps=FAKE, out=FAKE):
+        lp = None if limits is None else limits.ctypes.data_as(C.c_void_p)
+        return L.kb_stamp_filter(stamps, n, radius, lp, None, out, None)
+
+    assert filt(n=0) == K.KB_OK
+    assert filt(n=-1) == K.KB_ERR_INVALID_ARG
+    assert filt(radius=-1) == K.KB_ERR_INVALID_ARG and filt(radius=16) == K.KB_ERR_INVALID_ARG
+    assert filt(stamps=None) == K.KB_ERR_INVALID_ARG and filt(out=None) == K.KB_ERR_INVALID_ARG
+    bad = lim.copy()
+    bad[3] = np.nan
+    assert filt(limits=bad) == K.KB_ERR_INVALID_ARG and "NaN" in _err(L)
+
+    n = C.c_size_t()
+    assert L.kb_cluster_workspace_size(-1, C.byref(n)) == K.KB_ERR_INVALID_ARG
+    assert L.kb_cluster_workspace_size((1 << 24) + 1, C.byref(n)) == K.KB_ERR_UNSUPPORTED
+    assert L.kb_cluster_workspace_size(1000, C.byref(n)) == K.KB_OK and n.value > 0
+    need = n.value
+
+    def clus(n=1000, dt=3.0, radius=4.0, x0=FAKE, ws=C.c_void_p(1 << 20), wsb=need, rounds=None):
+        return L.kb_cluster(x0, FAKE, FAKE, FAKE, None, n, dt, radius, FAKE, FAKE, ws, wsb, rounds,
+                            None)
+
+    r = C.c_int(7)
+    assert clus(n=0, rounds=C.byref(r)) == K.KB_OK and r.value == 0
+    assert clus(n=-1) == K.KB_ERR_INVALID_ARG
+    assert clus(n=(1 << 24) + 1) == K.KB_ERR_UNSUPPORTED
+    assert clus(radius=0.5) == K.KB_ERR_INVALID_ARG
+    assert clus(radius=float("nan")) == K.KB_ERR_INVALID_ARG
+    assert clus(dt=float("inf")) == K.KB_ERR_INVALID_ARG
+    assert clus(x0=None) == K.KB_ERR_INVALID_ARG
+    assert clus(wsb=need - 1) == K.KB_ERR_WORKSPACE
+    assert clus(ws=None) == K.KB_ERR_WORKSPACE
+    assert clus(ws=C.c_void_p((1 << 20) + 16)) == K.KB_ERR_WORKSPACE
+
+
+def test_batch_validates_its_stacks(L):
+    from paper_2109_03296_b300 import _lib as K
+    T, H, W, n_traj = 10, 64, 64, 256
+    times = np.linspace(0, 1, T)
+
+    def stack(**kw):
+        s = K.StackC()
+        for name in ("psi", "phi", "vx", "vy", "out_lh", "out_flux", "out_idx", "out_nvalid",
+                     "out_nkept", "out_mask"):
+            setattr(s, name, 0x10000)
+        s.times = times.ctypes.data
+        s.T, s.H, s.W, s.n_traj = T, H, W, n_traj
+        L.kb_search_params_default(C.byref(s.params), H, W)
+        for k, v in kw.items():
+            if hasattr(s.params, k) and k not in ("T", "H", "W"):
+                setattr(s.params, k, v)
+            else:
+                setattr(s, k, v)
+        return s
+
+    def size(*stacks):
+        arr = (K.StackC * len(stacks))(*stacks)
+        n = C.c_size_t()
+        return L.kb_batch_workspace_size(arr, len(stacks), C.byref(n)), n.value
+
+    rc, one = size(stack())
+    assert rc == K.KB_OK
+    ws1 = C.c_size_t()
+    assert L.kb_search_workspace_size(T, H, W, n_traj, C.byref(stack().params), C.byref(ws1)) == 0
+    assert one >= ws1.value
+    rc, two = size(stack(), stack())
+    assert rc == K.KB_OK and two >= 2 * ws1.value
+    assert L.kb_batch_workspace_size(None, 1, C.byref(C.c_size_t())) == K.KB_ERR_INVALID_ARG
+    arr = (K.StackC * 1)(stack())
+    assert L.kb_batch_workspace_size(arr, 0, C.byref(C.c_size_t())) == K.KB_ERR_INVALID_ARG
+    assert size(stack(), stack(T=0))[0] == K.KB_ERR_INVALID_ARG and "stack 1" in _err(L)
+    assert size(stack(T=K.KB_MAX_T + 1))[0] == K.KB_ERR_UNSUPPORTED
+    assert size(stack(n_traj=(1 << 24) + 1))[0] == K.KB_ERR_UNSUPPORTED
+
+    def create(stacks, ws=C.c_void_p(1 << 30), wsb=None):
+        arr = (K.StackC * len(stacks))(*stacks)
+        h = C.c_void_p(0x1234)
+        wsb = size(*stacks)[1] if wsb is None else wsb
+        rc = L.kb_batch_create(arr, len(stacks), ws, wsb, C.byref(h))
+        return rc, h.value
+
+    assert L.kb_batch_create(arr, 1, C.c_void_p(1 << 30), 1 << 40, None) == K.KB_ERR_INVALID_ARG
+    assert create([stack()], wsb=one - 1) == (K.KB_ERR_WORKSPACE, None)
+    assert create([stack()], ws=C.c_void_p((1 << 30) + 64)) == (K.KB_ERR_WORKSPACE, None)
+    # the checks of kb_search run on every stack before any device work; the message names it
+    for kw in (dict(q_lo=0.8), dict(k_per_pixel=0), dict(bound_rows=3), dict(x_hi=W + 1),
+               dict(out_mask=None), dict(psi=None)):
+        rc, h = create([stack(**kw)])
+        assert rc == K.KB_ERR_INVALID_ARG and h is None, kw
+        assert "stack 0" in _err(L), kw
