@@ -45,7 +45,7 @@ extern "C" {
 /* Status codes. */
 #define KB_OK 0
 #define KB_ERR_INVALID_ARG 1   /* a null pointer, a bad size or a bad parameter value */
-#define KB_ERR_UNSUPPORTED 2   /* a valid request beyond this build's limits (e.g. T > KB_MAX_T) */
+#define KB_ERR_UNSUPPORTED 2   /* a valid request beyond the library's limits (e.g. T > KB_MAX_T) */
 #define KB_ERR_CUDA 3          /* a CUDA runtime call failed; kb_last_error() names it */
 #define KB_ERR_WORKSPACE 4     /* the workspace is null, misaligned or smaller than required */
 #define KB_ERR_TIMEOUT 5       /* a bounded device-side wait gave up (reported by kb_check) */
