@@ -77,3 +77,36 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
 
     bench.run_reference(A())   # returns at once: no oracle work, nothing printed
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_prints_one_contract_line(monkeypatch, capsys):
+    """Rank 0 of the reference arm times the oracle and prints one JSON line with the keys the
+    bench contract names (here on the tiny stack, a fraction of a second of CPU work)."""
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.delenv("RANK", raising=False)
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+
+    class A:
+        workload = "tiny"
+        warmup = 1
+        steps = 2
+        cpu_seconds = 0.05
+        gpus = 1
+
+    bench.run_reference(A())
+    lines = capsys.readouterr().out.strip().splitlines()
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["unit"] == "TE/s" and d["value"] > 0
+    assert (d["steps"], d["warmup"], d["n_gpus"]) == (2, 1, 1)
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["value"] == d["value"] == d["e2e"]["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["config"]["workload"].startswith("tiny") and "fit in L2" in d["config"]["l2"]
+    assert "larger than L2" in bench.workload_config("decam")["l2"]
