@@ -48,7 +48,7 @@ extern "C" {
 #define KB_ERR_UNSUPPORTED 2   /* a valid request beyond the library's limits (e.g. T > KB_MAX_T) */
 #define KB_ERR_CUDA 3          /* a CUDA runtime call failed; kb_last_error() names it */
 #define KB_ERR_WORKSPACE 4     /* the workspace is null, misaligned or smaller than required */
-#define KB_ERR_TIMEOUT 5       /* a bounded device-side wait gave up (reported by kb_check) */
+#define KB_ERR_TIMEOUT 5       /* a bounded device-side wait gave up (see kb_wait_check) */
 
 #define KB_MAX_T 128           /* epochs per stack */
 #define KB_MAX_K 32            /* results kept per start pixel */
@@ -485,6 +485,24 @@ KB_API int kb_candidate_params(const int32_t* cand_pix, const int32_t* cand_slot
  */
 KB_API int kb_l2_probe(const void* buf, size_t bytes, int reps, float* scratch, int blocks,
                        void* stream);
+
+/*
+ * kb_wait_check -- failure detection without a fault: runs the bounded device-side waits of the
+ * search kernel on waits that cannot complete and reports what the device saw.  One thread waits
+ * on an mbarrier phase that nothing completes, first as a producer retiring a ring slot, then as
+ * a consumer waiting for a staged box (each gives up after limit_ns of %globaltimer, as the
+ * search kernel's waits do after 2 s), then once more as a consumer with its block's abort flag
+ * raised (it must return at the flag, as the other warps of a search block do after one wait has
+ * given up).  The device writes its status; the call copies it back (synchronising the stream).
+ *   limit_ns  1e3 .. 1e10 ns; the kernel runs for about 2 limit_ns.
+ *   out       HOST [4] (nullable): status bits (0x1 producer wait gave up, 0x2 consumer wait gave
+ *             up, 0x4 consumer wait ended by the abort flag), then each wait's duration in ns.
+ * Returns KB_ERR_TIMEOUT when all three gave up as designed (the expected outcome: the device
+ * reported the timeouts and the context stays usable), KB_ERR_CUDA if a wait reported success or
+ * ignored the abort flag, KB_ERR_INVALID_ARG for a limit outside the range.  A search whose wait
+ * gives up reports it in kb_search_stats()[3] (kb_batch_stats totals[3]) bit 0x1.
+ */
+KB_API int kb_wait_check(unsigned long long limit_ns, unsigned long long* out, void* stream);
 
 /* Number of kernels this library has launched in the process so far (all entry points). */
 KB_API unsigned long long kb_launch_count(void);

@@ -30,7 +30,7 @@ __all__ = ["SearchParams", "make_psi_phi", "search", "search_workspace_size", "s
            "search_no_alloc", "RefineParams", "traj_eval", "traj_eval_backward", "TrajEval",
            "traj_likelihood", "refine", "candidate_params", "stamp_filter",
            "PAPER_MOMENT_LIMITS", "Schedule", "Batch", "cluster",
-           "KB_MAX_T", "KB_MAX_K", "lib", "version", "alloc_workspace"]
+           "KB_MAX_T", "KB_MAX_K", "lib", "version", "alloc_workspace", "wait_check"]
 
 
 def version():
@@ -300,6 +300,21 @@ def l2_read_bandwidth(mbytes=64, reps=40, device=None):
 def launch_count():
     """Kernels launched by the library in this process so far."""
     return int(lib().kb_launch_count())
+
+
+def wait_check(limit_ns=50_000_000, stream=None):
+    """Runs the search kernel's bounded device-side waits on waits that cannot complete (see
+    kb_wait_check) and returns (status bits, [duration of each wait in ns], message).  The
+    expected outcome, every wait giving up and the device reporting it, is status 7 with the
+    library's KB_ERR_TIMEOUT message; any other outcome raises KbError."""
+    from ._lib import KB_ERR_TIMEOUT
+    out = (C.c_ulonglong * 4)()
+    rc = lib().kb_wait_check(int(limit_ns), out, _stream(stream))
+    msg = lib().kb_last_error().decode(errors="replace")
+    if rc != KB_ERR_TIMEOUT:
+        check(rc)
+        raise KbError(rc, "kb_wait_check returned without the expected timeouts")
+    return int(out[0]), [int(v) for v in out[1:]], msg
 
 
 def profile_events(start=None, stop=None):

@@ -28,7 +28,7 @@ EXPORTS = ("kb_version", "kb_last_error", "kb_search_params_default", "kb_make_p
            "kb_schedule_default", "kb_batch_workspace_size", "kb_batch_create", "kb_batch_run",
            "kb_batch_run_graph", "kb_batch_set_schedule", "kb_batch_get_schedule",
            "kb_batch_autotune", "kb_batch_stats", "kb_batch_destroy",
-           "kb_cluster_workspace_size", "kb_cluster", "kb_l2_probe")
+           "kb_cluster_workspace_size", "kb_cluster", "kb_l2_probe", "kb_wait_check")
 
 
 class KbError(RuntimeError):
@@ -143,6 +143,8 @@ def lib():
                              C.POINTER(C.c_int), p]
     L.kb_l2_probe.restype = i
     L.kb_l2_probe.argtypes = [p, sz, i, p, i, p]
+    L.kb_wait_check.restype = i
+    L.kb_wait_check.argtypes = [C.c_ulonglong, p, p]
     L.kb_stamp_filter.restype = i
     L.kb_stamp_filter.argtypes = [p, i, i, p, p, p, p]
     L.kb_candidate_params.restype = i

@@ -97,15 +97,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity, ui
   return done != 0u;
 }
 
-// Returns true once the phase with the given parity has completed, false after kWaitLimitNs
+// Returns true once the phase with the given parity has completed, false after limit_ns
 // (the caller records the timeout and stops using the buffer).  Each attempt may suspend the
 // thread for up to 20 us, so a waiting warp issues few instructions.
-__device__ __forceinline__ bool mbar_wait_parity(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait_parity(uint64_t* bar, uint32_t parity,
+                                                 unsigned long long limit_ns = kWaitLimitNs) {
   if (mbar_try_wait(bar, parity, 20000u)) return true;
   const unsigned long long t0 = globaltimer_ns();
   for (;;) {
     if (mbar_try_wait(bar, parity, 20000u)) return true;
-    if (globaltimer_ns() - t0 > kWaitLimitNs) return false;
+    if (globaltimer_ns() - t0 > limit_ns) return false;
   }
 }
 

@@ -891,13 +891,14 @@ __device__ __forceinline__ __half half_round_down(float x) {
 // mbar_wait_parity for the consumers: the flag set by a warp that gave up is checked only while
 // waiting (the fast path is one try_wait), so the other warps stop promptly after a timeout.
 __device__ __forceinline__ bool consumer_wait(uint64_t* bar, uint32_t parity,
-                                              const unsigned int* abort_flag) {
+                                              const unsigned int* abort_flag,
+                                              unsigned long long limit_ns = kWaitLimitNs) {
   if (mbar_try_wait(bar, parity, 20000u)) return true;
   const unsigned long long t0 = globaltimer_ns();
   for (;;) {
     if (*(volatile const unsigned int*)abort_flag != 0u) return false;
     if (mbar_try_wait(bar, parity, 20000u)) return true;
-    if (globaltimer_ns() - t0 > kWaitLimitNs) return false;
+    if (globaltimer_ns() - t0 > limit_ns) return false;
   }
 }
 
@@ -2440,4 +2441,67 @@ extern "C" int kb_search_no_alloc(const float* psi, const float* phi, const doub
   return kb_search(psi, phi, times, T, H, W, vx, vy, n_traj, p, out_lh, out_flux, out_idx,
                    out_nvalid, out_nkept, out_mask, scratch, (size_t)KB_STATIC_SCRATCH_BYTES,
                    stream);
+}
+
+// ---------------------------------------------------------------------------------------------
+// kb_wait_check: the search kernel's bounded waits, on waits that cannot complete
+// ---------------------------------------------------------------------------------------------
+namespace kb {
+
+// [0] status bits, [1..3] duration of each wait in ns (kernel-written, read back by the host)
+static __device__ unsigned long long g_wait_status[4];
+
+// One thread waits on phase 0 of an mbarrier that expects one arrival and never gets it: first
+// as a producer retiring a slot (mbar_wait_parity), then as a consumer waiting for a staged box
+// (consumer_wait), both with the given limit; then, with the block's abort flag raised, once
+// more as a consumer, which must return at the flag rather than at the limit.  Every wait is
+// bounded by limit_ns of %globaltimer, so the kernel ends after about twice the limit.
+__global__ void wait_check_kernel(unsigned long long limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ unsigned int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1u);
+    abort_flag = 0u;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  unsigned long long st = 0ull;
+  const unsigned long long t0 = globaltimer_ns();
+  if (!mbar_wait_parity(&bar, 0u, limit_ns)) st |= 0x1ull;
+  const unsigned long long t1 = globaltimer_ns();
+  if (!consumer_wait(&bar, 0u, &abort_flag, limit_ns)) st |= 0x2ull;
+  const unsigned long long t2 = globaltimer_ns();
+  *(volatile unsigned int*)&abort_flag = 1u;
+  if (!consumer_wait(&bar, 0u, &abort_flag, limit_ns)) st |= 0x4ull;
+  const unsigned long long t3 = globaltimer_ns();
+  g_wait_status[0] = st;
+  g_wait_status[1] = t1 - t0;
+  g_wait_status[2] = t2 - t1;
+  g_wait_status[3] = t3 - t2;
+}
+
+}  // namespace kb
+
+extern "C" int kb_wait_check(unsigned long long limit_ns, unsigned long long* out, void* stream) {
+  using namespace kb;
+  if (limit_ns < 1000ull || limit_ns > 10000000000ull)
+    return fail(KB_ERR_INVALID_ARG, "kb_wait_check: limit_ns outside 1e3 .. 1e10");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  wait_check_kernel<<<1, 32, 0, st>>>(limit_ns);
+  KB_LAUNCH_CHECK("wait_check_kernel");
+  unsigned long long h[4] = {0ull, 0ull, 0ull, 0ull};
+  KB_CUDA_TRY(cudaMemcpyFromSymbolAsync(h, g_wait_status, sizeof(h), 0, cudaMemcpyDeviceToHost, st));
+  KB_CUDA_TRY(cudaStreamSynchronize(st));
+  if (out)
+    for (int i = 0; i < 4; ++i) out[i] = h[i];
+  if (h[0] != 0x7ull)
+    return fail(KB_ERR_CUDA, "kb_wait_check: status bits %llu, expected 7 (a wait that cannot "
+                "complete reported success)", h[0]);
+  if (h[3] >= limit_ns)
+    return fail(KB_ERR_CUDA, "kb_wait_check: the raised abort flag did not end the wait (%llu ns)",
+                h[3]);
+  return fail(KB_ERR_TIMEOUT, "kb_wait_check: device-side waits gave up after %llu and %llu ns "
+              "(limit %llu ns); the abort flag ended the third after %llu ns", h[1], h[2],
+              limit_ns, h[3]);
 }
