@@ -51,7 +51,8 @@ def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None,
-                    help="timed steps (default 3; for decam_refine, enough for ~1.5 s)")
+                    help="timed steps (default 5; 3 for batch64 and the reference arm; for "
+                         "decam_refine, enough for ~1.5 s)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
@@ -950,7 +951,9 @@ def main():
     args = parse()
     auto_steps = args.steps is None
     if auto_steps:
-        args.steps = 3
+        # the search: the median of 5 timed steps (~0.6 s each); a batch64 step takes ~10 s and
+        # a reference step ~12 s of CPU, so those time 3
+        args.steps = 5 if (args.impl == "ours" and args.workload != "batch64") else 3
     refine = args.workload.startswith("decam_refine")
     args.auto_steps = auto_steps and refine and args.impl == "ours"
     if args.impl == "reference":
