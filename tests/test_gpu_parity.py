@@ -187,6 +187,22 @@ def test_search_fast_movers_fallback(cuda_device, bound_rows):
     compare_search(g, o, 1.0)
 
 
+def test_search_non_finite_and_negative_planes(cuda_device):
+    """psi/phi planes given directly with NaN, +-inf and non-positive values: an epoch is valid
+    only where phi > 0 and both are finite, on both sides (the bound counts nothing there)."""
+    psi, phi, times, vx, vy = _likelihood_case(13, 12, 60, 75, 40)
+    rng = np.random.default_rng(13)
+    T, H, W = psi.shape
+    for value, frac, plane in ((np.nan, 0.01, psi), (np.inf, 0.005, psi), (-np.inf, 0.005, psi),
+                               (np.nan, 0.01, phi), (np.inf, 0.005, phi), (-1.0, 0.01, phi),
+                               (0.0, 0.01, phi)):
+        plane[rng.random((T, H, W)) < frac] = value
+    sp = kb.SearchParams(k=4, lh_min=1.5, min_obs=3)
+    g, o, stats = _run_both(psi, phi, times, vx, vy, sp)
+    compare_search(g, o, 1.5)
+    assert int((g["idx"] >= 0).sum()) > 0
+
+
 def test_search_degenerate(cuda_device):
     psi, phi, times, vx, vy = _likelihood_case(12, 5, 40, 40, 16)
     # min_obs above T: nothing can be selected
