@@ -164,7 +164,8 @@ void kbo_psi_phi(const float* img, const float* var, const uint8_t* mask, const 
     }
 }
 
-/* psi/phi at a list of sample pixels only (t, y, x triples), for full-size spot checks. */
+/* psi/phi at a list of sample pixels only (t, y, x triples), for full-size spot checks; a triple
+ * outside [0,T) x [0,H) x [0,W) gets NaN. */
 void kbo_psi_phi_at(const float* img, const float* var, const uint8_t* mask, const float* psf,
                     int T, int H, int W, int k, const int32_t* tyx, int n, double* psi,
                     double* phi) {
@@ -173,6 +174,11 @@ void kbo_psi_phi_at(const float* img, const float* var, const uint8_t* mask, con
 #pragma omp parallel for schedule(static)
   for (int s = 0; s < n; ++s) {
     int t = tyx[3 * s], y = tyx[3 * s + 1], x = tyx[3 * s + 2];
+    if (t < 0 || t >= T || y < 0 || y >= H || x < 0 || x >= W) {
+      psi[s] = NAN;
+      phi[s] = NAN;
+      continue;
+    }
     const float* P = psf + (size_t)t * k * k;
     size_t base = (size_t)t * hw;
     size_t o = base + (size_t)y * W + x;

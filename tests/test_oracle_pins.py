@@ -197,6 +197,10 @@ def test_psi_phi_at_matches_full():
     ps, ph = oracle.psi_phi_at(img, var, mask, psf, tyx)
     assert np.array_equal(ps, psi[tyx[:, 0], tyx[:, 1], tyx[:, 2]])
     assert np.array_equal(ph, phi[tyx[:, 0], tyx[:, 1], tyx[:, 2]])
+    # triples outside the stack read NaN
+    bad = np.array([[T, 0, 0], [0, -1, 3], [1, 2, W]])
+    ps, ph = oracle.psi_phi_at(img, var, mask, psf, bad)
+    assert np.isnan(ps).all() and np.isnan(ph).all()
 
 
 def test_psi_phi_match_scipy_correlate_with_varying_variance():
