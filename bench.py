@@ -137,27 +137,41 @@ class ClockSampler:
     def summary(self):
         if self.proc is None or not os.path.exists(self.path):
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        rows = []
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[4:]))
-            except ValueError:
-                continue
-        if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = set()
-        for r in rows:
-            for n, v in zip(names, r[3][1:]):
-                if v.lower() == "active":
-                    reasons.add(n)
-        return {"sm_mhz": statistics.median(r[0] for r in rows),
-                "sm_max_mhz": max(r[1] for r in rows),
-                "power_w_max": max(r[2] for r in rows), "samples": len(rows),
-                "reasons": sorted(reasons)}
+        with open(self.path) as f:
+            return summarize_clock_rows(f)
+
+
+def summarize_clock_rows(lines):
+    """Summary of nvidia-smi rows in ClockSampler.FIELDS order (csv, no header, no units): the
+    median SM clock, the largest max clock and power, and every throttle reason seen active.
+    Rows without numeric clocks are skipped; a power of [N/A] counts as unknown."""
+    rows = []
+    for line in lines:
+        parts = [p.strip() for p in line.split(",")]
+        if len(parts) < 9:
+            continue
+        try:
+            sm, sm_max = float(parts[1]), float(parts[2])
+        except ValueError:
+            continue
+        try:
+            power = float(parts[3])
+        except ValueError:
+            power = None
+        rows.append((sm, sm_max, power, parts[4:]))
+    if not rows:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = set()
+    for r in rows:
+        for n, v in zip(names, r[3][1:]):
+            if v.lower() == "active":
+                reasons.add(n)
+    powers = [r[2] for r in rows if r[2] is not None]
+    return {"sm_mhz": statistics.median(r[0] for r in rows),
+            "sm_max_mhz": max(r[1] for r in rows),
+            "power_w_max": max(powers) if powers else None, "samples": len(rows),
+            "reasons": sorted(reasons)}
 
 
 # ------------------------------------------------------------------------------------------------

@@ -110,3 +110,25 @@ def test_reference_arm_prints_one_contract_line(monkeypatch, capsys):
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["config"]["workload"].startswith("tiny") and "fit in L2" in d["config"]["l2"]
     assert "larger than L2" in bench.workload_config("decam")["l2"]
+
+
+def test_clock_summary_of_nvidia_smi_rows():
+    """The clocks block of the bench line: median SM clock under load, the max clock, and every
+    throttle reason seen active in any sample (rows that do not parse are skipped)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    rows = [
+        "0, 2032, 2032, 613.62, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2032, [N/A], 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2010, 2032, 700.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "[N/A], [N/A], [N/A], [N/A], [N/A], [N/A], [N/A], [N/A], [N/A]",
+        "garbage",
+    ]
+    s = bench.summarize_clock_rows(rows)
+    assert s["sm_mhz"] == 2010.0 and s["sm_max_mhz"] == 2032.0
+    assert s["power_w_max"] == 700.5 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"]
+    hot = rows[0].replace("Not Active, Not Active, Not Active, Not Active",
+                          "Active, Not Active, Active, Not Active")
+    assert bench.summarize_clock_rows([hot])["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    assert bench.summarize_clock_rows([])["reasons"] == ["no samples"]
