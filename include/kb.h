@@ -50,6 +50,12 @@ extern "C" {
 #define KB_ERR_WORKSPACE 4     /* the workspace is null, misaligned or smaller than required */
 #define KB_ERR_TIMEOUT 5       /* a bounded device-side wait gave up (see kb_wait_check) */
 
+/* Host-side fault injection, for tests of a caller's failure handling: every entry point named
+ * in the environment variable KB_FAULT_INJECT (a comma-separated list of names such as
+ * "kb_search,kb_collect", or "*" for all) returns KB_ERR_CUDA with the message
+ * "<name>: injected fault (KB_FAULT_INJECT)" after checking its arguments and before any device
+ * work.  The variable is read at every call; unset or empty, nothing is injected. */
+
 #define KB_MAX_T 128           /* epochs per stack */
 #define KB_MAX_K 32            /* results kept per start pixel */
 #define KB_WORKSPACE_ALIGN 256 /* required alignment of a workspace pointer, in bytes */

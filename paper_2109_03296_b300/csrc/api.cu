@@ -1,6 +1,7 @@
 // api.cu -- status reporting and parameter defaults of libkb_b300.so.
 #include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "kb_internal.cuh"
@@ -30,6 +31,19 @@ int fail(int code, const char* fmt, ...) {
   return code;
 }
 
+bool fault_injected(const char* site) {
+  const char* v = std::getenv("KB_FAULT_INJECT");
+  if (!v || !*v) return false;
+  const size_t n = std::strlen(site);
+  for (const char* p = v;;) {
+    const char* e = std::strchr(p, ',');
+    const size_t len = e ? (size_t)(e - p) : std::strlen(p);
+    if ((len == 1 && *p == '*') || (len == n && std::strncmp(p, site, n) == 0)) return true;
+    if (!e) return false;
+    p = e + 1;
+  }
+}
+
 static std::atomic<unsigned long long> g_launches{0};
 static thread_local cudaEvent_t g_prof_start = nullptr, g_prof_stop = nullptr;
 
@@ -49,7 +63,7 @@ extern "C" void kb_profile_events(void* start, void* stop) {
   kb::g_prof_stop = static_cast<cudaEvent_t>(stop);
 }
 
-extern "C" int kb_version(void) { return 140; }  // 0.1.5
+extern "C" int kb_version(void) { return 140; }  // 0.1.40
 
 extern "C" const char* kb_last_error(void) { return kb::g_last_error.c_str(); }
 

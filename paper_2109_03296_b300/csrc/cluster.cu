@@ -198,6 +198,7 @@ extern "C" int kb_cluster(const int32_t* x0, const int32_t* y0, const float* vx,
     return fail(KB_ERR_WORKSPACE, "kb_cluster: workspace of %zu bytes, %zu needed", ws_bytes, L.total);
   if (reinterpret_cast<uintptr_t>(workspace) % KB_WORKSPACE_ALIGN)
     return fail(KB_ERR_WORKSPACE, "kb_cluster: workspace not %d-byte aligned", KB_WORKSPACE_ALIGN);
+  KB_FAULT_POINT("kb_cluster");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   char* ws = static_cast<char*>(workspace);
   unsigned long long* keys = reinterpret_cast<unsigned long long*>(ws + L.keys);

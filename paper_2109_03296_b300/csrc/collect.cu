@@ -198,6 +198,7 @@ extern "C" int kb_candidate_tracks(const int32_t* cand_pix, const int32_t* cand_
   if (n == 0) return KB_OK;
   if (!cand_pix || !cand_slot || !idx || !vx || !vy || !x0 || !y0 || !out_vx || !out_vy || !traj)
     return fail(KB_ERR_INVALID_ARG, "kb_candidate_tracks: null pointer argument");
+  KB_FAULT_POINT("kb_candidate_tracks");
   candidate_tracks_kernel<<<(n + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(
       cand_pix, cand_slot, n, idx, K, vx, vy, x_lo, y_lo, wx, x0, y0, out_vx, out_vy, traj);
   KB_LAUNCH_CHECK("candidate_tracks_kernel");
@@ -229,6 +230,7 @@ extern "C" int kb_collect(const float* lh, const int32_t* idx, int npix, int K, 
     return fail(KB_ERR_WORKSPACE, "kb_collect: workspace of %zu bytes, %zu needed", ws_bytes, L.total);
   if (reinterpret_cast<uintptr_t>(workspace) % KB_WORKSPACE_ALIGN)
     return fail(KB_ERR_WORKSPACE, "kb_collect: workspace not aligned");
+  KB_FAULT_POINT("kb_collect");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   char* ws = static_cast<char*>(workspace);
   SelState* s = reinterpret_cast<SelState*>(ws + L.state);

@@ -38,6 +38,17 @@ void profile_events(cudaEvent_t* start, cudaEvent_t* stop);
                         cudaGetErrorString(_e));                                       \
   } while (0)
 
+// Host-side fault injection for tests of the callers' failure handling: an entry point named in
+// the environment variable KB_FAULT_INJECT (a comma-separated list of entry-point names, or "*"
+// for all) fails with KB_ERR_CUDA after validating its arguments and before any device work.
+bool fault_injected(const char* site);
+
+#define KB_FAULT_POINT(site)                                                           \
+  do {                                                                                 \
+    if (::kb::fault_injected(site))                                                    \
+      return ::kb::fail(KB_ERR_CUDA, "%s: injected fault (KB_FAULT_INJECT)", site);    \
+  } while (0)
+
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Device error flag bits (kb_search_stats()[3]).

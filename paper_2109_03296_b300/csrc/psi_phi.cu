@@ -130,6 +130,7 @@ extern "C" int kb_make_psi_phi(const float* img, const float* var, const uint8_t
     return fail(KB_ERR_INVALID_ARG, "kb_make_psi_phi: k must be odd and in 1..31 (got %d)", k);
   if (psi == img || phi == img || psi == phi)
     return fail(KB_ERR_INVALID_ARG, "kb_make_psi_phi: outputs alias inputs");
+  KB_FAULT_POINT("kb_make_psi_phi");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   switch (k) {
 #define KB_PP_CASE(K) \

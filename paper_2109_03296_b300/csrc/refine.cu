@@ -480,6 +480,7 @@ extern "C" int kb_traj_eval_fwd(const float* psi, const float* phi, const double
   if (n > 0 && !aligned16(out_grad))
     return fail(KB_ERR_INVALID_ARG, "kb_traj_eval_fwd: out_grad not 16-byte aligned");
   if (n == 0) return KB_OK;
+  KB_FAULT_POINT("kb_traj_eval_fwd");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int MW = (T + 31) / 32;
   const float4* p4 = reinterpret_cast<const float4*>(params);
@@ -504,6 +505,7 @@ extern "C" int kb_traj_eval_bwd(const float* psi, const float* phi, const double
     return fail(KB_ERR_INVALID_ARG, "kb_traj_eval_bwd: out_grad_params not 16-byte aligned");
   if (n == 0) return KB_OK;
   if (!out_grad_params && !grad_psi && !grad_phi) return KB_OK;
+  KB_FAULT_POINT("kb_traj_eval_bwd");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int MW = (T + 31) / 32;
   const float4* p4 = reinterpret_cast<const float4*>(params);
@@ -545,6 +547,7 @@ extern "C" int kb_refine(const float* psi, const float* phi, const double* times
     return fail(KB_ERR_INVALID_ARG, "kb_refine: eps must be finite and > 0");
   if (n > 0 && (!out_lh || !out_flux)) return fail(KB_ERR_INVALID_ARG, "kb_refine: null output");
   if (n == 0) return KB_OK;
+  KB_FAULT_POINT("kb_refine");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   AdamConsts ac{rp->n_steps, rp->lr_pos, rp->lr_vel, rp->beta1, rp->beta2, rp->eps};
   const int MW = (T + 31) / 32;
@@ -570,6 +573,7 @@ extern "C" int kb_candidate_params(const int32_t* cand_pix, const int32_t* cand_
     return fail(KB_ERR_INVALID_ARG, "kb_candidate_params: null pointer argument");
   if (!aligned16(out_params))
     return fail(KB_ERR_INVALID_ARG, "kb_candidate_params: out_params not 16-byte aligned");
+  KB_FAULT_POINT("kb_candidate_params");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   candidate_params_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
       cand_pix, cand_slot, n, idx, mask, K, (T + 31) / 32, vx, vy, x_lo, y_lo, wx,

@@ -1917,6 +1917,7 @@ extern "C" int kb_search(const float* psi, const float* phi, const double* times
                          out_flux, out_idx, out_nvalid, out_nkept, out_mask,
                          static_cast<char*>(workspace), ws_bytes, sp);
   if (rc != KB_OK) return rc;
+  KB_FAULT_POINT("kb_search");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   rc = launch_prep(sp, kDefaultSchedule, sp.pool, st);
   if (rc != KB_OK) return rc;
@@ -2181,6 +2182,10 @@ extern "C" int kb_batch_create(const kb_stack* stacks, int n, void* workspace, s
     b->te_total += b->sp[i].te;
     off = align_up(off + sz, KB_WORKSPACE_ALIGN);
   }
+  if (fault_injected("kb_batch_create")) {
+    delete b;
+    return fail(KB_ERR_CUDA, "kb_batch_create: injected fault (KB_FAULT_INJECT)");
+  }
   cudaError_t e = cudaGetDevice(&b->device);
   if (e == cudaSuccess && g_num_sms == 0)
     e = cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, b->device);
@@ -2208,12 +2213,14 @@ extern "C" int kb_batch_create(const kb_stack* stacks, int n, void* workspace, s
 extern "C" int kb_batch_run(kb_batch* b, void* stream) {
   using namespace kb;
   if (!b) return fail(KB_ERR_INVALID_ARG, "kb_batch_run: null batch");
+  KB_FAULT_POINT("kb_batch_run");
   return batch_enqueue(b, static_cast<cudaStream_t>(stream));
 }
 
 extern "C" int kb_batch_run_graph(kb_batch* b, void* stream) {
   using namespace kb;
   if (!b) return fail(KB_ERR_INVALID_ARG, "kb_batch_run_graph: null batch");
+  KB_FAULT_POINT("kb_batch_run_graph");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (!b->exec) {
     const unsigned long long before = kb_launch_count();

@@ -156,6 +156,7 @@ extern "C" int kb_stamps(const float* img, const float* var, const uint8_t* mask
     cs.dt[t] = (float)(times[t] - times[0]);
   }
   if (n == 0) return KB_OK;
+  KB_FAULT_POINT("kb_stamps");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int J = (T + 31) / 32;
   if (J == 1)
@@ -250,6 +251,7 @@ extern "C" int kb_stamp_filter(const float* stamps, int n, int radius, const flo
     for (int k = 0; k < 5; ++k)
       if (std::isnan(limits[k])) return fail(KB_ERR_INVALID_ARG, "kb_stamp_filter: NaN limit");
   }
+  KB_FAULT_POINT("kb_stamp_filter");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int warps = 8;
   stamp_moments_kernel<<<(unsigned)((n + warps - 1) / warps), warps * 32, 0, st>>>(

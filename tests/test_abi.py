@@ -381,3 +381,57 @@ def test_batch_validates_its_stacks(L):
         rc, h = create([stack(**kw)])
         assert rc == K.KB_ERR_INVALID_ARG and h is None, kw
         assert "stack 0" in _err(L), kw
+
+
+def test_host_fault_injection(L, monkeypatch):
+    """KB_FAULT_INJECT makes the named entry points fail with KB_ERR_CUDA after their argument
+    checks and before any device work (valid arguments, device pointers never dereferenced)."""
+    from paper_2109_03296_b300 import _lib as K
+    T = 5
+    times = np.linspace(0, 1, T)
+    tp = times.ctypes.data_as(C.c_void_p)
+    ws = C.c_void_p(1 << 20)
+    nb = C.c_size_t()
+    assert L.kb_collect_workspace_size(10, C.byref(nb)) == K.KB_OK
+    collect_ws = nb.value
+    assert L.kb_cluster_workspace_size(8, C.byref(nb)) == K.KB_OK
+    cluster_ws = nb.value
+    rp = K.RefineParamsC()
+    L.kb_refine_params_default(C.byref(rp))
+    calls = {
+        "kb_make_psi_phi": lambda: L.kb_make_psi_phi(FAKE, FAKE, None, FAKE, T, 10, 10, 3,
+                                                     C.c_void_p(0x20000), C.c_void_p(0x30000),
+                                                     None),
+        "kb_stamps": lambda: L.kb_stamps(FAKE, FAKE, None, tp, T, 10, 10, FAKE, FAKE, FAKE, FAKE,
+                                         None, 3, 10, FAKE, FAKE, None),
+        "kb_stamp_filter": lambda: L.kb_stamp_filter(FAKE, 3, 10, None, None, FAKE, None),
+        "kb_collect": lambda: L.kb_collect(FAKE, FAKE, 100, 8, 10, FAKE, FAKE, FAKE, ws,
+                                           collect_ws, None),
+        "kb_candidate_tracks": lambda: L.kb_candidate_tracks(FAKE, FAKE, 3, FAKE, 8, FAKE, FAKE,
+                                                             0, 0, 10, FAKE, FAKE, FAKE, FAKE,
+                                                             FAKE, None),
+        "kb_cluster": lambda: L.kb_cluster(FAKE, FAKE, FAKE, FAKE, None, 8, 3.0, 4.0, FAKE, FAKE,
+                                           ws, cluster_ws, None, None),
+        "kb_traj_eval_fwd": lambda: L.kb_traj_eval_fwd(FAKE, FAKE, tp, T, 10, 10, FAKE, None, 3,
+                                                       FAKE, FAKE, None, None),
+        "kb_traj_eval_bwd": lambda: L.kb_traj_eval_bwd(FAKE, FAKE, tp, T, 10, 10, FAKE, None, 3,
+                                                       None, None, FAKE, None, None, None),
+        "kb_refine": lambda: L.kb_refine(FAKE, FAKE, tp, T, 10, 10, FAKE, None, 3, C.byref(rp),
+                                         FAKE, FAKE, None, None),
+        "kb_candidate_params": lambda: L.kb_candidate_params(FAKE, FAKE, 3, FAKE, FAKE, 8, T, FAKE,
+                                                             FAKE, 0, 0, 10, FAKE, None, None),
+    }
+    monkeypatch.setenv("KB_FAULT_INJECT", "*")
+    for name, call in calls.items():
+        assert call() == K.KB_ERR_CUDA, name
+        assert _err(L) == "%s: injected fault (KB_FAULT_INJECT)" % name
+    # argument errors still come first
+    assert L.kb_collect(FAKE, FAKE, 100, 0, 10, FAKE, FAKE, FAKE, ws, collect_ws, None) == \
+        K.KB_ERR_INVALID_ARG
+    # a list names entry points exactly; the others are unaffected (here: nothing to do, n = 0)
+    monkeypatch.setenv("KB_FAULT_INJECT", "kb_refine_x,kb_collect")
+    assert calls["kb_collect"]() == K.KB_ERR_CUDA and "injected" in _err(L)
+    assert L.kb_refine(FAKE, FAKE, tp, T, 10, 10, FAKE, None, 0, C.byref(rp), FAKE, FAKE, None,
+                       None) == K.KB_OK
+    monkeypatch.setenv("KB_FAULT_INJECT", "kb_refine")
+    assert calls["kb_refine"]() == K.KB_ERR_CUDA and "injected" in _err(L)
