@@ -10,7 +10,8 @@ the pins live in tests/test_oracle_pins.py):
   sigma_g_coeff     closed form 1/(2 sqrt2 erfinv(1/2)) via scipy, and 0.7413 printed in Section 3.1
   percentile        numpy.percentile(method="linear") on random samples
   sigma_g_clip      hand-worked examples, constant lightcurve keeps all, +20 sigma spikes rejected
-  track_offsets     numpy float32 arithmetic on random and half-integer cases
+  track_offsets     numpy float32 arithmetic on random (epochs from 0 and as MJDs) and
+                    half-integer cases
   psi_phi           constant variance gives phi = sum P^2/var; delta image gives psi = P/var;
                     scipy.ndimage.correlate of I/var and 1/var with P and P^2 (varying variance)
   search            closed form L = SNR sqrt(T), alpha = F for a noiseless mover; an independent
@@ -22,7 +23,7 @@ the pins live in tests/test_oracle_pins.py):
                     differences of L for the gradient
   traj_vjp          central finite differences of L and alpha in the track parameters and in
                     single psi/phi pixels; tap support; Euler's theorem for the homogeneity
-                    degrees of L and alpha in psi and phi
+                    degrees of L and alpha in psi and phi; it adds to its output arrays
   stamp_moments     closed forms: a single lit pixel at (dx, dy) gives x = dx, y = dy, xy = dx dy,
                     xx = dx^2, yy = dy^2; a flat stamp with one dark pixel at its centre gives
                     xx = yy = side r(r+1)(2r+1) / (3 (side^2 - 1)) (36.75 > 36.5 for r = 10);

@@ -54,6 +54,8 @@ MUTANTS = [
        "offx[(size_t)j * T + t] = track_offset(vx[j], times[t], 0.0);", 1),
       ("offy[(size_t)j * T + t] = track_offset(vy[j], times[t], times[0]);",
        "offy[(size_t)j * T + t] = track_offset(vy[j], times[t], 0.0);", 1)]),
+    ("track_time_difference_in_float32",
+     [("float dt = (float)(t - t0);", "float dt = (float)t - (float)t0;", 1)]),
     ("track_y_uses_vx",
      [("offy[(size_t)j * T + t] = track_offset(vy[j]", "offy[(size_t)j * T + t] = track_offset(vx[j]",
        1)]),
@@ -71,6 +73,9 @@ MUTANTS = [
      [("            if (pixel_masked(img, var, mask, i)) continue;\n            double w",
        "            double w", 1),
       ("        if (pixel_masked(img, var, mask, i)) continue;\n        double w",
+       "        double w", 1)]),
+    ("sampled_psi_phi_use_masked_neighbours",
+     [("        if (pixel_masked(img, var, mask, i)) continue;\n        double w",
        "        double w", 1)]),
     ("masked_centre_not_zeroed",
      [("if (pixel_masked(img, var, mask, o)) { psi[o] = 0.0; phi[o] = 0.0; continue; }", "", 1),
@@ -105,6 +110,12 @@ MUTANTS = [
     ("stamp_ignores_the_kept_mask", [("if (keep_mask && !((keep_mask", "if (0 && keep_mask && !((keep_mask", 1)]),
     ("stamp_uses_masked_pixels",
      [("if (pixel_masked(img, var, mask, i)) continue;\n            vals[m++]", "vals[m++]", 1)]),
+    ("stamp_empty_pixel_zero_not_nan",
+     [("if (m == 0) { out_mean[o] = NAN; out_median[o] = NAN; continue; }",
+       "if (m == 0) { out_mean[o] = 0.0; out_median[o] = 0.0; continue; }", 1)]),
+    ("stamp_kept_mask_bit_off_by_one",
+     [("(keep_mask[(size_t)c * mw + (t >> 5)] >> (t & 31)) & 1u",
+       "(keep_mask[(size_t)c * mw + (t >> 5)] >> ((t + 1) & 31)) & 1u", 1)]),
     ("stamp_flipped", [("int x = x0[c] + ox[t] + sx, y = y0[c] + oy[t] + sy;",
                         "int x = x0[c] + ox[t] - sx, y = y0[c] + oy[t] - sy;", 1)]),
     # sub-pixel evaluation, its gradient and the VJP
@@ -128,12 +139,18 @@ MUTANTS = [
        "double cPh = -0.5 * gL * Ps / (Ph * sqrt(Ph));", 1)]),
     ("vjp_alpha_psi_term_squared",
      [("double cPs = gL / sqrt(Ph) + gA / Ph;", "double cPs = gL / sqrt(Ph) + gA / (Ph * Ph);", 1)]),
+    ("vjp_params_overwritten_not_accumulated",
+     [("grad_params[i] += cPs * dPs[i] + cPh * dPh[i];", "grad_params[i] = cPs * dPs[i] + cPh * dPh[i];",
+       1)]),
+    ("vjp_image_taps_overwritten_not_accumulated",
+     [("if (grad_psi) grad_psi[i] += cPs * w;", "if (grad_psi) grad_psi[i] = cPs * w;", 1)]),
     ("vjp_tap_weights_transposed",
      [("double w = ((k & 1) ? ax : 1.0 - ax) * ((k >> 1) ? ay : 1.0 - ay);",
        "double w = ((k & 1) ? ay : 1.0 - ay) * ((k >> 1) ? ax : 1.0 - ax);", 1)]),
     # Adam refinement
     ("adam_without_bias_correction",
      [("double mh = m[i] / (1.0 - b1k), vh = v[i] / (1.0 - b2k);", "double mh = m[i], vh = v[i];", 1)]),
+    ("adam_second_moment_decay_uses_beta1", [("b2k *= b2;", "b2k *= b1;", 1)]),
     ("adam_descends", [("params[i] += lr * mh / (sqrt(vh) + eps);", "params[i] -= lr * mh / (sqrt(vh) + eps);", 1)]),
     ("adam_rates_swapped", [("double lr = i < 2 ? lr_pos : lr_vel;", "double lr = i < 2 ? lr_vel : lr_pos;", 1)]),
     ("adam_second_moment_unsquared",
@@ -150,6 +167,9 @@ MUTANTS = [
     ("cluster_against_any_earlier", [("if (keep[j] && kbo_dup(", "if (kbo_dup(", 1)]),
     ("cluster_start_only", [("return dx1 * dx1 + dy1 * dy1 <= r2;", "return 1;", 1)]),
     ("cluster_end_only", [("if (dx0 * dx0 + dy0 * dy0 > r2) return 0;", "", 1)]),
+    ("cluster_ignores_valid", [("if (valid && !valid[i]) continue;", "", 1)]),
+    ("cluster_keeps_placeholders",
+     [("if (x0[i] < 0 || x0[i] >= (1 << 20) || y0[i] < 0 || y0[i] >= (1 << 20)) continue;", "", 1)]),
     ("cluster_radius_not_squared", [("double r2 = r * r;", "double r2 = r;", 1)]),
     ("cluster_end_y_uses_vx",
      [("(double)vy[i] * dt", "(double)vx[i] * dt", 1), ("(double)vy[j] * dt", "(double)vx[j] * dt", 1)]),

@@ -105,13 +105,15 @@ def np_offsets(times, v):
 
 def test_track_offsets_match_float32_arithmetic():
     rng = np.random.default_rng(7)
-    times = np.sort(rng.uniform(0, 4, 30))
     vx = rng.uniform(-600, 600, 200).astype(np.float32)
     vy = rng.uniform(-600, 600, 200).astype(np.float32)
-    ox, oy = oracle.track_offsets(times, vx, vy)
-    for j in range(200):
-        assert (ox[j] == np_offsets(times, vx[j])).all()
-        assert (oy[j] == np_offsets(times, vy[j])).all()
+    # epochs from 0 and as MJDs: the time difference is taken in float64, then rounded once
+    for t0 in (0.0, 57000.37):
+        times = t0 + np.sort(rng.uniform(0, 4, 30))
+        ox, oy = oracle.track_offsets(times, vx, vy)
+        for j in range(200):
+            assert (ox[j] == np_offsets(times, vx[j])).all()
+            assert (oy[j] == np_offsets(times, vy[j])).all()
 
 
 def test_track_offsets_half_up():
@@ -678,6 +680,29 @@ def test_vjp_images_against_finite_differences_and_support():
                 d[t, y, x] -= h
             fd = (obj(a, b) - obj(c, d)) / (2 * h)
             assert abs(grad[t, y, x] - fd) <= 1e-6 * max(abs(fd), 1.0), (which, t, y, x)
+
+
+def test_vjp_adds_to_its_outputs():
+    # the VJP adds to the arrays it is given (what a caller summing over candidates relies on):
+    # from arrays holding G0 it leaves G0 plus the values it writes into zeroed arrays
+    import oracle.oracle as oo
+    rng, times, psi, phi = _subpixel_case(23)
+    T, H, W = psi.shape
+    keep = np.array([0b11011111], np.uint32)
+    p = (15.37, 20.71, 23.3, -17.9)
+    gp0, gpsi0, gphi0 = oracle.traj_vjp(psi, phi, times, keep, *p, gL=0.7, gA=-1.3)
+    g0 = np.array([1.0, -2.0, 3.0, 0.5])
+    b_psi, b_phi = 1.0 + rng.random((T, H, W)), -1.0 - rng.random((T, H, W))
+    gp, gpsi, gphi = g0.copy(), b_psi.copy(), b_phi.copy()
+    psi64, phi64, t64 = (np.ascontiguousarray(a, np.float64) for a in (psi, phi, times))
+    rc = oo.lib().kbo_traj_vjp(oo._ptr(psi64), oo._ptr(phi64), oo._ptr(t64), T, H, W,
+                               oo._ptr(keep), *[float(v) for v in p], 0.7, -1.3, oo._ptr(gp),
+                               oo._ptr(gpsi), oo._ptr(gphi))
+    assert rc == 0
+    assert np.allclose(gp - g0, gp0, rtol=1e-12, atol=1e-12)
+    assert np.allclose(gpsi - b_psi, gpsi0, rtol=0, atol=1e-12)
+    assert np.allclose(gphi - b_phi, gphi0, rtol=0, atol=1e-12)
+    assert np.abs(gpsi0).max() > 1e-3 and np.abs(gphi0).max() > 1e-3
 
 
 def test_vjp_euler_homogeneity():
