@@ -435,3 +435,43 @@ def test_host_fault_injection(L, monkeypatch):
                        None) == K.KB_OK
     monkeypatch.setenv("KB_FAULT_INJECT", "kb_refine")
     assert calls["kb_refine"]() == K.KB_ERR_CUDA and "injected" in _err(L)
+
+
+def test_plain_c_program_links_and_calls_the_library(L, tmp_path):
+    """The ABI is usable from C alone: a C11 program includes kb.h, links libkb_b300.so and calls
+    the host-only entry points (defaults, workspace query, argument checks, error text)."""
+    import subprocess
+    from paper_2109_03296_b300 import _lib as K
+    libdir = os.path.dirname(K.LIB_PATH)
+    src = tmp_path / "use_kb.c"
+    src.write_text(r"""
+#include <stdio.h>
+#include <string.h>
+#include "kb.h"
+int main(void) {
+  kb_search_params p;
+  size_t bytes = 0;
+  kb_search_params_default(&p, 2046, 4094);
+  if (p.k_per_pixel != 8 || p.min_obs != 15 || p.x_hi != 4094 || p.y_hi != 2046) return 1;
+  if (kb_search_workspace_size(26, 2046, 4094, 32768, &p, &bytes) != KB_OK || bytes == 0) return 2;
+  if (kb_search_workspace_size(KB_MAX_T + 1, 10, 10, 5, &p, &bytes) != KB_ERR_UNSUPPORTED)
+    return 3;
+  if (kb_make_psi_phi(NULL, NULL, NULL, NULL, 1, 1, 1, 1, NULL, NULL, NULL) != KB_ERR_INVALID_ARG)
+    return 4;
+  if (strstr(kb_last_error(), "kb_make_psi_phi") == NULL) return 5;
+  printf("%d %zu\n", kb_version(), bytes);
+  return 0;
+}
+""")
+    exe = tmp_path / "use_kb"
+    subprocess.check_call(["gcc", "-std=c11", "-Wall", "-Wextra", "-Werror",
+                           "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe),
+                           "-L", libdir, "-lkb_b300", "-Wl,-rpath," + libdir])
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0, out
+    v, nbytes = out.stdout.split()
+    assert int(v) == L.kb_version()
+    n = C.c_size_t()
+    p = _params(L, 2046, 4094)
+    assert L.kb_search_workspace_size(26, 2046, 4094, 32768, C.byref(p), C.byref(n)) == 0
+    assert int(nbytes) == n.value
