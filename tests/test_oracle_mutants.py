@@ -45,6 +45,15 @@ MUTANTS = [
     ("clip_half_width_one_sigma",
      [("double lower = x_mid - n_sigma * sigma_g, upper = x_mid + n_sigma * sigma_g;",
        "double lower = x_mid - sigma_g, upper = x_mid + sigma_g;", 1)]),
+    ("clip_width_fixed_at_two",
+     [("double lower = x_mid - n_sigma * sigma_g, upper = x_mid + n_sigma * sigma_g;",
+       "double lower = x_mid - 2.0 * sigma_g, upper = x_mid + 2.0 * sigma_g;", 1)]),
+    ("clip_centre_fixed_at_the_median",
+     [("double x_mid = kbo_percentile_sorted(s, n, q_mid);",
+       "double x_mid = kbo_percentile_sorted(s, n, 0.5);", 1)]),
+    ("clip_quartiles_fixed",
+     [("double sigma_g = kbo_sigma_g_coeff(q_lo, q_hi) * (x_hi - x_lo);",
+       "double sigma_g = kbo_sigma_g_coeff(0.25, 0.75) * (x_hi - x_lo);", 1)]),
     # track rounding
     ("track_round_half_even", [("return (int32_t)floorf(e);", "return (int32_t)rintf(d);", 1)]),
     ("track_truncates", [("return (int32_t)floorf(e);", "return (int32_t)e;", 1)]),

@@ -375,14 +375,25 @@ def _tiny_case(seed, T=6, H=12, W=14, n_traj=40, mask_frac=0.08):
     return psi, phi, times, vx, vy
 
 
-@pytest.mark.parametrize("seed,clip,clip_on,K", [(0, True, 0, 3), (1, True, 1, 2),
-                                                 (2, False, 0, 4), (3, True, 0, 1)])
-def test_search_matches_numpy_brute_force(seed, clip, clip_on, K):
-    psi, phi, times, vx, vy = _tiny_case(seed)
+@pytest.mark.parametrize("seed,clip,clip_on,K,T,q,n_sigma", [
+    (0, True, 0, 3, 6, (0.25, 0.5, 0.75), 2.0),
+    (1, True, 1, 2, 6, (0.25, 0.5, 0.75), 2.0),
+    (2, False, 0, 4, 6, (0.25, 0.5, 0.75), 2.0),
+    (3, True, 0, 1, 6, (0.25, 0.5, 0.75), 2.0),
+    (4, True, 0, 5, 40, (0.1, 0.5, 0.9), 1.5),      # two mask words, other quantiles and width
+    (5, True, 1, 8, 12, (0.2, 0.45, 0.8), 2.5),     # an off-centre "median"
+])
+def test_search_matches_numpy_brute_force(seed, clip, clip_on, K, T, q, n_sigma):
+    psi, phi, times, vx, vy = _tiny_case(seed, T=T)
     lh_min, min_obs = 0.5, 3
-    ref = numpy_search(psi, phi, times, vx, vy, K, lh_min, min_obs, clip=clip, clip_on=clip_on)
+    # the search takes its quantiles and width as float32 (both sides use the rounded values)
+    q32 = [float(np.float32(v)) for v in q]
+    ref = numpy_search(psi, phi, times, vx, vy, K, lh_min, min_obs, clip=clip, clip_on=clip_on,
+                       n_sigma=n_sigma, q=tuple(100.0 * v for v in q32))
     got = oracle.search(psi, phi, times, vx, vy, dict(k=K, lh_min=lh_min, min_obs=min_obs,
-                                                      clip=int(clip), clip_on=clip_on))
+                                                      clip=int(clip), clip_on=clip_on,
+                                                      q_lo=q[0], q_mid=q[1], q_hi=q[2],
+                                                      n_sigma=n_sigma))
     assert np.array_equal(got["idx"], ref["idx"])
     filled = ref["idx"] >= 0
     assert filled.sum() > 50
