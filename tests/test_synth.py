@@ -98,3 +98,30 @@ def test_likelihood_stack_planes():
     zero = phi == 0.0
     assert abs(zero.mean() - 0.005) < 0.0015 and np.all(psi[zero] == 0.0)
     assert len(vx) == 256 * 128 and times[0] == 0.0
+
+
+def test_batch64_specs_and_torch_stacks():
+    """The 64-stack batch: sizes, epoch counts and grids from the stated sets, movers at the decam
+    density; one stack drawn by the torch generator (on the CPU here) follows the decam recipe."""
+    import torch
+    from synth.gpu_stacks import BATCH64, batch_specs, make_stack_torch
+    specs = batch_specs()
+    assert len(specs) == 64 and batch_specs() == specs
+    sizes = {(H, W) for H, W, *_ in specs}
+    assert sizes <= set(BATCH64["sizes"]) and len(sizes) == 3
+    assert all(10 <= T <= 40 for _, _, T, *_ in specs)
+    assert {(ns, na) for _, _, _, ns, na, _, _ in specs} <= set(BATCH64["grids"])
+    for H, W, T, ns, na, nm, seed in specs:
+        assert nm == max(1, int(round(200.0 / (2046 * 4094) * H * W)))
+    assert len({s[-1] for s in specs}) == 64
+    s = make_stack_torch(96, 128, 12, 16, 8, 6, 1234, "cpu")
+    img, var, mask = s["img"], s["var"], s["mask"].bool()
+    assert img.shape == var.shape == (12, 96, 128) and img.dtype == torch.float32
+    assert torch.isinf(var[mask]).all() and torch.isfinite(var[~mask]).all()
+    assert abs(mask.float().mean().item() - 0.005) < 0.003
+    assert s["vx"].numel() == 16 * 8 and s["times"][0] == 0.0
+    mv = s["movers"]
+    assert np.all(mv["spike"].sum(1) == 1)               # round(0.1 * 12) spike epochs
+    assert np.all((mv["snr"] >= 1.5) & (mv["snr"] <= 10.0))
+    again = make_stack_torch(96, 128, 12, 16, 8, 6, 1234, "cpu")
+    assert torch.equal(again["img"], img) and torch.equal(again["mask"], s["mask"])
