@@ -132,3 +132,23 @@ def test_clock_summary_of_nvidia_smi_rows():
                           "Active, Not Active, Active, Not Active")
     assert bench.summarize_clock_rows([hot])["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
     assert bench.summarize_clock_rows([])["reasons"] == ["no samples"]
+
+
+def test_refine_recovery_matching():
+    """The refine line's recovery figure: for each mover, the highest-L candidate whose track is
+    within 2.5 px of the true one at the first and at the last epoch, else -1."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    times = np.array([0.0, 0.5, 2.0])
+    movers = dict(x0=np.array([10.0, 50.0]), y0=np.array([20.0, 60.0]),
+                  vx=np.array([100.0, -40.0]), vy=np.array([5.0, 0.0]))
+    params = np.array([
+        [10.5, 20.0, 100.0, 5.0],     # mover 0, L 8
+        [11.0, 21.0, 100.5, 5.0],     # mover 0, L 9: within 2.5 px at both ends -> chosen
+        [10.0, 20.0, 102.0, 5.0],     # starts on mover 0 but 4 px off at the last epoch
+        [50.0, 60.0, -40.0, 0.0],     # mover 1, but L is NaN (refine stopped): not eligible
+    ], np.float32)
+    lh = np.array([8.0, 9.0, 30.0, np.nan], np.float32)
+    got = bench._match_movers(params, lh, movers, times)
+    assert got.tolist() == [1, -1]
