@@ -56,3 +56,45 @@ def test_bounded_waits_give_up_and_the_context_stays_usable(cuda_device):
     assert kb.search_stats(res["workspace"])[3] == 0
     o = oracle.search(psi32, phi32, times, vx, vy, dict(k=3, lh_min=3.0, min_obs=4))
     compare_search(gpu_result_numpy(res), o, sp.lh_min)
+
+
+@pytest.mark.gpu
+def test_injected_host_faults_are_reported_and_the_next_call_works(cuda_device, monkeypatch):
+    """KB_FAULT_INJECT makes the named entry points fail on the host, before any device work; the
+    binding raises, and the same search, batch and context then run normally."""
+    rng = np.random.default_rng(32)
+    T, H, W, n = 8, 50, 64, 120
+    times = np.sort(rng.uniform(0, 1.0, T))
+    times[0] = 0.0
+    phi = rng.uniform(0.2, 1.5, (T, H, W)).astype(np.float32)
+    psi = (rng.normal(size=(T, H, W)) * np.sqrt(phi) + 3.0 * phi * (rng.random((T, H, W)) < 0.05)
+           ).astype(np.float32)
+    vx = rng.uniform(-25, 25, n).astype(np.float32)
+    vy = rng.uniform(-25, 25, n).astype(np.float32)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    gpsi, gphi, gvx, gvy = d(psi), d(phi), d(vx), d(vy)
+    sp = kb.SearchParams(k=2, lh_min=2.0, min_obs=3)
+    launches = kb.launch_count()
+    monkeypatch.setenv("KB_FAULT_INJECT", "kb_search,kb_batch_create")
+    with pytest.raises(kb.KbError, match="kb_search: injected fault"):
+        kb.search(gpsi, gphi, times, gvx, gvy, sp)
+    stack = dict(psi=gpsi, phi=gphi, times=times, vx=gvx, vy=gvy, params=sp)
+    with pytest.raises(kb.KbError, match="kb_batch_create: injected fault"):
+        kb.Batch([stack])
+    assert kb.launch_count() == launches          # nothing reached the device
+    monkeypatch.delenv("KB_FAULT_INJECT")
+    b = kb.Batch([stack])
+    monkeypatch.setenv("KB_FAULT_INJECT", "*")
+    with pytest.raises(kb.KbError, match="kb_batch_run: injected fault"):
+        b.run()
+    with pytest.raises(kb.KbError, match="kb_batch_run_graph: injected fault"):
+        b.run(graph=True)
+    monkeypatch.delenv("KB_FAULT_INJECT")
+    got = b.run(graph=True)[0]
+    ref = kb.search(gpsi, gphi, times, gvx, gvy, sp)
+    torch.cuda.synchronize()
+    for key in ("idx", "nvalid", "nkept", "mask"):
+        assert torch.equal(got[key], ref[key]), key
+    assert torch.equal(got["lh"].view(torch.int32), ref["lh"].view(torch.int32))
+    o = oracle.search(psi, phi, times, vx, vy, dict(k=2, lh_min=2.0, min_obs=3))
+    compare_search(gpu_result_numpy(ref), o, sp.lh_min)
