@@ -475,3 +475,19 @@ int main(void) {
     p = _params(L, 2046, 4094)
     assert L.kb_search_workspace_size(26, 2046, 4094, 32768, C.byref(p), C.byref(n)) == 0
     assert int(nbytes) == n.value
+
+
+def test_no_alloc_scratch_holds_the_documented_sizes(L):
+    """The built-in scratch of kb_search_no_alloc (32 MiB, of which the evaluation records take
+    a fixed 16 MiB) holds T = 26 searches up to 212 x 212 pixels with 4096 trajectories and
+    120 x 120 with 32768, and no larger squares."""
+    from paper_2109_03296_b300 import _lib as K
+    n = C.c_size_t()
+    for side, n_traj in ((212, 4096), (120, 32768)):
+        for s, fits in ((side, True), (side + 4, False)):
+            p = _params(L, s, s)
+            assert L.kb_search_workspace_size(26, s, s, n_traj, C.byref(p), C.byref(n)) == 0
+            assert (n.value <= K.KB_STATIC_SCRATCH_BYTES) == fits, (s, n_traj, n.value)
+    p = _params(L, 64, 64)
+    assert L.kb_search_workspace_size(26, 64, 64, 1, C.byref(p), C.byref(n)) == 0
+    assert n.value > 16 * 2 ** 20          # the records alone
