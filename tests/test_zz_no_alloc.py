@@ -64,7 +64,7 @@ def test_no_alloc_matches_workspace_search_twice(cuda_device):
 
 
 def test_no_alloc_refuses_sizes_beyond_its_scratch(cuda_device):
-    # workspace need for 26 x 2046 x 4094 is ~0.9 GB, far above the built-in 32 MiB
+    # workspace need for 26 x 2046 x 4094 is ~2.6 GB, far above the built-in 32 MiB
     sp = _lib.SearchParamsC()
     _lib.lib().kb_search_params_default(C.byref(sp), 2046, 4094)
     need = C.c_size_t()
