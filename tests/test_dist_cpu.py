@@ -152,3 +152,18 @@ def test_refine_recovery_matching():
     lh = np.array([8.0, 9.0, 30.0, np.nan], np.float32)
     got = bench._match_movers(params, lh, movers, times)
     assert got.tolist() == [1, -1]
+
+
+def test_measured_peaks_and_fallback(tmp_path, monkeypatch):
+    """The roofline denominators come from MEASURED_PEAKS.json when present, else from the stated
+    fallback (6.4 TB/s HBM, 1.8 PFLOP/s bf16), labelled as such."""
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    peaks, src = bench.measured_peaks()
+    assert src == "fallback" and peaks["hbm_gbs"] == 6400.0 and peaks["bf16_tflops"] == 1800.0
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6505.9,
+                                                              "sm_max_mhz": 2032.0}))
+    peaks, src = bench.measured_peaks()
+    assert src == "measured" and peaks["hbm_gbs"] == 6505.9
