@@ -491,3 +491,17 @@ def test_no_alloc_scratch_holds_the_documented_sizes(L):
     p = _params(L, 64, 64)
     assert L.kb_search_workspace_size(26, 64, 64, 1, C.byref(p), C.byref(n)) == 0
     assert n.value > 16 * 2 ** 20          # the records alone
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """No fallback: without libkb_b300.so every call into the binding raises."""
+    import paper_2109_03296_b300 as kb
+    from paper_2109_03296_b300 import _lib as K
+    monkeypatch.setattr(K, "LIB_PATH", os.path.join(ROOT, "no_such_dir", "libkb_b300.so"))
+    monkeypatch.setattr(K, "_LIB", None)
+    with pytest.raises(ImportError, match="not built"):
+        K.lib()
+    with pytest.raises(ImportError):
+        kb.version()
+    with pytest.raises(ImportError):
+        kb.launch_count()
