@@ -505,3 +505,22 @@ def test_missing_library_fails_loudly(monkeypatch):
         kb.version()
     with pytest.raises(ImportError):
         kb.launch_count()
+
+
+def test_product_and_oracle_share_no_code():
+    """The package never imports the oracle, the oracle never imports the package or includes its
+    headers, and neither reads the other's sources."""
+    pkg = os.path.join(ROOT, "paper_2109_03296_b300")
+    orc = os.path.join(ROOT, "oracle")
+    for folder, banned in ((pkg, ("import oracle", "from oracle", "kb_oracle", "libkb_oracle")),
+                           (orc, ("import paper_2109_03296_b300", "from paper_2109_03296_b300",
+                                  "kb.h\"", "csrc/", "libkb_b300"))):
+        for dirpath, _, files in os.walk(folder):
+            if "_build" in dirpath or "__pycache__" in dirpath:
+                continue
+            for f in files:
+                if not f.endswith((".py", ".c", ".h", ".cu", ".cuh")):
+                    continue
+                text = open(os.path.join(dirpath, f)).read()
+                for b in banned:
+                    assert b not in text, (f, b)
