@@ -524,3 +524,15 @@ def test_product_and_oracle_share_no_code():
                 text = open(os.path.join(dirpath, f)).read()
                 for b in banned:
                     assert b not in text, (f, b)
+
+
+def test_header_is_clean_c_and_cxx(tmp_path):
+    """include/kb.h compiles warning-free as C11 and C++17 (-Wall -Wextra -Wpedantic)."""
+    import subprocess
+    inc = os.path.join(ROOT, "include")
+    for lang, compiler, std, ext in (("c", "gcc", "-std=c11", ".c"),
+                                     ("c++", "g++", "-std=c++17", ".cpp")):
+        src = tmp_path / ("h" + ext)
+        src.write_text('#include "kb.h"\nint main(void) { return KB_OK; }\n')
+        subprocess.check_call([compiler, std, "-Wall", "-Wextra", "-Wpedantic", "-Werror",
+                               "-I", inc, "-fsyntax-only", str(src)])
