@@ -536,3 +536,40 @@ def test_header_is_clean_c_and_cxx(tmp_path):
         src.write_text('#include "kb.h"\nint main(void) { return KB_OK; }\n')
         subprocess.check_call([compiler, std, "-Wall", "-Wextra", "-Wpedantic", "-Werror",
                                "-I", inc, "-fsyntax-only", str(src)])
+
+
+def test_comparison_harness_tolerance_edges():
+    """The parity bar as the harness applies it: LH' and alpha within 1e-4 relative (LH' scale
+    floored at 1) pass, just outside fail; counts, masks and empty slots are exact."""
+    import oracle
+    from helpers import compare_search
+    rng = np.random.default_rng(1)
+    T, H, W = 6, 12, 14
+    times = np.sort(rng.uniform(0, 1, T))
+    phi = rng.uniform(0.2, 1.5, (T, H, W))
+    psi = rng.normal(size=(T, H, W)) * np.sqrt(phi) + 2.0 * phi * (rng.random((T, H, W)) < 0.2)
+    vx = rng.uniform(-6, 6, 30).astype(np.float32)
+    vy = rng.uniform(-6, 6, 30).astype(np.float32)
+    o = oracle.search(psi, phi, times, vx, vy, dict(k=3, lh_min=0.5, min_obs=2))
+    y, x = np.argwhere(o["idx"][..., 2] >= 0)[0]          # a pixel with three entries
+
+    def planted(key, s, f):
+        g = {k: v.copy() for k, v in o.items()}
+        g[key][y, x, s] = f(g[key][y, x, s])
+        return g
+
+    L = o["lh"][y, x, 1]
+    scale = max(abs(L), 1.0)
+    assert compare_search(planted("lh", 1, lambda v: v + 0.9e-4 * scale), o, 0.5) == 0
+    with pytest.raises(AssertionError):
+        compare_search(planted("lh", 1, lambda v: v + 1.1e-4 * scale), o, 0.5)
+    assert compare_search(planted("flux", 2, lambda v: v * (1 + 0.5e-4)), o, 0.5) == 0
+    with pytest.raises(AssertionError):
+        compare_search(planted("nvalid", 2, lambda v: v + 1), o, 0.5)
+    with pytest.raises(AssertionError):
+        compare_search(planted("mask", 2, lambda v: v ^ np.uint32(1 << (T - 1))), o, 0.5)
+    e = np.argwhere(o["idx"] < 0)[0]
+    g = {k: v.copy() for k, v in o.items()}
+    g["lh"][tuple(e)] = 0.0                               # an empty slot must read -inf
+    with pytest.raises(AssertionError):
+        compare_search(g, o, 0.5)
