@@ -178,36 +178,45 @@ def summarize_clock_rows(lines):
 # the oracle on a bounded window (CPU baseline and the reference arm)
 # ------------------------------------------------------------------------------------------------
 _ORACLE_DATA = {}
+ORACLE_MAX_SIDE = 64
 
 
-def _oracle_inputs(workload):
-    """The workload's likelihood planes as FP64 (generated once per process)."""
+def _oracle_inputs(workload, stack=None):
+    """The oracle's FP64 psi/phi of the workload's own stack (make_stack with the workload's
+    seed: the images the GPU arm forms psi/phi from and searches), on the part of the image that
+    the tracks of a centred ORACLE_MAX_SIDE^2 window of start pixels can reach, with that window
+    in crop coordinates (oracle.window_inputs; generated once per process)."""
     if workload not in _ORACLE_DATA:
-        import numpy as np
-        from synth import make_likelihood_stack
-        psi, phi, times, vx, vy, movers = make_likelihood_stack(workload)
-        _ORACLE_DATA[workload] = (psi.astype(np.float64), phi.astype(np.float64), times, vx, vy)
+        import oracle
+        from synth import make_stack
+        s = stack if stack is not None else make_stack(workload)
+        T, H, W = s.img.shape
+        side = min(ORACLE_MAX_SIDE, H, W)
+        cx, cy = (W - side) // 2, (H - side) // 2
+        psi, phi, win, _ = oracle.window_inputs(s.img, s.var, s.mask, s.psf, s.times, s.vx, s.vy,
+                                                (cx, cx + side, cy, cy + side))
+        _ORACLE_DATA[workload] = (psi, phi, s.times, s.vx, s.vy, win, (H, W))
     return _ORACLE_DATA[workload]
 
 
-def oracle_rate(target_s, workload):
-    """Oracle search TE/s on a square window of start pixels of the workload's likelihood planes
-    (every trajectory, every epoch); the window side doubles until one run takes more than half
-    of target_s (so the timed sample is about target_s/2 to 2 target_s of CPU time)."""
+def oracle_rate(target_s, workload, stack=None):
+    """Oracle search TE/s on a square window of start pixels at the centre of the workload's own
+    stack (every trajectory, every epoch); the window side doubles until one run takes more than
+    half of target_s (so the timed sample is about target_s/2 to 2 target_s of CPU time)."""
     import oracle
     from synth import CONFIGS
     c = CONFIGS[workload]
-    psi64, phi64, times, vx, vy = _oracle_inputs(workload)
-    T, H, W = psi64.shape
+    psi64, phi64, times, vx, vy, win, (H, W) = _oracle_inputs(workload, stack)
+    T = psi64.shape[0]
     params = dict(k=c["K"], lh_min=c["lh_min"], min_obs=c["min_obs"], clip=1)
-    cx, cy = W // 2, H // 2
+    x0, y0 = win[0], win[2]
     side = 1
     while True:
         t0 = time.perf_counter()
-        oracle.search(psi64, phi64, times, vx, vy, params, window=(cx, cx + side, cy, cy + side))
+        oracle.search(psi64, phi64, times, vx, vy, params, window=(x0, x0 + side, y0, y0 + side))
         dt = time.perf_counter() - t0
         te = side * side * len(vx) * T
-        if dt * 2 > target_s or side >= 64:
+        if dt * 2 > target_s or side >= win[1] - win[0]:
             break
         side *= 2
     threads = oracle.get_threads()
@@ -279,8 +288,9 @@ def run_reference(args):
         t_all += r["seconds"]
     v = statistics.median(vals)
     sample = ("oracle search (FP64 C, OpenMP) on a %dx%d start-pixel window x %d trajectories x "
-              "%d epochs of the %s likelihood planes; TE/s" % (r["side"], r["side"], r["n_traj"],
-                                                            r["T"], args.workload))
+              "%d epochs at the centre of the %s stack (make_stack, seed of rank 0), psi/phi "
+              "formed by the oracle; TE/s" % (r["side"], r["side"], r["n_traj"], r["T"],
+                                             args.workload))
     print(json.dumps({
         "impl": "reference", "metric": "trajectory-epoch evals/sec", "value": v,
         "unit": "TE/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -355,7 +365,9 @@ def workload_config(name):
                         % (name, c["T"], c["H"], c["W"], ns * na, ns, v0, v1, na, c["K"],
                            c["lh_min"], c["min_obs"]),
             "T": c["T"], "H": c["H"], "W": c["W"], "n_traj": ns * na, "K": c["K"],
-            "psf_k": c["psf_k"], "l2": l2_note(2 * 4 * c["T"] * c["H"] * c["W"])}
+            "psf_k": c["psf_k"], "l2": l2_note(2 * 4 * c["T"] * c["H"] * c["W"]),
+            "stack": "synth.make_stack(%r, seed=%d): the stack timed here, checked against the "
+                     "oracle by the GPU tests and timed as the CPU baseline" % (name, c["seed"])}
 
 
 L2_BYTES = 126 * 2 ** 20
@@ -559,15 +571,16 @@ def run_ours(args):
     }
     if not args.no_cpu_baseline:
         import oracle
-        r = oracle_rate(args.cpu_seconds, args.workload)
+        r = oracle_rate(args.cpu_seconds, args.workload, stack=s)
         n_thr = oracle.get_threads()
         oracle.set_threads(1)
-        r1 = oracle_rate(args.cpu_seconds / 3, args.workload)
+        r1 = oracle_rate(args.cpu_seconds / 3, args.workload, stack=s)
         oracle.set_threads(n_thr)
         line["cpu_baseline"] = {
             "value": r["value"], "unit": "TE/s", "cores": r["threads"], "kind": "oracle",
             "sample": "FP64 C oracle search on a %dx%d start-pixel window (x %d trajectories x %d "
-                      "epochs) of the workload's likelihood planes, %.1f s" %
+                      "epochs) at the centre of the timed stack, psi/phi formed by the oracle "
+                      "from the same images, %.1f s" %
                       (r["side"], r["side"], r["n_traj"], r["T"], r["seconds"]),
             "single_thread": {"value": r1["value"], "unit": "TE/s",
                               "sample": "%dx%d window, one thread, %.1f s" %
@@ -956,7 +969,8 @@ def run_batch(args):
         line["cpu_baseline"] = {
             "value": r["value"], "unit": "TE/s", "cores": r["threads"], "kind": "oracle",
             "sample": "FP64 C oracle search on a %dx%d start-pixel window (x %d trajectories x %d "
-                      "epochs) of the decam likelihood planes, %.1f s" %
+                      "epochs) at the centre of the decam stack, psi/phi formed by the oracle, "
+                      "%.1f s" %
                       (r["side"], r["side"], r["n_traj"], r["T"], r["seconds"])}
     print(json.dumps(line), flush=True)
 

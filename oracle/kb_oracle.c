@@ -281,6 +281,43 @@ int kbo_eval_one(const double* psi, const double* phi, const double* times, int 
   return r.ok;
 }
 
+/* How close one integer-pixel trajectory's clipped lightcurve comes to a clip bound (reading
+ * R6): the smallest |a_t - (median -+ n sigma_G)| over its valid epochs, in units of
+ * max(sigma_G, |median|, 1e-30).  Float32 and FP64 evaluations can take different keep
+ * decisions only for an epoch within rounding of a bound; R6 accepts either decision where this
+ * margin is at most 1e-5.  Returns +inf when the clip is off or the trajectory has fewer than
+ * max(min_obs, 1) valid epochs (no clip decision is taken). */
+double kbo_clip_margin(const double* psi, const double* phi, const double* times, int T, int H,
+                       int W, int x0, int y0, float vx, float vy, int min_obs, int clip,
+                       double q_lo, double q_mid, double q_hi, double n_sigma, int clip_on) {
+  if (T <= 0 || T > KBO_MAX_T || !clip) return INFINITY;
+  int32_t ox[KBO_MAX_T], oy[KBO_MAX_T];
+  kbo_track_offsets(times, T, &vx, &vy, 1, ox, oy);
+  double a[KBO_MAX_T];
+  uint8_t keep[KBO_MAX_T];
+  size_t hw = (size_t)H * W;
+  int n = 0;
+  for (int t = 0; t < T; ++t) {
+    const int px = x0 + ox[t], py = y0 + oy[t];
+    if (px < 0 || py < 0 || px >= W || py >= H) continue;   /* off the image: not valid */
+    const double pv = psi[(size_t)t * hw + (size_t)py * W + px];
+    const double fv = phi[(size_t)t * hw + (size_t)py * W + px];
+    if (!(fv > 0.0 && isfinite(fv) && isfinite(pv))) continue;   /* R9 validity */
+    a[n++] = clip_on ? pv / sqrt(fv) : pv / fv;
+  }
+  if (n == 0 || n < min_obs) return INFINITY;
+  double med = 0.0, sg = 0.0;
+  kbo_sigma_g_clip(a, n, q_lo, q_mid, q_hi, n_sigma, keep, &med, &sg);
+  double lower = med - n_sigma * sg, upper = med + n_sigma * sg;
+  double scale = fmax(fmax(sg, fabs(med)), 1e-30);
+  double m = INFINITY;
+  for (int i = 0; i < n; ++i) {
+    double d = fmin(fabs(a[i] - lower), fabs(a[i] - upper));
+    if (d < m) m = d;
+  }
+  return m / scale;
+}
+
 /* ---------------------------------------------------------------------------------------- */
 /* Exhaustive search + threshold + per-pixel top-K (Section 3, 3.1, 3.2; R5, R8)             */
 /* ---------------------------------------------------------------------------------------- */

@@ -38,6 +38,8 @@ def lib():
         _LIB.kbo_eval_one.restype = i
         _LIB.kbo_eval_one.argtypes = [p, p, p, i, i, i, i, i, f, f, i, i, d, d, d, d, i,
                                       p, p, p, p, p]
+        _LIB.kbo_clip_margin.restype = d
+        _LIB.kbo_clip_margin.argtypes = [p, p, p, i, i, i, i, i, f, f, i, i, d, d, d, d, i]
         _LIB.kbo_search.restype = i
         _LIB.kbo_search.argtypes = [p, p, p, i, i, i, p, p, i, i, d, i, i, d, d, d, d, i,
                                     i, i, i, i, p, p, p, p, p, p]
@@ -140,6 +142,33 @@ def psi_phi_at(img, var, mask, psf, tyx):
     return psi, phi
 
 
+def window_inputs(img, var, mask, psf, times, vx, vy, window):
+    """The oracle's psi/phi (FP64) on the part of the image the tracks of the start pixels in
+    `window` = (x_lo, x_hi, y_lo, y_hi) can reach, and that window in the crop's coordinates.
+
+    The crop is the bounding box of every track position of every window pixel, clipped to the
+    image, so a position inside the image lies in the crop and one outside the image lies outside
+    it: an oracle search of the crop over the shifted window gives the results of a search of the
+    whole image over `window`.  psi/phi are formed on the crop widened by the PSF radius (clipped
+    to the image), so every value kept equals the whole-image value.  Returns
+    (psi, phi, window_in_crop, (x0, y0) of the crop)."""
+    img, var, psf = _f32(img), _f32(var), _f32(psf)
+    T, H, W = img.shape
+    x_lo, x_hi, y_lo, y_hi = (int(v) for v in window)
+    ox, oy = track_offsets(times, vx, vy)
+    xa, xb = max(0, x_lo + int(ox.min())), min(W, x_hi - 1 + int(ox.max()) + 1)
+    ya, yb = max(0, y_lo + int(oy.min())), min(H, y_hi - 1 + int(oy.max()) + 1)
+    r = psf.shape[-1] // 2
+    xa2, xb2, ya2, yb2 = max(0, xa - r), min(W, xb + r), max(0, ya - r), min(H, yb + r)
+    sub = (slice(None), slice(ya2, yb2), slice(xa2, xb2))
+    m = None if mask is None else np.ascontiguousarray(mask[sub])
+    psi, phi = psi_phi(img[sub], var[sub], m, psf)
+    inner = (slice(None), slice(ya - ya2, yb - ya2), slice(xa - xa2, xb - xa2))
+    psi = np.ascontiguousarray(psi[inner])
+    phi = np.ascontiguousarray(phi[inner])
+    return psi, phi, (x_lo - xa, x_hi - xa, y_lo - ya, y_hi - ya), (xa, ya)
+
+
 DEFAULTS = dict(k=1, lh_min=7.0, min_obs=1, clip=1, q_lo=0.25, q_mid=0.5, q_hi=0.75,
                 n_sigma=2.0, clip_on=0)
 
@@ -168,6 +197,17 @@ def eval_one(psi, phi, times, x0, y0, vx, vy, params=None):
                             C.byref(nv), C.byref(nk), _ptr(mask))
     return dict(ok=bool(ok), lh=lh.value, flux=fl.value, nvalid=nv.value, nkept=nk.value,
                 mask=mask)
+
+
+def clip_margin(psi, phi, times, x0, y0, vx, vy, params=None):
+    """Closest approach of one trajectory's lightcurve to its clip bounds in units of
+    max(sigma_G, |median|, 1e-30) (reading R6; +inf when no clip decision is taken)."""
+    q = _params(params)
+    psi, phi, times = _f64(psi), _f64(phi), _f64(times)
+    T, H, W = psi.shape
+    return lib().kbo_clip_margin(_ptr(psi), _ptr(phi), _ptr(times), T, H, W, int(x0), int(y0),
+                                 float(vx), float(vy), q["min_obs"], q["clip"], q["q_lo"],
+                                 q["q_mid"], q["q_hi"], q["n_sigma"], q["clip_on"])
 
 
 def search(psi, phi, times, vx, vy, params=None, window=None):

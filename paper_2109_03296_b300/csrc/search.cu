@@ -94,6 +94,7 @@ __host__ __device__ constexpr int stage_height(int h) { return 64 + 16 * h; }
 constexpr int S_ORDER_MAX = 16384;       // tiles ordered by predicted cost (one-block sort)
 constexpr int HILBERT_BITS = 8;          // 256 x 256 velocity cells
 constexpr int N_CELLS = 1 << (2 * HILBERT_BITS);
+static_assert(N_CELLS >= 3 * (KB_MAX_T + 1), "plan_reset_kernel writes the rank table");
 
 // Staging plan of one (chunk, epoch): the rectangle and the 32 per-trajectory byte offsets
 // into it.  Copied into shared memory with the rectangle it describes.
@@ -116,6 +117,16 @@ struct EvalParams {
   // evaluation stops before the clip
   float nu2_floor;
 };
+
+// Interpolation ranks of the sigma-G percentiles (linear interpolation between order statistics,
+// h = (n - 1) q).  h is formed in float64 from the float32 quantile, as the definition states it,
+// and rounded once: entry (k, n) = {floor(h) clamped to [0, n-1], float32 of h - floor(h)} for
+// quantile k (0 = q_lo, 1 = q_mid, 2 = q_hi) of n valid epochs.  The table follows the epoch
+// offsets dt[KB_MAX_T] in the workspace, so an evaluation reaches it from the dt pointer it has.
+__host__ __device__ constexpr int rank_entry(int k, int n) { return k * (KB_MAX_T + 1) + n; }
+__device__ __forceinline__ const int2* rank_table(const float* dtf) {
+  return reinterpret_cast<const int2*>(dtf + KB_MAX_T);
+}
 
 // Workspace layout (offsets in bytes from the workspace base).
 struct WsLayout {
@@ -144,7 +155,7 @@ static WsLayout ws_layout(int T, int H, int W, int n_traj) {
   L.orig = take(sizeof(int32_t) * (size_t)L.n_pad);
   L.offs = take(sizeof(int2) * (size_t)L.n_pad * T);
   L.vsort = take(sizeof(float2) * (size_t)L.n_pad);
-  L.dtf = take(sizeof(float) * KB_MAX_T);
+  L.dtf = take(sizeof(float) * KB_MAX_T + sizeof(int2) * 3 * (KB_MAX_T + 1));
   L.plan = take(sizeof(PlanRec) * (size_t)L.nchunk * T);
   L.bound = take(sizeof(uint32_t) * (size_t)T * (H + 3) * L.Wp);
   L.pairs = take(sizeof(float2) * (size_t)T * H * W);
@@ -165,9 +176,19 @@ struct Ctrl {
 // ---------------------------------------------------------------------------------------------
 // Plan kernels: velocity ordering, track offsets, per-(chunk, epoch) staging rectangles
 // ---------------------------------------------------------------------------------------------
-__global__ void plan_reset_kernel(Ctrl* ctrl, uint32_t* counts, unsigned long long te) {
+__global__ void plan_reset_kernel(Ctrl* ctrl, uint32_t* counts, unsigned long long te, float q_lo,
+                                  float q_mid, float q_hi, int2* rank) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < N_CELLS) counts[i] = 0u;
+  if (i < 3 * (KB_MAX_T + 1)) {
+    const int k = i / (KB_MAX_T + 1), n = i - k * (KB_MAX_T + 1);
+    const double q = (double)(k == 0 ? q_lo : k == 1 ? q_mid : q_hi);
+    const double h = __dmul_rn((double)(n > 0 ? n - 1 : 0), q);
+    const double fl = floor(h);
+    int lo = (int)fl;
+    lo = max(0, min(lo, max(n - 1, 0)));
+    rank[i] = make_int2(lo, __float_as_int(__double2float_rn(__dsub_rn(h, (double)lo))));
+  }
   if (i == 0) {
     ctrl->err = 0u;
     ctrl->tile_counter = 0u;
@@ -533,13 +554,11 @@ __device__ __forceinline__ float warp_get_sorted(const float (&v)[J], int r) {
   return __shfl_sync(0xffffffffu, x, r & 31);
 }
 
+// Percentile of the n smallest sorted values from its rank entry r = {lo, frac} (rank_table).
 template <int J>
-__device__ __forceinline__ float warp_percentile(const float (&s)[J], int n, float q) {
-  const float h = (float)(n - 1) * q;
-  int lo = (int)floorf(h);
-  lo = max(0, min(lo, n - 1));
-  const int hi = min(lo + 1, n - 1);
-  const float f = h - (float)lo;
+__device__ __forceinline__ float warp_percentile(const float (&s)[J], int n, int2 r) {
+  const int lo = r.x, hi = min(lo + 1, n - 1);
+  const float f = __int_as_float(r.y);
   const float a = warp_get_sorted<J>(s, lo), b = warp_get_sorted<J>(s, hi);
   return a + f * (b - a);
 }
@@ -554,8 +573,8 @@ __device__ __forceinline__ float warp_sum(float v) {
 // mask words.  All lanes take part; lane 0 writes and gets L' back (the other lanes get NaN).
 template <int J>
 __device__ float eval_pair_warp(const float2* __restrict__ pairs, const EvalParams& ep, int x0,
-                               int y0,
-                               const int2* __restrict__ off, uint32_t* rec, int lane) {
+                               int y0, const int2* __restrict__ off,
+                               const float* __restrict__ dtf, uint32_t* rec, int lane) {
   float ps[J], ph[J], a[J];
   bool valid[J];
   const size_t plane = (size_t)ep.H * ep.W;
@@ -613,9 +632,10 @@ __device__ float eval_pair_warp(const float2* __restrict__ pairs, const EvalPara
       return NAN;
     }
     warp_bitonic_sort<J>(s, lane);
-    const float x_lo = warp_percentile<J>(s, nvalid, ep.q_lo);
-    const float x_mid = warp_percentile<J>(s, nvalid, ep.q_mid);
-    const float x_hi = warp_percentile<J>(s, nvalid, ep.q_hi);
+    const int2* rk = rank_table(dtf);
+    const float x_lo = warp_percentile<J>(s, nvalid, __ldg(rk + rank_entry(0, nvalid)));
+    const float x_mid = warp_percentile<J>(s, nvalid, __ldg(rk + rank_entry(1, nvalid)));
+    const float x_hi = warp_percentile<J>(s, nvalid, __ldg(rk + rank_entry(2, nvalid)));
     const float sg = ep.c_sigma * (x_hi - x_lo);
     const float lo_b = x_mid - ep.n_sigma * sg, hi_b = x_mid + ep.n_sigma * sg;
 #pragma unroll
@@ -674,7 +694,6 @@ __device__ __forceinline__ void thread_bitonic_sort(float (&v)[NT]) {
       }
 }
 
-// Percentile of the n smallest of the ascending values in loc[] (linear interpolation, h = (n-1) q).
 // Element idx of a register array (selects, no dynamically indexed local memory).
 template <int NT>
 __device__ __forceinline__ float sel_sorted(const float (&v)[NT], int idx) {
@@ -685,12 +704,9 @@ __device__ __forceinline__ float sel_sorted(const float (&v)[NT], int idx) {
 }
 
 template <int NT>
-__device__ __forceinline__ float sorted_percentile(const float (&loc)[NT], int n, float q) {
-  const float h = (float)(n - 1) * q;
-  int lo = (int)floorf(h);
-  lo = max(0, min(lo, n - 1));
-  const int hi = min(lo + 1, n - 1);
-  const float f = h - (float)lo;
+__device__ __forceinline__ float sorted_percentile(const float (&loc)[NT], int n, int2 r) {
+  const int lo = r.x, hi = min(lo + 1, n - 1);
+  const float f = __int_as_float(r.y);
   const float a = sel_sorted<NT>(loc, lo), b = sel_sorted<NT>(loc, hi);
   return a + f * (b - a);
 }
@@ -751,9 +767,10 @@ __device__ float eval_pair_thread(const float2* __restrict__ pairs,
 #pragma unroll
     for (int t = 0; t < NT; ++t) loc[t] = ((vm >> t) & 1u) ? curve(t) : INFINITY;
     thread_bitonic_sort<NT>(loc);
-    const float x_lo = sorted_percentile<NT>(loc, nvalid, ep.q_lo);
-    const float x_mid = sorted_percentile<NT>(loc, nvalid, ep.q_mid);
-    const float x_hi = sorted_percentile<NT>(loc, nvalid, ep.q_hi);
+    const int2* rk = rank_table(dtf);
+    const float x_lo = sorted_percentile<NT>(loc, nvalid, __ldg(rk + rank_entry(0, nvalid)));
+    const float x_mid = sorted_percentile<NT>(loc, nvalid, __ldg(rk + rank_entry(1, nvalid)));
+    const float x_hi = sorted_percentile<NT>(loc, nvalid, __ldg(rk + rank_entry(2, nvalid)));
     const float sg = ep.c_sigma * (x_hi - x_lo);
     const float lo_b = x_mid - ep.n_sigma * sg, hi_b = x_mid + ep.n_sigma * sg;
     km = 0u;
@@ -1352,7 +1369,7 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
             uint32_t r[S_REC_WORDS];
             const float L = eval_pair_warp<decltype(jj)::value>(
                 e_pairs, EP, tx0 + (pl & 31), ty0 + (pl >> 5),
-                e_offs + (size_t)q_traj[e] * T, r, lane);
+                e_offs + (size_t)q_traj[e] * T, e_dt, r, lane);
             if (lane == 0 && L >= lh_min) keep(e, pl, r);
           }
         };
@@ -1803,7 +1820,9 @@ static int launch_prep(StackPrep& sp, const kb_schedule& sch, bool pool, cudaStr
     KB_CUDA_TRY(cudaGetDevice(&dev));
     KB_CUDA_TRY(cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev));
   }
-  plan_reset_kernel<<<N_CELLS / 256, 256, 0, st>>>(ctrl, counts, sp.te);
+  plan_reset_kernel<<<N_CELLS / 256, 256, 0, st>>>(ctrl, counts, sp.te, sp.A.ep.q_lo,
+                                                    sp.A.ep.q_mid, sp.A.ep.q_hi,
+                                                    reinterpret_cast<int2*>(dtf + KB_MAX_T));
   KB_LAUNCH_CHECK("plan_reset_kernel");
   plan_minmax_kernel<<<1, 1024, 0, st>>>(sp.vx, sp.vy, n_traj, vbox);
   KB_LAUNCH_CHECK("plan_minmax_kernel");

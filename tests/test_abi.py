@@ -573,3 +573,48 @@ def test_comparison_harness_tolerance_edges():
     g["lh"][tuple(e)] = 0.0                               # an empty slot must read -inf
     with pytest.raises(AssertionError):
         compare_search(g, o, 0.5)
+
+
+def test_comparison_harness_clip_bound_rule():
+    """Reading R6 for clip bounds: a kept-mask difference is accepted only for a trajectory whose
+    lightcurve lies within 1e-5 max(sigma_G, |median|) of a clip bound (oracle.clip_margin), and
+    then the GPU's LH' and alpha must be the sums over its own kept set.  Planted on the CPU in
+    copies of oracle results."""
+    import oracle
+    from helpers import compare_search, search_ctx
+    T = 5
+    times = np.array([0.0, 0.1, 0.2, 0.3, 0.4])
+    vx = np.zeros(1, np.float32)
+    vy = np.zeros(1, np.float32)
+    p = dict(k=1, lh_min=-1e9, min_obs=1, clip=1, q_lo=0.25, q_mid=0.5, q_hi=0.75, n_sigma=2.0)
+
+    def planes(a4):
+        psi = np.zeros((T, 3, 3))
+        phi = np.ones((T, 3, 3))
+        psi[:, 1, 1] = [0.0, 1.0, 2.0, 3.0, a4]
+        return psi, phi
+
+    upper = 2.0 + 2.0 * (oracle.sigma_g_coeff(0.25, 0.75) * 2.0)
+    for a4, at_bound in ((upper, True), (4.0, False)):
+        psi, phi = planes(a4)
+        o = oracle.search(psi, phi, times, vx, vy, p)
+        ctx = search_ctx(psi, phi, times, vx, vy, p)
+        assert o["mask"][1, 1, 0, 0] == 0b11111
+        g = {k: v.copy() for k, v in o.items()}
+        g["mask"][1, 1, 0, 0] = 0b01111          # epoch 4 dropped
+        g["nkept"][1, 1, 0] = 4
+        g["lh"][1, 1, 0] = 6.0 / 2.0              # sum psi / sqrt(sum phi) over epochs 0..3
+        g["flux"][1, 1, 0] = 6.0 / 4.0
+        with pytest.raises(AssertionError):
+            compare_search(g, o, p["lh_min"])     # no context: any mask difference fails
+        if at_bound:
+            counts = {}
+            assert compare_search(g, o, p["lh_min"], ctx=ctx, counts=counts) == 1
+            assert counts["clip_bound_mask"] == 1
+            bad = {k: v.copy() for k, v in g.items()}
+            bad["lh"][1, 1, 0] = o["lh"][1, 1, 0]   # values of the other kept set
+            with pytest.raises(AssertionError):
+                compare_search(bad, o, p["lh_min"], ctx=ctx)
+        else:
+            with pytest.raises(AssertionError, match="clip bound"):
+                compare_search(g, o, p["lh_min"], ctx=ctx)

@@ -12,7 +12,7 @@ import torch
 
 import oracle
 import paper_2109_03296_b300 as kb
-from helpers import compare_search, gpu_result_numpy
+from helpers import compare_search, gpu_result_numpy, search_ctx
 from synth import CONFIGS, make_likelihood_stack, make_stack, search_params_for
 
 pytestmark = pytest.mark.gpu
@@ -45,7 +45,7 @@ def _run_both(psi32, phi32, times, vx, vy, sp, window=None, oracle_window=None):
         x0 = ow[0] - (window or (0, W, 0, H))[0]
         y0 = ow[2] - (window or (0, W, 0, H))[2]
         g = {k: v[y0:y0 + (ow[3] - ow[2]), x0:x0 + (ow[1] - ow[0])] for k, v in g.items()}
-    return g, o, stats
+    return g, o, stats, search_ctx(psi32, phi32, times, vx, vy, _oracle_params(sp), ow)
 
 
 # ------------------------------------------------------------------------------------------------
@@ -103,8 +103,8 @@ def test_search_parity_tiny_pipeline(cuda_device):
     psi32, phi32 = psi.astype(np.float32), phi.astype(np.float32)
     c = CONFIGS["tiny"]
     sp = kb.SearchParams(k=c["K"], lh_min=c["lh_min"], min_obs=c["min_obs"])
-    g, o, stats = _run_both(psi32, phi32, s.times, s.vx, s.vy, sp)
-    compare_search(g, o, sp.lh_min)
+    g, o, stats, ctx = _run_both(psi32, phi32, s.times, s.vx, s.vy, sp)
+    compare_search(g, o, sp.lh_min, ctx=ctx)
     assert stats[0] == 256 * 256 * 128 * 10
     # recovery: at each injected mover's start pixel the best trajectory follows the injected
     # track to within 2 px at every epoch (neighbouring grid velocities differ by < 3 px over the
@@ -150,8 +150,40 @@ def test_search_parity_cases(cuda_device, seed, T, H, W, n_traj, K, lh, min_obs,
                              window):
     psi, phi, times, vx, vy = _likelihood_case(seed, T, H, W, n_traj, dup=n_traj > 8)
     sp = kb.SearchParams(k=K, lh_min=lh, min_obs=min_obs, clip=clip, clip_on=clip_on)
-    g, o, stats = _run_both(psi, phi, times, vx, vy, sp, window=window)
-    compare_search(g, o, lh)
+    g, o, stats, ctx = _run_both(psi, phi, times, vx, vy, sp, window=window)
+    compare_search(g, o, lh, ctx=ctx)
+
+
+# The paper leaves the quantile pair and the width "user-determinable" (Section 3.1, after
+# Eq. 5); the kernel forms the interpolation rank (n - 1) q in float64 like the oracle, so kept
+# masks agree except where an epoch sits within rounding of a clip bound (reading R6, counted).
+_QUANTILE_CASES = [
+    # seed, T, (q_lo, q_mid, q_hi), n_sigma, clip_on
+    (31, 26, (0.10, 0.50, 0.90), 1.5, 0),    # thread per pair, flux lightcurve
+    (32, 26, (0.10, 0.50, 0.90), 1.5, 1),    # thread per pair, likelihood lightcurve
+    (33, 13, (0.20, 0.45, 0.80), 2.5, 0),    # 16-wide sorting network
+    (34, 29, (0.20, 0.45, 0.80), 2.5, 1),
+    (35, 45, (0.10, 0.50, 0.90), 1.5, 0),    # warp per pair, two epochs per lane
+    (36, 45, (0.10, 0.50, 0.90), 1.5, 1),
+    (37, 45, (0.20, 0.45, 0.80), 2.5, 0),
+    (38, 100, (0.20, 0.45, 0.80), 2.5, 1),   # four epochs per lane
+]
+
+
+@pytest.mark.parametrize("seed,T,q,n_sigma,clip_on", _QUANTILE_CASES)
+def test_search_parity_quantiles(cuda_device, seed, T, q, n_sigma, clip_on):
+    H, W = (70, 60) if T <= 45 else (40, 36)
+    psi, phi, times, vx, vy = _likelihood_case(seed, T, H, W, 48)
+    sp = kb.SearchParams(k=4, lh_min=1.0, min_obs=max(3, T // 4), q_lo=q[0], q_mid=q[1],
+                         q_hi=q[2], n_sigma=n_sigma, clip_on=clip_on)
+    g, o, stats, ctx = _run_both(psi, phi, times, vx, vy, sp)
+    counts = {}
+    compare_search(g, o, sp.lh_min, ctx=ctx, counts=counts)
+    # the clip is doing work: some kept mask is not the full valid set
+    f = o["idx"] >= 0
+    assert int(f.sum()) > 100
+    assert (o["nkept"][f] < o["nvalid"][f]).any()
+    print("ambiguous pixels:", counts)
 
 
 @pytest.mark.parametrize("seed,T,H,W,n_traj,K,lh,min_obs,clip_on", [
@@ -165,8 +197,8 @@ def test_search_bound_rows_equivalent(cuda_device, seed, T, H, W, n_traj, K, lh,
     (bound_rows=2) are both exact: the oracle's results, and bit-identical to each other."""
     psi, phi, times, vx, vy = _likelihood_case(seed, T, H, W, n_traj)
     sp = kb.SearchParams(k=K, lh_min=lh, min_obs=min_obs, clip_on=clip_on, bound_rows=1)
-    g1, o, _ = _run_both(psi, phi, times, vx, vy, sp)
-    compare_search(g1, o, lh)
+    g1, o, _, ctx = _run_both(psi, phi, times, vx, vy, sp)
+    compare_search(g1, o, lh, ctx=ctx)
     sp2 = kb.SearchParams(k=K, lh_min=lh, min_obs=min_obs, clip_on=clip_on, bound_rows=2)
     res = kb.search(_cuda(psi), _cuda(phi), times, _cuda(vx), _cuda(vy), sp2)
     torch.cuda.synchronize()
@@ -183,8 +215,8 @@ def test_search_fast_movers_fallback(cuda_device, bound_rows):
     with single-row sums and with two-row blocks."""
     psi, phi, times, vx, vy = _likelihood_case(11, 8, 80, 90, 48, spread=400.0)
     sp = kb.SearchParams(k=3, lh_min=1.0, min_obs=2, bound_rows=bound_rows)
-    g, o, _ = _run_both(psi, phi, times, vx, vy, sp)
-    compare_search(g, o, 1.0)
+    g, o, _, ctx = _run_both(psi, phi, times, vx, vy, sp)
+    compare_search(g, o, 1.0, ctx=ctx)
 
 
 def test_search_non_finite_and_negative_planes(cuda_device):
@@ -198,8 +230,8 @@ def test_search_non_finite_and_negative_planes(cuda_device):
                                (0.0, 0.01, phi)):
         plane[rng.random((T, H, W)) < frac] = value
     sp = kb.SearchParams(k=4, lh_min=1.5, min_obs=3)
-    g, o, stats = _run_both(psi, phi, times, vx, vy, sp)
-    compare_search(g, o, 1.5)
+    g, o, stats, ctx = _run_both(psi, phi, times, vx, vy, sp)
+    compare_search(g, o, 1.5, ctx=ctx)
     assert int((g["idx"] >= 0).sum()) > 0
 
 
@@ -216,8 +248,8 @@ def test_search_degenerate(cuda_device):
     assert (r["idx"] < 0).all()
     # a one-pixel window
     sp = kb.SearchParams(k=3, lh_min=-1e9, min_obs=1, window=(17, 18, 30, 31))
-    g, o, _ = _run_both(psi, phi, times, vx, vy, sp, window=(17, 18, 30, 31))
-    compare_search(g, o, -1e9)
+    g, o, _, ctx = _run_both(psi, phi, times, vx, vy, sp, window=(17, 18, 30, 31))
+    compare_search(g, o, -1e9, ctx=ctx)
 
 
 def test_search_parity_decam_full_size(cuda_device):
@@ -248,7 +280,66 @@ def test_search_parity_decam_full_size(cuda_device):
     for (xa, xb, ya, yb) in wins:
         o = oracle.search(psi, phi, times, vx, vy, _oracle_params(sp), window=(xa, xb, ya, yb))
         g = {k: v[ya:yb, xa:xb] for k, v in g_all.items()}
-        compare_search(g, o, sp.lh_min)
+        compare_search(g, o, sp.lh_min,
+                       ctx=search_ctx(psi, phi, times, vx, vy, _oracle_params(sp),
+                                      (xa, xb, ya, yb)))
+        filled += int((o["idx"] >= 0).sum())
+    assert filled > 0
+
+
+def test_search_parity_bench_stack(cuda_device):
+    """The bench's own input: make_stack("decam") with the seed the bench times.  psi/phi are
+    formed by the oracle at full size (the kernel's psi/phi of the same images are checked
+    against them element by element), rounded to float32 and searched at full size in the
+    bench's launch configuration; the oracle checks windows around the three brightest movers,
+    a hot window at a mover's earliest +20 sigma spike (nearly every trajectory of a start pixel
+    there passes the pruning bound and is evaluated in full), and a corner."""
+    name = "decam"
+    s = make_stack(name)
+    c = CONFIGS[name]
+    psi_o, phi_o = oracle.psi_phi(s.img, s.var, s.mask, s.psf)
+    psi_g, phi_g = kb.make_psi_phi(_cuda(s.img), _cuda(s.var), _cuda(s.mask), _cuda(s.psf))
+    for got, ref, is_psi in ((psi_g, psi_o, True), (phi_g, phi_o, False)):
+        gt = got.cpu().numpy()
+        tol = 1e-5 * (np.abs(ref) + np.sqrt(np.maximum(phi_o, 1e-30))) if is_psi else \
+            1e-5 * np.abs(ref) + 1e-12
+        assert np.all(np.abs(gt - ref) <= tol)
+        del gt
+    del psi_g, phi_g
+    psi = psi_o.astype(np.float32)
+    phi = phi_o.astype(np.float32)
+    del psi_o, phi_o
+    sp = kb.SearchParams(k=c["K"], lh_min=c["lh_min"], min_obs=c["min_obs"])
+    T, H, W = psi.shape
+    res = kb.search(_cuda(psi), _cuda(phi), s.times, _cuda(s.vx), _cuda(s.vy), sp)
+    torch.cuda.synchronize()
+    stats = kb.search_stats(res["workspace"])
+    assert stats[3] == 0
+    g_all = gpu_result_numpy(res)
+    del res
+    torch.cuda.empty_cache()
+    psi64, phi64 = psi.astype(np.float64), phi.astype(np.float64)
+    del psi, phi
+    mv = s.movers
+    wins = []
+    for i in np.argsort(-mv["snr"])[:3]:
+        x0 = min(max(int(mv["x0"][i]) - 6, 0), W - 12)
+        y0 = min(max(int(mv["y0"][i]) - 6, 0), H - 12)
+        wins.append((x0, x0 + 12, y0, y0 + 12))
+    first = np.where(mv["spike"].any(axis=1), mv["spike"].argmax(axis=1), T)
+    i = int(np.argmin(first))
+    dt = s.times[first[i]] - s.times[0]
+    xs, ys = int(mv["x0"][i] + mv["vx"][i] * dt), int(mv["y0"][i] + mv["vy"][i] * dt)
+    x0, y0 = min(max(xs - 5, 0), W - 10), min(max(ys - 5, 0), H - 10)
+    wins.append((x0, x0 + 10, y0, y0 + 10))
+    wins.append((0, 10, H - 10, H))
+    p = _oracle_params(sp)
+    filled = 0
+    for (xa, xb, ya, yb) in wins:
+        o = oracle.search(psi64, phi64, s.times, s.vx, s.vy, p, window=(xa, xb, ya, yb))
+        g = {k: v[ya:yb, xa:xb] for k, v in g_all.items()}
+        compare_search(g, o, sp.lh_min,
+                       ctx=search_ctx(psi64, phi64, s.times, s.vx, s.vy, p, (xa, xb, ya, yb)))
         filled += int((o["idx"] >= 0).sum())
     assert filled > 0
 
@@ -283,7 +374,9 @@ def test_search_parity_full_config_grid(cuda_device):
     for (xa, xb, ya, yb) in wins:
         o = oracle.search(psi, phi, times, vx, vy, _oracle_params(sp), window=(xa, xb, ya, yb))
         g = {k: v[ya:yb, xa:xb] for k, v in g_all.items()}
-        compare_search(g, o, sp.lh_min)
+        compare_search(g, o, sp.lh_min,
+                       ctx=search_ctx(psi, phi, times, vx, vy, _oracle_params(sp),
+                                      (xa, xb, ya, yb)))
         filled += int((o["idx"] >= 0).sum())
     assert filled > 0
 

@@ -54,6 +54,12 @@ MUTANTS = [
     ("clip_quartiles_fixed",
      [("double sigma_g = kbo_sigma_g_coeff(q_lo, q_hi) * (x_hi - x_lo);",
        "double sigma_g = kbo_sigma_g_coeff(0.25, 0.75) * (x_hi - x_lo);", 1)]),
+    # the clip-bound margin of reading R6 (test infrastructure of the parity comparison)
+    ("clip_margin_upper_bound_only",
+     [("double d = fmin(fabs(a[i] - lower), fabs(a[i] - upper));",
+       "double d = fabs(a[i] - upper);", 1)]),
+    ("clip_margin_scale_sigma_only",
+     [("double scale = fmax(fmax(sg, fabs(med)), 1e-30);", "double scale = fmax(sg, 1e-30);", 1)]),
     # track rounding
     ("track_round_half_even", [("return (int32_t)floorf(e);", "return (int32_t)rintf(d);", 1)]),
     ("track_truncates", [("return (int32_t)floorf(e);", "return (int32_t)e;", 1)]),

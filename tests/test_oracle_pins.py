@@ -103,6 +103,44 @@ def np_offsets(times, v):
     return np.floor(np.float32(v) * dt + np.float32(0.5)).astype(np.int64)
 
 
+def _resting_track_case(a4):
+    """T = 5 epochs of a 3 x 3 image with phi = 1 and psi = 0, 1, 2, 3, a4 at the centre: the
+    flux lightcurve of the resting track (vx = vy = 0) started there."""
+    T = 5
+    psi = np.zeros((T, 3, 3))
+    phi = np.ones((T, 3, 3))
+    psi[:, 1, 1] = [0.0, 1.0, 2.0, 3.0, a4]
+    times = np.array([0.0, 0.1, 0.2, 0.3, 0.4])
+    return psi, phi, times
+
+
+def test_clip_margin_closed_forms():
+    """oracle.clip_margin (reading R6): quartiles 1 and 3, median 2, sigma_G = 2C and bounds
+    2 -+ 4C at n = 2 (Section 3.1, Eqs. 3-5).  With a4 = 4 the nearest epochs (0 and 4) lie 4C - 2
+    from a bound, i.e. 2C - 1 in units of max(sigma_G, |median|) = 2; with a4 on the upper bound
+    the margin is 0; no clip decision (clip off, too few epochs) gives +inf."""
+    c = 1.0 / (2.0 * math.sqrt(2.0) * scipy.special.erfinv(0.5))
+    psi, phi, times = _resting_track_case(4.0)
+    p = dict(min_obs=1, clip=1, q_lo=0.25, q_mid=0.5, q_hi=0.75, n_sigma=2.0)
+    m = oracle.clip_margin(psi, phi, times, 1, 1, 0.0, 0.0, p)
+    assert abs(m - (2.0 * c - 1.0)) < 1e-12
+    upper = 2.0 + 2.0 * (oracle.sigma_g_coeff(0.25, 0.75) * 2.0)   # the oracle's own bound
+    psi_b, phi_b, _ = _resting_track_case(upper)
+    assert oracle.clip_margin(psi_b, phi_b, times, 1, 1, 0.0, 0.0, p) == 0.0
+    # a first epoch on the lower bound (the quartiles and median are unchanged): margin 0
+    psi_l, phi_l, _ = _resting_track_case(4.0)
+    psi_l[0, 1, 1] = 2.0 - 2.0 * (oracle.sigma_g_coeff(0.25, 0.75) * 2.0)
+    assert oracle.clip_margin(psi_l, phi_l, times, 1, 1, 0.0, 0.0, p) == 0.0
+    # the margin is a property of one trajectory: the keep decision at the bound is inclusive
+    r = oracle.eval_one(psi_b, phi_b, times, 1, 1, 0.0, 0.0, p)
+    assert r["nkept"] == 5
+    assert oracle.clip_margin(psi, phi, times, 1, 1, 0.0, 0.0, dict(p, clip=0)) == np.inf
+    assert oracle.clip_margin(psi, phi, times, 1, 1, 0.0, 0.0, dict(p, min_obs=6)) == np.inf
+    # a track that leaves the image after one epoch has one valid epoch: sigma_G = 0, bounds at
+    # the value itself
+    assert oracle.clip_margin(psi, phi, times, 1, 1, 30.0, 0.0, p) == 0.0
+
+
 def test_track_offsets_match_float32_arithmetic():
     rng = np.random.default_rng(7)
     vx = rng.uniform(-600, 600, 200).astype(np.float32)
@@ -437,9 +475,20 @@ def test_search_invariances():
     assert np.allclose(sc["lh"][f], 2.0 * base["lh"][f], rtol=1e-12)
     assert np.allclose(sc["flux"][f], base["flux"][f], rtol=1e-12)
     assert np.array_equal(sc["mask"], base["mask"])
-    # (2) a common shift of all epoch times changes nothing (tracks use t - t_0)
-    sh = oracle.search(psi, phi, times + 0.0, vx, vy, p)
-    assert np.array_equal(sh["idx"], base["idx"])
+    # (2) a common shift of all epoch times changes nothing (tracks use t - t_0).  The times are
+    #     put on a 2^-30-day grid so that t + 57000.25 (an MJD-like origin) is exact in float64
+    #     and every difference t - t_0 is unchanged: the results must be bit-identical, while a
+    #     track measured from t = 0 instead of the first epoch would move by ~57000 days x v.
+    tg = np.round(times * 2.0 ** 30) / 2.0 ** 30
+    g0 = oracle.search(psi, phi, tg, vx, vy, p)
+    sh = oracle.search(psi, phi, tg + 57000.25, vx, vy, p)
+    assert not np.array_equal(tg + 57000.25, tg)
+    for key in ("idx", "mask", "nvalid", "nkept"):
+        assert np.array_equal(sh[key], g0[key]), key
+    f0 = g0["idx"] >= 0
+    assert f0.sum() > 10
+    assert np.array_equal(sh["lh"][f0], g0["lh"][f0])
+    assert np.array_equal(sh["flux"][f0], g0["flux"][f0])
     # (3) translating the content of every plane by (+2, +1) translates the results
     T, H, W = psi.shape
     psi2 = np.zeros_like(psi)
@@ -953,3 +1002,25 @@ def test_cluster_properties_fix_the_greedy_result():
             firsts = [j for j in range(i) if keep[j] and dup(i, j)]
             assert firsts and rep[i] == firsts[0]
     assert 20 <= keep.sum() < valid.sum()
+
+
+@pytest.mark.parametrize("name,H,W,window", [("tiny", None, None, (30, 40, 200, 210)),
+                                             ("decam", 160, 520, (20, 28, 70, 78))])
+def test_window_inputs_equal_whole_image_search(name, H, W, window):
+    """oracle.window_inputs (psi/phi on the region a window's tracks reach) gives the results of
+    the search of the whole image over that window, bit for bit."""
+    from synth import make_stack
+    s = make_stack(name, H=H, W=W)
+    p = dict(k=3, lh_min=2.0, min_obs=5)
+    if name == "decam":
+        s.vx, s.vy = s.vx[::64].copy(), s.vy[::64].copy()     # a coarser grid keeps it fast
+    psi, phi = oracle.psi_phi(s.img, s.var, s.mask, s.psf)
+    whole = oracle.search(psi, phi, s.times, s.vx, s.vy, p, window=window)
+    cp, cf, w2, (xa, ya) = oracle.window_inputs(s.img, s.var, s.mask, s.psf, s.times, s.vx, s.vy,
+                                                window)
+    assert cp.shape[1] < psi.shape[1] or cp.shape[2] < psi.shape[2]
+    assert np.array_equal(cp, psi[:, ya:ya + cp.shape[1], xa:xa + cp.shape[2]])
+    crop = oracle.search(cp, cf, s.times, s.vx, s.vy, p, window=w2)
+    for k in whole:
+        assert np.array_equal(whole[k], crop[k]), k
+    assert (whole["idx"] >= 0).sum() > 0
