@@ -23,8 +23,10 @@ best --n-refine survivors are gathered, and one step = 20 Adam steps of every ca
 (bilinear sub-pixel evaluation and its gradient, kept sets fixed) plus one forward and one
 backward pass at the refined tracks that also accumulates dL/dpsi and dL/dphi.
 
-N > 1 runs under torchrun, one rank per GPU; each rank searches its own stack (stacks are
-independent: weak scaling, no collective on the data path).  --impl reference times the FP64 CPU
+N > 1 runs one rank per GPU, each searching its own stack (stacks are independent: weak scaling,
+no collective on the data path; the only all-reduce takes the slowest rank's time).  Under
+torchrun the ranks are torchrun's; `python bench.py --gpus N` alone starts them itself
+(torch.distributed.run on this node).  --dry-run checks that path on CPU with gloo.  --impl reference times the FP64 CPU
 oracle on a bounded window of the same workload (rank 0 only).
 """
 import argparse
@@ -41,6 +43,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "decam"
+# workloads drawn on the device (synth.gpu_stacks.make_config_stack_torch) instead of numpy
+DEVICE_DRAWN = ("full",)
+
+
+class StackView:
+    """The arrays of a stack (host numpy views) under make_stack's field names."""
+
+    def __init__(self, **kw):
+        self.__dict__.update(kw)
 # Shared-memory bytes the bound pass reads per trajectory-epoch: one 32-bit word per (consumer
 # thread, trajectory, epoch) holds the fp16 maxima of two 2-row blocks, i.e. covers 4 start
 # pixels.
@@ -63,6 +74,9 @@ def parse():
                     help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--dry-run", action="store_true",
+                    help="CPU-only check of the multi-rank path: ranks join a gloo group, time a "
+                         "stand-in step and report as the real run does (no GPU work)")
     return ap.parse_args()
 
 
@@ -179,6 +193,9 @@ def summarize_clock_rows(lines):
 # ------------------------------------------------------------------------------------------------
 _ORACLE_DATA = {}
 ORACLE_MAX_SIDE = 64
+# the full-scale stack's tracks reach ~2200 x 1370 pixels from a start pixel; a small window keeps
+# the oracle's psi/phi of that region to a few tens of seconds
+ORACLE_MAX_SIDE_OF = {"full": 8}
 
 
 def _oracle_inputs(workload, stack=None):
@@ -189,9 +206,12 @@ def _oracle_inputs(workload, stack=None):
     if workload not in _ORACLE_DATA:
         import oracle
         from synth import make_stack
+        if stack is None and workload in DEVICE_DRAWN:
+            sys.exit("bench.py: the %s stack is drawn on the device; its CPU baseline is timed "
+                     "by the GPU arm" % workload)
         s = stack if stack is not None else make_stack(workload)
         T, H, W = s.img.shape
-        side = min(ORACLE_MAX_SIDE, H, W)
+        side = min(ORACLE_MAX_SIDE_OF.get(workload, ORACLE_MAX_SIDE), H, W)
         cx, cy = (W - side) // 2, (H - side) // 2
         psi, phi, win, _ = oracle.window_inputs(s.img, s.var, s.mask, s.psf, s.times, s.vx, s.vy,
                                                 (cx, cx + side, cy, cy + side))
@@ -269,10 +289,30 @@ def oracle_refine_rate(target_s, workload, n_steps):
     return dict(value=m * (n_steps + 1) * T / dt, seconds=dt, n=m, T=T, threads=1)
 
 
+def _device_drawn_stack(workload):
+    """The GPU arm's stack of a device-drawn workload (rank 0's seed), as host arrays."""
+    import torch
+    from synth import CONFIGS
+    from synth.gpu_stacks import make_config_stack_torch
+    if not torch.cuda.is_available():
+        return None
+    g = make_config_stack_torch(workload, torch.device("cuda", 0), seed=CONFIGS[workload]["seed"])
+    return StackView(img=g["img"].cpu().numpy(), var=g["var"].cpu().numpy(),
+                     mask=g["mask"].cpu().numpy(), psf=g["psf"].cpu().numpy(), times=g["times"],
+                     vx=g["vx"].cpu().numpy(), vy=g["vy"].cpu().numpy())
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
+    if args.workload in DEVICE_DRAWN and args.workload not in _ORACLE_DATA:
+        st = _device_drawn_stack(args.workload)
+        if st is None:
+            print(json.dumps({"impl": "reference", "unavailable": "the %s stack is drawn on the "
+                              "GPU and no GPU is visible" % args.workload}))
+            return
+        _oracle_inputs(args.workload, st)
     if args.workload.startswith("decam_refine"):
         return run_reference_refine(args)
     if args.workload == "batch64":
@@ -366,8 +406,10 @@ def workload_config(name):
                            c["lh_min"], c["min_obs"]),
             "T": c["T"], "H": c["H"], "W": c["W"], "n_traj": ns * na, "K": c["K"],
             "psf_k": c["psf_k"], "l2": l2_note(2 * 4 * c["T"] * c["H"] * c["W"]),
-            "stack": "synth.make_stack(%r, seed=%d): the stack timed here, checked against the "
-                     "oracle by the GPU tests and timed as the CPU baseline" % (name, c["seed"])}
+            "stack": ("%s(%r, seed=%d): the stack timed here, checked against the oracle by the "
+                      "GPU tests and timed as the CPU baseline"
+                      % ("synth.gpu_stacks.make_config_stack_torch" if name in DEVICE_DRAWN
+                         else "synth.make_stack", name, c["seed"]))}
 
 
 L2_BYTES = 126 * 2 ** 20
@@ -398,18 +440,33 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     c = CONFIGS[args.workload]
-    s = make_stack(args.workload, seed=rank_seed(c["seed"], rank))
+    seed = rank_seed(c["seed"], rank)
+    if args.workload in DEVICE_DRAWN:
+        # too large to draw with numpy in reasonable time: drawn on the device; the pinned host
+        # copies feed the end-to-end leg and the CPU baseline's window
+        from synth.gpu_stacks import make_config_stack_torch
+        g = make_config_stack_torch(args.workload, dev, seed=seed)
+        d = {k: g[k] for k in ("img", "var", "mask", "psf")}
+        host = {k: v.cpu().pin_memory() for k, v in d.items()}
+        s = StackView(img=host["img"].numpy(), var=host["var"].numpy(), mask=host["mask"].numpy(),
+                      psf=host["psf"].numpy(), times=g["times"], vx=g["vx"].cpu().numpy(),
+                      vy=g["vy"].cpu().numpy())
+        vx, vy = g["vx"], g["vy"]
+        del g
+    else:
+        s = make_stack(args.workload, seed=seed)
+        # pinned host copies (for the end-to-end leg) and device-resident inputs
+        host = {"img": torch.from_numpy(s.img).pin_memory(),
+                "var": torch.from_numpy(s.var).pin_memory(),
+                "mask": torch.from_numpy(s.mask).pin_memory(),
+                "psf": torch.from_numpy(s.psf).pin_memory()}
+        d = {k: v.to(dev, non_blocking=False) for k, v in host.items()}
+        vx, vy = torch.from_numpy(s.vx).to(dev), torch.from_numpy(s.vy).to(dev)
     T, H, W = s.img.shape
     n_traj = len(s.vx)
     K = c["K"]
     sp = kb.SearchParams(k=K, lh_min=c["lh_min"], min_obs=c["min_obs"])
     te_step = H * W * n_traj * T
-
-    # pinned host copies (for the end-to-end leg) and device-resident inputs
-    host = {"img": torch.from_numpy(s.img).pin_memory(), "var": torch.from_numpy(s.var).pin_memory(),
-            "mask": torch.from_numpy(s.mask).pin_memory(), "psf": torch.from_numpy(s.psf).pin_memory()}
-    d = {k: v.to(dev, non_blocking=False) for k, v in host.items()}
-    vx, vy = torch.from_numpy(s.vx).to(dev), torch.from_numpy(s.vy).to(dev)
     psi = torch.empty((T, H, W), dtype=torch.float32, device=dev)
     phi = torch.empty_like(psi)
     ws = kb.alloc_workspace(kb.search_workspace_size(T, H, W, n_traj, sp), dev)
@@ -975,8 +1032,58 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def launch_ranks(n, argv):
+    """bench.py --gpus N run outside torchrun: start N ranks on this node (one per GPU) with
+    torch.distributed.run, each running this script with the same arguments, and return their
+    exit status.  Rank 0 prints the JSON line."""
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+           "--nproc-per-node", str(n), "--master-addr", "127.0.0.1", "--master-port", str(port),
+           os.path.abspath(__file__)] + list(argv)
+    return subprocess.run(cmd).returncode
+
+
+def run_dry(args):
+    """The multi-rank path without a GPU: every rank joins a gloo group, times a stand-in step of
+    CPU work, the slowest rank's time is taken (as for the real steps) and rank 0 prints the
+    line with the real workload's trajectory-epochs, one independent stack per rank."""
+    import torch.distributed as dist
+    from synth import CONFIGS
+    rank, world, _ = dist_env()
+    if world > 1:
+        dist.init_process_group("gloo")
+    c = CONFIGS[args.workload]
+    v0, v1, ns, a0, a1, na = c["grid"]
+    te_step = c["T"] * c["H"] * c["W"] * ns * na
+    x = 0.0
+    t0 = time.perf_counter()
+    for i in range(200000 * (rank + 1)):
+        x += math.sqrt(i)
+    ms = max_over_ranks((time.perf_counter() - t0) * 1e3, world, "cpu")
+    seeds = [rank_seed(c["seed"], r) for r in range(world)]
+    if rank == 0:
+        print(json.dumps({"metric": "trajectory-epoch evals/sec", "dry_run": True,
+                          "value": world * te_step * args.steps / (ms / 1e3), "unit": "TE/s",
+                          "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": ms / args.steps, "scaling": "weak",
+                          "config": dict(workload_config(args.workload), seeds=seeds,
+                                         parallelism="one independent stack per GPU"
+                                         if world > 1 else "1 GPU")}), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(launch_ranks(args.gpus, sys.argv[1:]))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world != args.gpus:
+        sys.exit("bench.py: --gpus %d but %d ranks were started" % (args.gpus, world))
     auto_steps = args.steps is None
     if auto_steps:
         # the search: the median of 5 timed steps (~0.6 s each); a batch64 step takes ~10 s and
@@ -984,7 +1091,9 @@ def main():
         args.steps = 5 if (args.impl == "ours" and args.workload != "batch64") else 3
     refine = args.workload.startswith("decam_refine")
     args.auto_steps = auto_steps and refine and args.impl == "ours"
-    if args.impl == "reference":
+    if args.dry_run:
+        run_dry(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif refine:
         run_refine(args)

@@ -184,8 +184,13 @@ KB_API int kb_search(const float* psi, const float* phi, const double* times, in
  *    does not depend on the workspace's previous contents).  Calls whose work overlaps on the
  *    GPU (different streams, or threads without ordering) race on the array: serialise them.
  *  - No allocation of any kind (no cudaMalloc, no cudaFree, no allocating library routine).
+ *  - The looked-up address is kept for the life of the process: a cudaDeviceReset between calls
+ *    is not supported (the array may move when the module reloads).
+ *  - kb_search_no_alloc_stats reads the counters of the last call on the current device,
+ *    including the device-side error flags (a bounded wait that gave up).
  * Errors: as kb_search, plus KB_ERR_UNSUPPORTED for sizes beyond the built-in scratch and
- * KB_ERR_CUDA if the address lookup fails.
+ * KB_ERR_CUDA if the address lookup fails.  KB_FAULT_INJECT=kb_search_no_alloc injects a failure
+ * after the size check (the call also runs kb_search's own checks and injection point).
  */
 #define KB_STATIC_SCRATCH_BYTES (32u << 20)
 KB_API int kb_search_no_alloc(const float* psi, const float* phi, const double* times, int T,
@@ -193,6 +198,15 @@ KB_API int kb_search_no_alloc(const float* psi, const float* phi, const double* 
                               const kb_search_params* p, float* out_lh, float* out_flux,
                               int32_t* out_idx, uint16_t* out_nvalid, uint16_t* out_nkept,
                               uint32_t* out_mask, void* stream);
+
+/*
+ * kb_search_no_alloc_stats -- kb_search_stats of the last kb_search_no_alloc call on the current
+ * device (HOST array stats[4], same meaning; synchronises the stream).  A search whose
+ * device-side wait gave up returns KB_OK with partial lists; stats[3] != 0 tells the caller.
+ * Errors: KB_ERR_INVALID_ARG (null pointer, or no kb_search_no_alloc call on this device yet),
+ * KB_ERR_CUDA.  The paper has no counterpart.
+ */
+KB_API int kb_search_no_alloc_stats(unsigned long long* stats, void* stream);
 
 /*
  * kb_search_stats -- counters of the last kb_search that used `workspace` (device counters
@@ -203,6 +217,22 @@ KB_API int kb_search_no_alloc(const float* psi, const float* phi, const double* 
  *   stats[3] device-side error flags (0 = none; KB_ERR_TIMEOUT bit 0x1 if a bounded wait gave up).
  */
 KB_API int kb_search_stats(const void* workspace, unsigned long long* stats, void* stream);
+
+/*
+ * kb_search_stage_counts -- candidate counts at the stages of the last kb_search that used
+ * `workspace`, the per-stage counts Section 3.1 (Fig. 3) and Section 3.4 (Fig. 4) report for the
+ * pipeline (HOST array out[4]; synchronises the stream).  Over the (pixel, trajectory) pairs
+ * the search evaluated in full (kb_search_stats()[1]):
+ *   out[0] pairs with n_valid >= max(min_obs, 1) (eligible for the clip),
+ *   out[1] pairs whose clipped LH' reached lh_min,
+ *   out[2] the sum of n_kept over the out[1] pairs, out[3] the sum of their n_valid
+ *          (out[2] / out[3] = the mean kept fraction of the clip).
+ * Pruned pairs are not counted.  A pair is pruned only when its bound is below lh_min or below
+ * the K-th LH' of its start pixel's full list, so while no list is full every pair that reaches
+ * lh_min is evaluated (out[1..3] are then the exhaustive counts), and with lh_min <= 0 and K at
+ * least the number of trajectories every pair is (all four are).
+ */
+KB_API int kb_search_stage_counts(const void* workspace, unsigned long long* out, void* stream);
 
 /*
  * kb_stamps -- coadded postage stamps along trajectories (Section 3.3: per-pixel median over
@@ -491,6 +521,16 @@ KB_API int kb_candidate_params(const int32_t* cand_pix, const int32_t* cand_slot
  */
 KB_API int kb_l2_probe(const void* buf, size_t bytes, int reps, float* scratch, int blocks,
                        void* stream);
+
+/*
+ * kb_smem_probe -- measurement utility, not part of the method: `blocks` blocks of 1024 threads
+ * each stream `iters` x 32 shared-memory loads per warp, 32-bit and lane-contiguous (one 128-byte
+ * wavefront per load instruction, no bank conflict), the access of the search kernel's bound
+ * pass.  The caller times the call (CUDA events): blocks x 32 warps x iters x 32 x 128 bytes /
+ * time is the shared-memory read bandwidth the bound pass can reach.  scratch: `blocks` uint32
+ * (device), written only in a case the probe data never meet.
+ */
+KB_API int kb_smem_probe(int blocks, int iters, unsigned int* scratch, void* stream);
 
 /*
  * kb_wait_check -- failure detection without a fault: runs the bounded device-side waits of the

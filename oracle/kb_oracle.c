@@ -318,6 +318,60 @@ double kbo_clip_margin(const double* psi, const double* phi, const double* times
   return m / scale;
 }
 
+/* Candidate counts per stage over every (start pixel, trajectory) pair of a window (the stages
+ * Fig. 3 counts): out[0] pairs with at least max(min_obs, 1) valid epochs; out[1] pairs whose
+ * clipped L' is defined and reaches lh_min; out[2], out[3] the sums of n_kept and n_valid over
+ * the out[1] pairs.  Each pair is evaluated in full as in kbo_search. */
+int kbo_stage_counts(const double* psi, const double* phi, const double* times, int T, int H,
+                     int W, const float* vx, const float* vy, int n_traj, double lh_min,
+                     int min_obs, int clip, double q_lo, double q_mid, double q_hi,
+                     double n_sigma, int clip_on, int x_lo, int x_hi, int y_lo, int y_hi,
+                     unsigned long long* out) {
+  if (T <= 0 || T > KBO_MAX_T || n_traj < 0) return -1;
+  if (x_lo < 0 || x_hi > W || y_lo < 0 || y_hi > H || x_lo > x_hi || y_lo > y_hi) return -1;
+  int32_t* ox = (int32_t*)malloc(sizeof(int32_t) * (size_t)n_traj * T + 4);
+  int32_t* oy = (int32_t*)malloc(sizeof(int32_t) * (size_t)n_traj * T + 4);
+  kbo_track_offsets(times, T, vx, vy, n_traj, ox, oy);
+  int ww = x_hi - x_lo;
+  int npix = ww * (y_hi - y_lo);
+  unsigned long long c_valid = 0, c_pass = 0, c_kept = 0, c_nvalid = 0;
+#pragma omp parallel reduction(+ : c_valid, c_pass, c_kept, c_nvalid)
+  {
+    double* bp = (double*)malloc(sizeof(double) * T);
+    double* bf = (double*)malloc(sizeof(double) * T);
+    double* ba = (double*)malloc(sizeof(double) * T);
+    int* bt = (int*)malloc(sizeof(int) * T);
+    uint8_t* bk = (uint8_t*)malloc((size_t)T);
+#pragma omp for schedule(dynamic, 1)
+    for (int p = 0; p < npix; ++p) {
+      const int sx = x_lo + p % ww, sy = y_lo + p / ww;   /* start pixel */
+      for (int j = 0; j < n_traj; ++j) {
+        traj_result r;
+        eval_traj(psi, phi, T, H, W, sx, sy, ox + (size_t)j * T, oy + (size_t)j * T, min_obs,
+                  clip, q_lo, q_mid, q_hi, n_sigma, clip_on, &r, bp, bf, ba, bt, bk);
+        if (r.nvalid > 0 && r.nvalid >= min_obs) ++c_valid;
+        if (r.ok && r.lh >= lh_min) {
+          ++c_pass;
+          c_kept += (unsigned long long)r.nkept;
+          c_nvalid += (unsigned long long)r.nvalid;
+        }
+      }
+    }
+    free(bp);
+    free(bf);
+    free(ba);
+    free(bt);
+    free(bk);
+  }
+  free(ox);
+  free(oy);
+  out[0] = c_valid;
+  out[1] = c_pass;
+  out[2] = c_kept;
+  out[3] = c_nvalid;
+  return 0;
+}
+
 /* ---------------------------------------------------------------------------------------- */
 /* Exhaustive search + threshold + per-pixel top-K (Section 3, 3.1, 3.2; R5, R8)             */
 /* ---------------------------------------------------------------------------------------- */

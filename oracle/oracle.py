@@ -40,6 +40,9 @@ def lib():
                                       p, p, p, p, p]
         _LIB.kbo_clip_margin.restype = d
         _LIB.kbo_clip_margin.argtypes = [p, p, p, i, i, i, i, i, f, f, i, i, d, d, d, d, i]
+        _LIB.kbo_stage_counts.restype = i
+        _LIB.kbo_stage_counts.argtypes = [p, p, p, i, i, i, p, p, i, d, i, i, d, d, d, d, i,
+                                          i, i, i, i, p]
         _LIB.kbo_search.restype = i
         _LIB.kbo_search.argtypes = [p, p, p, i, i, i, p, p, i, i, d, i, i, d, d, d, d, i,
                                     i, i, i, i, p, p, p, p, p, p]
@@ -208,6 +211,24 @@ def clip_margin(psi, phi, times, x0, y0, vx, vy, params=None):
     return lib().kbo_clip_margin(_ptr(psi), _ptr(phi), _ptr(times), T, H, W, int(x0), int(y0),
                                  float(vx), float(vy), q["min_obs"], q["clip"], q["q_lo"],
                                  q["q_mid"], q["q_hi"], q["n_sigma"], q["clip_on"])
+
+
+def stage_counts(psi, phi, times, vx, vy, params=None, window=None):
+    """Stage counts over every pair of the window: (n_valid >= min_obs, LH' >= lh_min after the
+    clip, sum of n_kept and sum of n_valid over the latter)."""
+    q = _params(params)
+    psi, phi, times = _f64(psi), _f64(phi), _f64(times)
+    vx, vy = _f32(vx), _f32(vy)
+    T, H, W = psi.shape
+    x_lo, x_hi, y_lo, y_hi = (int(v) for v in (window or (0, W, 0, H)))
+    out = np.zeros(4, np.uint64)
+    rc = lib().kbo_stage_counts(_ptr(psi), _ptr(phi), _ptr(times), T, H, W, _ptr(vx), _ptr(vy),
+                                len(vx), q["lh_min"], q["min_obs"], q["clip"], q["q_lo"],
+                                q["q_mid"], q["q_hi"], q["n_sigma"], q["clip_on"], x_lo, x_hi,
+                                y_lo, y_hi, _ptr(out))
+    if rc != 0:
+        raise ValueError("oracle stage_counts rejected its arguments")
+    return tuple(int(v) for v in out)
 
 
 def search(psi, phi, times, vx, vy, params=None, window=None):

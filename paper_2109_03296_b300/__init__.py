@@ -146,6 +146,8 @@ def search(psi, phi, times, vx, vy, params=None, workspace=None, out=None, strea
                    mask=torch.empty((wy, wx, K, mw), dtype=torch.int32, device=dev))
     if workspace is None:
         workspace = alloc_workspace(search_workspace_size(T, H, W, vx.numel(), params), dev)
+    _same_device([("psi", psi), ("phi", phi), ("vx", vx), ("vy", vy), ("workspace", workspace)]
+                 + [("out[%s]" % k, v) for k, v in out.items() if k != "workspace"])
     check(lib().kb_search(_ptr(psi), _ptr(phi), times.ctypes.data_as(C.c_void_p), T, H, W,
                           _ptr(vx), _ptr(vy), vx.numel(), C.byref(pc), _ptr(out["lh"]),
                           _ptr(out["flux"]), _ptr(out["idx"]), _ptr(out["nvalid"]),
@@ -161,6 +163,32 @@ def search_stats(workspace, stream=None):
     arr = (C.c_ulonglong * 4)()
     check(lib().kb_search_stats(_ptr(workspace), arr, _stream(stream)))
     return tuple(int(v) for v in arr)
+
+
+def search_stage_counts(workspace, stream=None):
+    """Stage counts of the last search that used this workspace, over the pairs it evaluated in
+    full: (n_valid >= min_obs, LH' >= lh_min after the clip, sum of n_kept and sum of n_valid over
+    the latter).  Synchronises the stream."""
+    arr = (C.c_ulonglong * 4)()
+    check(lib().kb_search_stage_counts(_ptr(workspace), arr, _stream(stream)))
+    return tuple(int(v) for v in arr)
+
+
+def search_no_alloc_stats(stream=None):
+    """search_stats() of the last search_no_alloc() on the current device (stats[3] != 0: a
+    device-side wait gave up and the lists may be partial)."""
+    arr = (C.c_ulonglong * 4)()
+    check(lib().kb_search_no_alloc_stats(arr, _stream(stream)))
+    return tuple(int(v) for v in arr)
+
+
+def _same_device(name_tensors):
+    """Every tensor must live on the current CUDA device (the library launches there)."""
+    cur = torch.cuda.current_device()
+    for name, t in name_tensors:
+        if t is not None and t.device.index != cur:
+            raise ValueError("%s is on cuda:%s, the current device is cuda:%d"
+                             % (name, t.device.index, cur))
 
 
 def stamps(img, var, mask, times, x0, y0, vx, vy, radius=10, keep_mask=None, stream=None):
@@ -276,6 +304,28 @@ def candidate_tracks(pix, slot, result, vx, vy, window=None, stream=None):
     return x0, y0, ovx, ovy, traj
 
 
+def smem_read_bandwidth(iters=4000, device=None):
+    """Shared-memory read bandwidth in GB/s from kb_smem_probe: conflict-free 32-bit loads, one
+    128-byte wavefront each, from two 1024-thread blocks per SM (best of 3 timed calls after a
+    warm-up)."""
+    dev = torch.device("cuda") if device is None else device
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks = sms * 2
+    scratch = torch.zeros(blocks, dtype=torch.int32, device=dev)
+    s = _stream(None)
+    check(lib().kb_smem_probe(blocks, 200, _ptr(scratch), s))
+    best = 0.0
+    nbytes = blocks * 32 * iters * 32 * 128
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        check(lib().kb_smem_probe(blocks, iters, _ptr(scratch), s))
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, nbytes / (e0.elapsed_time(e1) / 1e3) / 1e9)
+    return best
+
+
 def l2_read_bandwidth(mbytes=64, reps=40, device=None):
     """L2 read bandwidth in GB/s from kb_l2_probe on a resident buffer of `mbytes` MB (best of 3
     timed calls after a warm-up)."""
@@ -347,6 +397,8 @@ def search_no_alloc(psi, phi, times, vx, vy, params=None, out=None, stream=None)
                    nvalid=torch.empty((wy, wx, K), dtype=torch.int16, device=dev),
                    nkept=torch.empty((wy, wx, K), dtype=torch.int16, device=dev),
                    mask=torch.empty((wy, wx, K, mw), dtype=torch.int32, device=dev))
+    _same_device([("psi", psi), ("phi", phi), ("vx", vx), ("vy", vy)]
+                 + [("out[%s]" % k, v) for k, v in out.items()])
     check(lib().kb_search_no_alloc(_ptr(psi), _ptr(phi), times.ctypes.data_as(C.c_void_p), T, H,
                                    W, _ptr(vx), _ptr(vy), vx.numel(), C.byref(pc),
                                    _ptr(out["lh"]), _ptr(out["flux"]), _ptr(out["idx"]),

@@ -107,6 +107,47 @@ __global__ void l2_probe_kernel(const float4* __restrict__ buf, size_t n_vec, in
 }
 }  // namespace kb
 
+// ------------------------------------------------------------------------------------------------
+// Shared-memory read probe (measurement utility): every warp streams conflict-free 32-bit
+// shared loads (lane-contiguous words, one 128-byte wavefront per instruction), the access the
+// search kernel's bound pass makes; the caller times it.
+// ------------------------------------------------------------------------------------------------
+namespace kb {
+constexpr int kSmemProbeThreads = 1024;
+__global__ void __launch_bounds__(kSmemProbeThreads) smem_probe_kernel(int iters,
+                                                                       unsigned int* out) {
+  __shared__ __align__(16) unsigned int buf[8192];  // 32 KB
+  for (int i = threadIdx.x; i < 8192; i += blockDim.x) buf[i] = (unsigned int)i * 2654435761u;
+  __syncthreads();
+  const unsigned int base =
+      static_cast<unsigned int>(__cvta_generic_to_shared(buf)) + (threadIdx.x & 31) * 4u;
+  unsigned int acc[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+  for (int it = 0; it < iters; ++it) {
+    const unsigned int b = base + (unsigned int)(it & 7) * 4096u;
+#pragma unroll
+    for (int u = 0; u < 32; ++u) {
+      unsigned int v;
+      asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(b + (unsigned int)u * 128u));
+      acc[u & 7] += v;
+    }
+  }
+  unsigned int s = 0u;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s ^= acc[k];
+  if (s == 0x9e3779b9u && threadIdx.x == 0) out[blockIdx.x] = s;  // keeps the loads
+}
+}  // namespace kb
+
+extern "C" int kb_smem_probe(int blocks, int iters, unsigned int* scratch, void* stream) {
+  using namespace kb;
+  if (!scratch || blocks < 1 || iters < 1)
+    return fail(KB_ERR_INVALID_ARG, "kb_smem_probe: bad arguments");
+  smem_probe_kernel<<<blocks, kSmemProbeThreads, 0, static_cast<cudaStream_t>(stream)>>>(iters,
+                                                                                        scratch);
+  KB_LAUNCH_CHECK("smem_probe_kernel");
+  return KB_OK;
+}
+
 extern "C" int kb_l2_probe(const void* buf, size_t bytes, int reps, float* scratch, int blocks,
                            void* stream) {
   using namespace kb;

@@ -83,13 +83,16 @@ constexpr int S_REC_BLOCKS = 256;        // most blocks of a launch (records in 
 constexpr float S_PRUNE_MARGIN = 1.0f - 1e-4f;
 static_assert(S_D % S_PWARPS == 0 && S_REGION_MAX <= S_RING_BYTES, "pipeline configuration");
 static_assert((S_D & (S_D - 1)) == 0, "slot indices from a 32-bit iteration count");
-// A staged rectangle is one TMA box: width class w = 1..3 (rows of 64/96/128 words) and
-// height class h = 0..4 (64/80/96/112/128 word rows); mode 0 = direct global loads.
-constexpr int S_NW = 3, S_NH = 5;
-__host__ __device__ constexpr int stage_width(int mode) {
-  return mode == 1 ? 64 : mode == 2 ? 96 : 128;
-}
-__host__ __device__ constexpr int stage_height(int h) { return 64 + 16 * h; }
+// A staged rectangle is one TMA box: width class w = 1..S_NW (rows of 32, 40, ..., 128 words)
+// and height class h = 0..S_NH-1 (S_TY, S_TY + 8, ..., 128 word rows); mode 0 = direct global
+// loads.  Classes 8 words apart keep the padding of a box small, so more boxes fit in the ring
+// and fewer bytes are staged.
+constexpr int S_NW = 13, S_NH = (128 - S_TY) / 8 + 1;
+__host__ __device__ constexpr int stage_width(int mode) { return 32 + 8 * (mode - 1); }
+__host__ __device__ constexpr int stage_height(int h) { return S_TY + 8 * h; }
+static_assert(stage_width(S_NW) == 128 && stage_height(S_NH - 1) == 128 && S_TY % 8 == 0,
+              "box classes");
+constexpr int S_MODE_MASK = 15, S_UNIFORM_BIT = 16;  // PlanRec box.w: mode | uniform
 
 constexpr int S_ORDER_MAX = 16384;       // tiles ordered by predicted cost (one-block sort)
 constexpr int HILBERT_BITS = 8;          // 256 x 256 velocity cells
@@ -166,12 +169,16 @@ static WsLayout ws_layout(int T, int H, int W, int n_traj) {
   return L;
 }
 
-// ctrl block: [0] error flags (u32), [8] stats: te, evals, inserts (u64 each)
+// ctrl block: error flags, the tile counter, and the statistics kb_search_stats reports
 struct Ctrl {
   unsigned int err;
   unsigned int tile_counter;  // dynamic tile scheduling of the search kernel
   unsigned long long te, evals, inserts;
+  // stage counts of the pairs evaluated in full: n_valid >= min_obs; LH' >= lh_min after the
+  // clip; and, over the latter, the sums of n_kept and n_valid (the mean kept fraction)
+  unsigned long long stage_valid, stage_pass, stage_kept, stage_nvalid;
 };
+static_assert(sizeof(Ctrl) <= 256, "control block");
 
 // ---------------------------------------------------------------------------------------------
 // Plan kernels: velocity ordering, track offsets, per-(chunk, epoch) staging rectangles
@@ -190,11 +197,8 @@ __global__ void plan_reset_kernel(Ctrl* ctrl, uint32_t* counts, unsigned long lo
     rank[i] = make_int2(lo, __float_as_int(__double2float_rn(__dsub_rn(h, (double)lo))));
   }
   if (i == 0) {
-    ctrl->err = 0u;
-    ctrl->tile_counter = 0u;
+    *ctrl = Ctrl{};
     ctrl->te = te;
-    ctrl->evals = 0ull;
-    ctrl->inserts = 0ull;
   }
 }
 
@@ -341,9 +345,9 @@ __global__ void plan_offsets_kernel(const float* __restrict__ vx, const float* _
 // One thread per (chunk, epoch): staging rectangle and per-trajectory byte offsets into it.
 // box = {x offset of the rectangle from the tile origin (x_lo + dxmin - xshift is a multiple
 // of 4 so that the TMA x coordinate is 16-byte aligned), y offset, height class, mode} with
-// mode 1..3 = rows of 64/96/128 words: the narrowest, then lowest, TMA box that holds the
-// rectangle; mode 0 = no box within S_REGION_MAX (direct loads); bit 3 of the last field set
-// when all of the chunk's offsets are equal in this epoch.
+// mode 1..S_NW = the width class and height class of the smallest TMA box that holds the
+// rectangle; mode 0 = no box within S_REGION_MAX (direct loads); S_UNIFORM_BIT of the last field
+// set when all of the chunk's offsets are equal in this epoch.
 __global__ void plan_boxes_kernel(const int2* __restrict__ offs, int nchunk, int T, int x_lo,
                                   PlanRec* plan) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -359,20 +363,19 @@ __global__ void plan_boxes_kernel(const int2* __restrict__ offs, int nchunk, int
   const int xshift = ((x_lo + dxmin) % 4 + 4) % 4;
   const int rw = S_TX + (dxmax - dxmin) + xshift;
   const int rh = S_TY + (dymax - dymin);
+  // the smallest width and height classes that hold the rectangle
+  const int m = 1 + max(0, (rw - stage_width(1) + 7) / 8);
+  const int h = max(0, (rh - stage_height(0) + 7) / 8);
   int mode = 0, pitch = 0, hcls = 0;
-  for (int m = 1; m <= S_NW && !mode; ++m)
-    for (int h = 0; h < S_NH; ++h)
-      if (rw <= stage_width(m) && rh <= stage_height(h) &&
-          stage_width(m) * stage_height(h) * 4 <= S_REGION_MAX) {
-        mode = m;
-        pitch = stage_width(m);
-        hcls = h;
-        break;
-      }
+  if (m <= S_NW && h < S_NH && stage_width(m) * stage_height(h) * 4 <= S_REGION_MAX) {
+    mode = m;
+    pitch = stage_width(m);
+    hcls = h;
+  }
   PlanRec& pr = plan[i];
-  // bit 3 of box.w: every trajectory of the chunk has the same offset in this epoch (always
-  // at t = 0, often in the first hours), so one load (per row pair) serves all of them
-  const int uniform = (dxmin == dxmax && dymin == dymax) ? 8 : 0;
+  // S_UNIFORM_BIT of box.w: every trajectory of the chunk has the same offset in this epoch
+  // (always at t = 0, often in the first hours), so one load (per row pair) serves all of them
+  const int uniform = (dxmin == dxmax && dymin == dymax) ? S_UNIFORM_BIT : 0;
   pr.box = make_int4(dxmin - xshift, dymin, hcls, mode | uniform);
   for (int v = 0; v < S_C; ++v) {
     int2 o = offs[(size_t)(c * S_C + v) * T + t];
@@ -578,24 +581,30 @@ __device__ float eval_pair_warp(const float2* __restrict__ pairs, const EvalPara
   float ps[J], ph[J], a[J];
   bool valid[J];
   const size_t plane = (size_t)ep.H * ep.W;
+  // all of the lane's offset loads, then all of its (psi, phi) loads, then the tests (an epoch
+  // off the image or beyond T reads element 0 of a plane and is masked off)
+  int2 o[J];
 #pragma unroll
   for (int j = 0; j < J; ++j) {
     const int t = (j << 5) | lane;
-    ps[j] = 0.0f;
-    ph[j] = 0.0f;
-    valid[j] = false;
-    if (t < ep.T) {
-      const int2 o = __ldg(off + t);
-      const int x = x0 + o.x, y = y0 + o.y;
-      if (x >= 0 && x < ep.W && y >= 0 && y < ep.H) {
-        const float2 pf = __ldg(pairs + (size_t)t * plane + (size_t)y * ep.W + x);
-        const float p = pf.x, f = pf.y;
-        if (f > 0.0f && isfinite(p) && isfinite(f)) {
-          ps[j] = p;
-          ph[j] = f;
-          valid[j] = true;
-        }
-      }
+    o[j] = t < ep.T ? __ldg(off + t) : make_int2(0, 0);
+  }
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    const int t = (j << 5) | lane;
+    const int x = x0 + o[j].x, y = y0 + o[j].y;
+    valid[j] = t < ep.T && x >= 0 && x < ep.W && y >= 0 && y < ep.H;
+    const size_t at = t < ep.T ? (size_t)t * plane + (valid[j] ? (size_t)y * ep.W + x : 0) : 0;
+    const float2 pf = __ldg(pairs + at);
+    ps[j] = pf.x;
+    ph[j] = pf.y;
+  }
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    valid[j] = valid[j] && ph[j] > 0.0f && isfinite(ps[j]) && isfinite(ph[j]);
+    if (!valid[j]) {
+      ps[j] = 0.0f;
+      ph[j] = 0.0f;
     }
   }
   int nvalid = 0;
@@ -711,16 +720,6 @@ __device__ __forceinline__ float sorted_percentile(const float (&loc)[NT], int n
   return a + f * (b - a);
 }
 
-__device__ __forceinline__ bool gather_pair(const float2* __restrict__ pairs,
-                                            const EvalParams& ep, size_t plane, int t, int x,
-                                            int y, float& p, float& f) {
-  if (x < 0 || x >= ep.W || y < 0 || y >= ep.H) return false;
-  const float2 pf = __ldg(pairs + (size_t)t * plane + (size_t)y * ep.W + x);
-  p = pf.x;
-  f = pf.y;
-  return f > 0.0f && isfinite(p) && isfinite(f);
-}
-
 // One pair, one thread.  psi_t and phi_t stay in registers from the single gather; the
 // lightcurve value of an epoch (flux psi/phi, or psi/sqrt(phi) when clip_on) is recomputed with
 // the same IEEE operations where it is needed (sort input, clip test), so no epoch is read twice.
@@ -734,21 +733,33 @@ __device__ float eval_pair_thread(const float2* __restrict__ pairs,
                                   const EvalParams& ep, int x0, int y0, float2 v,
                                   const float* __restrict__ dtf, uint32_t* rec) {
   float pv[NT], fv[NT];
-  uint32_t vm = 0u;
+  uint32_t vm = 0u, inb = 0u;
   const size_t plane = (size_t)ep.H * ep.W;
+  // every epoch's load is issued before any is used: an epoch off the image (or beyond T) reads
+  // element 0 of its plane instead and is masked off afterwards, so the gathers overlap instead
+  // of waiting one after another behind the bounds and validity tests
 #pragma unroll
   for (int t = 0; t < NT; ++t) {
-    pv[t] = 0.0f;
-    fv[t] = 0.0f;
+    size_t at = 0;
     if (t < ep.T) {
       const float dt = __ldg(dtf + t);
-      const int ox = track_offset(v.x, dt), oy = track_offset(v.y, dt);
-      float p, f;
-      if (gather_pair(pairs, ep, plane, t, x0 + ox, y0 + oy, p, f)) {
-        vm |= 1u << t;
-        pv[t] = p;
-        fv[t] = f;
-      }
+      const int x = x0 + track_offset(v.x, dt), y = y0 + track_offset(v.y, dt);
+      const bool in = x >= 0 && x < ep.W && y >= 0 && y < ep.H;
+      inb |= (in ? 1u : 0u) << t;
+      at = (size_t)t * plane + (in ? (size_t)y * ep.W + x : 0);
+    }
+    const float2 pf = __ldg(pairs + at);
+    pv[t] = pf.x;
+    fv[t] = pf.y;
+  }
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    const float p = pv[t], f = fv[t];
+    if (((inb >> t) & 1u) && f > 0.0f && isfinite(p) && isfinite(f)) {
+      vm |= 1u << t;
+    } else {
+      pv[t] = 0.0f;
+      fv[t] = 0.0f;
     }
   }
   const int nvalid = __popc(vm);
@@ -764,8 +775,46 @@ __device__ float eval_pair_thread(const float2* __restrict__ pairs,
   uint32_t km = vm;
   if (ep.clip) {
     float loc[NT];
+    // the lightcurve, with its smallest value a0, largest a1 and second largest a2, the sum of
+    // nu2 = psi^2/phi over the valid epochs with psi > 0 and the nu2 of the epoch of a1
+    float a0 = INFINITY, a1 = -INFINITY, a2 = -INFINITY, s_all = 0.0f, s_a1 = 0.0f;
 #pragma unroll
-    for (int t = 0; t < NT; ++t) loc[t] = ((vm >> t) & 1u) ? curve(t) : INFINITY;
+    for (int t = 0; t < NT; ++t) {
+      loc[t] = INFINITY;
+      if ((vm >> t) & 1u) {
+        const float a = curve(t);
+        loc[t] = a;
+        const float nu = pv[t] > 0.0f ? (on_lh ? a * a : pv[t] * a) : 0.0f;
+        s_all += nu;
+        a0 = fminf(a0, a);
+        if (a > a1) {
+          a2 = a1;
+          a1 = a;
+          s_a1 = nu;
+        } else {
+          a2 = fmaxf(a2, a);
+        }
+      }
+    }
+    // Outlier shortcut (exact).  When the interpolation ranks of q_mid and q_hi stay below the
+    // largest value (their upper order statistic has index <= n - 2), the median and q_hi lie
+    // at or below a2 and q_lo at or above a0, so every upper clip bound is at most
+    // a2 + n_sigma C (a2 - a0).  A largest value above that (with a margin for the float32
+    // rounding of the percentiles and bounds) is clipped whatever the quantiles are; the
+    // Cauchy-Schwarz bound over the other valid epochs with psi > 0 then caps LH' of any kept
+    // set, and a pair below lh_min (1 - 1e-3) skips the sort.  This is the common case of a pair
+    // whose pruning bound passed only through one +20 sigma spike.
+    if (ep.nu2_floor > 0.0f && s_all - s_a1 < ep.nu2_floor) {
+      const int2* rk = rank_table(dtf);
+      const float spread = ep.n_sigma * (ep.c_sigma * (a2 - a0));
+      const float ub = a2 + spread + 1e-5f * (fabsf(a2) + fabsf(a0) + spread) + 1e-30f;
+      if (a1 > ub && __ldg(rk + rank_entry(1, nvalid)).x <= nvalid - 3 &&
+          __ldg(rk + rank_entry(2, nvalid)).x <= nvalid - 3) {
+        rec[0] = __float_as_uint(NAN);
+        rec[2] = (uint32_t)nvalid;
+        return NAN;
+      }
+    }
     thread_bitonic_sort<NT>(loc);
     const int2* rk = rank_table(dtf);
     const float x_lo = sorted_percentile<NT>(loc, nvalid, __ldg(rk + rank_entry(0, nvalid)));
@@ -877,7 +926,7 @@ struct SmemLayout {
   static constexpr size_t full = sinfo + S_D * sizeof(int4);       // S_D mbarriers: data landed
   static constexpr size_t empty = full + S_D * sizeof(uint64_t);   // S_D mbarriers: slot released
   static constexpr size_t misc = empty + S_D * sizeof(uint64_t);
-  static constexpr size_t sargs = misc + 64;  // consumers' copy of the tile's stack arguments
+  static constexpr size_t sargs = misc + 128;  // consumers' copy of the tile's stack arguments
   static constexpr size_t total = sargs + (sizeof(SearchArgs) + 15) / 16 * 16;
 };
 static_assert(SmemLayout::total <= 232448, "shared memory budget");
@@ -1000,9 +1049,9 @@ __device__ void producer_loop(const TmapSet& pmaps, const SearchArgs& A0, const 
       maps = B.maps + stack;
       tile -= __ldg(B.tile_base + stack);
       if (stack != cur_stack) {  // the stack's tensor maps were written before the launch
-        if (lane < S_NW * S_NH) {
-          tmap_acquire(&maps->m[lane]);
-          prefetch_tmap(&maps->m[lane]);
+        for (int i = lane; i < S_NW * S_NH; i += 32) {
+          tmap_acquire(&maps->m[i]);
+          prefetch_tmap(&maps->m[i]);
         }
         __syncwarp();
         cur_stack = stack;
@@ -1038,7 +1087,7 @@ __device__ void producer_loop(const TmapSet& pmaps, const SearchArgs& A0, const 
         b.y = __shfl_sync(0xffffffffu, mine.y, kk);
         b.z = __shfl_sync(0xffffffffu, mine.z, kk);
         b.w = __shfl_sync(0xffffffffu, mine.w, kk);
-        const int mode = b.w & 7;
+        const int mode = b.w & S_MODE_MASK;
         const int sz = (!last && mode) ? stage_width(mode) * stage_height(b.z) * 4 : 0;
         int pos = 0;
         for (;;) {
@@ -1239,6 +1288,11 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
   TileRing* tr = reinterpret_cast<TileRing*>(s_qcount + 5);       // 20 bytes
   int* s_stack = reinterpret_cast<int*>(s_qcount + 10);
   long long* s_issued = reinterpret_cast<long long*>(smem + SmemLayout::misc + 48);  // [2]
+  // stage counters: pairs with n_valid >= min_obs, pairs reaching lh_min, and the sums of
+  // n_kept and n_valid over the latter
+  unsigned int* s_stage = reinterpret_cast<unsigned int*>(smem + SmemLayout::misc + 64);     // [2]
+  unsigned long long* s_stage64 =
+      reinterpret_cast<unsigned long long*>(smem + SmemLayout::misc + 72);                   // [2]
   SearchArgs* s_args = reinterpret_cast<SearchArgs*>(smem + SmemLayout::sargs);
   Ctrl* const ctrl = BATCH ? B.ctrl : A0.ctrl;
 
@@ -1253,6 +1307,8 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
     *s_qcount = 0u;
     *s_evals = 0u;
     *s_ins = 0u;
+    s_stage[0] = s_stage[1] = 0u;
+    s_stage64[0] = s_stage64[1] = 0ull;
     *s_abort = 0u;
     *s_tile = -1;
     tr->published = 0u;
@@ -1264,7 +1320,8 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
   if (warp >= S_CWARPS) {
     // ------------------------------- producer warps --------------------------------------
     const int pw = warp - S_CWARPS;
-    if (!BATCH && pw == 0 && lane < S_NW * S_NH) prefetch_tmap(&maps.m[lane]);
+    if (!BATCH && pw == 0)
+      for (int i = lane; i < S_NW * S_NH; i += 32) prefetch_tmap(&maps.m[i]);
     long long issued = -1;
     producer_loop<BATCH>(maps, A0, B, arena + pw * S_RING_BYTES, pw * S_RING_BYTES, slots, sinfo,
                          full, empty, s_abort, tr, &issued, pw, lane);
@@ -1353,14 +1410,29 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
           dst[0] = make_uint4(r[0], r[1], r[2], r[3]);
           dst[1] = make_uint4(r[4], r[5], r[6], 0u);
           q_next[e] = (int16_t)atomicExch(&head[pl], e);
+          atomicAdd(&s_stage[1], 1u);
+          atomicAdd(&s_stage64[0], (unsigned long long)(r[2] >> 16));
+          atomicAdd(&s_stage64[1], (unsigned long long)(r[2] & 0xffffu));
+        };
+        // pairs eligible for the clip (n_valid >= max(min_obs, 1)), counted per warp
+        auto count_valid = [&](bool evaluated, uint32_t nvk) {
+          const uint32_t nv = nvk & 0xffffu;
+          const bool v = evaluated && nv > 0u && (int)nv >= EP.min_obs;
+          const unsigned int n = __popc(__ballot_sync(0xffffffffu, v));
+          if (lane == 0 && n) atomicAdd(&s_stage[0], n);
         };
         auto by_thread = [&](auto nt) {
-          for (int e = tid; e < nq; e += S_CTHREADS) {
-            const int pl = q_pix[e], j = q_traj[e];
+          for (int eb = 0; eb < nq; eb += S_CTHREADS) {
+            const int e = eb + tid;
             uint32_t r[S_REC_WORDS];
-            const float L = eval_pair_thread<decltype(nt)::value>(
-                e_pairs, EP, tx0 + (pl & 31), ty0 + (pl >> 5), __ldg(e_vs + j), e_dt, r);
-            if (L >= lh_min) keep(e, pl, r);
+            r[2] = 0u;
+            if (e < nq) {
+              const int pl = q_pix[e], j = q_traj[e];
+              const float L = eval_pair_thread<decltype(nt)::value>(
+                  e_pairs, EP, tx0 + (pl & 31), ty0 + (pl >> 5), __ldg(e_vs + j), e_dt, r);
+              if (L >= lh_min) keep(e, pl, r);
+            }
+            count_valid(e < nq, r[2]);
           }
         };
         auto by_warp = [&](auto jj) {
@@ -1371,6 +1443,9 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
                 e_pairs, EP, tx0 + (pl & 31), ty0 + (pl >> 5),
                 e_offs + (size_t)q_traj[e] * T, e_dt, r, lane);
             if (lane == 0 && L >= lh_min) keep(e, pl, r);
+            const uint32_t nvk = __shfl_sync(0xffffffffu, r[2], 0);
+            if (lane == 0 && (nvk & 0xffffu) > 0u && (int)(nvk & 0xffffu) >= EP.min_obs)
+              atomicAdd(&s_stage[0], 1u);
           }
         };
         if (BATCH) {
@@ -1438,18 +1513,11 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
           const bool ok = consumer_wait(&full[slot], (it / S_D) & 1u, s_abort);
           if (ok) {
             const PlanRec* rec = &slots[slot];
-            const int mode = rec->box.w & 7;
+            const int mode = rec->box.w & S_MODE_MASK;
             const unsigned char* st = arena + sinfo[slot].x;
             if (mode != 0) {
-              const bool uni = (rec->box.w & 8) != 0;
-              if (POOL)
-                accumulate_stage<POOL, 0>(acc, st, stage_width(mode), uni, rec, warp, lane);
-              else if (mode == 1)
-                accumulate_stage<POOL, stage_width(1)>(acc, st, 0, uni, rec, warp, lane);
-              else if (mode == 2)
-                accumulate_stage<POOL, stage_width(2)>(acc, st, 0, uni, rec, warp, lane);
-              else
-                accumulate_stage<POOL, stage_width(3)>(acc, st, 0, uni, rec, warp, lane);
+              const bool uni = (rec->box.w & S_UNIFORM_BIT) != 0;
+              accumulate_stage<POOL, 0>(acc, st, stage_width(mode), uni, rec, warp, lane);
             } else {
               // direct loads from the block planes (word row = first image row + 3)
               const uint32_t* bp = A.bound + (size_t)t * (A.ep.H + 3) * A.Wp;
@@ -1572,6 +1640,10 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
   if (tid == 0) {
     atomicAdd(&ctrl->evals, (unsigned long long)*s_evals);
     atomicAdd(&ctrl->inserts, (unsigned long long)*s_ins);
+    atomicAdd(&ctrl->stage_valid, (unsigned long long)s_stage[0]);
+    atomicAdd(&ctrl->stage_pass, (unsigned long long)s_stage[1]);
+    atomicAdd(&ctrl->stage_kept, s_stage64[0]);
+    atomicAdd(&ctrl->stage_nvalid, s_stage64[1]);
   }
   if (warp >= S_CWARPS && lane == 0 && *(volatile unsigned int*)s_abort != 0u) {
     // a wait gave up: wait (bounded) for this producer's last copies
@@ -1963,11 +2035,8 @@ __global__ void batch_reset_kernel(Ctrl* ctrl, unsigned int* done_tiles,
     done_ns[i] = 0ull;
   }
   if (i == 0) {
-    ctrl->err = 0u;
-    ctrl->tile_counter = 0u;
+    *ctrl = Ctrl{};
     ctrl->te = te;
-    ctrl->evals = 0ull;
-    ctrl->inserts = 0ull;
     *start_ns = globaltimer_ns();
   }
 }
@@ -1976,15 +2045,23 @@ __global__ void stack_done_kernel(unsigned long long* done_ns) { *done_ns = glob
 
 // Totals of the concurrent mode: each stack's search counted into its own control block.
 __global__ void batch_sum_kernel(Ctrl* const* __restrict__ ctrls, int n, Ctrl* total) {
-  unsigned long long ev = 0, ins = 0;
+  unsigned long long ev = 0, ins = 0, sv = 0, sp = 0, sk = 0, sn = 0;
   unsigned int err = 0;
   for (int k = 0; k < n; ++k) {
     ev += ctrls[k]->evals;
     ins += ctrls[k]->inserts;
+    sv += ctrls[k]->stage_valid;
+    sp += ctrls[k]->stage_pass;
+    sk += ctrls[k]->stage_kept;
+    sn += ctrls[k]->stage_nvalid;
     err |= ctrls[k]->err;
   }
   total->evals = ev;
   total->inserts = ins;
+  total->stage_valid = sv;
+  total->stage_pass = sp;
+  total->stage_kept = sk;
+  total->stage_nvalid = sn;
   total->err = err;
 }
 
@@ -2416,6 +2493,21 @@ extern "C" int kb_search_stats(const void* workspace, unsigned long long* stats,
   return KB_OK;
 }
 
+extern "C" int kb_search_stage_counts(const void* workspace, unsigned long long* out,
+                                      void* stream) {
+  using namespace kb;
+  if (!workspace || !out) return fail(KB_ERR_INVALID_ARG, "kb_search_stage_counts: null pointer");
+  Ctrl c{};
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  KB_CUDA_TRY(cudaMemcpyAsync(&c, workspace, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+  KB_CUDA_TRY(cudaStreamSynchronize(st));
+  out[0] = c.stage_valid;
+  out[1] = c.stage_pass;
+  out[2] = c.stage_kept;
+  out[3] = c.stage_nvalid;
+  return KB_OK;
+}
+
 // ---------------------------------------------------------------------------------------------
 // kb_search_no_alloc: kb_search with scratch memory built into the library
 // ---------------------------------------------------------------------------------------------
@@ -2446,6 +2538,7 @@ extern "C" int kb_search_no_alloc(const float* psi, const float* phi, const doub
                 "kb_search_no_alloc: this search needs %zu bytes of scratch, more than the %u "
                 "built into the library; use kb_search with a workspace",
                 need, (unsigned)KB_STATIC_SCRATCH_BYTES);
+  KB_FAULT_POINT("kb_search_no_alloc");
   int dev = 0;
   KB_CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices)
@@ -2467,6 +2560,22 @@ extern "C" int kb_search_no_alloc(const float* psi, const float* phi, const doub
   return kb_search(psi, phi, times, T, H, W, vx, vy, n_traj, p, out_lh, out_flux, out_idx,
                    out_nvalid, out_nkept, out_mask, scratch, (size_t)KB_STATIC_SCRATCH_BYTES,
                    stream);
+}
+
+extern "C" int kb_search_no_alloc_stats(unsigned long long* stats, void* stream) {
+  using namespace kb;
+  if (!stats) return fail(KB_ERR_INVALID_ARG, "kb_search_no_alloc_stats: null pointer");
+  int dev = 0;
+  KB_CUDA_TRY(cudaGetDevice(&dev));
+  void* scratch = nullptr;
+  if (dev >= 0 && dev < kMaxDevices) {
+    std::lock_guard<std::mutex> lock(g_no_alloc_mu);
+    scratch = g_no_alloc_ptr[dev];
+  }
+  if (!scratch)
+    return fail(KB_ERR_INVALID_ARG,
+                "kb_search_no_alloc_stats: no kb_search_no_alloc call on device %d yet", dev);
+  return kb_search_stats(scratch, stats, stream);
 }
 
 // ---------------------------------------------------------------------------------------------

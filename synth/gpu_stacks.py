@@ -10,9 +10,9 @@ import math
 
 import numpy as np
 
-from .stacks import _split, _times, gaussian_psf, velocity_grid
+from .stacks import CONFIGS, _snr, _split, _times, gaussian_psf, velocity_grid
 
-__all__ = ["make_stack_torch", "BATCH64"]
+__all__ = ["make_stack_torch", "make_config_stack_torch", "BATCH64"]
 
 # 64 stacks: sizes uniform in {512x512, 1024x2048, 2046x4094}, epochs uniform in 10..40, velocity
 # grids of 4096..32768 trajectories (speeds x angles over 90-500 px/day and +-0.3 rad); movers at
@@ -92,3 +92,77 @@ def make_stack_torch(H, W, T, n_speed, n_angle, n_movers, seed, device, v=(90.0,
     return dict(img=img, var=var, mask=mask.to(torch.uint8), psf=torch.from_numpy(psf).to(device),
                 times=times, vx=torch.from_numpy(vx).to(device),
                 vy=torch.from_numpy(vy).to(device), movers=movers)
+
+
+def make_config_stack_torch(name, device, seed=None, H=None, W=None, n_movers=None):
+    """A named workload's stack (CONFIGS[name]: epochs and nights, image size, per-epoch variance
+    and PSF width, masked fraction, movers with their SNR distribution and spikes, velocity grid)
+    drawn on the device with torch, for sizes too large to draw with numpy in reasonable time
+    (the full-scale 4096 x 4096 x 100 stack).  Movers start at real positions with velocities
+    drawn uniformly in speed and angle over the grid's range.  The random draws differ from
+    make_stack's.  H, W, n_movers override the config (test sizes).  Returns dict(img, var, mask,
+    psf (torch, device), times, vx, vy (torch), movers, seed)."""
+    import torch
+    c = dict(CONFIGS[name])
+    for key, v in (("H", H), ("W", W), ("n_movers", n_movers)):
+        if v is not None:
+            c[key] = v
+    seed = c["seed"] if seed is None else seed
+    rng = np.random.default_rng(seed)
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    T, H, W, k = c["T"], c["H"], c["W"], c["psf_k"]
+    times = _times(c["times"], T, rng)
+    sig = rng.uniform(c["psf_sigma"][0], c["psf_sigma"][1], T)
+    psf = np.stack([gaussian_psf(s_, k) for s_ in sig]).astype(np.float32)
+    var_t = rng.uniform(c["var"][0], c["var"][1], T).astype(np.float32)
+    sd = torch.from_numpy(np.sqrt(var_t)).to(device)
+    img = torch.randn((T, H, W), generator=g, device=device, dtype=torch.float32)
+    img *= sd[:, None, None]
+    var = torch.from_numpy(var_t).to(device)[:, None, None].expand(T, H, W).contiguous()
+    vx, vy = velocity_grid(*c["grid"])
+    v0, v1, ns, a0, a1, na = c["grid"]
+    nm = c["n_movers"]
+    x0 = rng.uniform(0, W, nm)
+    y0 = rng.uniform(0, H, nm)
+    sp = rng.uniform(v0, v1, nm)
+    an = rng.uniform(a0, a1, nm)
+    mvx, mvy = sp * np.cos(an), sp * np.sin(an)
+    snr = _snr(c["snr"], nm, rng)
+    sum_p2 = (psf.astype(np.float64) ** 2).sum(axis=(1, 2))
+    flux = snr[:, None] * np.sqrt(var_t.astype(np.float64))[None, :] / np.sqrt(sum_p2)[None, :]
+    spike = np.zeros((nm, T), bool)
+    if c["spike_frac"] > 0:
+        n_sp = max(1, int(round(c["spike_frac"] * T)))
+        for i in range(nm):
+            spike[i, rng.choice(T, n_sp, replace=False)] = True
+        flux = np.where(spike, (20.0 * np.sqrt(var_t.astype(np.float64)) /
+                                np.sqrt(sum_p2))[None, :], flux)
+    r = k // 2
+    u = np.arange(-r, r + 1)
+    idx, val = [], []
+    for t in range(T):
+        dt = times[t] - times[0]
+        px, py = x0 + mvx * dt, y0 + mvy * dt
+        ix, iy = np.floor(px + 0.5).astype(np.int64), np.floor(py + 0.5).astype(np.int64)
+        fx, fy = px - ix, py - iy
+        norm = np.exp(-(u[:, None] ** 2 + u[None, :] ** 2) / (2 * sig[t] ** 2)).sum()
+        # [n][k][k] stamps of every mover at this epoch, centred on (fx, fy)
+        sx = np.exp(-((u[None, :] - fx[:, None]) ** 2) / (2 * sig[t] ** 2))
+        sy = np.exp(-((u[None, :] - fy[:, None]) ** 2) / (2 * sig[t] ** 2))
+        st = flux[:, t][:, None, None] * sy[:, :, None] * sx[:, None, :] / norm
+        yy = iy[:, None, None] + u[None, :, None]
+        xx = ix[:, None, None] + u[None, None, :]
+        yy, xx = np.broadcast_to(yy, st.shape), np.broadcast_to(xx, st.shape)
+        ok = (yy >= 0) & (yy < H) & (xx >= 0) & (xx < W)
+        idx.append((t * H + yy[ok]) * W + xx[ok])
+        val.append(st[ok])
+    ii = torch.from_numpy(np.concatenate(idx).astype(np.int64)).to(device)
+    vv = torch.from_numpy(np.concatenate(val).astype(np.float32)).to(device)
+    img.view(-1).index_add_(0, ii, vv)
+    mask = torch.rand((T, H, W), generator=g, device=device) < c["mask_frac"]
+    var[mask] = float("inf")
+    movers = dict(x0=x0, y0=y0, vx=mvx, vy=mvy, snr=snr, spike=spike)
+    return dict(img=img, var=var, mask=mask.to(torch.uint8), psf=torch.from_numpy(psf).to(device),
+                times=times, vx=torch.from_numpy(vx).to(device),
+                vy=torch.from_numpy(vy).to(device), movers=movers, seed=seed)

@@ -110,6 +110,13 @@ def test_other_entry_points_validate(L):
     from paper_2109_03296_b300 import _lib as K
     times = np.linspace(0, 1, 5)
     tp = times.ctypes.data_as(C.c_void_p)
+    arr = (C.c_ulonglong * 4)()
+    assert L.kb_smem_probe(0, 10, FAKE, None) == K.KB_ERR_INVALID_ARG
+    assert L.kb_smem_probe(4, 0, FAKE, None) == K.KB_ERR_INVALID_ARG
+    assert L.kb_smem_probe(4, 10, None, None) == K.KB_ERR_INVALID_ARG
+    assert L.kb_search_stage_counts(None, arr, None) == K.KB_ERR_INVALID_ARG
+    assert L.kb_search_stage_counts(FAKE, None, None) == K.KB_ERR_INVALID_ARG
+    assert L.kb_search_no_alloc_stats(None, None) == K.KB_ERR_INVALID_ARG
     assert L.kb_make_psi_phi(FAKE, FAKE, None, FAKE, 5, 10, 10, 4, FAKE, FAKE, None) == \
         K.KB_ERR_INVALID_ARG
     assert L.kb_make_psi_phi(FAKE, FAKE, None, FAKE, 5, 10, 10, 33, FAKE, FAKE, None) == \
@@ -398,7 +405,11 @@ def test_host_fault_injection(L, monkeypatch):
     cluster_ws = nb.value
     rp = K.RefineParamsC()
     L.kb_refine_params_default(C.byref(rp))
+    sp_ = _params(L, 10, 10)
     calls = {
+        "kb_search_no_alloc": lambda: L.kb_search_no_alloc(FAKE, FAKE, tp, T, 10, 10, FAKE, FAKE,
+                                                           4, C.byref(sp_), FAKE, FAKE, FAKE,
+                                                           FAKE, FAKE, FAKE, None),
         "kb_make_psi_phi": lambda: L.kb_make_psi_phi(FAKE, FAKE, None, FAKE, T, 10, 10, 3,
                                                      C.c_void_p(0x20000), C.c_void_p(0x30000),
                                                      None),

@@ -167,3 +167,35 @@ def test_measured_peaks_and_fallback(tmp_path, monkeypatch):
                                                               "sm_max_mhz": 2032.0}))
     peaks, src = bench.measured_peaks()
     assert src == "measured" and peaks["hbm_gbs"] == 6505.9
+
+
+def test_bench_launches_its_own_ranks_dry_run():
+    """`python bench.py --gpus 2` outside torchrun starts two ranks itself (torch.distributed.run
+    on this node); in --dry-run mode they join a gloo group on CPU, take the slowest rank's time
+    and rank 0 alone prints one line for the whole job, each rank with its own stack seed."""
+    import json
+    import subprocess
+    env = dict(os.environ)
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK", "MASTER_ADDR", "MASTER_PORT"):
+        env.pop(k, None)
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--gpus", "2",
+                          "--steps", "2", "--warmup", "3", "--dry-run"], capture_output=True,
+                         text=True, timeout=300, env=env, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1, out.stdout
+    d = json.loads(lines[0])
+    assert d["dry_run"] and d["n_gpus"] == 2 and d["scaling"] == "weak" and d["steps"] == 2
+    seeds = d["config"]["seeds"]
+    assert len(seeds) == 2 and seeds[0] != seeds[1]
+    te = 26 * 2046 * 4094 * 32768
+    assert abs(d["value"] - 2 * te * 2 / (d["ms_per_step"] * 2 / 1e3)) <= 1e-6 * d["value"]
+
+
+def test_bench_rejects_a_rank_count_other_than_gpus():
+    import subprocess
+    env = dict(os.environ, WORLD_SIZE="2", RANK="0", LOCAL_RANK="0")
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--gpus", "4",
+                          "--dry-run"], capture_output=True, text=True, timeout=120, env=env,
+                         cwd=ROOT)
+    assert out.returncode != 0 and "ranks were started" in out.stderr

@@ -209,6 +209,31 @@ def test_search_bound_rows_equivalent(cuda_device, seed, T, H, W, n_traj, K, lh,
     assert int((g1["idx"] >= 0).sum()) > 0
 
 
+@pytest.mark.parametrize("lh_min,K,n_traj", [(-1e9, 32, 30), (1.5, 32, 30), (1.5, 4, 40)])
+def test_search_stage_counts(cuda_device, lh_min, K, n_traj):
+    """kb_search_stage_counts against the oracle's counts over every pair (Fig. 3's stages).
+    With fewer trajectories than K no list can fill, so the admission threshold stays at lh_min:
+    with lh_min <= 0 every pair is evaluated and all four counts are exhaustive; with lh_min > 0
+    every pair that reaches lh_min is evaluated, so the pass count and the kept / valid sums are
+    exhaustive (the n_valid count covers the evaluated pairs only).  Once lists fill (K = 4) the
+    threshold rises to the K-th LH', and the counts cover only the pairs evaluated."""
+    psi, phi, times, vx, vy = _likelihood_case(41, 13, 70, 60, n_traj)
+    sp = kb.SearchParams(k=K, lh_min=lh_min, min_obs=3)
+    res = kb.search(_cuda(psi), _cuda(phi), times, _cuda(vx), _cuda(vy), sp)
+    torch.cuda.synchronize()
+    stats = kb.search_stats(res["workspace"])
+    assert stats[3] == 0
+    sc = kb.search_stage_counts(res["workspace"])
+    o = oracle.stage_counts(psi, phi, times, vx, vy, _oracle_params(sp))
+    assert o[1] > 0 and o[2] < o[3]
+    if K < n_traj:
+        assert all(a <= b for a, b in zip(sc, o)) and 0 < sc[1] <= o[1]
+    elif lh_min <= 0:
+        assert sc == o and stats[1] == 70 * 60 * n_traj
+    else:
+        assert sc[1:] == o[1:] and sc[0] <= o[0] and stats[1] < 70 * 60 * n_traj
+
+
 @pytest.mark.parametrize("bound_rows", [1, 2])
 def test_search_fast_movers_fallback(cuda_device, bound_rows):
     """Velocities spread so widely that the staged rectangle overflows: the direct-load path,
@@ -379,6 +404,60 @@ def test_search_parity_full_config_grid(cuda_device):
                                       (xa, xb, ya, yb)))
         filled += int((o["idx"] >= 0).sum())
     assert filled > 0
+
+
+def test_search_parity_full_config_stated_size(cuda_device):
+    """The full-scale configuration at its stated size: T = 100 over five nights, 4096 x 4096,
+    the paper's 512 x 256 grid of 131072 trajectories (Section 4.1), drawn on the device as the
+    bench draws it.  The kernel forms psi/phi; over the region each checked window's tracks can
+    reach, those planes are replaced by the oracle's psi/phi of the same images (rounded to
+    float32), so both sides search identical values there.  The whole image is searched in the
+    bench's launch configuration and the oracle checks a window at the brightest mover's start
+    and one at a corner."""
+    from synth.gpu_stacks import make_config_stack_torch
+    name = "full"
+    c = CONFIGS[name]
+    g = make_config_stack_torch(name, torch.device("cuda"))
+    psi, phi = kb.make_psi_phi(g["img"], g["var"], g["mask"], g["psf"])
+    T, H, W = psi.shape
+    assert (T, H, W) == (100, 4096, 4096) and g["vx"].numel() == 131072
+    img, var, mask = g["img"].cpu().numpy(), g["var"].cpu().numpy(), g["mask"].cpu().numpy()
+    psf = g["psf"].cpu().numpy()
+    vx, vy = g["vx"].cpu().numpy(), g["vy"].cpu().numpy()
+    times = g["times"]
+    mv = g["movers"]
+    del g
+    sp = kb.SearchParams(k=c["K"], lh_min=c["lh_min"], min_obs=c["min_obs"])
+    p = _oracle_params(sp)
+    span = times[-1] - times[0]
+    xe, ye = mv["x0"] + mv["vx"] * span, mv["y0"] + mv["vy"] * span
+    inside = (mv["x0"] > 4) & (mv["x0"] < W - 4) & (mv["y0"] > 4) & (mv["y0"] < H - 4) & \
+        (xe > 4) & (xe < W - 4) & (ye > 4) & (ye < H - 4)     # on the image at every epoch
+    i = int(np.argmax(np.where(inside, mv["snr"], -1.0)))
+    x0, y0 = int(mv["x0"][i]), int(mv["y0"][i])
+    wins = [(x0 - 1, x0 + 2, y0 - 1, y0 + 2), (0, 3, H - 3, H)]
+    crops = []
+    for w in wins:
+        cp, cf, wc, (xa, ya) = oracle.window_inputs(img, var, mask, psf, times, vx, vy, w)
+        cp32, cf32 = cp.astype(np.float32), cf.astype(np.float32)
+        hh, ww = cp.shape[1], cp.shape[2]
+        psi[:, ya:ya + hh, xa:xa + ww] = torch.from_numpy(cp32).cuda()
+        phi[:, ya:ya + hh, xa:xa + ww] = torch.from_numpy(cf32).cuda()
+        crops.append((cp32.astype(np.float64), cf32.astype(np.float64), wc, w))
+    del img, var, mask
+    res = kb.search(psi, phi, times, torch.from_numpy(vx).cuda(), torch.from_numpy(vy).cuda(), sp)
+    torch.cuda.synchronize()
+    assert kb.search_stats(res["workspace"])[3] == 0
+    g_all = gpu_result_numpy(res)
+    del res, psi, phi
+    torch.cuda.empty_cache()
+    filled = 0
+    for cp, cf, wc, (xa, xb, ya, yb) in crops:
+        o = oracle.search(cp, cf, times, vx, vy, p, window=wc)
+        g_w = {k: v[ya:yb, xa:xb] for k, v in g_all.items()}
+        compare_search(g_w, o, sp.lh_min, ctx=search_ctx(cp, cf, times, vx, vy, p, wc))
+        filled += int((o["idx"] >= 0).sum())
+    assert filled > 0     # the brightest mover is found at its start
 
 
 # ------------------------------------------------------------------------------------------------

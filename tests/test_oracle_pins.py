@@ -1024,3 +1024,32 @@ def test_window_inputs_equal_whole_image_search(name, H, W, window):
     for k in whole:
         assert np.array_equal(whole[k], crop[k]), k
     assert (whole["idx"] >= 0).sum() > 0
+
+
+def test_stage_counts_against_the_listing_and_a_numpy_count():
+    """oracle.stage_counts: with lh_min far below every LH' and K = n_traj, the search lists every
+    pair that passes, so the pass count and the n_kept / n_valid sums equal the listing's; the
+    count of pairs with n_valid >= min_obs equals a numpy count of in-image epochs with phi > 0."""
+    psi, phi, times, vx, vy = _tiny_case(9)
+    T, H, W = psi.shape
+    n = len(vx)
+    for lh_min, min_obs in ((-1e9, 3), (0.8, 4)):
+        p = dict(k=n, lh_min=lh_min, min_obs=min_obs)
+        sc = oracle.stage_counts(psi, phi, times, vx, vy, p)
+        r = oracle.search(psi, phi, times, vx, vy, p)
+        f = r["idx"] >= 0
+        assert sc[1] == int(f.sum()) > 0
+        assert sc[2] == int(r["nkept"][f].sum()) and sc[3] == int(r["nvalid"][f].sum())
+        assert sc[2] < sc[3]                    # the clip removes some epochs
+        ox, oy = oracle.track_offsets(times, vx, vy)
+        valid = 0
+        for y in range(H):
+            for x in range(W):
+                xs, ys = x + ox, y + oy                               # [n][T]
+                inside = (xs >= 0) & (xs < W) & (ys >= 0) & (ys < H)
+                f_at = np.zeros(xs.shape)
+                tt = np.broadcast_to(np.arange(T), xs.shape)
+                f_at[inside] = phi[tt[inside], ys[inside], xs[inside]]
+                nv = (inside & (f_at > 0)).sum(axis=1)
+                valid += int(((nv >= min_obs) & (nv > 0)).sum())
+        assert sc[0] == valid

@@ -125,3 +125,31 @@ def test_batch64_specs_and_torch_stacks():
     assert np.all((mv["snr"] >= 1.5) & (mv["snr"] <= 10.0))
     again = make_stack_torch(96, 128, 12, 16, 8, 6, 1234, "cpu")
     assert torch.equal(again["img"], img) and torch.equal(again["mask"], s["mask"])
+
+
+def test_config_stack_torch_follows_the_full_recipe():
+    """The device generator of the full-scale workload (drawn here on the CPU at a reduced image
+    size): five nights of 20 epochs at a 20-minute cadence, per-epoch variance in [0.5, 2] with 1%
+    of pixels masked (var = inf), PSF widths in [1, 2.5] on 15 x 15 normalised kernels, movers at
+    SNR 1-8, the paper's 512 x 256 grid; seeded."""
+    import torch
+    from synth.gpu_stacks import make_config_stack_torch
+    d = make_config_stack_torch("full", "cpu", H=256, W=320, n_movers=40)
+    T, H, W = d["img"].shape
+    assert (T, H, W) == (100, 256, 320)
+    t = d["times"]
+    gaps = np.diff(t)
+    assert t[0] == 0.0 and (gaps > 0).all() and (gaps > 0.5).sum() == 4
+    assert np.allclose(gaps[gaps < 0.5], 20.0 / 1440.0)
+    m = d["mask"].bool()
+    assert abs(m.float().mean().item() - 0.01) < 0.002
+    assert torch.isinf(d["var"][m]).all()
+    v = d["var"][~m]
+    assert v.min().item() >= 0.5 and v.max().item() <= 2.0
+    psf = d["psf"].numpy()
+    assert psf.shape == (100, 15, 15) and np.allclose(psf.sum(axis=(1, 2)), 1.0, atol=1e-5)
+    assert len(d["vx"]) == 512 * 256
+    snr = d["movers"]["snr"]
+    assert snr.min() >= 1.0 and snr.max() <= 8.0 and not d["movers"]["spike"].any()
+    d2 = make_config_stack_torch("full", "cpu", H=256, W=320, n_movers=40)
+    assert torch.equal(d["img"], d2["img"]) and torch.equal(d["mask"], d2["mask"])

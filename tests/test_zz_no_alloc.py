@@ -59,6 +59,9 @@ def test_no_alloc_matches_workspace_search_twice(cuda_device):
         got = kb.search_no_alloc(psi, phi, times, vx, vy, sp)
         torch.cuda.synchronize()
         _assert_same(got, ref)
+        # the built-in scratch's counters: no device-side wait gave up, every pair was covered
+        st = kb.search_no_alloc_stats()
+        assert st[3] == 0 and st[0] == H * W * n * T == kb.search_stats(ref["workspace"])[0]
         filled += int((got["idx"] >= 0).sum())
     assert filled > 100
 
