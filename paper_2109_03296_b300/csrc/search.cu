@@ -63,14 +63,19 @@ namespace kb {
 // ---------------------------------------------------------------------------------------------
 // Compile-time configuration of the search kernel
 // ---------------------------------------------------------------------------------------------
-constexpr int S_TX = 32;                 // tile width (lane = x)
+constexpr int S_TX = 32;                 // columns of one warp (lane = x)
 constexpr int S_ROWS = 4;                // rows per consumer thread (two row pairs)
 constexpr int S_CWARPS = 14;             // consumer warps
 constexpr int S_PWARPS = 2;              // producer warps: iteration `it` belongs to it % S_PWARPS
 constexpr int S_CTHREADS = S_CWARPS * 32;
 constexpr int S_THREADS = (S_CWARPS + S_PWARPS) * 32;
 constexpr int S_TY = S_CWARPS * S_ROWS;  // 56
-constexpr int S_NPIX = S_TX * S_TY;      // 1792 start pixels per tile
+// Two-row-block kernels give each thread two columns (x and x + 32): tiles 64 wide, so a staged
+// box serves twice the start pixels for the same halo and one offset load serves two data loads.
+// Single-row kernels (which keep twice the sums per column) stay 32 wide.
+__host__ __device__ constexpr int tile_cols(bool pool) { return pool ? 2 : 1; }
+__host__ __device__ constexpr int tile_w(bool pool) { return S_TX * tile_cols(pool); }
+constexpr int S_NPIX = 2 * S_TX * S_TY;  // start pixels of the widest tile (3584)
 constexpr int S_C = 32;                  // trajectories per chunk
 constexpr int S_D = 8;                   // pipeline slots (iterations in flight), S_D % S_PWARPS == 0
 constexpr int S_ARENA_BYTES = 168 * 1024;  // rings of staged rectangles, one per producer
@@ -349,7 +354,7 @@ __global__ void plan_offsets_kernel(const float* __restrict__ vx, const float* _
 // rectangle; mode 0 = no box within S_REGION_MAX (direct loads); S_UNIFORM_BIT of the last field
 // set when all of the chunk's offsets are equal in this epoch.
 __global__ void plan_boxes_kernel(const int2* __restrict__ offs, int nchunk, int T, int x_lo,
-                                  PlanRec* plan) {
+                                  int tx, PlanRec* plan) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nchunk * T) return;
   int c = i / T, t = i - c * T;
@@ -361,7 +366,7 @@ __global__ void plan_boxes_kernel(const int2* __restrict__ offs, int nchunk, int
   }
   // offsets are clamped to +-2^24, so these spans cannot overflow
   const int xshift = ((x_lo + dxmin) % 4 + 4) % 4;
-  const int rw = S_TX + (dxmax - dxmin) + xshift;
+  const int rw = tx + (dxmax - dxmin) + xshift;
   const int rh = S_TY + (dymax - dymin);
   // the smallest width and height classes that hold the rectangle
   const int m = 1 + max(0, (rw - stage_width(1) + 7) / 8);
@@ -452,16 +457,16 @@ __global__ void pair_planes_kernel(const float* __restrict__ psi, const float* _
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) tile_score_kernel(
     const uint32_t* __restrict__ bound, int T, int H, int W, int Wp, const float4* vbox,
-    SearchConsts cs, int x_lo, int y_lo, int x_hi, int y_hi, int ntx, int ntiles, float tau,
-    int span, unsigned long long* __restrict__ keys) {
+    SearchConsts cs, int x_lo, int y_lo, int x_hi, int y_hi, int ntx, int tx, int ntiles,
+    float tau, int span, unsigned long long* __restrict__ keys) {
   const int tile = blockIdx.x;
   if (tile >= ntiles) return;
   __shared__ unsigned int s_count;
   if (threadIdx.x == 0) s_count = 0u;
   __syncthreads();
   const float4 b = *vbox;  // vx min, vx max, vy min, vy max
-  const int tx0 = x_lo + (tile % ntx) * S_TX, ty0 = y_lo + (tile / ntx) * S_TY;
-  const int tx1 = min(tx0 + S_TX, x_hi), ty1 = min(ty0 + S_TY, y_hi);
+  const int tx0 = x_lo + (tile % ntx) * tx, ty0 = y_lo + (tile / ntx) * S_TY;
+  const int tx1 = min(tx0 + tx, x_hi), ty1 = min(ty0 + S_TY, y_hi);
   unsigned int cnt = 0u;
   for (int t = 0; t < T; ++t) {
     const int oxa = track_offset(b.x, cs.dt[t]), oxb = track_offset(b.y, cs.dt[t]);
@@ -879,6 +884,7 @@ struct SearchArgs {
   EvalParams ep;
   int n_traj, nchunk, Wp;
   int x_lo, x_hi, y_lo, y_hi, ntx, nty, ntiles;
+  int tx;  // tile width in pixels: tile_w(pool)
 };
 
 struct TmapSet {
@@ -1061,7 +1067,7 @@ __device__ void producer_loop(const TmapSet& pmaps, const SearchArgs& A0, const 
     const int T = last ? 1 : Sp->ep.T;
     if (!last && Sp->order) tile = __ldg(Sp->order + tile);
     const int n_it = last ? 1 : Sp->nchunk * T;
-    const int tx0 = last ? 0 : Sp->x_lo + (tile % Sp->ntx) * S_TX;
+    const int tx0 = last ? 0 : Sp->x_lo + (tile % Sp->ntx) * Sp->tx;
     const int ty0 = last ? 0 : Sp->y_lo + (tile / Sp->ntx) * S_TY;
     // this producer's iterations of the tile: q = first_q, first_q + S_PWARPS, ...
     const int first_q = (int)(((pw - it_base) % S_PWARPS + S_PWARPS) % S_PWARPS);
@@ -1182,30 +1188,26 @@ __device__ __forceinline__ int4 lds_v4(uint32_t addr) {
 }
 
 // Sums one staged (chunk, epoch), a rectangle of `pitch`-word rows, into the fp16 accumulators.
-// POOL: per trajectory one address add, one shared load and one fp16x2 add (the thread's two
-// blocks are the halves of one word; acc[0]).  Otherwise two loads, two rows apart, and two adds
-// (rows 0-1 into acc[0], rows 2-3 into acc[1]).  One code path for every box width (the pitch
-// only moves the row bases; single rows take the pitch as a template constant PITCH, so that the
-// second load is at an immediate offset and costs no address add).  uniform: all trajectories
-// share rel[0] (the same values in the same order as the general path).
-template <bool POOL, int PITCH>
-__device__ __forceinline__ void accumulate_stage(__half2 (&acc)[POOL ? 1 : 2][S_C],
-                                                 const unsigned char* st, int pitch_rt,
-                                                 bool uniform, const PlanRec* slot, int warp,
-                                                 int lane) {
-  const int pitch = PITCH > 0 ? PITCH : pitch_rt;
+// POOL: the thread's two columns x and x + 32; per trajectory one address add, two shared loads
+// (the second at an immediate offset, 32 words on) and two fp16x2 adds; each word holds the
+// thread's two blocks of a column (acc[c]).  Otherwise one column, its two row pairs two rows
+// apart (acc[0] rows 0-1, acc[1] rows 2-3).  One code path for every box width (the pitch only
+// moves the row bases).  uniform: all trajectories share rel[0] (the same values in the same
+// order as the general path).
+template <bool POOL>
+__device__ __forceinline__ void accumulate_stage(__half2 (&acc)[2][S_C], const unsigned char* st,
+                                                 int pitch, bool uniform, const PlanRec* slot,
+                                                 int warp, int lane) {
   const uint32_t base = smem_u32(st) + (uint32_t)(warp * S_ROWS * pitch + lane) * 4u;
   const uint32_t base1 = base + 8u * (uint32_t)pitch;  // two rows further (single rows only)
   if (uniform) {
-    const uint32_t w0 = lds_u32(base + (uint32_t)slot->rel[0]);
-    uint32_t w1 = 0u;
-    if (!POOL) w1 = lds_u32(base1 + (uint32_t)slot->rel[0]);
+    const uint32_t r0 = (uint32_t)slot->rel[0];
+    const uint32_t w0 = lds_u32(base + r0);
+    const uint32_t w1 = POOL ? lds_u32_off<4 * S_TX>(base + r0) : lds_u32(base1 + r0);
 #pragma unroll
     for (int v = 0; v < S_C; ++v) {
       acc[0][v] = __hadd2(acc[0][v], *reinterpret_cast<const __half2*>(&w0));
-      if (!POOL)
-        acc[POOL ? 0 : 1][v] =
-            __hadd2(acc[POOL ? 0 : 1][v], *reinterpret_cast<const __half2*>(&w1));
+      acc[1][v] = __hadd2(acc[1][v], *reinterpret_cast<const __half2*>(&w1));
     }
     return;
   }
@@ -1218,13 +1220,9 @@ __device__ __forceinline__ void accumulate_stage(__half2 (&acc)[POOL ? 1 : 2][S_
     for (int u = 0; u < 4; ++u) {
       const uint32_t q = base + (uint32_t)rr[u];
       const uint32_t w0 = lds_u32(q);
+      const uint32_t w1 = POOL ? lds_u32_off<4 * S_TX>(q) : lds_u32(base1 + (uint32_t)rr[u]);
       acc[0][vq * 4 + u] = __hadd2(acc[0][vq * 4 + u], *reinterpret_cast<const __half2*>(&w0));
-      if (!POOL) {
-        const uint32_t w1 = PITCH > 0 ? lds_u32_off<8 * (PITCH > 0 ? PITCH : 1)>(q)
-                                      : lds_u32(base1 + (uint32_t)rr[u]);
-        acc[POOL ? 0 : 1][vq * 4 + u] =
-            __hadd2(acc[POOL ? 0 : 1][vq * 4 + u], *reinterpret_cast<const __half2*>(&w1));
-      }
+      acc[1][vq * 4 + u] = __hadd2(acc[1][vq * 4 + u], *reinterpret_cast<const __half2*>(&w1));
     }
   }
 }
@@ -1297,6 +1295,9 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
   Ctrl* const ctrl = BATCH ? B.ctrl : A0.ctrl;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // tile geometry of this kernel's bound kind: NCOL columns per thread, TXW = 2^TXS pixels wide
+  constexpr int NCOL = tile_cols(POOL), TXW = tile_w(POOL), TXS = POOL ? 6 : 5;
+  static_assert((1 << TXS) == TXW && TXW * S_TY <= S_NPIX, "tile geometry");
 
   for (int i = tid; i < S_NPIX; i += S_THREADS) head[i] = -1;
   if (tid == 0) {
@@ -1360,31 +1361,34 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
       const int T = A.ep.T, K = A.ep.K, mw = A.ep.mw;
       const float lh_min = A.ep.lh_min;
       const size_t wx = (size_t)(A.x_hi - A.x_lo);
-      const int tx0 = A.x_lo + (tile % A.ntx) * S_TX;
+      const int tx0 = A.x_lo + (tile % A.ntx) * TXW;
       const int ty0 = A.y_lo + (tile / A.ntx) * S_TY;
-      const int px = tx0 + lane;
-      float thr2[S_ROWS];
+      const int px = tx0 + lane;  // column c of the thread: px + 32 c
+      // per (column c, row i): bit c * S_ROWS + i of active, thr2[c * S_ROWS + i]
+      float thr2[NCOL * S_ROWS];
       uint32_t active = 0u;
 #pragma unroll
-      for (int i = 0; i < S_ROWS; ++i) {
-        const int row = warp * S_ROWS + i;
-        const int py = ty0 + row;
-        const bool act = px < A.x_hi && py < A.y_hi;
-        active |= (act ? 1u : 0u) << i;
-        s_filled[(row << 5) | lane] = 0;
-        thr2[i] = admission_threshold(lh_min, A.ep);
-        if (act) {
-          const size_t wp = (size_t)(py - A.y_lo) * wx + (size_t)(px - A.x_lo);
-          for (int s = 0; s < K; ++s) {
-            A.out_lh[wp * K + s] = -INFINITY;
-            A.out_flux[wp * K + s] = 0.0f;
-            A.out_idx[wp * K + s] = -1;
-            A.out_nvalid[wp * K + s] = 0;
-            A.out_nkept[wp * K + s] = 0;
-            for (int m = 0; m < mw; ++m) A.out_mask[(wp * K + s) * mw + m] = 0u;
+      for (int c = 0; c < NCOL; ++c)
+#pragma unroll
+        for (int i = 0; i < S_ROWS; ++i) {
+          const int row = warp * S_ROWS + i;
+          const int py = ty0 + row, pxc = px + S_TX * c;
+          const bool act = pxc < A.x_hi && py < A.y_hi;
+          active |= (act ? 1u : 0u) << (c * S_ROWS + i);
+          s_filled[(row << TXS) | (lane + S_TX * c)] = 0;
+          thr2[c * S_ROWS + i] = admission_threshold(lh_min, A.ep);
+          if (act) {
+            const size_t wp = (size_t)(py - A.y_lo) * wx + (size_t)(pxc - A.x_lo);
+            for (int s = 0; s < K; ++s) {
+              A.out_lh[wp * K + s] = -INFINITY;
+              A.out_flux[wp * K + s] = 0.0f;
+              A.out_idx[wp * K + s] = -1;
+              A.out_nvalid[wp * K + s] = 0;
+              A.out_nkept[wp * K + s] = 0;
+              for (int m = 0; m < mw; ++m) A.out_mask[(wp * K + s) * mw + m] = 0u;
+            }
           }
         }
-      }
 
       // Evaluate every queued pair (all consumer threads), insert the results (owner threads
       // walk their pixels' lists), empty the queue.  Called by all consumer threads after a
@@ -1429,7 +1433,8 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
             if (e < nq) {
               const int pl = q_pix[e], j = q_traj[e];
               const float L = eval_pair_thread<decltype(nt)::value>(
-                  e_pairs, EP, tx0 + (pl & 31), ty0 + (pl >> 5), __ldg(e_vs + j), e_dt, r);
+                  e_pairs, EP, tx0 + (pl & (TXW - 1)), ty0 + (pl >> TXS), __ldg(e_vs + j), e_dt,
+                  r);
               if (L >= lh_min) keep(e, pl, r);
             }
             count_valid(e < nq, r[2]);
@@ -1440,7 +1445,7 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
             const int pl = q_pix[e];
             uint32_t r[S_REC_WORDS];
             const float L = eval_pair_warp<decltype(jj)::value>(
-                e_pairs, EP, tx0 + (pl & 31), ty0 + (pl >> 5),
+                e_pairs, EP, tx0 + (pl & (TXW - 1)), ty0 + (pl >> TXS),
                 e_offs + (size_t)q_traj[e] * T, e_dt, r, lane);
             if (lane == 0 && L >= lh_min) keep(e, pl, r);
             const uint32_t nvk = __shfl_sync(0xffffffffu, r[2], 0);
@@ -1461,12 +1466,14 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
         consumer_sync();
         if (tid == 0) atomicAdd(s_evals, (unsigned int)nq);
 #pragma unroll 1
-        for (int i = 0; i < S_ROWS; ++i) {
+        for (int ci = 0; ci < NCOL * S_ROWS; ++ci) {
+          const int c = ci / S_ROWS, i = ci % S_ROWS;
           const int row = warp * S_ROWS + i;
-          const int pl = (row << 5) | lane;
+          const int pl = (row << TXS) | (lane + S_TX * c);
           int e = head[pl];
           if (e < 0) continue;
-          const size_t wp = (size_t)(ty0 + row - A.y_lo) * wx + (size_t)(px - A.x_lo);
+          const size_t wp =
+              (size_t)(ty0 + row - A.y_lo) * wx + (size_t)(px + S_TX * c - A.x_lo);
           int nf = s_filled[pl];
           while (e >= 0) {
             const uint32_t* rc = recs + e * S_REC_WORDS;
@@ -1484,8 +1491,8 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
           if (nf == K) {
             const float t2 = admission_threshold(fmaxf(A.out_lh[wp * K + K - 1], lh_min), A.ep);
 #pragma unroll
-            for (int ii = 0; ii < S_ROWS; ++ii)
-              if (ii == i) thr2[ii] = t2;
+            for (int ii = 0; ii < NCOL * S_ROWS; ++ii)
+              if (ii == ci) thr2[ii] = t2;
           }
         }
         consumer_sync();
@@ -1500,11 +1507,11 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
       };
 
       for (int c = 0; c < A.nchunk; ++c) {
-        // per trajectory: POOL: (block of rows 0-1, block of rows 2-3) of this thread in acc[0];
+        // per trajectory: POOL: column cc's (block of rows 0-1, block of rows 2-3) in acc[cc];
         // otherwise (row 0, row 1) in acc[0] and (row 2, row 3) in acc[1]
-        __half2 acc[POOL ? 1 : 2][S_C];
+        __half2 acc[2][S_C];
 #pragma unroll
-        for (int pp = 0; pp < (POOL ? 1 : 2); ++pp)
+        for (int pp = 0; pp < 2; ++pp)
 #pragma unroll
           for (int v = 0; v < S_C; ++v) acc[pp][v] = __float2half2_rn(0.0f);
 
@@ -1517,17 +1524,18 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
             const unsigned char* st = arena + sinfo[slot].x;
             if (mode != 0) {
               const bool uni = (rec->box.w & S_UNIFORM_BIT) != 0;
-              accumulate_stage<POOL, 0>(acc, st, stage_width(mode), uni, rec, warp, lane);
+              accumulate_stage<POOL>(acc, st, stage_width(mode), uni, rec, warp, lane);
             } else {
               // direct loads from the block planes (word row = first image row + 3)
               const uint32_t* bp = A.bound + (size_t)t * (A.ep.H + 3) * A.Wp;
 #pragma unroll
               for (int v = 0; v < S_C; ++v) {
                 const int2 o = __ldg(A.offs + (size_t)(c * S_C + v) * T + t);
-                const int x = px + o.x;
 #pragma unroll
-                for (int pp = 0; pp < (POOL ? 1 : 2); ++pp) {
-                  const int r = ty0 + warp * S_ROWS + 2 * pp + o.y + 3;
+                for (int pp = 0; pp < 2; ++pp) {
+                  // POOL: column pp of the thread; otherwise its row pair pp
+                  const int x = px + o.x + (POOL ? S_TX * pp : 0);
+                  const int r = ty0 + warp * S_ROWS + (POOL ? 0 : 2 * pp) + o.y + 3;
                   if (x >= 0 && x < A.Wp && r >= 0 && r < A.ep.H + 3) {
                     const uint32_t w = __ldg(bp + (size_t)r * A.Wp + x);
                     acc[pp][v] = __hadd2(acc[pp][v], *reinterpret_cast<const __half2*>(&w));
@@ -1546,13 +1554,15 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
         const int nv = min(S_C, A.n_traj - c * S_C);
         const uint32_t vmask = nv >= 32 ? 0xffffffffu : ((1u << nv) - 1u);
         // POOL: a block passes against the smaller threshold of its two pixels; both are then
-        // queued.  Otherwise each row against its own threshold.
-        uint32_t cb[S_ROWS];
+        // queued.  Otherwise each row against its own threshold.  cb[cc * S_ROWS + i]: the
+        // passing trajectories of the pixel in column cc, row i.
+        uint32_t cb[NCOL * S_ROWS];
 #pragma unroll
-        for (int pp = 0; pp < (POOL ? 1 : 2); ++pp) {
+        for (int pp = 0; pp < 2; ++pp) {
+          const int o = POOL ? pp * S_ROWS : 0;  // thresholds of column pp (POOL)
           const __half2 th =
-              POOL ? __halves2half2(half_round_down(fminf(thr2[0], thr2[1])),
-                                    half_round_down(fminf(thr2[2], thr2[3])))
+              POOL ? __halves2half2(half_round_down(fminf(thr2[o], thr2[o + 1])),
+                                    half_round_down(fminf(thr2[o + 2], thr2[o + 3])))
                    : __halves2half2(half_round_down(thr2[2 * pp]), half_round_down(thr2[2 * pp + 1]));
           uint32_t b0 = 0u, b1 = 0u;
           // most chunks have no candidate in the whole warp: test the maxima first
@@ -1567,10 +1577,10 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
               b1 |= ((m >> 16) & 1u) << v;
             }
           if (POOL) {
-            cb[0] = (active & 1u) ? (b0 & vmask) : 0u;
-            cb[1] = (active & 2u) ? (b0 & vmask) : 0u;
-            cb[2] = (active & 4u) ? (b1 & vmask) : 0u;
-            cb[3] = (active & 8u) ? (b1 & vmask) : 0u;
+            cb[o] = ((active >> o) & 1u) ? (b0 & vmask) : 0u;
+            cb[o + 1] = ((active >> (o + 1)) & 1u) ? (b0 & vmask) : 0u;
+            cb[o + 2] = ((active >> (o + 2)) & 1u) ? (b1 & vmask) : 0u;
+            cb[o + 3] = ((active >> (o + 3)) & 1u) ? (b1 & vmask) : 0u;
           } else {
             cb[2 * pp] = ((active >> (2 * pp)) & 1u) ? (b0 & vmask) : 0u;
             cb[2 * pp + 1] = ((active >> (2 * pp + 1)) & 1u) ? (b1 & vmask) : 0u;
@@ -1581,7 +1591,7 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
         for (;;) {
           int ncand = 0;
 #pragma unroll
-          for (int i = 0; i < S_ROWS; ++i) ncand += __popc(cb[i]);
+          for (int i = 0; i < NCOL * S_ROWS; ++i) ncand += __popc(cb[i]);
           int incl = ncand;
 #pragma unroll
           for (int o = 1; o < 32; o <<= 1) {
@@ -1595,26 +1605,25 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
           int pos = (int)wbase + incl - ncand;
           bool deferred = false;
           if (ncand > 0) {
-#pragma unroll 1
-            for (int i = 0; i < S_ROWS; ++i) {
-              uint32_t bits = i == 0 ? cb[0] : i == 1 ? cb[1] : i == 2 ? cb[2] : cb[3];
+#pragma unroll
+            for (int ci = 0; ci < NCOL * S_ROWS; ++ci) {
+              uint32_t bits = cb[ci];
               uint32_t left = 0u;
+              const uint16_t pl =
+                  (uint16_t)(((warp * S_ROWS + ci % S_ROWS) << TXS) | (lane + S_TX * (ci / S_ROWS)));
               while (bits) {
                 const int v = __ffs(bits) - 1;
                 bits &= bits - 1u;
                 if (pos < S_QCAP) {
                   q_traj[pos] = c * S_C + v;
-                  q_pix[pos] = (uint16_t)(((warp * S_ROWS + i) << 5) | lane);
+                  q_pix[pos] = pl;
                 } else {
                   left |= 1u << v;
                   deferred = true;
                 }
                 ++pos;
               }
-              if (i == 0) cb[0] = left;
-              else if (i == 1) cb[1] = left;
-              else if (i == 2) cb[2] = left;
-              else cb[3] = left;
+              cb[ci] = left;
             }
           }
           // one barrier per chunk decides, for all consumer threads alike, whether to flush
@@ -1862,7 +1871,8 @@ static int prepare_stack(const char* who, const float* psi, const float* phi, co
   A.x_hi = p->x_hi;
   A.y_lo = p->y_lo;
   A.y_hi = p->y_hi;
-  A.ntx = (p->x_hi - p->x_lo + S_TX - 1) / S_TX;
+  A.tx = tile_w(sp.pool);
+  A.ntx = (p->x_hi - p->x_lo + A.tx - 1) / A.tx;
   A.nty = (p->y_hi - p->y_lo + S_TY - 1) / S_TY;
   A.ntiles = A.ntx * A.nty;
   return KB_OK;
@@ -1909,7 +1919,8 @@ static int launch_prep(StackPrep& sp, const kb_schedule& sch, bool pool, cudaStr
   plan_offsets_kernel<<<(L.n_pad + 255) / 256, 256, 0, st>>>(sp.vx, sp.vy, sorted, n_traj, L.n_pad,
                                                                T, sp.cs, orig, offs, vsort, dtf);
   KB_LAUNCH_CHECK("plan_offsets_kernel");
-  plan_boxes_kernel<<<(L.nchunk * T + 255) / 256, 256, 0, st>>>(offs, L.nchunk, T, sp.x_lo, plan);
+  plan_boxes_kernel<<<(L.nchunk * T + 255) / 256, 256, 0, st>>>(offs, L.nchunk, T, sp.x_lo,
+                                                               sp.A.tx, plan);
   KB_LAUNCH_CHECK("plan_boxes_kernel");
   {
     size_t total = (size_t)T * (H + 3) * L.Wp;
@@ -1928,8 +1939,8 @@ static int launch_prep(StackPrep& sp, const kb_schedule& sch, bool pool, cudaStr
     unsigned long long* tkeys = reinterpret_cast<unsigned long long*>(ws + L.tkeys);
     int32_t* torder = reinterpret_cast<int32_t*>(ws + L.torder);
     tile_score_kernel<<<ntiles, 256, 0, st>>>(bound, T, H, W, L.Wp, vbox, sp.cs, sp.x_lo, sp.y_lo,
-                                              sp.x_hi, sp.y_hi, sp.A.ntx, ntiles, sch.hot_nu2,
-                                              sch.score_span, tkeys);
+                                              sp.x_hi, sp.y_hi, sp.A.ntx, sp.A.tx, ntiles,
+                                              sch.hot_nu2, sch.score_span, tkeys);
     KB_LAUNCH_CHECK("tile_score_kernel");
     int n2 = 1;
     while (n2 < ntiles) n2 <<= 1;
@@ -2261,13 +2272,23 @@ extern "C" int kb_batch_create(const kb_stack* stacks, int n, void* workspace, s
   b->ws = static_cast<char*>(workspace);
   b->tb = batch_tables(n);
   size_t off = b->tb.total;
+  // one kind of bound for the whole batch (one persistent launch runs one kernel): two-row
+  // blocks only if every stack takes them; the stacks' tile geometry follows it
+  bool batch_pool = true;
+  for (int i = 0; i < n; ++i) {
+    const kb_search_params& q = stacks[i].params;
+    batch_pool = batch_pool &&
+                 (q.bound_rows == 2 || (q.bound_rows == 0 && pool_blocks(stacks[i].T, q.lh_min)));
+  }
   for (int i = 0; i < n; ++i) {
     const kb_stack& s = stacks[i];
     const size_t sz = stack_ws_bytes(s);
     char who[48];
     snprintf(who, sizeof(who), "kb_batch_create (stack %d)", i);
+    kb_search_params prm = s.params;
+    if (prm.bound_rows >= 0 && prm.bound_rows <= 2) prm.bound_rows = batch_pool ? 2 : 1;
     rc = prepare_stack(who, s.psi, s.phi, s.times, s.T, s.H, s.W, s.vx, s.vy, s.n_traj,
-                       &s.params, s.out_lh, s.out_flux, s.out_idx, s.out_nvalid, s.out_nkept,
+                       &prm, s.out_lh, s.out_flux, s.out_idx, s.out_nvalid, s.out_nkept,
                        s.out_mask, b->ws + off, sz, b->sp[i]);
     if (rc != KB_OK) {
       delete b;
