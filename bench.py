@@ -382,17 +382,20 @@ def cluster_ws_bytes(kb, n):
 
 
 def search_traffic(version, workload):
-    """DRAM bytes per search_kernel launch on this workload, from the ncu summary in profiles/
-    (a line `traffic: <workload> <bytes> kernel_version <v>`); None if absent or taken on another
-    kernel version."""
+    """DRAM bytes per search_kernel launch on this workload with their source, from the ncu
+    summary in profiles/ (a line `traffic: <workload> <bytes> kernel_version <v> source <text>`);
+    None if absent or taken on another kernel version (the counters then describe another
+    kernel)."""
     import re
     p = os.path.join(ROOT, "profiles", "search_kernel_decam.md")
     if not os.path.exists(p):
         return None
     for line in open(p):
-        m = re.match(r"\s*traffic:\s+(\S+)\s+([0-9.e+]+)\s+kernel_version\s+(\d+)", line)
+        m = re.match(r"\s*traffic:\s+(\S+)\s+([0-9.e+]+)\s+kernel_version\s+(\d+)(?:\s+source\s+(.*))?",
+                     line)
         if m and m.group(1) == workload and int(m.group(3)) == version:
-            return float(m.group(2))
+            return {"bytes": float(m.group(2)),
+                    "source": (m.group(4) or "ncu summary in profiles/").strip()}
     return None
 
 
@@ -532,6 +535,8 @@ def run_ours(args):
     ms_max = max_over_ranks(ms, world, dev)
     value = world * te_step * args.steps / (ms_max / 1e3)
     stats = kb.search_stats(ws)
+    stage = kb.search_stage_counts(ws)
+    pc = kb.search_pass_counts(ws)
 
     # ---- end to end through the C ABI from pinned host buffers ----
     # Every step copies its inputs from pinned host memory and reads its results back inside the
@@ -586,13 +591,14 @@ def run_ours(args):
     peaks, peaks_src = measured_peaks()
     k_ms = statistics.median(kernel_ms)
     l2_gbs = kb.l2_read_bandwidth(device=dev)
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
-    # Shared-memory load roofline of the bound pass: one 128-byte wavefront per SM per clock;
-    # the bound pass reads SEARCH_SMEM_BYTES_PER_TE from shared memory per trajectory-epoch.
-    smem_peak = sms * 128 * sm_max * 1e6 / 1e9                 # GB/s
+    smem_gbs = kb.smem_read_bandwidth(device=dev)
     te_per_s_kernel = te_step / (k_ms / 1e3)
-    achieved = te_per_s_kernel * SEARCH_SMEM_BYTES_PER_TE / 1e9
+    # The search kernel's bound is its shared-memory reads: the staged bound words it sums
+    # (counted per launch from its staging plan by kb_search_pass_counts) against the
+    # shared-memory read bandwidth measured by kb_smem_probe in this run.
+    bytes_launch = pc[0]
+    achieved = bytes_launch / (k_ms / 1e3) / 1e9
+    smem_all = pc[0] + pc[1] + pc[2]
     traffic = search_traffic(kb.version(), args.workload)
     line = {
         "metric": "trajectory-epoch evals/sec", "value": value, "unit": "TE/s",
@@ -601,12 +607,20 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded DECam-shaped stack)",
         "config": dict(workload_config(args.workload), n_stamps=n_st,
                        parallelism="one independent stack per GPU" if world > 1 else "1 GPU"),
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": smem_peak, "unit": "GB/s",
-                     "frac": achieved / smem_peak, "traffic": traffic,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": smem_gbs, "unit": "GB/s",
+                     "frac": achieved / smem_gbs,
+                     "traffic": None if traffic is None else traffic["bytes"],
+                     "traffic_source": None if traffic is None else traffic["source"],
                      "kernel": "search_kernel", "kernel_ms": k_ms,
-                     "peak_source": "derived: %d SMs x 128 B/clk shared-memory loads x %g MHz "
-                                    "(sm_max_mhz, %s)" % (sms, sm_max, peaks_src),
-                     "algorithmic_bytes_per_te": SEARCH_SMEM_BYTES_PER_TE,
+                     "what": "on-chip: shared-memory loads of the pruning bound's staged words",
+                     "peak_source": "measured in this run: kb_smem_probe, conflict-free 32-bit "
+                                    "shared loads on every SM",
+                     "algorithmic_bytes_per_launch": bytes_launch,
+                     "algorithmic_bytes_per_te": bytes_launch / te_step,
+                     "smem_traffic": {"bound_words": pc[0], "offsets": pc[1], "tma_staged": pc[2],
+                                      "direct_load_iterations": pc[3],
+                                      "gbs": smem_all / (k_ms / 1e3) / 1e9,
+                                      "frac": smem_all / (k_ms / 1e3) / 1e9 / smem_gbs},
                      "hbm_gather_equiv": {"bytes_per_te": 8,
                                           "achieved_gbs": te_per_s_kernel * 8 / 1e9,
                                           "hbm_peak_gbs": peaks["hbm_gbs"],
@@ -618,12 +632,15 @@ def run_ours(args):
                                    "frac": te_per_s_kernel * 8 / 1e9 / l2_gbs,
                                    "note": "the naive gather roofline (8 B of psi+phi per "
                                            "trajectory-epoch against the L2 read bandwidth "
-                                           "measured by kb_l2_probe at bench start); above 1 "
-                                           "because the exact bound reads 1 B per "
-                                           "trajectory-epoch from staged shared memory and only "
-                                           "0.2% of pairs are gathered in full"}},
+                                           "measured by kb_l2_probe in this run); above 1 "
+                                           "because the exact bound reads its staged words from "
+                                           "shared memory and only ~0.2% of pairs are gathered "
+                                           "in full"}},
         "search_stats": {"te": stats[0], "full_evals": stats[1], "inserts": stats[2],
-                         "full_eval_frac": stats[1] / max(1, stats[0] / T)},
+                         "full_eval_frac": stats[1] / max(1, stats[0] / T),
+                         "stages": {"n_valid_ge_min_obs": stage[0], "lh_ge_lh_min": stage[1],
+                                    "mean_kept_fraction": stage[2] / max(1, stage[3]),
+                                    "over": "the pairs evaluated in full"}},
         "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
     }
     if not args.no_cpu_baseline:

@@ -235,6 +235,21 @@ KB_API int kb_search_stats(const void* workspace, unsigned long long* stats, voi
 KB_API int kb_search_stage_counts(const void* workspace, unsigned long long* out, void* stream);
 
 /*
+ * kb_search_pass_counts -- the shared-memory traffic of the last kb_search that used `workspace`
+ * (HOST array out[4]; synchronises the stream), counted from the staging plan of every
+ * (tile, chunk of 32 trajectories, epoch) the search swept:
+ *   out[0] bytes of the pruning bound's words the search kernel read from staged shared memory
+ *          (two 4-byte words per bound-pass thread and trajectory, or per thread when the
+ *          chunk's trajectories share one offset in that epoch),
+ *   out[1] bytes of the per-trajectory offsets it read with them (16 per four trajectories and
+ *          warp),
+ *   out[2] bytes staged into shared memory by the tensor-memory copies,
+ *   out[3] iterations that read the bound from global memory instead (no staged box).
+ * Measurement utility: the paper has no counterpart.
+ */
+KB_API int kb_search_pass_counts(const void* workspace, unsigned long long* out, void* stream);
+
+/*
  * kb_stamps -- coadded postage stamps along trajectories (Section 3.3: per-pixel median over
  * the epochs of the trajectory; also the mean).  For candidate c and stamp pixel (sy, sx) in
  * [-radius, radius]^2, the values img[t, y_t + sy, x_t + sx] of every epoch t that is inside the

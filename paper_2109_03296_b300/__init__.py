@@ -174,6 +174,14 @@ def search_stage_counts(workspace, stream=None):
     return tuple(int(v) for v in arr)
 
 
+def search_pass_counts(workspace, stream=None):
+    """Shared-memory traffic of the last search that used this workspace: (bound words read,
+    offsets read, bytes staged by TMA) in bytes, and iterations with direct global loads."""
+    arr = (C.c_ulonglong * 4)()
+    check(lib().kb_search_pass_counts(_ptr(workspace), arr, _stream(stream)))
+    return tuple(int(v) for v in arr)
+
+
 def search_no_alloc_stats(stream=None):
     """search_stats() of the last search_no_alloc() on the current device (stats[3] != 0: a
     device-side wait gave up and the lists may be partial)."""

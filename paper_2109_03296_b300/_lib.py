@@ -29,7 +29,8 @@ EXPORTS = ("kb_version", "kb_last_error", "kb_search_params_default", "kb_make_p
            "kb_batch_run_graph", "kb_batch_set_schedule", "kb_batch_get_schedule",
            "kb_batch_autotune", "kb_batch_stats", "kb_batch_destroy",
            "kb_cluster_workspace_size", "kb_cluster", "kb_l2_probe", "kb_wait_check",
-           "kb_search_stage_counts", "kb_search_no_alloc_stats", "kb_smem_probe")
+           "kb_search_stage_counts", "kb_search_no_alloc_stats", "kb_smem_probe",
+           "kb_search_pass_counts")
 
 
 class KbError(RuntimeError):
@@ -97,6 +98,8 @@ def lib():
     L.kb_search_stage_counts.argtypes = [p, p, p]
     L.kb_search_no_alloc_stats.restype = i
     L.kb_search_no_alloc_stats.argtypes = [p, p]
+    L.kb_search_pass_counts.restype = i
+    L.kb_search_pass_counts.argtypes = [p, p, p]
     L.kb_smem_probe.restype = i
     L.kb_smem_probe.argtypes = [i, i, p, p]
     L.kb_stamps.restype = i

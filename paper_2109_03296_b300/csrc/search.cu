@@ -182,6 +182,9 @@ struct Ctrl {
   // stage counts of the pairs evaluated in full: n_valid >= min_obs; LH' >= lh_min after the
   // clip; and, over the latter, the sums of n_kept and n_valid (the mean kept fraction)
   unsigned long long stage_valid, stage_pass, stage_kept, stage_nvalid;
+  // bound-pass iterations (tile, chunk, epoch) by kind: staged box with per-trajectory offsets,
+  // staged box with one offset for the chunk, direct global loads; and the bytes staged by TMA
+  unsigned long long it_staged, it_uniform, it_direct, tma_bytes;
 };
 static_assert(sizeof(Ctrl) <= 256, "control block");
 
@@ -732,8 +735,9 @@ __device__ __forceinline__ float sorted_percentile(const float (&loc)[NT], int n
 // The track offsets are recomputed from the pair's velocity with the plan's own arithmetic
 // (track_offset on the same float dt), so they equal the stored ones bit for bit; this replaces
 // T scattered offset loads per pair (one per lane and epoch) by one velocity load and broadcast
-// loads of dt.  Returns L' (NaN when the pair is not eligible).
-template <int NT>
+// loads of dt.  Returns L' (NaN when the pair is not eligible).  FILTER: only the gather and the
+// exact filter below (no sort); returns NaN for a pair that cannot reach lh_min, +inf otherwise.
+template <int NT, bool FILTER>
 __device__ float eval_pair_thread(const float2* __restrict__ pairs,
                                   const EvalParams& ep, int x0, int y0, float2 v,
                                   const float* __restrict__ dtf, uint32_t* rec) {
@@ -778,48 +782,64 @@ __device__ float eval_pair_thread(const float2* __restrict__ pairs,
     return on_lh ? __fdiv_rn(pv[t], __fsqrt_rn(fv[t])) : __fdiv_rn(pv[t], fv[t]);
   };
   uint32_t km = vm;
-  if (ep.clip) {
-    float loc[NT];
-    // the lightcurve, with its smallest value a0, largest a1 and second largest a2, the sum of
-    // nu2 = psi^2/phi over the valid epochs with psi > 0 and the nu2 of the epoch of a1
-    float a0 = INFINITY, a1 = -INFINITY, a2 = -INFINITY, s_all = 0.0f, s_a1 = 0.0f;
+  if (FILTER) {
+    // Exact filter before the sort.  With a0 the smallest and a4 the fourth largest lightcurve
+    // value: when the interpolation ranks of q_mid and q_hi stay at or below index n - 4
+    // (their upper order statistic is at most the fourth largest), the median and q_hi lie at
+    // or below a4 and q_lo at or above a0, so the upper clip bound is at most
+    // ub = a4 + n_sigma C (a4 - a0) (plus a margin for the float32 rounding of the percentiles
+    // and bounds).  Every epoch above ub is clipped whatever the quantiles are, and by
+    // Cauchy-Schwarz LH' of any kept set is at most the square root of the sum of
+    // nu2 = psi^2/phi over the other valid epochs with psi > 0; a pair whose sum is below
+    // lh_min^2 (1 - 1e-3) cannot reach lh_min.  Without the clip (or the rank condition) the sum
+    // runs over every valid epoch.  This drops most pairs whose pruning bound passed only
+    // through one bright epoch (a +20 sigma spike) or through the other pixel of a two-row
+    // block.  Returns NaN for a dropped pair, +inf for one that needs the full evaluation.
+    if (!(ep.nu2_floor > 0.0f)) {
+      rec[2] = (uint32_t)nvalid;
+      return INFINITY;
+    }
+    float a0 = INFINITY, t1 = -INFINITY, t2 = -INFINITY, t3 = -INFINITY, t4 = -INFINITY;
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
-      loc[t] = INFINITY;
       if ((vm >> t) & 1u) {
         const float a = curve(t);
-        loc[t] = a;
-        const float nu = pv[t] > 0.0f ? (on_lh ? a * a : pv[t] * a) : 0.0f;
-        s_all += nu;
         a0 = fminf(a0, a);
-        if (a > a1) {
-          a2 = a1;
-          a1 = a;
-          s_a1 = nu;
-        } else {
-          a2 = fmaxf(a2, a);
-        }
+        // top four, with as few selects as a sorted insertion allows
+        const float m1 = fmaxf(t1, a), r1 = fminf(t1, a);
+        const float m2 = fmaxf(t2, r1), r2 = fminf(t2, r1);
+        const float m3 = fmaxf(t3, r2), r3 = fminf(t3, r2);
+        t4 = fmaxf(t4, r3);
+        t1 = m1;
+        t2 = m2;
+        t3 = m3;
       }
     }
-    // Outlier shortcut (exact).  When the interpolation ranks of q_mid and q_hi stay below the
-    // largest value (their upper order statistic has index <= n - 2), the median and q_hi lie
-    // at or below a2 and q_lo at or above a0, so every upper clip bound is at most
-    // a2 + n_sigma C (a2 - a0).  A largest value above that (with a margin for the float32
-    // rounding of the percentiles and bounds) is clipped whatever the quantiles are; the
-    // Cauchy-Schwarz bound over the other valid epochs with psi > 0 then caps LH' of any kept
-    // set, and a pair below lh_min (1 - 1e-3) skips the sort.  This is the common case of a pair
-    // whose pruning bound passed only through one +20 sigma spike.
-    if (ep.nu2_floor > 0.0f && s_all - s_a1 < ep.nu2_floor) {
+    float ub = INFINITY;
+    if (ep.clip) {
       const int2* rk = rank_table(dtf);
-      const float spread = ep.n_sigma * (ep.c_sigma * (a2 - a0));
-      const float ub = a2 + spread + 1e-5f * (fabsf(a2) + fabsf(a0) + spread) + 1e-30f;
-      if (a1 > ub && __ldg(rk + rank_entry(1, nvalid)).x <= nvalid - 3 &&
-          __ldg(rk + rank_entry(2, nvalid)).x <= nvalid - 3) {
-        rec[0] = __float_as_uint(NAN);
-        rec[2] = (uint32_t)nvalid;
-        return NAN;
+      if (__ldg(rk + rank_entry(1, nvalid)).x <= nvalid - 5 &&
+          __ldg(rk + rank_entry(2, nvalid)).x <= nvalid - 5) {
+        const float spread = ep.n_sigma * (ep.c_sigma * (t4 - a0));
+        ub = t4 + spread + 1e-5f * (fabsf(t4) + fabsf(a0) + spread) + 1e-30f;
+        if (!(ub == ub)) ub = INFINITY;  // NaN (infinite values): no epoch is excluded
       }
     }
+    float s_keep = 0.0f;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      if (((vm >> t) & 1u) && pv[t] > 0.0f) {
+        const float a = curve(t);
+        if (!(a > ub)) s_keep += on_lh ? a * a : pv[t] * a;
+      }
+    }
+    rec[2] = (uint32_t)nvalid;
+    return s_keep < ep.nu2_floor ? NAN : INFINITY;
+  }
+  if (ep.clip) {
+    float loc[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) loc[t] = ((vm >> t) & 1u) ? curve(t) : INFINITY;
     thread_bitonic_sort<NT>(loc);
     const int2* rk = rank_table(dtf);
     const float x_lo = sorted_percentile<NT>(loc, nvalid, __ldg(rk + rank_entry(0, nvalid)));
@@ -925,7 +945,8 @@ struct SmemLayout {
   static constexpr size_t qtraj = arena + S_ARENA_BYTES;
   static constexpr size_t qpix = qtraj + S_QCAP * sizeof(int32_t);
   static constexpr size_t qnext = qpix + S_QCAP * sizeof(uint16_t);
-  static constexpr size_t head = (qnext + S_QCAP * sizeof(int16_t) + 15) / 16 * 16;  // [pixel]
+  static constexpr size_t surv = qnext + S_QCAP * sizeof(int16_t);  // pairs past the filter
+  static constexpr size_t head = (surv + S_QCAP * sizeof(int16_t) + 15) / 16 * 16;  // [pixel]
   static constexpr size_t filled = head + S_NPIX * sizeof(int32_t);
   static constexpr size_t slots = (filled + S_NPIX + 15) / 16 * 16;          // S_D plan records
   static constexpr size_t sinfo = slots + S_D * sizeof(PlanRec);  // S_D x {offset, tile, bytes}
@@ -1016,6 +1037,7 @@ __device__ void producer_loop(const TmapSet& pmaps, const SearchArgs& A0, const 
   long long oldest = pw;        // oldest unretired iteration of this producer
   long long last_issued = -1;
   int head = 0, tail = 0, live = 0;  // ring: [tail, head) cyclically, `live` regions
+  unsigned long long n_staged = 0, n_uniform = 0, n_direct = 0, n_bytes = 0;  // lane 0
   for (int k = 0;; ++k) {
     int tile = 0;  // the global tile (counter value) first; resolved below
     if (pw == 0) {
@@ -1156,12 +1178,24 @@ __device__ void producer_loop(const TmapSet& pmaps, const SearchArgs& A0, const 
                         ty0 + b.y + 3, t);
           }
         }
+        if (!last && lane == 0) {
+          if (mode == 0) ++n_direct;
+          else if (b.w & S_UNIFORM_BIT) ++n_uniform;
+          else ++n_staged;
+          n_bytes += (unsigned long long)sz;
+        }
         last_issued = it;
         __syncwarp();
       }
     }
     it_base += n_it;
     if (last) break;
+  }
+  if (lane == 0) {
+    atomicAdd(&ctrl->it_staged, n_staged);
+    atomicAdd(&ctrl->it_uniform, n_uniform);
+    atomicAdd(&ctrl->it_direct, n_direct);
+    atomicAdd(&ctrl->tma_bytes, n_bytes);
   }
   *issued_out = last_issued;
 }
@@ -1272,6 +1306,7 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
   int32_t* q_traj = reinterpret_cast<int32_t*>(smem + SmemLayout::qtraj);
   uint16_t* q_pix = reinterpret_cast<uint16_t*>(smem + SmemLayout::qpix);
   int16_t* q_next = reinterpret_cast<int16_t*>(smem + SmemLayout::qnext);
+  int16_t* q_surv = reinterpret_cast<int16_t*>(smem + SmemLayout::surv);
   PlanRec* slots = reinterpret_cast<PlanRec*>(smem + SmemLayout::slots);
   int4* sinfo = reinterpret_cast<int4*>(smem + SmemLayout::sinfo);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + SmemLayout::full);
@@ -1290,7 +1325,8 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
   // n_kept and n_valid over the latter
   unsigned int* s_stage = reinterpret_cast<unsigned int*>(smem + SmemLayout::misc + 64);     // [2]
   unsigned long long* s_stage64 =
-      reinterpret_cast<unsigned long long*>(smem + SmemLayout::misc + 72);                   // [2]
+      reinterpret_cast<unsigned long long*>(smem + SmemLayout::misc + 80);                   // [2]
+  // s_stage[2] (misc + 72): pairs of the current flush that need the full evaluation
   SearchArgs* s_args = reinterpret_cast<SearchArgs*>(smem + SmemLayout::sargs);
   Ctrl* const ctrl = BATCH ? B.ctrl : A0.ctrl;
 
@@ -1308,7 +1344,7 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
     *s_qcount = 0u;
     *s_evals = 0u;
     *s_ins = 0u;
-    s_stage[0] = s_stage[1] = 0u;
+    s_stage[0] = s_stage[1] = s_stage[2] = 0u;
     s_stage64[0] = s_stage64[1] = 0ull;
     *s_abort = 0u;
     *s_tile = -1;
@@ -1425,20 +1461,50 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
           const unsigned int n = __popc(__ballot_sync(0xffffffffu, v));
           if (lane == 0 && n) atomicAdd(&s_stage[0], n);
         };
+        // A pair per thread, in two phases: every queued pair is gathered and passed through
+        // the exact filter (no sort); the pairs it cannot drop are collected and evaluated in
+        // full, so that the sorting networks run in warps of pairs that all need them.
         auto by_thread = [&](auto nt) {
+          constexpr int NTv = decltype(nt)::value;
+          unsigned int* s_nsurv = s_stage + 2;
           for (int eb = 0; eb < nq; eb += S_CTHREADS) {
             const int e = eb + tid;
             uint32_t r[S_REC_WORDS];
             r[2] = 0u;
+            bool more = false;
             if (e < nq) {
               const int pl = q_pix[e], j = q_traj[e];
-              const float L = eval_pair_thread<decltype(nt)::value>(
+              const float F = eval_pair_thread<NTv, true>(
+                  e_pairs, EP, tx0 + (pl & (TXW - 1)), ty0 + (pl >> TXS), __ldg(e_vs + j), e_dt,
+                  r);
+              more = F > 0.0f;  // +inf: needs the full evaluation (NaN: dropped)
+            }
+            // the dropped pairs are counted here, the others after their full evaluation
+            count_valid(e < nq && !more, r[2]);
+            const unsigned int mb = __ballot_sync(0xffffffffu, more);
+            unsigned int wpos = 0u;
+            if (lane == 0 && mb) wpos = atomicAdd(s_nsurv, (unsigned int)__popc(mb));
+            wpos = __shfl_sync(0xffffffffu, wpos, 0);
+            if (more) q_surv[wpos + __popc(mb & ((1u << lane) - 1u))] = (int16_t)e;
+          }
+          consumer_sync();
+          const int ns = (int)*s_nsurv;
+          for (int kb = 0; kb < ns; kb += S_CTHREADS) {
+            const int k = kb + tid;
+            uint32_t r[S_REC_WORDS];
+            r[2] = 0u;
+            if (k < ns) {
+              const int e = q_surv[k];
+              const int pl = q_pix[e], j = q_traj[e];
+              const float L = eval_pair_thread<NTv, false>(
                   e_pairs, EP, tx0 + (pl & (TXW - 1)), ty0 + (pl >> TXS), __ldg(e_vs + j), e_dt,
                   r);
               if (L >= lh_min) keep(e, pl, r);
             }
-            count_valid(e < nq, r[2]);
+            count_valid(k < ns, r[2]);
           }
+          consumer_sync();
+          if (tid == 0) *s_nsurv = 0u;
         };
         auto by_warp = [&](auto jj) {
           for (int e = warp; e < nq; e += S_CWARPS) {
@@ -2066,6 +2132,10 @@ __global__ void batch_sum_kernel(Ctrl* const* __restrict__ ctrls, int n, Ctrl* t
     sk += ctrls[k]->stage_kept;
     sn += ctrls[k]->stage_nvalid;
     err |= ctrls[k]->err;
+    total->it_staged += ctrls[k]->it_staged;
+    total->it_uniform += ctrls[k]->it_uniform;
+    total->it_direct += ctrls[k]->it_direct;
+    total->tma_bytes += ctrls[k]->tma_bytes;
   }
   total->evals = ev;
   total->inserts = ins;
@@ -2526,6 +2596,25 @@ extern "C" int kb_search_stage_counts(const void* workspace, unsigned long long*
   out[1] = c.stage_pass;
   out[2] = c.stage_kept;
   out[3] = c.stage_nvalid;
+  return KB_OK;
+}
+
+extern "C" int kb_search_pass_counts(const void* workspace, unsigned long long* out,
+                                     void* stream) {
+  using namespace kb;
+  if (!workspace || !out) return fail(KB_ERR_INVALID_ARG, "kb_search_pass_counts: null pointer");
+  Ctrl c{};
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  KB_CUDA_TRY(cudaMemcpyAsync(&c, workspace, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+  KB_CUDA_TRY(cudaStreamSynchronize(st));
+  // per (tile, chunk, epoch): each bound-pass thread makes two 4-byte shared loads per
+  // trajectory (its two columns, or its two row pairs), or two in all when the chunk shares
+  // one offset; and one 16-byte offset load per four trajectories (a warp-wide broadcast)
+  const unsigned long long words = 2ull * S_CTHREADS;
+  out[0] = (c.it_staged * S_C + c.it_uniform) * words * 4ull;
+  out[1] = c.it_staged * (unsigned long long)(S_C / 4) * S_CWARPS * 16ull;
+  out[2] = c.tma_bytes;
+  out[3] = c.it_direct;
   return KB_OK;
 }
 
