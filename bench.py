@@ -52,10 +52,6 @@ class StackView:
 
     def __init__(self, **kw):
         self.__dict__.update(kw)
-# Shared-memory bytes the bound pass reads per trajectory-epoch: one 32-bit word per (consumer
-# thread, trajectory, epoch) holds the fp16 maxima of two 2-row blocks, i.e. covers 4 start
-# pixels.
-SEARCH_SMEM_BYTES_PER_TE = 1
 
 
 def parse():
@@ -979,6 +975,7 @@ def run_batch(args):
             done, tot = b.stats()
             batch_lat.append((done / 1e6).tolist())
     launches = kb.launch_count() - launches0
+    pc = b.pass_counts()
     clocks = clk.summary()
     same = all(torch.equal(a[k], c[k]) for a, c in zip(plain_out, b.results)
                for k in ("idx", "nvalid", "nkept", "mask")) and \
@@ -990,11 +987,10 @@ def run_batch(args):
     pms = statistics.median(plain_ms)
     bl = np.array(batch_lat[-1])
     pl = np.array(plain_lat[-1])
-    peaks, peaks_src = measured_peaks()
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
-    smem_peak = sms * 128 * sm_max * 1e6 / 1e9
-    achieved = te_step * SEARCH_SMEM_BYTES_PER_TE / (ms / 1e3) / 1e9
+    smem_peak = kb.smem_read_bandwidth(device=dev)
+    # counted shared-memory bytes of the bound pass over all 64 stacks (kb_batch_pass_counts)
+    # per step, against the shared-memory read bandwidth measured in this run
+    achieved = pc[0] / (ms / 1e3) / 1e9
     sizes = {}
     for (H, W, T, ns, na, nm, seed) in specs:
         sizes["%dx%d" % (H, W)] = sizes.get("%dx%d" % (H, W), 0) + 1
@@ -1025,14 +1021,19 @@ def run_batch(args):
                               "one persistent launch"),
                      "tile_order": sched.tile_order, "hot_nu2": sched.hot_nu2,
                      "score_span": sched.score_span, "stack_order": sched.stack_order,
+                     "tile_cols": sched.tile_cols,
                      "autotune_s": tune_s},
         "results_identical_to_plain": bool(same),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": smem_peak, "unit": "GB/s",
                      "frac": achieved / smem_peak, "traffic": None,
                      "kernel": "search_kernel (batch) + per-stack preparation", "kernel_ms": ms,
-                     "peak_source": "derived: %d SMs x 128 B/clk shared-memory loads x %g MHz "
-                                    "(sm_max_mhz, %s)" % (sms, sm_max, peaks_src),
-                     "algorithmic_bytes_per_te": SEARCH_SMEM_BYTES_PER_TE},
+                     "what": "on-chip: shared-memory loads of the pruning bound's staged words",
+                     "peak_source": "measured in this run: kb_smem_probe, conflict-free 32-bit "
+                                    "shared loads on every SM",
+                     "algorithmic_bytes_per_launch": pc[0],
+                     "algorithmic_bytes_per_te": pc[0] / te_step,
+                     "smem_traffic": {"bound_words": pc[0], "offsets": pc[1], "tma_staged": pc[2],
+                                      "direct_load_iterations": pc[3]}},
         "search_stats": tot, "clocks": clocks, "gpu_launches": launches,
         "e2e": None,
         "e2e_note": "the stacks' psi/phi are device-resident outputs of kb_make_psi_phi; the "

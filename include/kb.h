@@ -239,13 +239,16 @@ KB_API int kb_search_stage_counts(const void* workspace, unsigned long long* out
  * (HOST array out[4]; synchronises the stream), counted from the staging plan of every
  * (tile, chunk of 32 trajectories, epoch) the search swept:
  *   out[0] bytes of the pruning bound's words the search kernel read from staged shared memory
- *          (two 4-byte words per bound-pass thread and trajectory, or per thread when the
- *          chunk's trajectories share one offset in that epoch),
+ *          (per bound-pass thread and trajectory two 4-byte words, or one with two-row-block
+ *          bounds in 32-wide tiles; as many per thread when the chunk's trajectories share one
+ *          offset in that epoch),
  *   out[1] bytes of the per-trajectory offsets it read with them (16 per four trajectories and
  *          warp),
  *   out[2] bytes staged into shared memory by the tensor-memory copies,
  *   out[3] iterations that read the bound from global memory instead (no staged box).
  * Measurement utility: the paper has no counterpart.
+ * kb_batch_pass_counts: the same over the last run of a batch (kb_batch, below).
+ * Errors: KB_ERR_INVALID_ARG (null pointer), KB_ERR_CUDA.
  */
 KB_API int kb_search_pass_counts(const void* workspace, unsigned long long* out, void* stream);
 
@@ -291,8 +294,11 @@ KB_API int kb_stamps(const float* img, const float* var, const uint8_t* mask, co
  *                                 arguments live in parameter space), spread over four
  *                                 streams of the batch, so that a stack's kernel starts on the
  *                                 SMs that the previous one's last tiles leave idle.
+ *                    tile_cols    1 or 2: columns summed by each thread of the bound pass, i.e.
+ *                                 tiles 32 or 64 pixels wide (stacks with two-row-block bounds;
+ *                                 single-row bounds always take 32).
  *                  kb_schedule_default: {tile_order 1, hot_nu2 64, score_span 64, stack_order 1,
- *                  mode 1} (kb_search uses the same tile order).
+ *                  mode 1, tile_cols 2} (kb_search uses the same tile order and width).
  *   kb_batch       opaque handle: kb_batch_create validates every stack (the checks of
  *                  kb_search), lays out the workspace and writes the batch tables to the device
  *                  (synchronous copies); the stacks' buffers must stay valid while it is used.
@@ -305,9 +311,10 @@ KB_API int kb_stamps(const float* img, const float* var, const uint8_t* mask, co
  *   call).
  * kb_batch_set_schedule / kb_batch_get_schedule: knobs above (set waits for the device).
  * kb_batch_autotune: times the batch (kb_batch_run, best of `reps`) under schedules chosen by
- *   coordinate descent from the default (mode and stack order, tile order, hot_nu2 in
- *   {64, 16, 144}, score_span in {64, 32, 128}), keeps the fastest and returns it in *best
- *   (nullable).  Runs the batch about 9 x reps times; its outputs are those of a normal run.
+ *   coordinate descent from the default (mode and stack order, tile order and tile width,
+ *   hot_nu2 in {64, 16, 144}, score_span in {64, 32, 128}), keeps the fastest and returns it in
+ *   *best (nullable).  Runs the batch about 10 x reps times; its outputs are those of a normal
+ *   run.
  * kb_batch_stats: after a run, done_ns[i] = ns from the start of the run to the completion of
  *   stack i's last tile (the caller's order), totals[4] = {trajectory-epochs, full evaluations,
  *   insertions, error flags} of the run (blocks the host).
@@ -338,6 +345,7 @@ typedef struct kb_schedule {
   int score_span;
   int stack_order;
   int mode;
+  int tile_cols;
 } kb_schedule;
 
 typedef struct kb_batch kb_batch;
@@ -353,6 +361,7 @@ KB_API int kb_batch_get_schedule(const kb_batch* b, kb_schedule* s);
 KB_API int kb_batch_autotune(kb_batch* b, void* stream, int reps, kb_schedule* best);
 KB_API int kb_batch_stats(kb_batch* b, unsigned long long* done_ns, unsigned long long* totals,
                           void* stream);
+KB_API int kb_batch_pass_counts(kb_batch* b, unsigned long long* out, void* stream);
 KB_API void kb_batch_destroy(kb_batch* b);
 
 /*

@@ -572,14 +572,15 @@ class Schedule:
     score_span: int = 64
     stack_order: int = 1
     mode: int = 1           # 0: one persistent launch; 1: concurrent per-stack launches
+    tile_cols: int = 2      # tiles 32 * tile_cols pixels wide (two-row-block bounds)
 
     def to_c(self):
         return ScheduleC(int(self.tile_order), float(self.hot_nu2), int(self.score_span),
-                         int(self.stack_order), int(self.mode))
+                         int(self.stack_order), int(self.mode), int(self.tile_cols))
 
     @staticmethod
     def from_c(c):
-        return Schedule(c.tile_order, c.hot_nu2, c.score_span, c.stack_order, c.mode)
+        return Schedule(c.tile_order, c.hot_nu2, c.score_span, c.stack_order, c.mode, c.tile_cols)
 
 
 class Batch:
@@ -666,6 +667,12 @@ class Batch:
                                    tot.ctypes.data_as(C.c_void_p), _stream(stream)))
         return done, dict(te=int(tot[0]), evals=int(tot[1]), inserts=int(tot[2]),
                           err=int(tot[3]))
+
+    def pass_counts(self, stream=None):
+        """search_pass_counts() over the last run of the batch."""
+        arr = (C.c_ulonglong * 4)()
+        check(lib().kb_batch_pass_counts(self._h, arr, _stream(stream)))
+        return tuple(int(v) for v in arr)
 
     def close(self):
         if getattr(self, "_h", None):

@@ -30,7 +30,7 @@ EXPORTS = ("kb_version", "kb_last_error", "kb_search_params_default", "kb_make_p
            "kb_batch_autotune", "kb_batch_stats", "kb_batch_destroy",
            "kb_cluster_workspace_size", "kb_cluster", "kb_l2_probe", "kb_wait_check",
            "kb_search_stage_counts", "kb_search_no_alloc_stats", "kb_smem_probe",
-           "kb_search_pass_counts")
+           "kb_search_pass_counts", "kb_batch_pass_counts")
 
 
 class KbError(RuntimeError):
@@ -63,7 +63,7 @@ class StackC(C.Structure):
 
 class ScheduleC(C.Structure):
     _fields_ = [("tile_order", C.c_int32), ("hot_nu2", C.c_float), ("score_span", C.c_int32),
-                ("stack_order", C.c_int32), ("mode", C.c_int32)]
+                ("stack_order", C.c_int32), ("mode", C.c_int32), ("tile_cols", C.c_int32)]
 
 
 _LIB = None
@@ -144,6 +144,8 @@ def lib():
     L.kb_batch_autotune.argtypes = [p, p, i, SCP]
     L.kb_batch_stats.restype = i
     L.kb_batch_stats.argtypes = [p, p, p, p]
+    L.kb_batch_pass_counts.restype = i
+    L.kb_batch_pass_counts.argtypes = [p, p, p]
     L.kb_batch_destroy.restype = None
     L.kb_batch_destroy.argtypes = [p]
     L.kb_cluster_workspace_size.restype = i

@@ -70,12 +70,12 @@ constexpr int S_PWARPS = 2;              // producer warps: iteration `it` belon
 constexpr int S_CTHREADS = S_CWARPS * 32;
 constexpr int S_THREADS = (S_CWARPS + S_PWARPS) * 32;
 constexpr int S_TY = S_CWARPS * S_ROWS;  // 56
-// Two-row-block kernels give each thread two columns (x and x + 32): tiles 64 wide, so a staged
-// box serves twice the start pixels for the same halo and one offset load serves two data loads.
-// Single-row kernels (which keep twice the sums per column) stay 32 wide.
-__host__ __device__ constexpr int tile_cols(bool pool) { return pool ? 2 : 1; }
-__host__ __device__ constexpr int tile_w(bool pool) { return S_TX * tile_cols(pool); }
+// Two-row-block kernels can give each thread two columns (x and x + 32): tiles 64 wide, so a
+// staged box serves twice the start pixels for the same halo and one offset load serves two data
+// loads (kb_schedule.tile_cols = 2, the default); with one column the tiles are 32 wide.
+// Single-row kernels (which keep twice the sums per column) are always 32 wide.
 constexpr int S_NPIX = 2 * S_TX * S_TY;  // start pixels of the widest tile (3584)
+constexpr int S_TILE_COLS_DEFAULT = 2;
 constexpr int S_C = 32;                  // trajectories per chunk
 constexpr int S_D = 8;                   // pipeline slots (iterations in flight), S_D % S_PWARPS == 0
 constexpr int S_ARENA_BYTES = 168 * 1024;  // rings of staged rectangles, one per producer
@@ -185,6 +185,8 @@ struct Ctrl {
   // bound-pass iterations (tile, chunk, epoch) by kind: staged box with per-trajectory offsets,
   // staged box with one offset for the chunk, direct global loads; and the bytes staged by TMA
   unsigned long long it_staged, it_uniform, it_direct, tma_bytes;
+  // 4-byte shared loads per trajectory of each bound-pass thread in the kernel that ran (1 or 2)
+  unsigned int loads_per_traj;
 };
 static_assert(sizeof(Ctrl) <= 256, "control block");
 
@@ -904,7 +906,7 @@ struct SearchArgs {
   EvalParams ep;
   int n_traj, nchunk, Wp;
   int x_lo, x_hi, y_lo, y_hi, ntx, nty, ntiles;
-  int tx;  // tile width in pixels: tile_w(pool)
+  int tx;  // tile width in pixels: 32 x columns per bound-pass thread
 };
 
 struct TmapSet {
@@ -1029,7 +1031,8 @@ template <bool BATCH>
 __device__ void producer_loop(const TmapSet& pmaps, const SearchArgs& A0, const BatchArgs& B,
                               unsigned char* ring, int ring_base, PlanRec* slots, int4* sinfo,
                               uint64_t* full, uint64_t* empty, unsigned int* s_abort,
-                              TileRing* tr, long long* issued_out, int pw, int lane) {
+                              TileRing* tr, long long* issued_out, int pw, int lane,
+                              unsigned int loads_per_traj) {
   Ctrl* const ctrl = BATCH ? B.ctrl : A0.ctrl;
   const int total_tiles = BATCH ? B.total_tiles : A0.ntiles;
   int cur_stack = -1;
@@ -1192,6 +1195,7 @@ __device__ void producer_loop(const TmapSet& pmaps, const SearchArgs& A0, const 
     if (last) break;
   }
   if (lane == 0) {
+    if (pw == 0 && blockIdx.x == 0) ctrl->loads_per_traj = loads_per_traj;
     atomicAdd(&ctrl->it_staged, n_staged);
     atomicAdd(&ctrl->it_uniform, n_uniform);
     atomicAdd(&ctrl->it_direct, n_direct);
@@ -1222,26 +1226,31 @@ __device__ __forceinline__ int4 lds_v4(uint32_t addr) {
 }
 
 // Sums one staged (chunk, epoch), a rectangle of `pitch`-word rows, into the fp16 accumulators.
-// POOL: the thread's two columns x and x + 32; per trajectory one address add, two shared loads
-// (the second at an immediate offset, 32 words on) and two fp16x2 adds; each word holds the
-// thread's two blocks of a column (acc[c]).  Otherwise one column, its two row pairs two rows
-// apart (acc[0] rows 0-1, acc[1] rows 2-3).  One code path for every box width (the pitch only
+// POOL, NCOL = 2: the thread's two columns x and x + 32; per trajectory one address add, two
+// shared loads (the second at an immediate offset, 32 words on) and two fp16x2 adds; each word
+// holds the thread's two blocks of a column (acc[c]).  POOL, NCOL = 1: one column, one load and
+// one add (acc[0]).  Otherwise one column, its two row pairs two rows apart (acc[0] rows 0-1,
+// acc[1] rows 2-3).  One code path for every box width (the pitch only
 // moves the row bases).  uniform: all trajectories share rel[0] (the same values in the same
 // order as the general path).
-template <bool POOL>
+template <bool POOL, int NCOL>
 __device__ __forceinline__ void accumulate_stage(__half2 (&acc)[2][S_C], const unsigned char* st,
                                                  int pitch, bool uniform, const PlanRec* slot,
                                                  int warp, int lane) {
+  // words per trajectory: two (two columns, or two row pairs), or one (two-row blocks of one
+  // column: both blocks of the thread in one word)
+  constexpr bool TWO = !(POOL && NCOL == 1);
   const uint32_t base = smem_u32(st) + (uint32_t)(warp * S_ROWS * pitch + lane) * 4u;
   const uint32_t base1 = base + 8u * (uint32_t)pitch;  // two rows further (single rows only)
   if (uniform) {
     const uint32_t r0 = (uint32_t)slot->rel[0];
     const uint32_t w0 = lds_u32(base + r0);
-    const uint32_t w1 = POOL ? lds_u32_off<4 * S_TX>(base + r0) : lds_u32(base1 + r0);
+    uint32_t w1 = 0u;
+    if (TWO) w1 = POOL ? lds_u32_off<4 * S_TX>(base + r0) : lds_u32(base1 + r0);
 #pragma unroll
     for (int v = 0; v < S_C; ++v) {
       acc[0][v] = __hadd2(acc[0][v], *reinterpret_cast<const __half2*>(&w0));
-      acc[1][v] = __hadd2(acc[1][v], *reinterpret_cast<const __half2*>(&w1));
+      if (TWO) acc[1][v] = __hadd2(acc[1][v], *reinterpret_cast<const __half2*>(&w1));
     }
     return;
   }
@@ -1254,9 +1263,11 @@ __device__ __forceinline__ void accumulate_stage(__half2 (&acc)[2][S_C], const u
     for (int u = 0; u < 4; ++u) {
       const uint32_t q = base + (uint32_t)rr[u];
       const uint32_t w0 = lds_u32(q);
-      const uint32_t w1 = POOL ? lds_u32_off<4 * S_TX>(q) : lds_u32(base1 + (uint32_t)rr[u]);
       acc[0][vq * 4 + u] = __hadd2(acc[0][vq * 4 + u], *reinterpret_cast<const __half2*>(&w0));
-      acc[1][vq * 4 + u] = __hadd2(acc[1][vq * 4 + u], *reinterpret_cast<const __half2*>(&w1));
+      if (TWO) {
+        const uint32_t w1 = POOL ? lds_u32_off<4 * S_TX>(q) : lds_u32(base1 + (uint32_t)rr[u]);
+        acc[1][vq * 4 + u] = __hadd2(acc[1][vq * 4 + u], *reinterpret_cast<const __half2*>(&w1));
+      }
     }
   }
 }
@@ -1298,7 +1309,7 @@ __device__ __noinline__ bool insert_sorted(const SearchArgs& A, size_t wp, int K
 // POOL: the bound planes hold two-row block maxima (see bound_prep_kernel); a passing block
 // queues both of its pixels.  Otherwise the planes hold single rows and each pixel is tested on
 // its own sum.
-template <int NT, int J, bool BATCH, bool POOL>
+template <int NT, int J, bool BATCH, bool POOL, int NCOL>
 __global__ void __launch_bounds__(S_THREADS, 1)
 search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const BatchArgs B) {
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -1331,9 +1342,12 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
   Ctrl* const ctrl = BATCH ? B.ctrl : A0.ctrl;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  // tile geometry of this kernel's bound kind: NCOL columns per thread, TXW = 2^TXS pixels wide
-  constexpr int NCOL = tile_cols(POOL), TXW = tile_w(POOL), TXS = POOL ? 6 : 5;
-  static_assert((1 << TXS) == TXW && TXW * S_TY <= S_NPIX, "tile geometry");
+  // tile geometry: NCOL columns per bound-pass thread, TXW = 2^TXS pixels wide; NACC fp16x2 sums
+  // per trajectory (two columns, or two row pairs, or one word of two blocks)
+  constexpr int TXW = S_TX * NCOL, TXS = NCOL == 2 ? 6 : 5;
+  constexpr int NACC = (POOL && NCOL == 1) ? 1 : 2;
+  static_assert((NCOL == 1 || (NCOL == 2 && POOL)) && (1 << TXS) == TXW && TXW * S_TY <= S_NPIX,
+                "tile geometry");
 
   for (int i = tid; i < S_NPIX; i += S_THREADS) head[i] = -1;
   if (tid == 0) {
@@ -1361,7 +1375,7 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
       for (int i = lane; i < S_NW * S_NH; i += 32) prefetch_tmap(&maps.m[i]);
     long long issued = -1;
     producer_loop<BATCH>(maps, A0, B, arena + pw * S_RING_BYTES, pw * S_RING_BYTES, slots, sinfo,
-                         full, empty, s_abort, tr, &issued, pw, lane);
+                         full, empty, s_abort, tr, &issued, pw, lane, (unsigned int)NACC);
     if (lane == 0) s_issued[pw] = issued;
   } else {
     // ------------------------------- consumer warps --------------------------------------
@@ -1520,9 +1534,11 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
           }
         };
         if (BATCH) {
-          if (T <= 16) by_thread(std::integral_constant<int, 16>{});
-          else if (T <= 32) by_thread(std::integral_constant<int, 32>{});
-          else if (T <= 64) by_warp(std::integral_constant<int, 2>{});
+          // two evaluation paths serve every stack (fewer registers than one per epoch class):
+          // the 32-wide network sorts a T <= 16 lightcurve into the same order as the 16-wide
+          // one, and four epochs per lane give the sums of two (the extra lanes add zeros), so
+          // the results are bit-identical to kb_search's
+          if (T <= 32) by_thread(std::integral_constant<int, 32>{});
           else by_warp(std::integral_constant<int, 4>{});
         } else if (NT > 0) {
           by_thread(std::integral_constant<int, (NT > 0 ? NT : 1)>{});
@@ -1577,7 +1593,7 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
         // otherwise (row 0, row 1) in acc[0] and (row 2, row 3) in acc[1]
         __half2 acc[2][S_C];
 #pragma unroll
-        for (int pp = 0; pp < 2; ++pp)
+        for (int pp = 0; pp < NACC; ++pp)
 #pragma unroll
           for (int v = 0; v < S_C; ++v) acc[pp][v] = __float2half2_rn(0.0f);
 
@@ -1590,7 +1606,7 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
             const unsigned char* st = arena + sinfo[slot].x;
             if (mode != 0) {
               const bool uni = (rec->box.w & S_UNIFORM_BIT) != 0;
-              accumulate_stage<POOL>(acc, st, stage_width(mode), uni, rec, warp, lane);
+              accumulate_stage<POOL, NCOL>(acc, st, stage_width(mode), uni, rec, warp, lane);
             } else {
               // direct loads from the block planes (word row = first image row + 3)
               const uint32_t* bp = A.bound + (size_t)t * (A.ep.H + 3) * A.Wp;
@@ -1598,7 +1614,7 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
               for (int v = 0; v < S_C; ++v) {
                 const int2 o = __ldg(A.offs + (size_t)(c * S_C + v) * T + t);
 #pragma unroll
-                for (int pp = 0; pp < 2; ++pp) {
+                for (int pp = 0; pp < NACC; ++pp) {
                   // POOL: column pp of the thread; otherwise its row pair pp
                   const int x = px + o.x + (POOL ? S_TX * pp : 0);
                   const int r = ty0 + warp * S_ROWS + (POOL ? 0 : 2 * pp) + o.y + 3;
@@ -1624,7 +1640,7 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
         // passing trajectories of the pixel in column cc, row i.
         uint32_t cb[NCOL * S_ROWS];
 #pragma unroll
-        for (int pp = 0; pp < 2; ++pp) {
+        for (int pp = 0; pp < NACC; ++pp) {
           const int o = POOL ? pp * S_ROWS : 0;  // thresholds of column pp (POOL)
           const __half2 th =
               POOL ? __halves2half2(half_round_down(fminf(thr2[o], thr2[o + 1])),
@@ -1842,6 +1858,15 @@ static bool pool_blocks(int T, float lh_min) {
 
 // Validates one stack, lays out its workspace, encodes its tensor maps and fills its kernel
 // arguments (no launch).  ctrl: the control block the search kernel will use.
+// Tiles of `cols` columns per bound-pass thread (32 * cols pixels wide; single-row bounds always
+// take one column) over the stack's window.
+static void set_tile_geometry(SearchArgs& A, bool pool, int cols) {
+  A.tx = S_TX * (pool ? cols : 1);
+  A.ntx = (A.x_hi - A.x_lo + A.tx - 1) / A.tx;
+  A.nty = (A.y_hi - A.y_lo + S_TY - 1) / S_TY;
+  A.ntiles = A.ntx * A.nty;
+}
+
 static int prepare_stack(const char* who, const float* psi, const float* phi, const double* times,
                          int T, int H, int W, const float* vx, const float* vy, int n_traj,
                          const kb_search_params* p, float* out_lh, float* out_flux,
@@ -1937,10 +1962,7 @@ static int prepare_stack(const char* who, const float* psi, const float* phi, co
   A.x_hi = p->x_hi;
   A.y_lo = p->y_lo;
   A.y_hi = p->y_hi;
-  A.tx = tile_w(sp.pool);
-  A.ntx = (p->x_hi - p->x_lo + A.tx - 1) / A.tx;
-  A.nty = (p->y_hi - p->y_lo + S_TY - 1) / S_TY;
-  A.ntiles = A.ntx * A.nty;
+  set_tile_geometry(A, sp.pool, S_TILE_COLS_DEFAULT);
   return KB_OK;
 }
 
@@ -2029,21 +2051,22 @@ static int launch_search_single(const StackPrep& sp, cudaStream_t st) {
     return fail(KB_ERR_UNSUPPORTED, "kb_search: %d SMs, at most %d supported", g_num_sms,
                 S_REC_BLOCKS);
   const size_t smem = SmemLayout::total;
-#define KB_SEARCH_LAUNCH(NT, JJ, PL)                                                           \
-  do {                                                                                         \
-    KB_CUDA_TRY(cudaFuncSetAttribute(search_kernel<NT, JJ, false, PL>,                         \
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-    search_kernel<NT, JJ, false, PL><<<grid, S_THREADS, smem, st>>>(sp.maps, A, BatchArgs{});  \
+#define KB_SEARCH_LAUNCH(NT, JJ, PL, NC)                                                          \
+  do {                                                                                           \
+    KB_CUDA_TRY(cudaFuncSetAttribute(search_kernel<NT, JJ, false, PL, NC>,                       \
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));   \
+    search_kernel<NT, JJ, false, PL, NC><<<grid, S_THREADS, smem, st>>>(sp.maps, A, BatchArgs{}); \
   } while (0)
-#define KB_SEARCH_LAUNCH_T(PL)                  \
-  do {                                          \
-    if (T <= 16) KB_SEARCH_LAUNCH(16, 1, PL);   \
-    else if (T <= 32) KB_SEARCH_LAUNCH(32, 1, PL); \
-    else if (T <= 64) KB_SEARCH_LAUNCH(0, 2, PL);  \
-    else KB_SEARCH_LAUNCH(0, 4, PL);            \
+#define KB_SEARCH_LAUNCH_T(PL, NC)                     \
+  do {                                                 \
+    if (T <= 16) KB_SEARCH_LAUNCH(16, 1, PL, NC);      \
+    else if (T <= 32) KB_SEARCH_LAUNCH(32, 1, PL, NC); \
+    else if (T <= 64) KB_SEARCH_LAUNCH(0, 2, PL, NC);  \
+    else KB_SEARCH_LAUNCH(0, 4, PL, NC);               \
   } while (0)
-  if (sp.pool) KB_SEARCH_LAUNCH_T(true);
-  else KB_SEARCH_LAUNCH_T(false);
+  if (!sp.pool) KB_SEARCH_LAUNCH_T(false, 1);
+  else if (A.tx == 2 * S_TX) KB_SEARCH_LAUNCH_T(true, 2);
+  else KB_SEARCH_LAUNCH_T(true, 1);
 #undef KB_SEARCH_LAUNCH_T
 #undef KB_SEARCH_LAUNCH
   KB_LAUNCH_CHECK("search_kernel");
@@ -2052,7 +2075,7 @@ static int launch_search_single(const StackPrep& sp, cudaStream_t st) {
 
 // hot_nu2 64: with block maxima in the planes a lower threshold counts noise; on decam_half
 // 16 -> 64 took the search from 276.5 to 272.7 ms (25..100 all within 0.5%)
-static const kb_schedule kDefaultSchedule = {1, 64.0f, 64, 1, 1};
+static const kb_schedule kDefaultSchedule = {1, 64.0f, 64, 1, 1, S_TILE_COLS_DEFAULT};
 
 static int check_schedule(const kb_schedule* s) {
   if (!s) return fail(KB_ERR_INVALID_ARG, "schedule: null pointer");
@@ -2065,6 +2088,8 @@ static int check_schedule(const kb_schedule* s) {
   if (s->score_span < 0 || s->score_span > (1 << 20))
     return fail(KB_ERR_INVALID_ARG, "schedule: score_span outside 0..2^20");
   if (s->mode != 0 && s->mode != 1) return fail(KB_ERR_INVALID_ARG, "schedule: mode must be 0 or 1");
+  if (s->tile_cols != 1 && s->tile_cols != 2)
+    return fail(KB_ERR_INVALID_ARG, "schedule: tile_cols must be 1 or 2");
   return KB_OK;
 }
 
@@ -2136,6 +2161,7 @@ __global__ void batch_sum_kernel(Ctrl* const* __restrict__ ctrls, int n, Ctrl* t
     total->it_uniform += ctrls[k]->it_uniform;
     total->it_direct += ctrls[k]->it_direct;
     total->tma_bytes += ctrls[k]->tma_bytes;
+    total->loads_per_traj = max(total->loads_per_traj, ctrls[k]->loads_per_traj);
   }
   total->evals = ev;
   total->inserts = ins;
@@ -2292,7 +2318,10 @@ static int batch_enqueue(kb_batch* b, cudaStream_t st) {
   B.done_tiles = done_tiles;
   B.done_ns = done_ns;
   const size_t smem = SmemLayout::total;
-  auto kern = pool ? search_kernel<0, 1, true, true> : search_kernel<0, 1, true, false>;
+  // every stack of the batch has the batch's bound kind and tile width
+  const bool wide = b->sp[0].A.tx == 2 * S_TX;
+  auto kern = !pool ? search_kernel<0, 1, true, false, 1>
+                    : (wide ? search_kernel<0, 1, true, true, 2> : search_kernel<0, 1, true, true, 1>);
   KB_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int grid = std::min(b->total_tiles, g_num_sms);
   if (grid > S_REC_BLOCKS)
@@ -2454,6 +2483,7 @@ extern "C" int kb_batch_set_schedule(kb_batch* b, const kb_schedule* s) {
   KB_CUDA_TRY(cudaDeviceSynchronize());
   b->sch = *s;
   drop_graph(b);
+  for (kb::StackPrep& sp : b->sp) set_tile_geometry(sp.A, sp.pool, s->tile_cols);
   return write_tables(b);
 }
 
@@ -2501,6 +2531,11 @@ extern "C" int kb_batch_autotune(kb_batch* b, void* stream, int reps, kb_schedul
       kb_schedule c = cur;
       c.tile_order = 1 - cur.tile_order;
       cand.push_back(c);
+      if (b->sp[0].pool) {  // the tile width (two-row blocks only)
+        c = cur;
+        c.tile_cols = 3 - cur.tile_cols;
+        cand.push_back(c);
+      }
     } else if (pass == 2 && cur.tile_order) {
       for (float h : hot)
         if (h != cur.hot_nu2) {
@@ -2599,23 +2634,43 @@ extern "C" int kb_search_stage_counts(const void* workspace, unsigned long long*
   return KB_OK;
 }
 
-extern "C" int kb_search_pass_counts(const void* workspace, unsigned long long* out,
-                                     void* stream) {
-  using namespace kb;
-  if (!workspace || !out) return fail(KB_ERR_INVALID_ARG, "kb_search_pass_counts: null pointer");
-  Ctrl c{};
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  KB_CUDA_TRY(cudaMemcpyAsync(&c, workspace, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
-  KB_CUDA_TRY(cudaStreamSynchronize(st));
-  // per (tile, chunk, epoch): each bound-pass thread makes two 4-byte shared loads per
-  // trajectory (its two columns, or its two row pairs), or two in all when the chunk shares
-  // one offset; and one 16-byte offset load per four trajectories (a warp-wide broadcast)
-  const unsigned long long words = 2ull * S_CTHREADS;
+namespace kb {
+
+// Shared-memory traffic of the bound pass from a control block's counters.
+static void pass_counts_of(const Ctrl& c, unsigned long long* out) {
+  // per (tile, chunk, epoch): each bound-pass thread makes one or two 4-byte shared loads per
+  // trajectory (two: its two columns, or its two row pairs; one: two-row blocks of one column),
+  // and as many in all when the chunk shares one offset; and one 16-byte offset load per four
+  // trajectories (a warp-wide broadcast)
+  const unsigned long long words = (unsigned long long)c.loads_per_traj * S_CTHREADS;
   out[0] = (c.it_staged * S_C + c.it_uniform) * words * 4ull;
   out[1] = c.it_staged * (unsigned long long)(S_C / 4) * S_CWARPS * 16ull;
   out[2] = c.tma_bytes;
   out[3] = c.it_direct;
+}
+
+static int read_pass_counts(const char* who, const void* ctrl, unsigned long long* out,
+                            void* stream) {
+  if (!ctrl || !out) return fail(KB_ERR_INVALID_ARG, "%s: null pointer", who);
+  Ctrl c{};
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  KB_CUDA_TRY(cudaMemcpyAsync(&c, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+  KB_CUDA_TRY(cudaStreamSynchronize(st));
+  pass_counts_of(c, out);
   return KB_OK;
+}
+
+}  // namespace kb
+
+extern "C" int kb_search_pass_counts(const void* workspace, unsigned long long* out,
+                                     void* stream) {
+  return kb::read_pass_counts("kb_search_pass_counts", workspace, out, stream);
+}
+
+extern "C" int kb_batch_pass_counts(kb_batch* b, unsigned long long* out, void* stream) {
+  using namespace kb;
+  if (!b) return fail(KB_ERR_INVALID_ARG, "kb_batch_pass_counts: null batch");
+  return read_pass_counts("kb_batch_pass_counts", b->ws + b->tb.ctrl, out, stream);
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -118,6 +118,7 @@ def test_other_entry_points_validate(L):
     assert L.kb_search_stage_counts(FAKE, None, None) == K.KB_ERR_INVALID_ARG
     assert L.kb_search_pass_counts(None, arr, None) == K.KB_ERR_INVALID_ARG
     assert L.kb_search_pass_counts(FAKE, None, None) == K.KB_ERR_INVALID_ARG
+    assert L.kb_batch_pass_counts(None, arr, None) == K.KB_ERR_INVALID_ARG
     assert L.kb_search_no_alloc_stats(None, None) == K.KB_ERR_INVALID_ARG
     assert L.kb_make_psi_phi(FAKE, FAKE, None, FAKE, 5, 10, 10, 4, FAKE, FAKE, None) == \
         K.KB_ERR_INVALID_ARG

@@ -84,19 +84,22 @@ def test_batch_equals_per_stack_search(cuda_device, batch_case):
 
 
 @pytest.mark.parametrize("mode", [0, 1])
-def test_batch_two_row_blocks(cuda_device, batch_case, mode):
+@pytest.mark.parametrize("tile_cols", [1, 2])
+def test_batch_two_row_blocks(cuda_device, batch_case, mode, tile_cols):
     """Every stack summed over two-row blocks (bound_rows = 2; the automatic choice takes single
-    rows for these small thresholds), so one persistent launch (mode 0) runs the block kernel:
-    results still bit-identical to kb_search with single rows."""
+    rows for these small thresholds), so one persistent launch (mode 0) runs the block kernel, in
+    tiles 32 or 64 pixels wide: results still bit-identical to kb_search with single rows."""
     stacks, ref = batch_case
     blocks = [dict(s, params=dataclasses.replace(s["params"], bound_rows=2)) for s in stacks]
     b = kb.Batch(blocks)
-    b.schedule = kb.Schedule(mode=mode)
+    b.schedule = kb.Schedule(mode=mode, tile_cols=tile_cols)
     res = b.run(graph=True)
     torch.cuda.synchronize()
     for i, (r, g) in enumerate(zip(ref, res)):
-        assert _equal(r, g), "stack %d differs (mode %d)" % (i, mode)
+        assert _equal(r, g), "stack %d differs (mode %d, tile_cols %d)" % (i, mode, tile_cols)
     assert b.stats()[1]["err"] == 0
+    words, offsets, staged, direct = b.pass_counts()
+    assert words > 0 and offsets > 0 and staged > 0
 
 
 def test_batch_graph_replay_and_schedules(cuda_device, batch_case):
@@ -104,7 +107,8 @@ def test_batch_graph_replay_and_schedules(cuda_device, batch_case):
     b = kb.Batch(stacks)
     for sched in (kb.Schedule(), kb.Schedule(mode=0), kb.Schedule(tile_order=0, stack_order=0),
                   kb.Schedule(mode=0, hot_nu2=9.0, score_span=128, stack_order=0),
-                  kb.Schedule(score_span=0)):
+                  kb.Schedule(score_span=0), kb.Schedule(tile_cols=1),
+                  kb.Schedule(mode=0, tile_cols=1, tile_order=0)):
         b.schedule = sched
         assert b.schedule == sched
         for _ in range(2):          # capture, then replay
@@ -127,6 +131,8 @@ def test_batch_graph_replay_and_schedules(cuda_device, batch_case):
         b.schedule = kb.Schedule(hot_nu2=0.0)
     with pytest.raises(kb.KbError):
         b.schedule = kb.Schedule(mode=3)
+    with pytest.raises(kb.KbError):
+        b.schedule = kb.Schedule(tile_cols=3)
 
 
 def test_batch_stacks_against_oracle(cuda_device, batch_case):
