@@ -80,7 +80,7 @@ constexpr int S_NPIX = 2 * S_TX * S_TY;  // start pixels of the widest tile (358
 constexpr int S_TILE_COLS_DEFAULT = 2;
 constexpr int S_C = 32;                  // trajectories per chunk
 constexpr int S_D = 8;                   // pipeline slots (iterations in flight), S_D % S_PWARPS == 0
-constexpr int S_ARENA_BYTES = 168 * 1024;  // rings of staged rectangles, one per producer
+constexpr int S_ARENA_BYTES = 184 * 1024;  // rings of staged rectangles, one per producer
 constexpr int S_RING_BYTES = S_ARENA_BYTES / S_PWARPS;
 constexpr int S_REGION_MAX = 64 * 1024;  // larger rectangles use direct loads
 constexpr int S_QCAP = 2048;             // block queue of full evaluations
