@@ -9,14 +9,17 @@ trajectory-epoch evaluations per second: start pixels x trajectories x epochs of
 the step's device time.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+  python bench.py --workload full             # 4096^2, T=100, the paper's 512 x 256 grid
   python bench.py --workload decam_refine     # off-grid refinement of the best candidates
-  python bench.py --workload batch64          # 64 uneven stacks: one persistent launch vs 64
+  python bench.py --workload batch64          # 64 uneven stacks as one batch vs 64 launches
 
-The batch64 line times the search of 64 stacks of uneven size and epoch count (one step = all 64)
-as one persistent launch replayed from a CUDA graph, after autotuning its schedule, against the
-same 64 searches as separate kb_search launches; it reports both throughputs and the per-stack
-latencies (completion time from the start of the step), and checks that both give identical
-results.
+The full line runs the same step on the full-scale stack (drawn on the device with the same
+recipe; numpy would take minutes).  The batch64 line times the search of 64 stacks of uneven
+size and epoch count (one step = all 64) as one batch replayed from a CUDA graph, under the
+schedule its autotuner picks (one persistent launch, or per-stack launches on four streams; the
+tile width), against the same 64 searches as separate kb_search launches; it reports both
+throughputs and the per-stack latencies (completion time from the start of the step), and
+checks that both give identical results.
 
 The decam_refine line times the refinement stage on its own: the stack is searched once, the
 best --n-refine survivors are gathered, and one step = 20 Adam steps of every candidate

@@ -76,19 +76,16 @@ constexpr int S_TY = S_CWARPS * S_ROWS;  // 56
 // staged box serves twice the start pixels for the same halo and one offset load serves two data
 // loads (kb_schedule.tile_cols = 2, the default); with one column the tiles are 32 wide.
 // Single-row kernels (which keep twice the sums per column) are always 32 wide.
-constexpr int S_NPIX = 2 * S_TX * S_TY;  // start pixels of the widest tile (3584)
 constexpr int S_TILE_COLS_DEFAULT = 2;
 constexpr int S_C = 32;                  // trajectories per chunk
 constexpr int S_D = 8;                   // pipeline slots (iterations in flight), S_D % S_PWARPS == 0
-constexpr int S_ARENA_BYTES = 184 * 1024;  // rings of staged rectangles, one per producer
-constexpr int S_RING_BYTES = S_ARENA_BYTES / S_PWARPS;
 constexpr int S_REGION_MAX = 64 * 1024;  // larger rectangles use direct loads
 constexpr int S_QCAP = 2048;             // block queue of full evaluations
 constexpr int S_FLUSH_MIN = 2 * S_CTHREADS;  // evaluate once the queue holds two pairs per thread
 constexpr int S_REC_WORDS = 8;           // L', alpha, nvalid|nkept<<16, mask[4], pad
 constexpr int S_REC_BLOCKS = 256;        // most blocks of a launch (records in the workspace)
 constexpr float S_PRUNE_MARGIN = 1.0f - 1e-4f;
-static_assert(S_D % S_PWARPS == 0 && S_REGION_MAX <= S_RING_BYTES, "pipeline configuration");
+static_assert(S_D % S_PWARPS == 0, "pipeline configuration");
 static_assert((S_D & (S_D - 1)) == 0, "slot indices from a 32-bit iteration count");
 // A staged rectangle is one TMA box: width class w = 1..S_NW (rows of 32, 40, ..., 128 words)
 // and height class h = 0..S_NH-1 (S_TY, S_TY + 8, ..., 128 word rows); mode 0 = direct global
@@ -1040,24 +1037,44 @@ __device__ __forceinline__ void tmap_acquire(const void* tmap) {
                : "memory");
 }
 
+// Shared memory of one kernel instance: the staging arena (one ring of staged rectangles per
+// producer) and the tables, the pixel tables sized for the instance's tile width and the
+// survivor list only where a thread-per-pair evaluation uses it.  The unified L1/shared memory
+// of an SM is split in fixed steps (228, 196, 164, ... KB of shared memory); the driver takes the
+// smallest step that holds the block and the rest is L1, which caches the evaluations' gathers.
+// So the arena is sized per instance (arena_kb) to land below a step: 152 KB keeps every block
+// under 196 KB (about 60 KB of L1; decam_half 226.8 ms with a 184 KB arena and 28 KB of L1,
+// 224.6 ms with this), and the T > 32 kernels, whose evaluations dominate, keep 136 KB under
+// 164 KB (about 92 KB of L1).
+__host__ __device__ constexpr int arena_kb(int nt, bool batch, bool pool, int ncol) {
+  return (nt == 0 && !batch) ? 136 : 152;
+}
+
+template <int NT, bool BATCH, bool POOL, int NCOL>
 struct SmemLayout {
+  static constexpr int arena_bytes = arena_kb(NT, BATCH, POOL, NCOL) * 1024;
+  static constexpr int ring_bytes = arena_bytes / S_PWARPS;
+  static constexpr int npix = S_TX * NCOL * S_TY;  // start pixels of a tile
+  static constexpr bool has_surv = NT > 0 || BATCH;
   static constexpr size_t arena = 0;
-  static constexpr size_t qtraj = arena + S_ARENA_BYTES;
+  static constexpr size_t qtraj = arena + arena_bytes;
   static constexpr size_t qpix = qtraj + S_QCAP * sizeof(int32_t);
   static constexpr size_t qnext = qpix + S_QCAP * sizeof(uint16_t);
   static constexpr size_t surv = qnext + S_QCAP * sizeof(int16_t);  // pairs past the filter
-  static constexpr size_t head = (surv + S_QCAP * sizeof(int16_t) + 15) / 16 * 16;  // [pixel]
-  static constexpr size_t filled = head + S_NPIX * sizeof(int32_t);
-  static constexpr size_t slots = (filled + S_NPIX + 15) / 16 * 16;          // S_D plan records
+  static constexpr size_t head =
+      (surv + (has_surv ? S_QCAP * sizeof(int16_t) : 0) + 15) / 16 * 16;  // [pixel]
+  static constexpr size_t filled = head + npix * sizeof(int32_t);
+  static constexpr size_t slots = (filled + npix + 15) / 16 * 16;          // S_D plan records
   static constexpr size_t sinfo = slots + S_D * sizeof(PlanRec);  // S_D x {offset, tile, bytes}
   static constexpr size_t full = sinfo + S_D * sizeof(int4);       // S_D mbarriers: data landed
   static constexpr size_t empty = full + S_D * sizeof(uint64_t);   // S_D mbarriers: slot released
   static constexpr size_t misc = empty + S_D * sizeof(uint64_t);
   static constexpr size_t sargs = misc + 128;  // consumers' copy of the tile's stack arguments
   static constexpr size_t total = sargs + (sizeof(SearchArgs) + 15) / 16 * 16;
+  static_assert(total <= 232448, "shared memory budget");
+  static_assert(slots % 16 == 0 && full % 8 == 0, "alignment");
+  static_assert(S_REGION_MAX <= ring_bytes, "a ring holds the largest staged rectangle");
 };
-static_assert(SmemLayout::total <= 232448, "shared memory budget");
-static_assert(SmemLayout::slots % 16 == 0 && SmemLayout::full % 8 == 0, "alignment");
 
 // Admission threshold of a pixel for the fp16 bound sums.  With every stored term rounded up,
 // an RN fp16 sum of T non-negative terms satisfies  exact <= sum (1 + 2^-11)^T + T 2^-25  (the
@@ -1130,7 +1147,7 @@ __device__ void producer_loop(const TmapSet& pmaps, const SearchArgs& A0, const 
                               unsigned char* ring, int ring_base, PlanRec* slots, int4* sinfo,
                               uint64_t* full, uint64_t* empty, unsigned int* s_abort,
                               TileRing* tr, long long* issued_out, int pw, int lane,
-                              unsigned int loads_per_traj) {
+                              unsigned int loads_per_traj, int ring_bytes) {
   Ctrl* const ctrl = BATCH ? B.ctrl : A0.ctrl;
   const int total_tiles = BATCH ? B.total_tiles : A0.ntiles;
   int cur_stack = -1;
@@ -1226,7 +1243,7 @@ __device__ void producer_loop(const TmapSet& pmaps, const SearchArgs& A0, const 
               head = tail = 0;
               pos = 0;
             } else if (head > tail) {
-              if (head + sz <= S_RING_BYTES) pos = head;
+              if (head + sz <= ring_bytes) pos = head;
               else if (sz <= tail) pos = 0;
               else room = false;
             } else if (head + sz <= tail) {
@@ -1411,32 +1428,33 @@ template <int NT, int J, bool BATCH, bool POOL, int NCOL>
 __global__ void __launch_bounds__(S_THREADS, 1)
 search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const BatchArgs B) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* arena = smem + SmemLayout::arena;
-  int32_t* q_traj = reinterpret_cast<int32_t*>(smem + SmemLayout::qtraj);
-  uint16_t* q_pix = reinterpret_cast<uint16_t*>(smem + SmemLayout::qpix);
-  int16_t* q_next = reinterpret_cast<int16_t*>(smem + SmemLayout::qnext);
-  int16_t* q_surv = reinterpret_cast<int16_t*>(smem + SmemLayout::surv);
-  PlanRec* slots = reinterpret_cast<PlanRec*>(smem + SmemLayout::slots);
-  int4* sinfo = reinterpret_cast<int4*>(smem + SmemLayout::sinfo);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + SmemLayout::full);
-  uint64_t* empty = reinterpret_cast<uint64_t*>(smem + SmemLayout::empty);
-  int* head = reinterpret_cast<int*>(smem + SmemLayout::head);
-  uint8_t* s_filled = reinterpret_cast<uint8_t*>(smem + SmemLayout::filled);
-  unsigned int* s_qcount = reinterpret_cast<unsigned int*>(smem + SmemLayout::misc);
+  using SL = SmemLayout<NT, BATCH, POOL, NCOL>;
+  unsigned char* arena = smem + SL::arena;
+  int32_t* q_traj = reinterpret_cast<int32_t*>(smem + SL::qtraj);
+  uint16_t* q_pix = reinterpret_cast<uint16_t*>(smem + SL::qpix);
+  int16_t* q_next = reinterpret_cast<int16_t*>(smem + SL::qnext);
+  int16_t* q_surv = reinterpret_cast<int16_t*>(smem + SL::surv);
+  PlanRec* slots = reinterpret_cast<PlanRec*>(smem + SL::slots);
+  int4* sinfo = reinterpret_cast<int4*>(smem + SL::sinfo);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + SL::full);
+  uint64_t* empty = reinterpret_cast<uint64_t*>(smem + SL::empty);
+  int* head = reinterpret_cast<int*>(smem + SL::head);
+  uint8_t* s_filled = reinterpret_cast<uint8_t*>(smem + SL::filled);
+  unsigned int* s_qcount = reinterpret_cast<unsigned int*>(smem + SL::misc);
   unsigned int* s_evals = s_qcount + 1;
   unsigned int* s_ins = s_qcount + 2;
   unsigned int* s_abort = s_qcount + 3;
   int* s_tile = reinterpret_cast<int*>(s_qcount + 4);
   TileRing* tr = reinterpret_cast<TileRing*>(s_qcount + 5);       // 20 bytes
   int* s_stack = reinterpret_cast<int*>(s_qcount + 10);
-  long long* s_issued = reinterpret_cast<long long*>(smem + SmemLayout::misc + 48);  // [2]
+  long long* s_issued = reinterpret_cast<long long*>(smem + SL::misc + 48);  // [2]
   // stage counters: pairs with n_valid >= min_obs, pairs reaching lh_min, and the sums of
   // n_kept and n_valid over the latter
-  unsigned int* s_stage = reinterpret_cast<unsigned int*>(smem + SmemLayout::misc + 64);     // [2]
+  unsigned int* s_stage = reinterpret_cast<unsigned int*>(smem + SL::misc + 64);     // [2]
   unsigned long long* s_stage64 =
-      reinterpret_cast<unsigned long long*>(smem + SmemLayout::misc + 80);                   // [2]
+      reinterpret_cast<unsigned long long*>(smem + SL::misc + 80);                   // [2]
   // s_stage[2] (misc + 72): pairs of the current flush that need the full evaluation
-  SearchArgs* s_args = reinterpret_cast<SearchArgs*>(smem + SmemLayout::sargs);
+  SearchArgs* s_args = reinterpret_cast<SearchArgs*>(smem + SL::sargs);
   Ctrl* const ctrl = BATCH ? B.ctrl : A0.ctrl;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1444,10 +1462,10 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
   // per trajectory (two columns, or two row pairs, or one word of two blocks)
   constexpr int TXW = S_TX * NCOL, TXS = NCOL == 2 ? 6 : 5;
   constexpr int NACC = (POOL && NCOL == 1) ? 1 : 2;
-  static_assert((NCOL == 1 || (NCOL == 2 && POOL)) && (1 << TXS) == TXW && TXW * S_TY <= S_NPIX,
+  static_assert((NCOL == 1 || (NCOL == 2 && POOL)) && (1 << TXS) == TXW && TXW * S_TY == SL::npix,
                 "tile geometry");
 
-  for (int i = tid; i < S_NPIX; i += S_THREADS) head[i] = -1;
+  for (int i = tid; i < SL::npix; i += S_THREADS) head[i] = -1;
   if (tid == 0) {
     for (int i = 0; i < S_D; ++i) {
       mbar_init(&full[i], 1);
@@ -1472,8 +1490,9 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
     if (!BATCH && pw == 0)
       for (int i = lane; i < S_NW * S_NH; i += 32) prefetch_tmap(&maps.m[i]);
     long long issued = -1;
-    producer_loop<BATCH>(maps, A0, B, arena + pw * S_RING_BYTES, pw * S_RING_BYTES, slots, sinfo,
-                         full, empty, s_abort, tr, &issued, pw, lane, (unsigned int)NACC);
+    producer_loop<BATCH>(maps, A0, B, arena + pw * SL::ring_bytes, pw * SL::ring_bytes, slots,
+                         sinfo, full, empty, s_abort, tr, &issued, pw, lane, (unsigned int)NACC,
+                         SL::ring_bytes);
     if (lane == 0) s_issued[pw] = issued;
   } else {
     // ------------------------------- consumer warps --------------------------------------
@@ -2158,9 +2177,9 @@ static int launch_search_single(const StackPrep& sp, cudaStream_t st) {
   if (grid > S_REC_BLOCKS)
     return fail(KB_ERR_UNSUPPORTED, "kb_search: %d SMs, at most %d supported", g_num_sms,
                 S_REC_BLOCKS);
-  const size_t smem = SmemLayout::total;
 #define KB_SEARCH_LAUNCH(NT, JJ, PL, NC)                                                          \
   do {                                                                                           \
+    const size_t smem = SmemLayout<NT, false, PL, NC>::total;                                    \
     KB_CUDA_TRY(cudaFuncSetAttribute(search_kernel<NT, JJ, false, PL, NC>,                       \
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));   \
     search_kernel<NT, JJ, false, PL, NC><<<grid, S_THREADS, smem, st>>>(sp.maps, A, BatchArgs{}); \
@@ -2425,11 +2444,13 @@ static int batch_enqueue(kb_batch* b, cudaStream_t st) {
   B.ctrl = ctrl;
   B.done_tiles = done_tiles;
   B.done_ns = done_ns;
-  const size_t smem = SmemLayout::total;
   // every stack of the batch has the batch's bound kind and tile width
   const bool wide = b->sp[0].A.tx == 2 * S_TX;
   auto kern = !pool ? search_kernel<0, 1, true, false, 1>
                     : (wide ? search_kernel<0, 1, true, true, 2> : search_kernel<0, 1, true, true, 1>);
+  const size_t smem = !pool ? SmemLayout<0, true, false, 1>::total
+                            : (wide ? SmemLayout<0, true, true, 2>::total
+                                    : SmemLayout<0, true, true, 1>::total);
   KB_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int grid = std::min(b->total_tiles, g_num_sms);
   if (grid > S_REC_BLOCKS)
