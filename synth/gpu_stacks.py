@@ -35,6 +35,16 @@ def batch_specs(cfg=BATCH64):
     return out
 
 
+def _add_unique(img, idx, val, device):
+    """img.view(-1)[idx] += val with repeated indices summed on the host first (float64), so that
+    the device add sees each pixel once and the stack is the same bit for bit in every process
+    (an index_add_ with repeated indices adds in an order that varies between runs)."""
+    import torch
+    uniq, inv = np.unique(np.asarray(idx, np.int64), return_inverse=True)
+    sums = np.bincount(inv.ravel(), weights=np.asarray(val, np.float64).ravel()).astype(np.float32)
+    img.view(-1).index_add_(0, torch.from_numpy(uniq).to(device), torch.from_numpy(sums).to(device))
+
+
 def make_stack_torch(H, W, T, n_speed, n_angle, n_movers, seed, device, v=(90.0, 500.0),
                      a=(-0.3, 0.3)):
     """Returns dict(img, var, mask, psf (torch on device), times, vx, vy (torch), movers)."""
@@ -83,9 +93,7 @@ def make_stack_torch(H, W, T, n_speed, n_angle, n_movers, seed, device, v=(90.0,
             idx.append((t * H + yy[ok]) * W + xx[ok])
             val.append(st[ok])
     if idx:
-        ii = torch.from_numpy(np.concatenate(idx).astype(np.int64)).to(device)
-        vv = torch.from_numpy(np.concatenate(val).astype(np.float32)).to(device)
-        img.view(-1).index_add_(0, ii, vv)
+        _add_unique(img, np.concatenate(idx), np.concatenate(val), device)
     mask = torch.rand((T, H, W), generator=g, device=device) < 0.005
     var[mask] = float("inf")
     movers = dict(x0=x0, y0=y0, vx=mvx, vy=mvy, snr=snr, spike=spike)
@@ -157,9 +165,7 @@ def make_config_stack_torch(name, device, seed=None, H=None, W=None, n_movers=No
         ok = (yy >= 0) & (yy < H) & (xx >= 0) & (xx < W)
         idx.append((t * H + yy[ok]) * W + xx[ok])
         val.append(st[ok])
-    ii = torch.from_numpy(np.concatenate(idx).astype(np.int64)).to(device)
-    vv = torch.from_numpy(np.concatenate(val).astype(np.float32)).to(device)
-    img.view(-1).index_add_(0, ii, vv)
+    _add_unique(img, np.concatenate(idx), np.concatenate(val), device)
     mask = torch.rand((T, H, W), generator=g, device=device) < c["mask_frac"]
     var[mask] = float("inf")
     movers = dict(x0=x0, y0=y0, vx=mvx, vy=mvy, snr=snr, spike=spike)
