@@ -35,14 +35,14 @@
 //
 //  * Full evaluation.  After each chunk, the pairs whose bound passes are appended to a queue
 //    in shared memory; once it holds S_FLUSH_MIN pairs the largest whole number of rounds (one
-//    pair per consumer thread, or per warp) is evaluated and the rest stays queued, and at the
+//    pair per consumer thread, half-warp or warp) is evaluated and the rest stays queued, and at the
 //    end of a tile everything, so no round leaves threads idle and no warp waits at a barrier for
 //    a lone candidate.  For T <= 32 one thread evaluates one pair: gather into registers, an
 //    exact filter that drops pairs which cannot reach lh_min once the epochs the clip must
 //    reject are left out, then for the rest a bitonic sorting network on the lightcurve,
 //    percentiles, clip, sums in epoch order (identical tracks give bit-identical LH').  For
-//    T > 32 a warp evaluates one pair with lanes over epochs, with an exact filter of the same
-//    kind before its sort.  Results that reach lh_min (a small fraction) are pushed onto
+//    32 < T <= 64 a half-warp evaluates one pair with lanes over epochs (two pairs per warp),
+//    for T > 64 a warp, each with an exact filter of the same kind before its sort.  Results that reach lh_min (a small fraction) are pushed onto
 //    a per-pixel list; the owner thread of each start pixel then walks its list and inserts
 //    them into the pixel's output list (LH' descending, trajectory index ascending).
 #include <cuda.h>
@@ -749,6 +749,271 @@ __device__ float eval_pair_warp(const float2* __restrict__ pairs, const EvalPara
 }
 
 // ---------------------------------------------------------------------------------------------
+// Half-warp full evaluation (32 < T <= 64): lanes 0-15 evaluate one (start pixel, trajectory)
+// pair and lanes 16-31 another, with the same instruction stream.  Epoch t = 16 j + h (h = lane & 15) is
+// slot j of lane h of the pair's half; J slots hold up to 16 J epochs.
+// ---------------------------------------------------------------------------------------------
+constexpr unsigned int kAll = 0xffffffffu;
+
+// Sum over the 16 lanes of each half (every lane of a half gets its half's sum, in an order that
+// depends on the lane: callers take one lane's value).
+__device__ __forceinline__ float half_sum(float v) {
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(kAll, v, o);
+  return v;
+}
+
+// Ascending bitonic sort of each half's 16 J values (index (j << 4) | h): exchanges between
+// lanes (distance < 16) stay inside the half; longer ones are between slots of a lane.
+template <int J>
+__device__ __forceinline__ void half_bitonic_sort(float (&v)[J], int h) {
+#pragma unroll
+  for (int k = 2; k <= 16 * J; k <<= 1) {
+#pragma unroll
+    for (int d = k >> 1; d > 0; d >>= 1) {
+      if (d >= 16) {
+        const int dj = d >> 4;
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+          const int jp = j ^ dj;
+          if (jp > j) {
+            const bool up = (((j << 4) | h) & k) == 0;
+            const float x = v[j], y = v[jp];
+            const float lo = fminf(x, y), hi = fmaxf(x, y);
+            v[j] = up ? lo : hi;
+            v[jp] = up ? hi : lo;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+          const float other = __shfl_xor_sync(kAll, v[j], d);
+          const bool up = (((j << 4) | h) & k) == 0;
+          const bool lower = (h & d) == 0;
+          v[j] = (lower == up) ? fminf(v[j], other) : fmaxf(v[j], other);
+        }
+      }
+    }
+  }
+}
+
+// Element r of each half's sorted values (r may differ between the halves; hb = lane & 16).
+template <int J>
+__device__ __forceinline__ float half_get_sorted(const float (&v)[J], int r, int hb) {
+  float x = v[0];
+#pragma unroll
+  for (int j = 1; j < J; ++j)
+    if ((r >> 4) == j) x = v[j];
+  return __shfl_sync(kAll, x, hb | (r & 15));
+}
+
+// Percentile of the n smallest sorted values from its rank entry r = {lo, frac} (rank_table).
+template <int J>
+__device__ __forceinline__ float half_percentile(const float (&s)[J], int n, int2 r, int hb) {
+  const int lo = r.x, hi = min(lo + 1, n - 1);
+  const float f = __int_as_float(r.y);
+  const float a = half_get_sorted<J>(s, lo, hb), b = half_get_sorted<J>(s, hi, hb);
+  return a + f * (b - a);
+}
+
+// The gathered (psi, phi) of one pair for a half-warp.
+template <int J>
+struct HalfPair {
+  float ps[J], ph[J];
+  uint32_t inb;  // bit j: epoch 16 j + h lies on the image
+};
+
+// Issues the loads of one pair (none for a half without a pair).  The track offsets are
+// recomputed from the pair's velocity with the plan's own arithmetic (track_offset on the same
+// float dt), bit-identical to the stored ones, so no offset load precedes the gathers; an epoch
+// off the image or beyond T reads element 0 of a plane and is masked off later.
+template <int J>
+__device__ __forceinline__ void half_gather(const float2* __restrict__ pairs, const EvalParams& ep,
+                                            int x0, int y0, float2 v,
+                                            const float* __restrict__ dtf, int h, bool active,
+                                            HalfPair<J>& g) {
+  const size_t plane = (size_t)ep.H * ep.W;
+  g.inb = 0u;
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    const int t = (j << 4) | h;
+    float2 pf = make_float2(0.0f, 0.0f);
+    if (active) {
+      size_t at = 0;
+      if (t < ep.T) {
+        const float dt = __ldg(dtf + t);
+        const int x = x0 + track_offset(v.x, dt), y = y0 + track_offset(v.y, dt);
+        const bool in = x >= 0 && x < ep.W && y >= 0 && y < ep.H;
+        g.inb |= (in ? 1u : 0u) << j;
+        at = (size_t)t * plane + (in ? (size_t)y * ep.W + x : 0);
+      }
+      pf = __ldg(pairs + at);
+    }
+    g.ps[j] = pf.x;
+    g.ph[j] = pf.y;
+  }
+}
+
+// Evaluates each half's pair.  The lane of h = 0 of a half writes its rec[0..7]: L' (NaN when
+// the pair is not eligible or cannot reach lh_min), alpha, nvalid | nkept << 16, mask words, and
+// gets L' back (the other lanes get NaN).  All 32 lanes take part; steps that no half needs are
+// skipped by the whole warp.
+template <int J>
+__device__ float eval_pair_half(HalfPair<J>& g, const EvalParams& ep,
+                                const float* __restrict__ dtf, uint32_t* rec, int lane) {
+  const int h = lane & 15, hb = lane & 16;
+  const bool lead = h == 0;
+  float* const ps = g.ps;
+  float* const ph = g.ph;
+  bool valid[J];
+  int nvalid = 0;
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    valid[j] = ((g.inb >> j) & 1u) && ph[j] > 0.0f && isfinite(ps[j]) && isfinite(ph[j]);
+    if (!valid[j]) {
+      ps[j] = 0.0f;
+      ph[j] = 0.0f;
+    }
+    nvalid += __popc((__ballot_sync(kAll, valid[j]) >> hb) & 0xffffu);
+  }
+  bool live = nvalid >= ep.min_obs && nvalid > 0;  // the same in every lane of a half
+  auto dead = [&]() {
+    if (lead) {
+      rec[0] = __float_as_uint(NAN);
+      rec[2] = (uint32_t)nvalid;
+    }
+    return NAN;
+  };
+  if (!__any_sync(kAll, live)) return dead();
+  float a[J];
+  bool keep[J];
+  if (ep.clip) {
+    float s[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      a[j] = valid[j] ? (ep.clip_on ? __fdiv_rn(ps[j], __fsqrt_rn(ph[j])) : __fdiv_rn(ps[j], ph[j]))
+                      : INFINITY;
+      s[j] = a[j];
+    }
+    if (ep.nu2_floor > 0.0f) {
+      // Exact filter before the sort.  A percentile interpolates between the order statistics
+      // of ranks lo and lo + 1 (rank table), so q_mid and q_hi are at most any value V with at
+      // least min(lo + 2, n) valid values <= V, and q_lo is at least any value V with at most lo
+      // valid values < V.  Candidates for the three V come from the sorted lightcurve values of
+      // the half's first 32 epochs (a sample), taken a few ranks outward; counts over all
+      // epochs check them.  When all three hold, the upper clip bound is at most
+      // ub = V_mid + n_sigma C (V_hi - V_lo) (the same float32 operations on larger operands,
+      // plus a margin for the rounding of the interpolation), every epoch above ub is clipped,
+      // and by Cauchy-Schwarz LH' of any kept set is at most the square root of the sum of
+      // nu2 = psi^2/phi (psi a for the flux curve, a^2 for the likelihood curve) over the other
+      // valid epochs with psi > 0.  A pair whose sum is below lh_min^2 (1 - 1e-3) cannot reach
+      // lh_min.  Without the checks (or the sample) ub is +inf: the sum over every valid epoch.
+      float ub = INFINITY;
+      float x0 = a[0], x1 = a[1];  // +inf where the epoch is not valid
+      const int m = __popc((__ballot_sync(kAll, valid[0]) >> hb) & 0xffffu) +
+                    __popc((__ballot_sync(kAll, valid[1]) >> hb) & 0xffffu);
+      // ascending sort of the half's 32 samples (index (j << 4) | h, j = 0, 1)
+#pragma unroll
+      for (int k = 2; k <= 32; k <<= 1)
+#pragma unroll
+        for (int d = k >> 1; d > 0; d >>= 1) {
+          if (d == 16) {
+            const float lo = fminf(x0, x1), hi = fmaxf(x0, x1);
+            x0 = lo;  // k = 32: ascending
+            x1 = hi;
+          } else {
+            const float o0 = __shfl_xor_sync(kAll, x0, d), o1 = __shfl_xor_sync(kAll, x1, d);
+            const bool lower = (h & d) == 0;
+            const bool up0 = (h & k) == 0, up1 = ((16 | h) & k) == 0;
+            x0 = (lower == up0) ? fminf(x0, o0) : fmaxf(x0, o0);
+            x1 = (lower == up1) ? fminf(x1, o1) : fmaxf(x1, o1);
+          }
+        }
+      const float xs[2] = {x0, x1};
+      // sample ranks a few places outward of the quantiles (the sample's order statistics
+      // scatter by about sqrt(m q (1 - q)) ranks)
+      const int i_lo = max(0, (int)(ep.q_lo * (float)(m - 1)) - 3);
+      const int i_mid = min(m - 1, (int)(ep.q_mid * (float)(m - 1)) + 4);
+      const int i_hi = min(m - 1, (int)(ep.q_hi * (float)(m - 1)) + 4);
+      const float v_lo = half_get_sorted<2>(xs, i_lo, hb);
+      const float v_mid = half_get_sorted<2>(xs, max(i_mid, 0), hb);
+      const float v_hi = half_get_sorted<2>(xs, max(i_hi, 0), hb);
+      // the three counts in one word (each at most 16 J <= 128 < 2^10)
+      unsigned int c = 0u;
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        c += (valid[j] && a[j] < v_lo) ? 1u : 0u;
+        c += (valid[j] && a[j] <= v_mid) ? (1u << 10) : 0u;
+        c += (valid[j] && a[j] <= v_hi) ? (1u << 20) : 0u;
+      }
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) c += __shfl_xor_sync(kAll, c, o);
+      const int c_lo = (int)(c & 1023u), c_mid = (int)((c >> 10) & 1023u), c_hi = (int)(c >> 20);
+      const int2* rk = rank_table(dtf);
+      const int n_r = live ? nvalid : 0;
+      const int r_lo = __ldg(rk + rank_entry(0, n_r)).x;
+      const int r_mid = __ldg(rk + rank_entry(1, n_r)).x;
+      const int r_hi = __ldg(rk + rank_entry(2, n_r)).x;
+      if (m >= 16 && c_lo <= r_lo && c_mid >= min(r_mid + 2, nvalid) &&
+          c_hi >= min(r_hi + 2, nvalid)) {
+        const float spread = ep.n_sigma * (ep.c_sigma * (v_hi - v_lo));
+        ub = v_mid + spread + 1e-5f * (fabsf(v_mid) + fabsf(v_hi) + fabsf(v_lo) + spread) + 1e-30f;
+        if (!(ub == ub)) ub = INFINITY;  // NaN (infinite values): no epoch is excluded
+      }
+      float s_keep = 0.0f;
+#pragma unroll
+      for (int j = 0; j < J; ++j)
+        if (valid[j] && ps[j] > 0.0f && !(a[j] > ub))
+          s_keep += ep.clip_on ? a[j] * a[j] : ps[j] * a[j];
+      // the half's lead lane's total decides for the half (lanes may differ in the last bit);
+      // every lane takes part in the shuffles, live or not
+      const float s_tot = __shfl_sync(kAll, half_sum(s_keep), hb);
+      live = live && !(s_tot < ep.nu2_floor);
+      if (!__any_sync(kAll, live)) return dead();
+    }
+    half_bitonic_sort<J>(s, h);
+    const int2* rk = rank_table(dtf);
+    const int n_r = live ? nvalid : 0;
+    const float x_lo = half_percentile<J>(s, nvalid, __ldg(rk + rank_entry(0, n_r)), hb);
+    const float x_mid = half_percentile<J>(s, nvalid, __ldg(rk + rank_entry(1, n_r)), hb);
+    const float x_hi = half_percentile<J>(s, nvalid, __ldg(rk + rank_entry(2, n_r)), hb);
+    const float sg = ep.c_sigma * (x_hi - x_lo);
+    const float lo_b = x_mid - ep.n_sigma * sg, hi_b = x_mid + ep.n_sigma * sg;
+#pragma unroll
+    for (int j = 0; j < J; ++j) keep[j] = valid[j] && a[j] >= lo_b && a[j] <= hi_b;
+  } else {
+#pragma unroll
+    for (int j = 0; j < J; ++j) keep[j] = valid[j];
+  }
+  float sp = 0.0f, sf = 0.0f;
+  int nkept = 0;
+  uint32_t mw[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    sp += keep[j] ? ps[j] : 0.0f;
+    sf += keep[j] ? ph[j] : 0.0f;
+    const uint32_t b = (__ballot_sync(kAll, keep[j]) >> hb) & 0xffffu;
+    mw[j >> 1] |= b << ((j & 1) * 16);
+    nkept += __popc(b);
+  }
+  sp = half_sum(sp);
+  sf = half_sum(sf);
+  if (!lead) return NAN;
+  if (!live) return dead();
+  float L = NAN, alpha = 0.0f;
+  if (nkept > 0 && sf > 0.0f) {
+    L = __fdiv_rn(sp, __fsqrt_rn(sf));
+    alpha = __fdiv_rn(sp, sf);
+  }
+  rec[0] = __float_as_uint(L);
+  rec[1] = __float_as_uint(alpha);
+  rec[2] = (uint32_t)nvalid | ((uint32_t)nkept << 16);
+#pragma unroll
+  for (int w = 0; w < 4; ++w) rec[3 + w] = mw[w];
+  return L;
+}
+
+// ---------------------------------------------------------------------------------------------
 // Thread-level full evaluation (T <= NT <= 32): one thread, one (start pixel, trajectory) pair
 // ---------------------------------------------------------------------------------------------
 template <int NT>
@@ -1008,7 +1273,7 @@ __device__ __forceinline__ void tmap_acquire(const void* tmap) {
 // 224.6 ms with this), and the T > 32 kernels, whose evaluations dominate, keep 136 KB under
 // 164 KB (about 92 KB of L1).
 __host__ __device__ constexpr int arena_kb(int nt, bool batch, bool pool, int ncol) {
-  return (nt == 0 && !batch) ? 136 : 152;
+  return (nt <= 0 && !batch) ? 136 : 152;
 }
 
 template <int NT, bool BATCH, bool POOL, int NCOL>
@@ -1377,6 +1642,7 @@ __device__ __noinline__ bool insert_sorted(const SearchArgs& A, size_t wp, int K
 }
 
 // NT > 0: thread-per-pair evaluation with an NT-wide sorting network (T <= NT <= 32);
+// NT == -1: two pairs per warp, one per half-warp, with J slots per lane (32 < T <= 16 J);
 // NT == 0: warp-per-pair evaluation with J epochs per lane (32 < T <= 32 J).
 //
 // BATCH: the tiles of several stacks (BatchArgs), each with its own T; the evaluation path is
@@ -1525,7 +1791,9 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
       // and keep the remainder queued for the next flush, so no round leaves most threads idle.
       auto flush = [&](bool all) {
         const int nq_all = min((int)*s_qcount, S_QCAP);
-        const int round = (NT > 0 || (BATCH && T <= 32)) ? S_CTHREADS : S_CWARPS;
+        const int round = (NT > 0 || (BATCH && T <= 32)) ? S_CTHREADS
+                          : (NT < 0 || (BATCH && T <= 64)) ? 2 * S_CWARPS
+                                                           : S_CWARPS;
         const int nq = all ? nq_all : nq_all - nq_all % round;
         // a batch's arguments live in shared memory: the evaluations read theirs from registers
         EvalParams ep_copy;
@@ -1598,6 +1866,29 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
           consumer_sync();
           if (tid == 0) *s_nsurv = 0u;
         };
+        // Two pairs per warp, one per half (32 < T <= 64)
+        auto by_half = [&](auto jj) {
+          constexpr int JH = decltype(jj)::value;
+          const int half = lane >> 4;
+          for (int eb = 2 * warp; eb < nq; eb += 2 * S_CWARPS) {
+            const int e = eb + half;
+            const bool active = e < nq;
+            const int pl = active ? q_pix[e] : 0;
+            const float2 v = active ? __ldg(e_vs + q_traj[e]) : make_float2(0.0f, 0.0f);
+            HalfPair<JH> g;
+            half_gather<JH>(e_pairs, EP, tx0 + (pl & (TXW - 1)), ty0 + (pl >> TXS), v, e_dt,
+                            lane & 15, active, g);
+            uint32_t r[S_REC_WORDS];
+            r[2] = 0u;
+            const float L = eval_pair_half<JH>(g, EP, e_dt, r, lane);
+            if ((lane & 15) == 0 && active && L >= lh_min) keep(e, pl, r);
+            // pairs eligible for the clip, counted by the halves' lead lanes
+            const bool ev = (lane & 15) == 0 && active && (r[2] & 0xffffu) > 0u &&
+                            (int)(r[2] & 0xffffu) >= EP.min_obs;
+            const unsigned int n = __popc(__ballot_sync(0xffffffffu, ev));
+            if (lane == 0 && n) atomicAdd(&s_stage[0], n);
+          }
+        };
         auto by_warp = [&](auto jj) {
           for (int e = warp; e < nq; e += S_CWARPS) {
             const int pl = q_pix[e];
@@ -1612,14 +1903,17 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
           }
         };
         if (BATCH) {
-          // two evaluation paths serve every stack (fewer registers than one per epoch class):
-          // the 32-wide network sorts a T <= 16 lightcurve into the same order as the 16-wide
-          // one, and four epochs per lane give the sums of two (the extra lanes add zeros), so
-          // the results are bit-identical to kb_search's
+          // three evaluation paths serve every stack (fewer registers than one per epoch
+          // class): the 32-wide network sorts a T <= 16 lightcurve into the same order as the
+          // 16-wide one (the extra entries sort last), so the results are bit-identical to
+          // kb_search's, which takes the same half-warp and warp paths for T > 32
           if (T <= 32) by_thread(std::integral_constant<int, 32>{});
+          else if (T <= 64) by_half(std::integral_constant<int, 4>{});
           else by_warp(std::integral_constant<int, 4>{});
         } else if (NT > 0) {
           by_thread(std::integral_constant<int, (NT > 0 ? NT : 1)>{});
+        } else if (NT < 0) {
+          by_half(std::integral_constant<int, J>{});
         } else {
           by_warp(std::integral_constant<int, J>{});
         }
@@ -2139,7 +2433,7 @@ static int launch_search_single(const StackPrep& sp, cudaStream_t st) {
   do {                                                 \
     if (T <= 16) KB_SEARCH_LAUNCH(16, 1, PL, NC);      \
     else if (T <= 32) KB_SEARCH_LAUNCH(32, 1, PL, NC); \
-    else if (T <= 64) KB_SEARCH_LAUNCH(0, 2, PL, NC);  \
+    else if (T <= 64) KB_SEARCH_LAUNCH(-1, 4, PL, NC); \
     else KB_SEARCH_LAUNCH(0, 4, PL, NC);               \
   } while (0)
   if (!sp.pool) KB_SEARCH_LAUNCH_T(false, 1);
