@@ -850,15 +850,13 @@ def run_refine(args):
             dist.barrier()
             dist.destroy_process_group()
         return
-    peaks, peaks_src = measured_peaks()
     r_ms = part["refine"]
     te_refine = n * T * (rp.n_steps + 1)
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
     # The refine kernel reads its taps through L1 (a candidate's taps stay on chip across its
-    # steps; DRAM traffic is a few tens of MB): roofline = the L1 load path, one 128-byte wavefront
-    # per SM per clock, against 8 float32 taps (4 of psi, 4 of phi) per trajectory-epoch.
-    l1_peak = sms * 128 * sm_max * 1e6 / 1e9
+    # steps; DRAM traffic is a few tens of MB): roofline = the L1/shared-memory load path (one
+    # 128-byte wavefront per SM per clock), as measured in this run by kb_smem_probe, against
+    # 8 float32 taps (4 of psi, 4 of phi) per trajectory-epoch.
+    l1_peak = kb.smem_read_bandwidth(device=dev)
     achieved = te_refine * 32 / (r_ms / 1e3) / 1e9
     line = {
         "metric": "refine trajectory-epoch evals/sec", "value": value, "unit": "TE/s",
@@ -873,8 +871,8 @@ def run_refine(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": l1_peak, "unit": "GB/s",
                      "frac": achieved / l1_peak, "traffic": None,
                      "kernel": "refine_kernel", "kernel_ms": r_ms,
-                     "peak_source": "derived: %d SMs x 128 B/clk L1 loads x %g MHz (sm_max_mhz, "
-                                    "%s)" % (sms, sm_max, peaks_src),
+                     "peak_source": "measured in this run: kb_smem_probe (the load path that L1 "
+                                    "and shared memory share, 128 B per SM per clock)",
                      "algorithmic_bytes_per_te": 32,
                      "note": "8 x 4 B bilinear taps per trajectory-epoch, %d evaluations per "
                              "candidate; each 4 B tap occupies a 32 B sector, and the kernel is "
