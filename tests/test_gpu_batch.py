@@ -1,9 +1,9 @@
 """Batched search (many stacks, one persistent launch): every stack's results must equal those of
 kb_search on it, bit for bit (same kernels, same per-tile arithmetic; only the scheduling
-differs), under every schedule, through the CUDA graph and on replay; two stacks are also checked
-against the FP64 oracle.  Stacks mix T (thread- and warp-evaluated), sizes, windows, K, clip
-settings and velocity counts.  Inputs are seeded likelihood planes (no input comes from the CUDA
-path)."""
+differs), under every schedule, through the CUDA graph and on replay; three stacks are also
+checked against the FP64 oracle.  Stacks mix T (thread-, half-warp- and warp-evaluated), sizes,
+windows, K, clip settings and velocity counts.  Inputs are seeded likelihood planes (no input
+comes from the CUDA path)."""
 import dataclasses
 
 import numpy as np
@@ -47,6 +47,8 @@ def _stacks():
                                                               window=(17, 170, 9, 101))),
         _stack(6, 33, 40, 40, 33, spread=10.0, params=kb.SearchParams(k=1, lh_min=1.0,
                                                                       min_obs=2)),
+        _stack(7, 80, 36, 44, 40, spread=12.0, params=kb.SearchParams(k=2, lh_min=2.0,
+                                                                      min_obs=20)),
     ]
 
 
@@ -140,7 +142,8 @@ def test_batch_stacks_against_oracle(cuda_device, batch_case):
     b = kb.Batch(stacks)
     res = b.run(graph=True)
     torch.cuda.synchronize()
-    for i in (1, 2):   # T = 26 (thread path, clip on likelihood) and T = 40 (warp path)
+    # T = 26 (thread path, clip on likelihood), T = 40 (half-warp pairs), T = 80 (warp per pair)
+    for i in (1, 2, 6):
         s = stacks[i]
         sp = s["params"]
         o = oracle.search(s["psi32"], s["phi32"], s["times"], s["vxn"], s["vyn"],
