@@ -351,6 +351,15 @@ __global__ void plan_offsets_kernel(const float* __restrict__ vx, const float* _
     offs[(size_t)s * T + t] = make_int2(track_offset(x, cs.dt[t]), track_offset(y, cs.dt[t]));
 }
 
+// Epoch of the k-th (chunk, epoch) iteration of a chunk: 0, T-1, 1, T-2, ...  The footprint of
+// a chunk's 32 trajectories grows with the time since the first epoch, so early epochs stage
+// small boxes and late ones large boxes; alternating them keeps the staging rings from filling
+// with the largest boxes at the end of every chunk.  The bound pass may sum the epochs in any
+// order: the admission threshold's rounding allowance holds for every order.
+__host__ __device__ __forceinline__ int epoch_of(int k, int T) {
+  return (k & 1) ? T - 1 - (k >> 1) : (k >> 1);
+}
+
 // One thread per (chunk, epoch): staging rectangle and per-trajectory byte offsets into it.
 // box = {x offset of the rectangle from the tile origin (x_lo + dxmin - xshift is a multiple
 // of 4 so that the TMA x coordinate is 16-byte aligned), y offset, height class, mode} with
@@ -361,7 +370,7 @@ __global__ void plan_boxes_kernel(const int2* __restrict__ offs, int nchunk, int
                                   int tx, PlanRec* plan) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nchunk * T) return;
-  int c = i / T, t = i - c * T;
+  const int c = i / T, t = epoch_of(i - c * T, T);
   int dxmin = INT_MAX, dxmax = INT_MIN, dymin = INT_MAX, dymax = INT_MIN;
   for (int v = 0; v < S_C; ++v) {
     int2 o = offs[(size_t)(c * S_C + v) * T + t];
@@ -1452,7 +1461,7 @@ __device__ void producer_loop(const TmapSet& pmaps, const SearchArgs& A0, const 
         const int q = qb + kk * S_PWARPS;
         if (q >= n_it) break;
         const long long it = it_base + q;
-        const int t = q % T;
+        const int t = last ? 0 : epoch_of(q % T, T);
         const int slot = (int)(it % S_D);
         int4 b;
         b.x = __shfl_sync(0xffffffffu, mine.x, kk);
@@ -1969,7 +1978,8 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
 #pragma unroll
           for (int v = 0; v < S_C; ++v) acc[pp][v] = __float2half2_rn(0.0f);
 
-        for (int t = 0; t < T; ++t, ++it) {
+        for (int k = 0; k < T; ++k, ++it) {
+          const int t = epoch_of(k, T);  // the plan's epoch order
           const int slot = (int)(it % S_D);
           const bool ok = consumer_wait(&full[slot], (it / S_D) & 1u, s_abort);
           if (ok) {
