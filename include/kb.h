@@ -214,7 +214,9 @@ KB_API int kb_search_no_alloc_stats(unsigned long long* stats, void* stream);
  *   stats[0] trajectory-epochs covered (start pixels x trajectories x T),
  *   stats[1] (pixel, trajectory) pairs whose bound required a full clipped evaluation,
  *   stats[2] pairs inserted into a top-K list,
- *   stats[3] device-side error flags (0 = none; KB_ERR_TIMEOUT bit 0x1 if a bounded wait gave up).
+ *   stats[3] device-side error flags (0 = none; bit 0x1 if a bounded wait gave up; bit 0x2 if
+ *            a device-side bounds check failed -- only the checked build libkb_b300_checked.so,
+ *            with the search kernel compiled with KB_BOUNDS_CHECK=1, makes those checks).
  */
 KB_API int kb_search_stats(const void* workspace, unsigned long long* stats, void* stream);
 

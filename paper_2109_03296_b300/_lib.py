@@ -7,7 +7,9 @@ import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libkb_b300.so")
+# KB_B300_LIBRARY=checked selects the build with device-side bounds checks (build.py --checked)
+LIB_PATH = os.path.join(HERE, "libkb_b300_checked.so"
+                        if os.environ.get("KB_B300_LIBRARY") == "checked" else "libkb_b300.so")
 
 KB_OK = 0
 KB_ERR_INVALID_ARG = 1
@@ -75,8 +77,8 @@ def lib():
     if _LIB is not None:
         return _LIB
     if not os.path.exists(LIB_PATH):
-        raise ImportError("libkb_b300.so is not built: run paper_2109_03296_b300/build.py "
-                          "(or __graft_entry__.build())")
+        raise ImportError("%s is not built: run paper_2109_03296_b300/build.py "
+                          "(or __graft_entry__.build())" % os.path.basename(LIB_PATH))
     L = C.CDLL(LIB_PATH)
     p, i, f, sz = C.c_void_p, C.c_int, C.c_float, C.c_size_t
     L.kb_version.restype = i

@@ -53,6 +53,15 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Device error flag bits (kb_search_stats()[3]).
 constexpr unsigned int kErrTimeout = 0x1u;
+constexpr unsigned int kErrBounds = 0x2u;  // a device-side check of the checked build failed
+
+// The checked build (nvcc -DKB_BOUNDS_CHECK=1: libkb_b300_checked.so) tests, before each access,
+// that a staged-box read lies inside the box, that a TMA x coordinate is 16-byte aligned and
+// that a result slot lies inside the output window; a failed check sets kErrBounds and skips
+// the access.  The regular build compiles the checks away.
+#ifndef KB_BOUNDS_CHECK
+#define KB_BOUNDS_CHECK 0
+#endif
 
 // Every device-side wait is bounded in time: after this many nanoseconds of %globaltimer the
 // waiter gives up, records an error flag and stops using the buffer it waited for.

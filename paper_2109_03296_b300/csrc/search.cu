@@ -1525,6 +1525,10 @@ __device__ void producer_loop(const TmapSet& pmaps, const SearchArgs& A0, const 
           sinfo[slot] = make_int4(ring_base + pos, last ? -1 : tile, sz, stack);
           if (sz == 0) {
             mbar_arrive(&full[slot]);
+          } else if (KB_BOUNDS_CHECK && ((tx0 + b.x) & 3) != 0) {
+            // checked build: a TMA x coordinate off the 16-byte grid is reported, not issued
+            atomicOr(&ctrl->err, kErrBounds);
+            mbar_arrive(&full[slot]);
           } else {  // word row = first image row + 3 (the planes carry three leading rows)
             mbar_arrive_expect_tx(&full[slot], (uint32_t)sz);
             tma_load_3d(ring + pos, &maps->m[(mode - 1) * S_NH + b.z], &full[slot], tx0 + b.x,
@@ -1586,14 +1590,25 @@ __device__ __forceinline__ int4 lds_v4(uint32_t addr) {
 template <bool POOL, int NCOL>
 __device__ __forceinline__ void accumulate_stage(__half2 (&acc)[2][S_C], const unsigned char* st,
                                                  int pitch, bool uniform, const PlanRec* slot,
-                                                 int warp, int lane) {
+                                                 int warp, int lane, int box_bytes,
+                                                 unsigned int* err) {
   // words per trajectory: two (two columns, or two row pairs), or one (two-row blocks of one
   // column: both blocks of the thread in one word)
   constexpr bool TWO = !(POOL && NCOL == 1);
   const uint32_t base = smem_u32(st) + (uint32_t)(warp * S_ROWS * pitch + lane) * 4u;
   const uint32_t base1 = base + 8u * (uint32_t)pitch;  // two rows further (single rows only)
+  // checked build: the last byte this thread reads for a trajectory at offset rel lies in the box
+  const uint32_t first = (uint32_t)(warp * S_ROWS * pitch + lane) * 4u;
+  const uint32_t span = (TWO ? (POOL ? 4u * S_TX : 8u * (uint32_t)pitch) : 0u) + 4u;
+  auto outside = [&](uint32_t rel) {
+    if (!KB_BOUNDS_CHECK) return false;
+    const bool bad = (int)rel < 0 || first + rel + span > (uint32_t)box_bytes;
+    if (bad) atomicOr(err, kErrBounds);
+    return bad;
+  };
   if (uniform) {
     const uint32_t r0 = (uint32_t)slot->rel[0];
+    if (outside(r0)) return;
     const uint32_t w0 = lds_u32(base + r0);
     uint32_t w1 = 0u;
     if (TWO) w1 = POOL ? lds_u32_off<4 * S_TX>(base + r0) : lds_u32(base1 + r0);
@@ -1611,6 +1626,7 @@ __device__ __forceinline__ void accumulate_stage(__half2 (&acc)[2][S_C], const u
     const int rr[4] = {r4.x, r4.y, r4.z, r4.w};
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
+      if (outside((uint32_t)rr[u])) continue;
       const uint32_t q = base + (uint32_t)rr[u];
       const uint32_t w0 = lds_u32(q);
       acc[0][vq * 4 + u] = __hadd2(acc[0][vq * 4 + u], *reinterpret_cast<const __half2*>(&w0));
@@ -1626,6 +1642,11 @@ __device__ __forceinline__ void accumulate_stage(__half2 (&acc)[2][S_C], const u
 // (LH' descending, trajectory index ascending).  Returns true if it entered the list.
 __device__ __noinline__ bool insert_sorted(const SearchArgs& A, size_t wp, int K, int mw, int nf,
                                            float L, int j, const uint32_t* rc) {
+  if (KB_BOUNDS_CHECK &&
+      wp >= (size_t)(A.x_hi - A.x_lo) * (size_t)(A.y_hi - A.y_lo)) {  // outside the window
+    atomicOr(&A.ctrl->err, kErrBounds);
+    return false;
+  }
   float* lh = A.out_lh + wp * K;
   int32_t* ix = A.out_idx + wp * K;
   int s = 0;
@@ -1988,7 +2009,8 @@ search_kernel(const __grid_constant__ TmapSet maps, const SearchArgs A0, const B
             const unsigned char* st = arena + sinfo[slot].x;
             if (mode != 0) {
               const bool uni = (rec->box.w & S_UNIFORM_BIT) != 0;
-              accumulate_stage<POOL, NCOL>(acc, st, stage_width(mode), uni, rec, warp, lane);
+              accumulate_stage<POOL, NCOL>(acc, st, stage_width(mode), uni, rec, warp, lane,
+                                           sinfo[slot].z, &ctrl->err);
             } else {
               // direct loads from the block planes (word row = first image row + 3)
               const uint32_t* bp = A.bound + (size_t)t * (A.ep.H + 3) * A.Wp;

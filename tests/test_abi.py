@@ -36,6 +36,18 @@ def test_exports_every_declared_symbol(L):
         assert hasattr(L, n), n
 
 
+def test_checked_build_exports_the_same_symbols():
+    """libkb_b300_checked.so (the search kernel with KB_BOUNDS_CHECK=1) is the same C ABI."""
+    from paper_2109_03296_b300 import _lib, build
+    if not os.path.exists(build.LIB_CHECKED):
+        build.build(checked=True)
+    Lc = C.CDLL(build.LIB_CHECKED)
+    for n in header_symbols():
+        assert hasattr(Lc, n), n
+    Lc.kb_version.restype = C.c_int
+    assert Lc.kb_version() == _lib.lib().kb_version()
+
+
 def test_version_and_defaults(L):
     from paper_2109_03296_b300._lib import SearchParamsC
     assert L.kb_version() >= 100
