@@ -1023,6 +1023,9 @@ def run_batch(args):
                      "tile_order": sched.tile_order, "hot_nu2": sched.hot_nu2,
                      "score_span": sched.score_span, "stack_order": sched.stack_order,
                      "tile_cols": sched.tile_cols,
+                     "tile_width": {0: "automatic per stack (64 px where the window holds >= 8 "
+                                       "waves of such tiles, else 32)",
+                                    1: "32 px", 2: "64 px"}[sched.tile_cols],
                      "autotune_s": tune_s},
         "results_identical_to_plain": bool(same),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": smem_peak, "unit": "GB/s",

@@ -298,9 +298,11 @@ KB_API int kb_stamps(const float* img, const float* var, const uint8_t* mask, co
  *                                 SMs that the previous one's last tiles leave idle.
  *                    tile_cols    1 or 2: columns summed by each thread of the bound pass, i.e.
  *                                 tiles 32 or 64 pixels wide (stacks with two-row-block bounds;
- *                                 single-row bounds always take 32).
+ *                                 single-row bounds always take 32); 0: automatic, per stack
+ *                                 64 wide when its window holds at least 8 tiles of that width
+ *                                 per SM, else 32 (mode 0: 64 for every stack).
  *                  kb_schedule_default: {tile_order 1, hot_nu2 64, score_span 64, stack_order 1,
- *                  mode 1, tile_cols 2} (kb_search uses the same tile order and width).
+ *                  mode 1, tile_cols 0} (kb_search uses the same tile order and width rule).
  *   kb_batch       opaque handle: kb_batch_create validates every stack (the checks of
  *                  kb_search), lays out the workspace and writes the batch tables to the device
  *                  (synchronous copies); the stacks' buffers must stay valid while it is used.

@@ -572,7 +572,7 @@ class Schedule:
     score_span: int = 64
     stack_order: int = 1
     mode: int = 1           # 0: one persistent launch; 1: concurrent per-stack launches
-    tile_cols: int = 2      # tiles 32 * tile_cols pixels wide (two-row-block bounds)
+    tile_cols: int = 0      # tiles 32 * tile_cols pixels wide (two-row blocks); 0 = automatic
 
     def to_c(self):
         return ScheduleC(int(self.tile_order), float(self.hot_nu2), int(self.score_span),

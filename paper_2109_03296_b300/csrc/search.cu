@@ -74,9 +74,13 @@ constexpr int S_THREADS = (S_CWARPS + S_PWARPS) * 32;
 constexpr int S_TY = S_CWARPS * S_ROWS;  // 56
 // Two-row-block kernels can give each thread two columns (x and x + 32): tiles 64 wide, so a
 // staged box serves twice the start pixels for the same halo and one offset load serves two data
-// loads (kb_schedule.tile_cols = 2, the default); with one column the tiles are 32 wide.
-// Single-row kernels (which keep twice the sums per column) are always 32 wide.
-constexpr int S_TILE_COLS_DEFAULT = 2;
+// loads; with one column the tiles are 32 wide.  Single-row kernels (which keep twice the sums
+// per column) are always 32 wide.  The width is automatic by default (kb_schedule.tile_cols = 0):
+// 64-wide only when the window holds at least S_WIDE_MIN_WAVES tiles of that width per SM, since
+// with fewer the last wave of tiles leaves SMs idle (decam recipe, one stack: 1024 x 2048
+// 148.5 ms with 32-wide tiles against 163.7 ms with 64-wide; 2046 x 2048 300.0 against 242.3).
+constexpr int S_TILE_COLS_DEFAULT = 0;
+constexpr int S_WIDE_MIN_WAVES = 8;
 constexpr int S_C = 32;                  // trajectories per chunk
 constexpr int S_D = 8;                   // pipeline slots (iterations in flight), S_D % S_PWARPS == 0
 constexpr int S_REGION_MAX = 64 * 1024;  // larger rectangles use direct loads
@@ -2262,9 +2266,27 @@ static bool pool_blocks(int T, float lh_min) {
 
 // Validates one stack, lays out its workspace, encodes its tensor maps and fills its kernel
 // arguments (no launch).  ctrl: the control block the search kernel will use.
+// SMs of the current device (148 if it cannot be queried: the tile width is then still valid).
+static int sm_count() {
+  if (g_num_sms == 0) {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0)
+      g_num_sms = n;
+    else
+      (void)cudaGetLastError();  // clear the failed query's error
+  }
+  return g_num_sms > 0 ? g_num_sms : 148;
+}
+
 // Tiles of `cols` columns per bound-pass thread (32 * cols pixels wide; single-row bounds always
-// take one column) over the stack's window.
+// take one column) over the stack's window; cols = 0: automatic (S_WIDE_MIN_WAVES).
 static void set_tile_geometry(SearchArgs& A, bool pool, int cols) {
+  if (cols == 0) {
+    const long long wide = (long long)((A.x_hi - A.x_lo + 2 * S_TX - 1) / (2 * S_TX)) *
+                           ((A.y_hi - A.y_lo + S_TY - 1) / S_TY);
+    cols = wide >= (long long)S_WIDE_MIN_WAVES * sm_count() ? 2 : 1;
+  }
   A.tx = S_TX * (pool ? cols : 1);
   A.ntx = (A.x_hi - A.x_lo + A.tx - 1) / A.tx;
   A.nty = (A.y_hi - A.y_lo + S_TY - 1) / S_TY;
@@ -2492,8 +2514,8 @@ static int check_schedule(const kb_schedule* s) {
   if (s->score_span < 0 || s->score_span > (1 << 20))
     return fail(KB_ERR_INVALID_ARG, "schedule: score_span outside 0..2^20");
   if (s->mode != 0 && s->mode != 1) return fail(KB_ERR_INVALID_ARG, "schedule: mode must be 0 or 1");
-  if (s->tile_cols != 1 && s->tile_cols != 2)
-    return fail(KB_ERR_INVALID_ARG, "schedule: tile_cols must be 1 or 2");
+  if (s->tile_cols < 0 || s->tile_cols > 2)
+    return fail(KB_ERR_INVALID_ARG, "schedule: tile_cols must be 0 (automatic), 1 or 2");
   return KB_OK;
 }
 
@@ -2889,7 +2911,10 @@ extern "C" int kb_batch_set_schedule(kb_batch* b, const kb_schedule* s) {
   KB_CUDA_TRY(cudaDeviceSynchronize());
   b->sch = *s;
   drop_graph(b);
-  for (kb::StackPrep& sp : b->sp) set_tile_geometry(sp.A, sp.pool, s->tile_cols);
+  // one persistent launch runs one kernel: every stack takes the same width (automatic: 64-wide;
+  // the batch has one tail, at its end)
+  const int cols = (s->mode == 0 && s->tile_cols == 0) ? 2 : s->tile_cols;
+  for (kb::StackPrep& sp : b->sp) set_tile_geometry(sp.A, sp.pool, cols);
   return write_tables(b);
 }
 
@@ -2937,11 +2962,13 @@ extern "C" int kb_batch_autotune(kb_batch* b, void* stream, int reps, kb_schedul
       kb_schedule c = cur;
       c.tile_order = 1 - cur.tile_order;
       cand.push_back(c);
-      if (b->sp[0].pool) {  // the tile width (two-row blocks only)
-        c = cur;
-        c.tile_cols = 3 - cur.tile_cols;
-        cand.push_back(c);
-      }
+      if (b->sp[0].pool)  // the tile width (two-row blocks only): automatic, 32 or 64
+        for (int w = 0; w <= 2; ++w)
+          if (w != cur.tile_cols) {
+            c = cur;
+            c.tile_cols = w;
+            cand.push_back(c);
+          }
     } else if (pass == 2 && cur.tile_order) {
       for (float h : hot)
         if (h != cur.hot_nu2) {

@@ -86,7 +86,7 @@ def test_batch_equals_per_stack_search(cuda_device, batch_case):
 
 
 @pytest.mark.parametrize("mode", [0, 1])
-@pytest.mark.parametrize("tile_cols", [1, 2])
+@pytest.mark.parametrize("tile_cols", [0, 1, 2])
 def test_batch_two_row_blocks(cuda_device, batch_case, mode, tile_cols):
     """Every stack summed over two-row blocks (bound_rows = 2; the automatic choice takes single
     rows for these small thresholds), so one persistent launch (mode 0) runs the block kernel, in
@@ -109,7 +109,7 @@ def test_batch_graph_replay_and_schedules(cuda_device, batch_case):
     b = kb.Batch(stacks)
     for sched in (kb.Schedule(), kb.Schedule(mode=0), kb.Schedule(tile_order=0, stack_order=0),
                   kb.Schedule(mode=0, hot_nu2=9.0, score_span=128, stack_order=0),
-                  kb.Schedule(score_span=0), kb.Schedule(tile_cols=1),
+                  kb.Schedule(score_span=0), kb.Schedule(tile_cols=1), kb.Schedule(tile_cols=2),
                   kb.Schedule(mode=0, tile_cols=1, tile_order=0)):
         b.schedule = sched
         assert b.schedule == sched
