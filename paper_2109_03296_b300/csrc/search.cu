@@ -25,8 +25,10 @@
 //    rounded up: word (t, r, x) of a [T][H+3][Wp] uint32 array (Wp = W rounded up to 32) holds
 //    rows r-3 and r-2 (single rows) or the maxima of rows (r-3, r-2) and (r-1, r) (blocks) at
 //    column x.  A block owns a tile of 32 x 56 start pixels (lane = x, 4 rows per consumer
-//    thread), or 64 x 56 with blocks (columns x and x + 32 per thread), and sweeps the velocity list in chunks of 32 trajectories that are close in
-//    velocity space (Hilbert order of (vx, vy) from the plan kernels).  For each (chunk, epoch)
+//    thread), or 64 x 56 with blocks on large windows (columns x and x + 32 per thread), and
+//    sweeps the velocity list in chunks of 32 trajectories that are close in velocity space
+//    (Hilbert order of (vx, vy) from the plan kernels), the epochs of a chunk in the order
+//    0, T-1, 1, T-2, ...  For each (chunk, epoch)
 //    the union of the tile's 32 shifted footprints is one small rectangle, fetched with one TMA
 //    box into a shared-memory ring by producer warps while the consumer warps sum earlier ones.
 //    A consumer thread then does, per trajectory, one address add, one 32-bit shared load and
@@ -35,16 +37,17 @@
 //
 //  * Full evaluation.  After each chunk, the pairs whose bound passes are appended to a queue
 //    in shared memory; once it holds S_FLUSH_MIN pairs the largest whole number of rounds (one
-//    pair per consumer thread, half-warp or warp) is evaluated and the rest stays queued, and at the
-//    end of a tile everything, so no round leaves threads idle and no warp waits at a barrier for
-//    a lone candidate.  For T <= 32 one thread evaluates one pair: gather into registers, an
-//    exact filter that drops pairs which cannot reach lh_min once the epochs the clip must
-//    reject are left out, then for the rest a bitonic sorting network on the lightcurve,
-//    percentiles, clip, sums in epoch order (identical tracks give bit-identical LH').  For
-//    32 < T <= 64 a half-warp evaluates one pair with lanes over epochs (two pairs per warp),
-//    for T > 64 a warp, each with an exact filter of the same kind before its sort.  Results that reach lh_min (a small fraction) are pushed onto
-//    a per-pixel list; the owner thread of each start pixel then walks its list and inserts
-//    them into the pixel's output list (LH' descending, trajectory index ascending).
+//    pair per consumer thread, half-warp or warp) is evaluated and the rest stays queued, and at
+//    the end of a tile everything, so no round leaves threads idle and no warp waits at a
+//    barrier for a lone candidate.  For T <= 32 one thread evaluates one pair: gather into
+//    registers, an exact filter that drops pairs which cannot reach lh_min once the epochs the
+//    clip must reject are left out, then for the rest a bitonic sorting network on the
+//    lightcurve, percentiles, clip, sums in epoch order (identical tracks give bit-identical
+//    LH').  For 32 < T <= 64 a half-warp evaluates one pair with lanes over epochs (two pairs per
+//    warp), for T > 64 a warp, each with an exact filter of the same kind before its sort.
+//    Results that reach lh_min (a small fraction) are pushed onto a per-pixel list; the owner
+//    thread of each start pixel then walks its list and inserts them into the pixel's output
+//    list (LH' descending, trajectory index ascending).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
