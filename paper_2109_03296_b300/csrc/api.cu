@@ -63,7 +63,7 @@ extern "C" void kb_profile_events(void* start, void* stop) {
   kb::g_prof_stop = static_cast<cudaEvent_t>(stop);
 }
 
-extern "C" int kb_version(void) { return 157; }  // 0.1.57
+extern "C" int kb_version(void) { return 158; }  // 0.1.58
 
 extern "C" const char* kb_last_error(void) { return kb::g_last_error.c_str(); }
 

@@ -1122,47 +1122,65 @@ __device__ float eval_pair_thread(const float2* __restrict__ pairs,
   };
   uint32_t km = vm;
   if (FILTER) {
-    // Exact filter before the sort.  With a0 the smallest and a4 the fourth largest lightcurve
-    // value: when the interpolation ranks of q_mid and q_hi stay at or below index n - 4
-    // (their upper order statistic is at most the fourth largest), the median and q_hi lie at
-    // or below a4 and q_lo at or above a0, so the upper clip bound is at most
-    // ub = a4 + n_sigma C (a4 - a0) (plus a margin for the float32 rounding of the percentiles
-    // and bounds).  Every epoch above ub is clipped whatever the quantiles are, and by
-    // Cauchy-Schwarz LH' of any kept set is at most the square root of the sum of
-    // nu2 = psi^2/phi over the other valid epochs with psi > 0; a pair whose sum is below
-    // lh_min^2 (1 - 1e-3) cannot reach lh_min.  Without the clip (or the rank condition) the sum
-    // runs over every valid epoch.  This drops most pairs whose pruning bound passed only
-    // through one bright epoch (a +20 sigma spike) or through the other pixel of a two-row
+    // Exact filter before the sort.  A percentile interpolates between the order statistics of
+    // ranks lo and lo + 1 (rank table), so with the M largest and M smallest lightcurve values
+    // kept in registers: q_mid and q_hi are at most the value of rank n - k (k = min(n - (lo + 1),
+    // M) largest, which is at or above rank lo + 1), and q_lo is at least the value of rank
+    // min(lo, M - 1) (at or below rank lo).  The upper clip bound is then at most
+    // ub = V_mid + n_sigma C (V_hi - V_lo) (the same float32 operations on larger operands, plus
+    // a margin for the rounding of the interpolation).  Every epoch above ub is clipped whatever
+    // the quantiles are, and by Cauchy-Schwarz LH' of any kept set is at most the square root of
+    // the sum of nu2 = psi^2/phi over the other valid epochs with psi > 0; a pair whose sum is
+    // below lh_min^2 (1 - 1e-3) cannot reach lh_min.  Without the clip the sum runs over every
+    // valid epoch.  This drops most pairs whose pruning bound passed only through a few bright
+    // epochs (a +20 sigma spike, a mover crossed once) or through the other pixel of a two-row
     // block.  Returns NaN for a dropped pair, +inf for one that needs the full evaluation.
     if (!(ep.nu2_floor > 0.0f)) {
       rec[2] = (uint32_t)nvalid;
       return INFINITY;
     }
-    float a0 = INFINITY, t1 = -INFINITY, t2 = -INFINITY, t3 = -INFINITY, t4 = -INFINITY;
+    // the M largest (descending) and the M smallest (ascending) lightcurve values
+    constexpr int M = 8;
+    float top[M], bot[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      top[i] = -INFINITY;
+      bot[i] = INFINITY;
+    }
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
       if ((vm >> t) & 1u) {
         const float a = curve(t);
-        a0 = fminf(a0, a);
-        // top four, with as few selects as a sorted insertion allows
-        const float m1 = fmaxf(t1, a), r1 = fminf(t1, a);
-        const float m2 = fmaxf(t2, r1), r2 = fminf(t2, r1);
-        const float m3 = fmaxf(t3, r2), r3 = fminf(t3, r2);
-        t4 = fmaxf(t4, r3);
-        t1 = m1;
-        t2 = m2;
-        t3 = m3;
+        float ch = a, cl = a;
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+          const float hi = fmaxf(top[i], ch), lo = fminf(bot[i], cl);
+          ch = fminf(top[i], ch);
+          cl = fmaxf(bot[i], cl);
+          top[i] = hi;
+          bot[i] = lo;
+        }
       }
     }
     float ub = INFINITY;
     if (ep.clip) {
       const int2* rk = rank_table(dtf);
-      if (__ldg(rk + rank_entry(1, nvalid)).x <= nvalid - 5 &&
-          __ldg(rk + rank_entry(2, nvalid)).x <= nvalid - 5) {
-        const float spread = ep.n_sigma * (ep.c_sigma * (t4 - a0));
-        ub = t4 + spread + 1e-5f * (fabsf(t4) + fabsf(a0) + spread) + 1e-30f;
-        if (!(ub == ub)) ub = INFINITY;  // NaN (infinite values): no epoch is excluded
+      const int u_mid = min(__ldg(rk + rank_entry(1, nvalid)).x + 1, nvalid - 1);
+      const int u_hi = min(__ldg(rk + rank_entry(2, nvalid)).x + 1, nvalid - 1);
+      const int l_lo = __ldg(rk + rank_entry(0, nvalid)).x;
+      // sorted[u] <= top[k - 1] for k = min(n - u, M); sorted[l] >= bot[min(l, M - 1)]
+      const int k_mid = min(nvalid - u_mid, M) - 1, k_hi = min(nvalid - u_hi, M) - 1;
+      const int k_lo = min(l_lo, M - 1);
+      float v_mid = top[0], v_hi = top[0], v_lo = bot[0];
+#pragma unroll
+      for (int i = 1; i < M; ++i) {
+        v_mid = i == k_mid ? top[i] : v_mid;
+        v_hi = i == k_hi ? top[i] : v_hi;
+        v_lo = i == k_lo ? bot[i] : v_lo;
       }
+      const float spread = ep.n_sigma * (ep.c_sigma * (v_hi - v_lo));
+      ub = v_mid + spread + 1e-5f * (fabsf(v_mid) + fabsf(v_hi) + fabsf(v_lo) + spread) + 1e-30f;
+      if (!(ub == ub)) ub = INFINITY;  // NaN (infinite values): no epoch is excluded
     }
     float s_keep = 0.0f;
 #pragma unroll
